@@ -1,0 +1,146 @@
+/*
+ * ssmul.h -- verified integer multiplication by complex interval FFT
+ * convolution (a rigorous Schoenhage-Strassen multiplier) on one GPU.
+ *
+ * The method is that of T. Steinke and R. Sainudiin, "A Rigorous Extension
+ * of the Schoenhage-Strassen Integer Multiplication Algorithm Using Complex
+ * Interval Arithmetic" (CCA 2010):
+ *   - Section 2 (digit convention): an operand is a little-endian vector
+ *     of base-256 digits, x = sum_i x_i 256^i, digit 0 least significant;
+ *   - Section 2.3 (fast convolution): the digit vectors are zero padded to
+ *     a power-of-two length N >= na + nb - 1, transformed, multiplied
+ *     pointwise and transformed back;
+ *   - Section 2.5: every complex number is replaced by a rectangular complex
+ *     interval whose bounds are rounded outward (directed rounding), so each
+ *     output interval provably contains the exact coefficient of x * y;
+ *   - Section 1: the unique integer in each containment set is taken; a set
+ *     holding several integers is reported as an error (more precision is
+ *     needed), never rounded;
+ *   - Section 2.4: the integer coefficients are carried into base-256 digits.
+ *
+ * Every function returns an ssmul_status and never aborts or exits.
+ * Device pointers are CUDA device addresses in the current device's memory;
+ * host pointers are ordinary host memory.  The caller owns every buffer it
+ * passes; a plan owns its workspace, twiddle tables and stream state.
+ * A plan is bound to the device that was current when it was created and
+ * is not thread-safe: one host thread at a time may use it.
+ */
+#ifndef SSMUL_H
+#define SSMUL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSMUL_OK = 0,
+    /* some coefficient's containment set holds two or more integers at the
+     * last precision tried (Section 1: more precision is needed) */
+    SSMUL_ISOLATION_FAILED = 1,
+    /* a containment set holds no integer, or is not finite: an internal
+     * rigor violation, reported and never rounded away */
+    SSMUL_CONTAINMENT_FAILED = 2,
+    SSMUL_INVALID_ARG = 3,
+    SSMUL_TOO_LARGE = 4,        /* sizes beyond the plan's maxima */
+    SSMUL_CUDA_ERROR = 5,
+    SSMUL_OUT_OF_MEMORY = 6,
+    SSMUL_TIMEOUT = 7           /* a bounded device-side wait gave up */
+} ssmul_status;
+
+typedef enum {
+    SSMUL_PREC_FP64 = 0,        /* binary64 inf-sup intervals only */
+    SSMUL_PREC_FP32 = 1,        /* binary32 inf-sup intervals only */
+    SSMUL_PREC_LADDER = 2       /* binary32 first; products that do not
+                                 * isolate are redone in binary64 */
+} ssmul_precision;
+
+/* Per-product outcome. */
+typedef struct {
+    int32_t  status;            /* ssmul_status of this product */
+    int32_t  precision_used;    /* ssmul_precision of the deciding rung
+                                 * (SSMUL_PREC_FP64 or SSMUL_PREC_FP32) */
+    uint32_t fft_log2;          /* log2 of the transform length N */
+    uint32_t n_unisolated;      /* coefficients whose set holds >= 2 integers */
+    uint32_t n_empty;           /* coefficients whose set holds no integer */
+    uint32_t reserved;
+    double   max_width;         /* largest coefficient interval width
+                                 * (rounded up), in units of 1 */
+} ssmul_result;
+
+/* One product of a batch: digits a_pool[a_off .. a_off+na), b_pool[b_off ..
+ * b_off+nb), result digits z_pool[z_off .. z_off+na+nb). */
+typedef struct {
+    uint64_t a_off, b_off, z_off;
+    uint32_t na, nb;
+} ssmul_desc;
+
+typedef struct ssmul_plan_s* ssmul_plan_t;
+
+/*
+ * Create a plan for products with na <= max_na and nb <= max_nb digits.
+ * Allocates the device workspace for one product of the largest size, and
+ * builds the twiddle enclosures omega_N^j = e^{2 pi i j / N} (the DFT root
+ * of Section 2.2) on the device for N up to the largest transform length.
+ * max_products bounds the count of one ssmul_mul_batched call (0: batches
+ * are not used).  prec selects the precision rule.  cuda_stream is a
+ * cudaStream_t (NULL: the legacy default stream) on which all work of the
+ * plan is ordered.
+ * Errors: SSMUL_INVALID_ARG (null out, zero sizes, unknown precision),
+ * SSMUL_TOO_LARGE (transform length above 2^23), SSMUL_OUT_OF_MEMORY,
+ * SSMUL_CUDA_ERROR.  On error *out is set to NULL.
+ */
+ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb,
+                        size_t max_products, ssmul_precision prec,
+                        void* cuda_stream);
+
+/*
+ * z = a * b for one product (Sections 2.3-2.5 and the carry of Section 2.4).
+ * d_a: na digits, d_b: nb digits, d_z: na+nb digits, all device memory,
+ * little-endian base 256 (leading zero digits are allowed).  The work is
+ * ordered on the plan's stream and the call waits for it: the return value
+ * is the product's status, and *h_res (host memory, may be NULL) receives
+ * the per-product outcome.  When the status is not SSMUL_OK, d_z is
+ * zero-filled: no unverified digit is ever returned.
+ * Errors: SSMUL_INVALID_ARG (null pointers, na or nb zero), SSMUL_TOO_LARGE
+ * (na > max_na or nb > max_nb), SSMUL_CUDA_ERROR, and the product statuses.
+ */
+ssmul_status ssmul_mul(ssmul_plan_t plan, const uint8_t* d_a, size_t na,
+                       const uint8_t* d_b, size_t nb, uint8_t* d_z,
+                       ssmul_result* h_res);
+
+/*
+ * Same as ssmul_mul, with a, b and z in host memory.  The host-device copies
+ * go through the plan's device buffers on the plan's stream.
+ */
+ssmul_status ssmul_mul_host(ssmul_plan_t plan, const uint8_t* h_a, size_t na,
+                            const uint8_t* h_b, size_t nb, uint8_t* h_z,
+                            ssmul_result* h_res);
+
+/*
+ * count independent products described by h_desc (host memory, count
+ * entries) over device digit pools.  Every product obeys the plan's size
+ * maxima and count <= max_products.  The work is only enqueued on the
+ * plan's stream: the return value covers argument and launch errors, and
+ * the per-product outcomes land in d_res (device memory, count entries),
+ * valid after the stream is synchronised.  Products whose status is not
+ * SSMUL_OK have their digits zero-filled.
+ */
+ssmul_status ssmul_mul_batched(ssmul_plan_t plan, size_t count,
+                               const ssmul_desc* h_desc,
+                               const uint8_t* d_a_pool, const uint8_t* d_b_pool,
+                               uint8_t* d_z_pool, ssmul_result* d_res);
+
+/* Release everything the plan owns.  NULL is allowed. */
+void ssmul_plan_destroy(ssmul_plan_t plan);
+
+/* A static string naming the status. */
+const char* ssmul_status_string(ssmul_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSMUL_H */

@@ -1,0 +1,55 @@
+/*
+ * ssmul_debug.h -- inspection entry points of the ssmul library, used by its
+ * tests.  They expose intermediate results of the method so that its rigor
+ * (every interval contains the exact value) can be checked from outside.
+ * Same conventions as ssmul.h: plain pointers, ssmul_status results, no
+ * aborts.  They are not on the performance path.
+ */
+#ifndef SSMUL_DEBUG_H
+#define SSMUL_DEBUG_H
+
+#include "ssmul.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Copy the plan's twiddle table to host memory: the enclosures of
+ * cos(2 pi j / Ntab) and sin(2 pi j / Ntab) for j = 0 .. Ntab/8 (the roots
+ * of unity of the DFT, Section 2.2), as 4 doubles per entry
+ * (cos_lo, cos_hi, sin_lo, sin_hi); f32 != 0 selects the binary32 table
+ * (values widened to double exactly).  *log_ntab receives log2 Ntab.
+ * cap is the capacity of h_out in doubles; SSMUL_INVALID_ARG when too small.
+ */
+ssmul_status ssmul_debug_twiddles(ssmul_plan_t plan, int f32, double* h_out, size_t cap,
+                                  int* log_ntab);
+
+/*
+ * One product as ssmul_mul, forced to a single precision rung (prec is
+ * SSMUL_PREC_FP64 or SSMUL_PREC_FP32), that also writes the enclosure of
+ * every convolution coefficient c_i = sum_j a_j b_{i-j} (Section 2.1) to
+ * d_iv (device memory, 2 * (na + nb - 1) doubles: lo_i, hi_i) after the
+ * inverse transform and the division by N (Sections 2.3, 2.5).
+ */
+ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t plan, const uint8_t* d_a, size_t na,
+                                       const uint8_t* d_b, size_t nb, uint8_t* d_z,
+                                       ssmul_result* h_res, ssmul_precision prec,
+                                       double* d_iv);
+
+/*
+ * Elementwise complex interval operation on n operands (Section 2.5), for
+ * unit tests of the device arithmetic.  d_x, d_y, d_out: device arrays of
+ * 4 doubles per operand (re_lo, re_hi, im_lo, im_hi).  op: 0 add, 1
+ * subtract, 2 product by a twiddle enclosure d_y (components that do not
+ * contain 0 unless they are the point 0), 3 general product.  f32 != 0
+ * runs the binary32 arithmetic on operands that must be binary32 values.
+ */
+ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double* d_y,
+                               double* d_out, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSMUL_DEBUG_H */

@@ -1,0 +1,184 @@
+"""ctypes binding of the ssmul C ABI (include/ssmul.h, include/ssmul_debug.h).
+
+Argument marshalling only: every step of the multiplication runs in the
+CUDA library libssmul.so.  Loading fails loudly when the library is
+missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+# ssmul_status
+SSMUL_OK = 0
+SSMUL_ISOLATION_FAILED = 1
+SSMUL_CONTAINMENT_FAILED = 2
+SSMUL_INVALID_ARG = 3
+SSMUL_TOO_LARGE = 4
+SSMUL_CUDA_ERROR = 5
+SSMUL_OUT_OF_MEMORY = 6
+SSMUL_TIMEOUT = 7
+
+# ssmul_precision
+SSMUL_PREC_FP64 = 0
+SSMUL_PREC_FP32 = 1
+SSMUL_PREC_LADDER = 2
+
+#: every symbol the headers declare
+EXPORTS = (
+    "ssmul_plan", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched",
+    "ssmul_plan_destroy", "ssmul_status_string",
+    "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op",
+)
+
+
+class ssmul_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("precision_used", ctypes.c_int32),
+        ("fft_log2", ctypes.c_uint32),
+        ("n_unisolated", ctypes.c_uint32),
+        ("n_empty", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("max_width", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ssmul_desc(ctypes.Structure):
+    _fields_ = [
+        ("a_off", ctypes.c_uint64),
+        ("b_off", ctypes.c_uint64),
+        ("z_off", ctypes.c_uint64),
+        ("na", ctypes.c_uint32),
+        ("nb", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+def load(path: str | None = None, build_if_missing: bool = True):
+    """Load libssmul.so (building it first when absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.LIB
+        if build_if_missing:
+            try:
+                _build.build()
+            except Exception as e:  # no nvcc: fall through to the existence check
+                if not os.path.exists(path):
+                    raise LibraryMissing(f"libssmul.so could not be built: {e}") from e
+    if not os.path.exists(path):
+        raise LibraryMissing(f"CUDA library not found: {path}")
+    L = ctypes.CDLL(path)
+    vp, sz, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    L.ssmul_plan.argtypes = [ctypes.POINTER(vp), sz, sz, sz, ctypes.c_int, vp]
+    L.ssmul_plan.restype = st
+    L.ssmul_mul.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result)]
+    L.ssmul_mul.restype = st
+    L.ssmul_mul_host.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result)]
+    L.ssmul_mul_host.restype = st
+    L.ssmul_mul_batched.argtypes = [vp, sz, ctypes.POINTER(ssmul_desc), vp, vp, vp, vp]
+    L.ssmul_mul_batched.restype = st
+    L.ssmul_plan_destroy.argtypes = [vp]
+    L.ssmul_plan_destroy.restype = None
+    L.ssmul_status_string.argtypes = [ctypes.c_int]
+    L.ssmul_status_string.restype = ctypes.c_char_p
+    L.ssmul_debug_twiddles.argtypes = [vp, ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_int)]
+    L.ssmul_debug_twiddles.restype = st
+    L.ssmul_debug_mul_intervals.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result),
+                                            ctypes.c_int, vp]
+    L.ssmul_debug_mul_intervals.restype = st
+    L.ssmul_debug_ci_op.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, sz]
+    L.ssmul_debug_ci_op.restype = st
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return load().ssmul_status_string(s).decode()
+
+
+class SsmulError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)}")
+        self.status = status
+
+
+def _check(s: int, what: str):
+    if s != SSMUL_OK:
+        raise SsmulError(s, what)
+
+
+# ---- the C calls, one Python function each -------------------------------------
+
+def ssmul_plan(max_na: int, max_nb: int, max_products: int = 0,
+               prec: int = SSMUL_PREC_FP64, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().ssmul_plan(ctypes.byref(h), max_na, max_nb, max_products, prec,
+                             ctypes.c_void_p(stream or 0)), "ssmul_plan")
+    return h.value
+
+
+def ssmul_plan_destroy(plan: int) -> None:
+    load().ssmul_plan_destroy(ctypes.c_void_p(plan))
+
+
+def ssmul_mul(plan: int, d_a: int, na: int, d_b: int, nb: int, d_z: int):
+    """Returns (status, ssmul_result)."""
+    r = ssmul_result()
+    s = load().ssmul_mul(ctypes.c_void_p(plan), ctypes.c_void_p(d_a), na, ctypes.c_void_p(d_b),
+                         nb, ctypes.c_void_p(d_z), ctypes.byref(r))
+    return s, r
+
+
+def ssmul_mul_host(plan: int, h_a: int, na: int, h_b: int, nb: int, h_z: int):
+    r = ssmul_result()
+    s = load().ssmul_mul_host(ctypes.c_void_p(plan), ctypes.c_void_p(h_a), na,
+                              ctypes.c_void_p(h_b), nb, ctypes.c_void_p(h_z), ctypes.byref(r))
+    return s, r
+
+
+def ssmul_mul_batched(plan: int, descs, d_a_pool: int, d_b_pool: int, d_z_pool: int,
+                      d_res: int) -> int:
+    """descs: a ctypes array of ssmul_desc (or a sequence of 5-tuples)."""
+    if not isinstance(descs, ctypes.Array):
+        arr = (ssmul_desc * len(descs))()
+        for i, (ao, bo, zo, na, nb) in enumerate(descs):
+            arr[i] = ssmul_desc(ao, bo, zo, na, nb)
+        descs = arr
+    return load().ssmul_mul_batched(ctypes.c_void_p(plan), len(descs), descs,
+                                    ctypes.c_void_p(d_a_pool), ctypes.c_void_p(d_b_pool),
+                                    ctypes.c_void_p(d_z_pool), ctypes.c_void_p(d_res))
+
+
+def ssmul_debug_twiddles(plan: int, f32: bool, h_out: int, cap: int):
+    ln = ctypes.c_int()
+    s = load().ssmul_debug_twiddles(ctypes.c_void_p(plan), int(f32), ctypes.c_void_p(h_out), cap,
+                                    ctypes.byref(ln))
+    return s, ln.value
+
+
+def ssmul_debug_mul_intervals(plan: int, d_a: int, na: int, d_b: int, nb: int, d_z: int,
+                              prec: int, d_iv: int):
+    r = ssmul_result()
+    s = load().ssmul_debug_mul_intervals(ctypes.c_void_p(plan), ctypes.c_void_p(d_a), na,
+                                         ctypes.c_void_p(d_b), nb, ctypes.c_void_p(d_z),
+                                         ctypes.byref(r), prec, ctypes.c_void_p(d_iv))
+    return s, r
+
+
+def ssmul_debug_ci_op(op: int, f32: bool, d_x: int, d_y: int, d_out: int, n: int) -> int:
+    return load().ssmul_debug_ci_op(op, int(f32), ctypes.c_void_p(d_x), ctypes.c_void_p(d_y),
+                                    ctypes.c_void_p(d_out), n)

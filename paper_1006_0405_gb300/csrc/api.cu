@@ -1,0 +1,448 @@
+// api.cu -- the C ABI of include/ssmul.h and include/ssmul_debug.h.
+//
+// Host-side orchestration only: argument checks, plan workspace, launch
+// geometry and the precision ladder.  Every arithmetic step of the method
+// runs in the kernels of kernels.cuh.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+#include "../../include/ssmul_debug.h"
+
+using namespace ssm;
+
+namespace {
+
+// the binary32 rung is tried when the product's transform is at most this
+// long and the shorter operand has at most this many digits: beyond them a
+// binary32 containment set cannot isolate base-256 coefficients (measured;
+// the isolation limit is reported by the tests and the benchmark)
+constexpr int FP32_MAX_LOG_N = LOG_SMALL;
+constexpr size_t FP32_MAX_MIN_DIGITS = 24;
+
+struct Geom {
+    int log_n;       // transform length N = 2^log_n
+    bool small;      // whole product in one CTA
+    int log_n1, log_n2;
+    int log_c1, log_c3;
+};
+
+int log_n_for(size_t na, size_t nb) {
+    const size_t L = na + nb - 1;
+    int k = 2;                          // N >= 4: the half-length inverse needs N/2 >= 2
+    while ((size_t(1) << k) < L) ++k;
+    return k;
+}
+
+Geom geom_for(int log_n) {
+    Geom g{};
+    g.log_n = log_n;
+    g.small = log_n <= LOG_SMALL;
+    if (!g.small) {
+        g.log_n2 = (log_n + 1) / 2 < LOG_N2_MAX ? (log_n + 1) / 2 : LOG_N2_MAX;
+        g.log_n1 = log_n - g.log_n2;
+        int c = LOG_CTA_ELEMS - g.log_n1;
+        if (c < 0) c = 0;
+        g.log_c1 = c < g.log_n2 ? c : g.log_n2;
+        g.log_c3 = c < g.log_n2 - 1 ? c : g.log_n2 - 1;
+    }
+    return g;
+}
+
+int threads_for(int elems) {          // block_fft: nl * L / 8 threads
+    int t = elems / 8;
+    if (t < 32) t = 32;
+    return t;
+}
+
+size_t carry_tiles(size_t nz) { return (nz + CARRY_TILE - 1) / CARRY_TILE; }
+
+ssmul_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SSMUL_OK;
+    if (e == cudaErrorMemoryAllocation) return SSMUL_OUT_OF_MEMORY;
+    return SSMUL_CUDA_ERROR;
+}
+
+#define SS_TRY(x)                                             \
+    do {                                                      \
+        cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) return cuda_status(e_);        \
+    } while (0)
+
+}  // namespace
+
+struct ssmul_plan_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ssmul_precision prec = SSMUL_PREC_FP64;
+    size_t max_na = 0, max_nb = 0, max_products = 0;
+    int log_n_max = 0;
+    int log_tab = 0;
+    TwEntry<double>* t64 = nullptr;
+    TwEntry<float>* t32 = nullptr;
+    // single-product workspace
+    void* Z = nullptr;
+    void* W = nullptr;
+    int64_t* coeff = nullptr;
+    uint32_t* flags = nullptr;          // carry look-back words
+    size_t flags_per_product = 0;
+    ProdState* st = nullptr;            // max(1, max_products) entries
+    ProdDesc* d_desc = nullptr;         // max(1, max_products) entries
+    ssmul_result* d_res = nullptr;
+    ProdDesc* h_desc = nullptr;         // pinned
+    ssmul_result* h_res = nullptr;      // pinned
+    cudaEvent_t desc_free = nullptr;    // h_desc may be rewritten once this fired
+    uint8_t* stage = nullptr;           // device staging for ssmul_mul_host
+    TwTable tw() const { return TwTable{t64, t32, log_tab}; }
+};
+
+namespace {
+
+template <typename T>
+ssmul_status set_smem_attrs() {
+    const int big = 160 * 1024;
+    SS_TRY(cudaFuncSetAttribute(k_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    return SSMUL_OK;
+}
+
+// Enqueue the interval convolution of `count` products that share one
+// transform length, described by d_desc[0 .. count).  gate: skip products
+// the binary32 rung already decided.
+template <typename T>
+ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
+                          int gate) {
+    const TwTable tw = p->tw();
+    if (g.small) {
+        const int n = 1 << g.log_n;
+        k_small<T><<<count, threads_for(n), n * sizeof(CI<T>), p->stream>>>(d_desc, tw, gate);
+    } else {
+        const int n1 = 1 << g.log_n1, n2 = 1 << g.log_n2;
+        const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
+        k_fwd_cols<T><<<dim3(n2 >> g.log_c1, count), threads_for(e1), e1 * sizeof(CI<T>),
+                        p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
+        k_rows<T><<<dim3(n1 / 2 + 1, count), threads_for(2 * n2), 2 * n2 * sizeof(CI<T>),
+                    p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
+        k_inv_cols<T><<<dim3((n2 / 2) >> g.log_c3, count), threads_for(e3), e3 * sizeof(CI<T>),
+                        p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c3, gate);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+bool fp32_eligible(size_t na, size_t nb, int log_n) {
+    const size_t mn = na < nb ? na : nb;
+    return log_n <= FP32_MAX_LOG_N && mn <= FP32_MAX_MIN_DIGITS;
+}
+
+// Enqueue one complete product (rungs, carry, outcome) for d_desc[0].
+ssmul_status enqueue_product(ssmul_plan_t p, const ProdDesc* d_desc, size_t na, size_t nb,
+                             ssmul_precision prec) {
+    const Geom g = geom_for(log_n_for(na, nb));
+    bool ran32 = false;
+    if (prec == SSMUL_PREC_FP32 || (prec == SSMUL_PREC_LADDER && fp32_eligible(na, nb, g.log_n))) {
+        ssmul_status s = enqueue_rung<float>(p, d_desc, 1, g, 0);
+        if (s != SSMUL_OK) return s;
+        ran32 = true;
+    }
+    if (prec == SSMUL_PREC_FP64 || prec == SSMUL_PREC_LADDER) {
+        ssmul_status s = enqueue_rung<double>(p, d_desc, 1, g, ran32 ? 1 : 0);
+        if (s != SSMUL_OK) return s;
+    }
+    const size_t tiles = carry_tiles(na + nb);
+    k_carry<<<dim3(unsigned(tiles), 1), CARRY_THREADS, 0, p->stream>>>(d_desc);
+    k_finalize<<<1, 256, 0, p->stream>>>(d_desc);
+    return cuda_status(cudaGetLastError());
+}
+
+ssmul_status check_device(ssmul_plan_t p) {
+    int cur = -1;
+    SS_TRY(cudaGetDevice(&cur));
+    if (cur != p->device) SS_TRY(cudaSetDevice(p->device));
+    return SSMUL_OK;
+}
+
+ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t* b, size_t nb,
+                     uint8_t* z, size_t slot) {
+    ProdDesc d{};
+    d.a = a;
+    d.b = b;
+    d.z = z;
+    d.na = uint32_t(na);
+    d.nb = uint32_t(nb);
+    d.log_n = log_n_for(na, nb);
+    d.Z = p->Z;
+    d.W = p->W;
+    d.coeff = p->coeff;
+    d.flags = p->flags + slot * p->flags_per_product;
+    d.st = p->st + slot;
+    d.res = p->d_res + slot;
+    d.iv = nullptr;
+    return d;
+}
+
+// one product on device buffers; fills h_res; waits for the result
+ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
+                        size_t nb, uint8_t* d_z, ssmul_result* h_res, ssmul_precision prec,
+                        double* d_iv) {
+    if (!d_a || !d_b || !d_z || na == 0 || nb == 0) return SSMUL_INVALID_ARG;
+    if (na > p->max_na || nb > p->max_nb) return SSMUL_TOO_LARGE;
+    ssmul_status s = check_device(p);
+    if (s != SSMUL_OK) return s;
+    SS_TRY(cudaEventSynchronize(p->desc_free));
+    p->h_desc[0] = single_desc(p, d_a, na, d_b, nb, d_z, 0);
+    p->h_desc[0].iv = d_iv;
+    SS_TRY(cudaMemsetAsync(p->st, 0, sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->flags, 0, carry_tiles(na + nb) * sizeof(uint32_t), p->stream));
+    SS_TRY(cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ProdDesc), cudaMemcpyHostToDevice,
+                           p->stream));
+    SS_TRY(cudaEventRecord(p->desc_free, p->stream));
+    s = enqueue_product(p, p->d_desc, na, nb, prec);
+    if (s != SSMUL_OK) return s;
+    SS_TRY(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(ssmul_result), cudaMemcpyDeviceToHost,
+                           p->stream));
+    SS_TRY(cudaStreamSynchronize(p->stream));
+    if (h_res) *h_res = p->h_res[0];
+    return ssmul_status(p->h_res[0].status);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ssmul_status_string(ssmul_status s) {
+    switch (s) {
+        case SSMUL_OK: return "SSMUL_OK";
+        case SSMUL_ISOLATION_FAILED: return "SSMUL_ISOLATION_FAILED";
+        case SSMUL_CONTAINMENT_FAILED: return "SSMUL_CONTAINMENT_FAILED";
+        case SSMUL_INVALID_ARG: return "SSMUL_INVALID_ARG";
+        case SSMUL_TOO_LARGE: return "SSMUL_TOO_LARGE";
+        case SSMUL_CUDA_ERROR: return "SSMUL_CUDA_ERROR";
+        case SSMUL_OUT_OF_MEMORY: return "SSMUL_OUT_OF_MEMORY";
+        case SSMUL_TIMEOUT: return "SSMUL_TIMEOUT";
+    }
+    return "SSMUL_UNKNOWN_STATUS";
+}
+
+void ssmul_plan_destroy(ssmul_plan_t p) {
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    cudaFree(p->t64);
+    cudaFree(p->t32);
+    cudaFree(p->Z);
+    cudaFree(p->W);
+    cudaFree(p->coeff);
+    cudaFree(p->flags);
+    cudaFree(p->st);
+    cudaFree(p->d_desc);
+    cudaFree(p->d_res);
+    cudaFree(p->stage);
+    cudaFreeHost(p->h_desc);
+    cudaFreeHost(p->h_res);
+    if (p->desc_free) cudaEventDestroy(p->desc_free);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t max_products,
+                        ssmul_precision prec, void* cuda_stream) {
+    if (!out) return SSMUL_INVALID_ARG;
+    *out = nullptr;
+    if (max_na == 0 || max_nb == 0) return SSMUL_INVALID_ARG;
+    if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32 && prec != SSMUL_PREC_LADDER)
+        return SSMUL_INVALID_ARG;
+    if (max_na > (size_t(1) << LOG_N_MAX) || max_nb > (size_t(1) << LOG_N_MAX))
+        return SSMUL_TOO_LARGE;
+    const int log_n = log_n_for(max_na, max_nb);
+    if (log_n > LOG_N_MAX) return SSMUL_TOO_LARGE;
+
+    ssmul_plan_s* p = new (std::nothrow) ssmul_plan_s();
+    if (!p) return SSMUL_OUT_OF_MEMORY;
+    ssmul_status s = SSMUL_OK;
+    auto fail = [&](ssmul_status e) {
+        ssmul_plan_destroy(p);
+        return e;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(SSMUL_CUDA_ERROR);
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+    p->prec = prec;
+    p->max_na = max_na;
+    p->max_nb = max_nb;
+    p->max_products = max_products;
+    p->log_n_max = log_n;
+    p->log_tab = log_n < 4 ? 4 : log_n;
+
+    const size_t n = size_t(1) << log_n;
+    const size_t slots = max_products ? max_products : 1;
+    const size_t tab = (size_t(1) << p->log_tab) / 8 + 1;
+    p->flags_per_product = carry_tiles(max_na + max_nb);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&p->t64, tab * sizeof(TwEntry<double>));
+    if (e == cudaSuccess) e = cudaMalloc(&p->t32, tab * sizeof(TwEntry<float>));
+    if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
+    if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
+    if (e == cudaSuccess) e = cudaMalloc(&p->coeff, n * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->flags, slots * p->flags_per_product * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->st, slots * sizeof(ProdState));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, slots * sizeof(ProdDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_res, slots * sizeof(ssmul_result));
+    if (e == cudaSuccess) e = cudaMalloc(&p->stage, 2 * (max_na + max_nb));
+    if (e == cudaSuccess) e = cudaMallocHost(&p->h_desc, slots * sizeof(ProdDesc));
+    if (e == cudaSuccess) e = cudaMallocHost(&p->h_res, slots * sizeof(ssmul_result));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->desc_free, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+
+    if ((s = set_smem_attrs<double>()) != SSMUL_OK) return fail(s);
+    if ((s = set_smem_attrs<float>()) != SSMUL_OK) return fail(s);
+
+    const int threads = 256;
+    const int blocks = int((tab + threads - 1) / threads);
+    k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->t32, p->log_tab);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaEventRecord(p->desc_free, p->stream)) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
+    *out = p;
+    return SSMUL_OK;
+}
+
+ssmul_status ssmul_mul(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
+                       size_t nb, uint8_t* d_z, ssmul_result* h_res) {
+    if (!p) return SSMUL_INVALID_ARG;
+    return run_single(p, d_a, na, d_b, nb, d_z, h_res, p->prec, nullptr);
+}
+
+ssmul_status ssmul_mul_host(ssmul_plan_t p, const uint8_t* h_a, size_t na, const uint8_t* h_b,
+                            size_t nb, uint8_t* h_z, ssmul_result* h_res) {
+    if (!p || !h_a || !h_b || !h_z || na == 0 || nb == 0) return SSMUL_INVALID_ARG;
+    if (na > p->max_na || nb > p->max_nb) return SSMUL_TOO_LARGE;
+    ssmul_status s = check_device(p);
+    if (s != SSMUL_OK) return s;
+    uint8_t* da = p->stage;
+    uint8_t* db = da + na;
+    uint8_t* dz = db + nb;
+    SS_TRY(cudaMemcpyAsync(da, h_a, na, cudaMemcpyHostToDevice, p->stream));
+    SS_TRY(cudaMemcpyAsync(db, h_b, nb, cudaMemcpyHostToDevice, p->stream));
+    s = run_single(p, da, na, db, nb, dz, h_res, p->prec, nullptr);
+    if (s != SSMUL_OK && s != SSMUL_ISOLATION_FAILED && s != SSMUL_CONTAINMENT_FAILED &&
+        s != SSMUL_TIMEOUT)
+        return s;
+    SS_TRY(cudaMemcpyAsync(h_z, dz, na + nb, cudaMemcpyDeviceToHost, p->stream));
+    SS_TRY(cudaStreamSynchronize(p->stream));
+    return s;
+}
+
+ssmul_status ssmul_mul_batched(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
+                               const uint8_t* d_a_pool, const uint8_t* d_b_pool,
+                               uint8_t* d_z_pool, ssmul_result* d_res) {
+    if (!p || (count && (!h_desc || !d_a_pool || !d_b_pool || !d_z_pool || !d_res)))
+        return SSMUL_INVALID_ARG;
+    if (count > p->max_products) return SSMUL_TOO_LARGE;
+    for (size_t i = 0; i < count; ++i) {
+        if (h_desc[i].na == 0 || h_desc[i].nb == 0) return SSMUL_INVALID_ARG;
+        if (h_desc[i].na > p->max_na || h_desc[i].nb > p->max_nb) return SSMUL_TOO_LARGE;
+    }
+    if (count == 0) return SSMUL_OK;
+    ssmul_status s = check_device(p);
+    if (s != SSMUL_OK) return s;
+    SS_TRY(cudaEventSynchronize(p->desc_free));
+    for (size_t i = 0; i < count; ++i) {
+        const ssmul_desc& h = h_desc[i];
+        ProdDesc d = single_desc(p, d_a_pool + h.a_off, h.na, d_b_pool + h.b_off, h.nb,
+                                 d_z_pool + h.z_off, i);
+        d.res = d_res + i;
+        p->h_desc[i] = d;
+    }
+    SS_TRY(cudaMemsetAsync(p->st, 0, count * sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->flags, 0, count * p->flags_per_product * sizeof(uint32_t),
+                           p->stream));
+    SS_TRY(cudaMemcpyAsync(p->d_desc, p->h_desc, count * sizeof(ProdDesc),
+                           cudaMemcpyHostToDevice, p->stream));
+    SS_TRY(cudaEventRecord(p->desc_free, p->stream));
+    for (size_t i = 0; i < count; ++i) {
+        s = enqueue_product(p, p->d_desc + i, h_desc[i].na, h_desc[i].nb, p->prec);
+        if (s != SSMUL_OK) return s;
+    }
+    return SSMUL_OK;
+}
+
+// ---- inspection entry points (include/ssmul_debug.h) ----------------------------
+
+ssmul_status ssmul_debug_twiddles(ssmul_plan_t p, int f32, double* h_out, size_t cap,
+                                  int* log_ntab) {
+    if (!p || !h_out || !log_ntab) return SSMUL_INVALID_ARG;
+    const size_t tab = (size_t(1) << p->log_tab) / 8 + 1;
+    if (cap < 4 * tab) return SSMUL_INVALID_ARG;
+    ssmul_status s = check_device(p);
+    if (s != SSMUL_OK) return s;
+    *log_ntab = p->log_tab;
+    if (!f32) {
+        SS_TRY(cudaMemcpy(h_out, p->t64, tab * sizeof(TwEntry<double>), cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<TwEntry<float>> t(tab);
+        SS_TRY(cudaMemcpy(t.data(), p->t32, tab * sizeof(TwEntry<float>), cudaMemcpyDeviceToHost));
+        for (size_t j = 0; j < tab; ++j) {
+            h_out[4 * j] = t[j].cl;
+            h_out[4 * j + 1] = t[j].ch;
+            h_out[4 * j + 2] = t[j].sl;
+            h_out[4 * j + 3] = t[j].sh;
+        }
+    }
+    return SSMUL_OK;
+}
+
+ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t p, const uint8_t* d_a, size_t na,
+                                       const uint8_t* d_b, size_t nb, uint8_t* d_z,
+                                       ssmul_result* h_res, ssmul_precision prec,
+                                       double* d_iv) {
+    if (!p || !d_iv) return SSMUL_INVALID_ARG;
+    if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32) return SSMUL_INVALID_ARG;
+    return run_single(p, d_a, na, d_b, nb, d_z, h_res, prec, d_iv);
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+__global__ void k_ci_op(int op, const double* x, const double* y, double* out, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        const CI<T> a{T(x[4 * i]), T(x[4 * i + 1]), T(x[4 * i + 2]), T(x[4 * i + 3])};
+        const CI<T> b{T(y[4 * i]), T(y[4 * i + 1]), T(y[4 * i + 2]), T(y[4 * i + 3])};
+        CI<T> r;
+        switch (op) {
+            case 0: r = a + b; break;
+            case 1: r = a - b; break;
+            case 2: r = mul_tw(a, b); break;
+            default: r = mul_ci(a, b); break;
+        }
+        out[4 * i] = r.rl;
+        out[4 * i + 1] = r.rh;
+        out[4 * i + 2] = r.il;
+        out[4 * i + 3] = r.ih;
+    }
+}
+
+}  // namespace
+
+extern "C" ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double* d_y,
+                                          double* d_out, size_t n) {
+    if (op < 0 || op > 3 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
+    if (n == 0) return SSMUL_OK;
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);
+    if (f32)
+        k_ci_op<float><<<blocks, threads>>>(op, d_x, d_y, d_out, n);
+    else
+        k_ci_op<double><<<blocks, threads>>>(op, d_x, d_y, d_out, n);
+    SS_TRY(cudaGetLastError());
+    SS_TRY(cudaDeviceSynchronize());
+    return SSMUL_OK;
+}

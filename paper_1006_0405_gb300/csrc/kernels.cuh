@@ -1,0 +1,498 @@
+// kernels.cuh -- the interval convolution pipeline and the carry scan.
+//
+// One product z = a * b (Section 2.4) runs as:
+//
+//   pack      z_j = a_j + i b_j as point intervals, zero padded to N
+//             (N = 2^k >= na + nb - 1, Section 2.3).  Both operands are
+//             real, so one complex transform carries both.
+//   forward   Z = DFT_N(z) (Section 2.2), interval arithmetic (Section 2.5).
+//   split +   A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / 2i
+//   pointwise are the transforms of a and b, and C_k = A_k B_k is the
+//             transform of the convolution (the convolution theorem,
+//             Section 2.3).  C_{N-k} = conj C_k because c is real.
+//   pack      D_k = (C_k + C_{k+N/2}) + i omega_N^{-k} (C_k - C_{k+N/2}),
+//             k < N/2: the length-N/2 inverse of D is c_{2j} + i c_{2j+1}.
+//   inverse   d = IDFT_{N/2}(D) scaled by 1/N (exact power of two).
+//   isolate   each of c_{2j} = Re d_j and c_{2j+1} = Im d_j must hold exactly
+//             one integer (Section 1); coefficients past na + nb - 2 must
+//             contain 0.
+//   carry     the integer coefficients become na + nb base-256 digits.
+//
+// For N <= 4096 one CTA does everything up to the isolation in shared
+// memory (k_small).  Larger N use the four-step factorisation N = N1 * N2,
+// with the spectrum kept in "transposed" order (index k1 + N1 k2 stored at
+// row k1, column k2) so no reordering pass is needed:
+//   k_fwd_cols  column DFTs of length N1 and the twiddles omega_N^{j2 k1}
+//   k_rows      row DFTs of length N2 for the row pair (k1, N1 - k1), the
+//               split / pointwise / pack steps, the inverse row DFTs of
+//               length N2/2 and the twiddles omega_{N/2}^{-j2 k1}
+//   k_inv_cols  inverse column DFTs of length N1, scaling and isolation
+#pragma once
+#include <cuda_runtime.h>
+#include "../../include/ssmul.h"
+#include "interval.cuh"
+#include "twiddle.cuh"
+#include "fft.cuh"
+
+namespace ssm {
+
+constexpr int LOG_SMALL = 12;          // k_small handles N <= 2^12
+constexpr int LOG_N2_MAX = 11;         // four-step row length limit
+constexpr int LOG_N1_MAX = 12;         // four-step column length limit
+constexpr int LOG_N_MAX = LOG_N1_MAX + LOG_N2_MAX;   // 2^23
+constexpr int LOG_CTA_ELEMS = 11;      // column kernels hold >= 2^11 elements
+constexpr int CARRY_TILE = 4096;       // digits per carry CTA
+constexpr int CARRY_THREADS = 256;
+constexpr int CARRY_PER_THREAD = CARRY_TILE / CARRY_THREADS;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;   // bounded look-back polls
+
+// Per-product accumulators of one call, zeroed before the call.
+// Index 0: binary32 rung, index 1: binary64 rung.
+struct ProdState {
+    unsigned int ran[2];
+    unsigned int unisolated[2];
+    unsigned int empty[2];
+    unsigned int timeout;
+    unsigned int carry_ticket;
+    unsigned long long maxw[2];        // bit pattern of a nonnegative double
+};
+
+struct ProdDesc {
+    const uint8_t* a;
+    const uint8_t* b;
+    uint8_t* z;
+    uint32_t na, nb;
+    int32_t log_n;                     // transform length N = 2^log_n
+    int32_t pad0;
+    void* Z;                           // four-step workspace, N intervals
+    void* W;                           // four-step workspace, N/2 intervals
+    int64_t* coeff;                    // N integer coefficients
+    uint32_t* flags;                   // carry look-back words, one per tile
+    ProdState* st;
+    ssmul_result* res;
+    double* iv;                        // optional: coefficient enclosures (tests)
+};
+
+// ---- the rung gate of the precision ladder ------------------------------------
+
+// true when the binary32 rung already decided this product
+__device__ __forceinline__ bool fp32_decided(const ProdState* st) {
+    return st->ran[0] && (st->unisolated[0] == 0 || st->empty[0] != 0);
+}
+
+template <typename T> struct Rung;
+template <> struct Rung<float> { static constexpr int idx = 0; };
+template <> struct Rung<double> { static constexpr int idx = 1; };
+
+// ---- shared-memory stages common to k_small and k_rows -----------------------
+
+// Pointwise product on the pairs (k, N - k).  Line l of `sm` holds the
+// forward transform of row rows[l]; the partner of (row r, column k2) is
+// row (N1 - r) mod N1, column (N2 - k2) mod N2 for r = 0 and N2 - 1 - k2
+// otherwise.  With two lines the rows are partners of each other; with
+// one line the row is its own partner.
+template <typename T>
+__device__ void pair_products(CI<T>* sm, int nl, int row0, int logN2) {
+    const int N2 = 1 << logN2;
+    for (int k2 = threadIdx.x; k2 < N2; k2 += blockDim.x) {
+        const int pc = (row0 == 0) ? ((N2 - k2) & (N2 - 1)) : (N2 - 1 - k2);
+        if (nl == 1 && k2 > pc) continue;
+        const int pi = (nl == 2 ? N2 : 0) + pc;
+        const CI<T> zk = sm[k2];
+        const CI<T> czp = conj(sm[pi]);
+        const CI<T> a2 = zk + czp;                 // 2 A_k
+        const CI<T> b2 = mul_negi(zk - czp);       // 2 B_k
+        const CI<T> c4 = mul_ci(a2, b2);           // 4 C_k
+        sm[k2] = c4;
+        if (pi != k2) sm[pi] = conj(c4);           // 4 C_{N-k}
+    }
+}
+
+// D_k for k2 < N2/2 of each line, written over the first half of the line.
+template <typename T>
+__device__ void pack_half(CI<T>* sm, int nl, const int* rows, int logN1, int logN2,
+                          const TwTable& tw) {
+    const int N2 = 1 << logN2, M2 = N2 >> 1;
+    const int logN = logN1 + logN2;
+    for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
+        const int l = t >> (logN2 - 1), k2 = t & (M2 - 1);
+        CI<T>* x = sm + l * N2;
+        const CI<T> c0 = x[k2], c1 = x[k2 + M2];
+        const uint32_t k = uint32_t(rows[l]) + (uint32_t(k2) << logN1);
+        const CI<T> w = twiddle<T, -1>(tw, k << (tw.log_n - logN));
+        x[k2] = (c0 + c1) + mul_i(mul_tw(c0 - c1, w));
+    }
+}
+
+// ---- isolation (Section 1) --------------------------------------------------
+
+struct IsoAcc {
+    unsigned int unisolated = 0, empty = 0;
+    double maxw = 0.0;
+};
+
+// Decide coefficient `idx` from its enclosure [lo, hi]; L = na + nb - 1.
+template <typename T>
+__device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, int64_t L,
+                                            int64_t* coeff, IsoAcc& acc, double* iv) {
+    const double dl = double(lo), dh = double(hi);    // exact widening
+    if (iv != nullptr && idx < L) {
+        iv[2 * idx] = dl;
+        iv[2 * idx + 1] = dh;
+    }
+    const double w = __dsub_ru(dh, dl);
+    acc.maxw = (w > acc.maxw || w != w) ? w : acc.maxw;
+    if (idx < L) {
+        const double kl = ceil(dl), kh = floor(dh);
+        int64_t v = 0;
+        if (kl == kh && kl >= 0.0) {
+            v = int64_t(kl);
+        } else if (kl < kh) {
+            acc.unisolated++;
+        } else {
+            acc.empty++;           // no integer, a negative one, or NaN
+        }
+        coeff[idx] = v;
+    } else {
+        if (!(dl <= 0.0 && 0.0 <= dh)) acc.empty++;   // exact value is 0
+    }
+}
+
+__device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.unisolated += __shfl_xor_sync(0xffffffffu, acc.unisolated, o);
+        acc.empty += __shfl_xor_sync(0xffffffffu, acc.empty, o);
+        const double w = __shfl_xor_sync(0xffffffffu, acc.maxw, o);
+        acc.maxw = (w > acc.maxw || w != w) ? w : acc.maxw;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (acc.unisolated) atomicAdd(&st->unisolated[rung], acc.unisolated);
+        if (acc.empty) atomicAdd(&st->empty[rung], acc.empty);
+        atomicMax(&st->maxw[rung], (unsigned long long)__double_as_longlong(acc.maxw));
+    }
+}
+
+// ---- k_small: the whole interval convolution of one product in one CTA -----
+
+template <typename T>
+__global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    const ProdDesc d = descs[blockIdx.x];
+    if (gate && fp32_decided(d.st)) return;
+    const int logN = d.log_n, N = 1 << logN;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const T re = j < int(d.na) ? T(d.a[j]) : T(0);
+        const T im = j < int(d.nb) ? T(d.b[j]) : T(0);
+        sm[j] = {re, re, im, im};
+    }
+    __syncthreads();
+    block_fft<T, +1>(sm, logN, 1, N, tw);
+    pair_products(sm, 1, 0, logN);
+    __syncthreads();
+    const int rows[2] = {0, 0};
+    pack_half(sm, 1, rows, 0, logN, tw);
+    __syncthreads();
+    block_fft<T, -1>(sm, logN - 1, 1, N, tw);
+    const T scale = T(ldexp(1.0, -(logN + 2)));
+    const int64_t L = int64_t(d.na) + d.nb - 1;
+    IsoAcc acc;
+    for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) {
+        const CI<T> v = scale_out(sm[j], scale);
+        isolate_one(v.rl, v.rh, 2 * int64_t(j), L, d.coeff, acc, d.iv);
+        isolate_one(v.il, v.ih, 2 * int64_t(j) + 1, L, d.coeff, acc, d.iv);
+    }
+    flush_acc(acc, d.st, Rung<T>::idx);
+    if (threadIdx.x == 0) atomicOr(&d.st->ran[Rung<T>::idx], 1u);
+}
+
+// ---- four-step kernels --------------------------------------------------------
+
+template <typename T>
+__global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
+                           int gate) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    const ProdDesc d = descs[blockIdx.y];
+    if (gate && fp32_decided(d.st)) return;
+    const int N1 = 1 << logN1, C = 1 << logC;
+    const uint32_t j2_0 = blockIdx.x << logC;
+    CI<T>* Z = reinterpret_cast<CI<T>*>(d.Z);
+    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
+        const int c = idx & (C - 1), j1 = idx >> logC;
+        const uint32_t j = (uint32_t(j1) << logN2) + j2_0 + c;
+        const T re = j < d.na ? T(d.a[j]) : T(0);
+        const T im = j < d.nb ? T(d.b[j]) : T(0);
+        sm[(c << logN1) + j1] = {re, re, im, im};
+    }
+    __syncthreads();
+    block_fft<T, +1>(sm, logN1, C, N1, tw);
+    const int logN = logN1 + logN2;
+    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
+        const int c = idx & (C - 1), k1 = idx >> logC;
+        const uint32_t j2 = j2_0 + c;
+        CI<T> v = sm[(c << logN1) + k1];
+        const uint32_t e = j2 * uint32_t(k1);             // < N
+        if (e) v = mul_tw(v, twiddle<T, +1>(tw, e << (tw.log_n - logN)));
+        Z[(size_t(k1) << logN2) + j2] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    const ProdDesc d = descs[blockIdx.y];
+    if (gate && fp32_decided(d.st)) return;
+    const int N1 = 1 << logN1, N2 = 1 << logN2, M2 = N2 >> 1;
+    const int k1 = blockIdx.x;                              // 0 .. N1/2
+    const int k1b = (N1 - k1) & (N1 - 1);
+    const int nl = (k1 == k1b) ? 1 : 2;
+    const int rows[2] = {k1, k1b};
+    const CI<T>* Z = reinterpret_cast<const CI<T>*>(d.Z);
+    CI<T>* W = reinterpret_cast<CI<T>*>(d.W);
+    for (int t = threadIdx.x; t < nl * N2; t += blockDim.x) {
+        const int l = t >> logN2, k2 = t & (N2 - 1);
+        sm[t] = Z[(size_t(rows[l]) << logN2) + k2];
+    }
+    __syncthreads();
+    block_fft<T, +1>(sm, logN2, nl, N2, tw);
+    pair_products(sm, nl, k1, logN2);
+    __syncthreads();
+    pack_half(sm, nl, rows, logN1, logN2, tw);
+    __syncthreads();
+    block_fft<T, -1>(sm, logN2 - 1, nl, N2, tw);
+    const int logM = logN1 + logN2 - 1;
+    for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
+        const int l = t >> (logN2 - 1), j2 = t & (M2 - 1);
+        CI<T> v = sm[l * N2 + j2];
+        const uint32_t e = uint32_t(rows[l]) * uint32_t(j2);    // < N/2
+        if (e) v = mul_tw(v, twiddle<T, -1>(tw, e << (tw.log_n - logM)));
+        W[(size_t(rows[l]) << (logN2 - 1)) + j2] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
+                           int gate) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    const ProdDesc d = descs[blockIdx.y];
+    if (gate && fp32_decided(d.st)) return;
+    const int N1 = 1 << logN1, C = 1 << logC;
+    const int logM2 = logN2 - 1;
+    const uint32_t j2_0 = blockIdx.x << logC;
+    const CI<T>* W = reinterpret_cast<const CI<T>*>(d.W);
+    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
+        const int c = idx & (C - 1), k1 = idx >> logC;
+        sm[(c << logN1) + k1] = W[(size_t(k1) << logM2) + j2_0 + c];
+    }
+    __syncthreads();
+    block_fft<T, -1>(sm, logN1, C, N1, tw);
+    const int logN = logN1 + logN2;
+    const T scale = T(ldexp(1.0, -(logN + 2)));
+    const int64_t L = int64_t(d.na) + d.nb - 1;
+    IsoAcc acc;
+    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
+        const int c = idx & (C - 1), j1 = idx >> logC;
+        const int64_t j = (int64_t(j1) << logM2) + j2_0 + c;
+        const CI<T> v = scale_out(sm[(c << logN1) + j1], scale);
+        isolate_one(v.rl, v.rh, 2 * j, L, d.coeff, acc, d.iv);
+        isolate_one(v.il, v.ih, 2 * j + 1, L, d.coeff, acc, d.iv);
+    }
+    flush_acc(acc, d.st, Rung<T>::idx);
+    if (threadIdx.x == 0) atomicOr(&d.st->ran[Rung<T>::idx], 1u);
+}
+
+// ---- the decision of a product ---------------------------------------------
+
+__device__ __forceinline__ int decide(const ProdState* st, int* rung) {
+    if (st->timeout) { *rung = 1; return SSMUL_TIMEOUT; }
+    if (st->ran[0]) {
+        if (st->empty[0]) { *rung = 0; return SSMUL_CONTAINMENT_FAILED; }
+        if (st->unisolated[0] == 0) { *rung = 0; return SSMUL_OK; }
+    }
+    if (st->ran[1]) {
+        *rung = 1;
+        if (st->empty[1]) return SSMUL_CONTAINMENT_FAILED;
+        return st->unisolated[1] ? SSMUL_ISOLATION_FAILED : SSMUL_OK;
+    }
+    *rung = 0;
+    return SSMUL_ISOLATION_FAILED;
+}
+
+// ---- carry (Section 2.4) as a parallel carry-lookahead scan ------------------
+//
+// The coefficients c_i (0 <= c_i < 2^48) are split into bytes; the bytes
+// that land on digit position k sum to u_k <= 6 * 255, and
+// v_k = (u_k mod 256) + floor(u_{k-1} / 256) <= 260 satisfies
+// sum_k v_k 256^k = sum_i c_i 256^i.  What remains is one carry bit per
+// position: position k generates a carry when v_k >= 256 and propagates
+// an incoming one when v_k = 255.  Within a warp the 32 (generate,
+// propagate) pairs are evaluated by one binary addition of the bit masks
+// A = generate|propagate and B = generate (the carry into lane i is bit i
+// of (A + B + carry_in) ^ A ^ B); warps combine through shared memory and
+// CTAs through a decoupled look-back whose waits are bounded.
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// look-back word: bit 0 aggregate ready, bit 1 inclusive ready,
+// bit 2 generate / carry-out, bit 3 propagate, bit 4 timed out upstream
+constexpr uint32_t LB_AGG = 1u, LB_INC = 2u, LB_G = 4u, LB_P = 8u, LB_ERR = 16u;
+
+__device__ __forceinline__ uint32_t digit_byte_sum(const int64_t* c, int64_t L, int64_t k) {
+    uint32_t u = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        const int64_t i = k - t;
+        if (i >= 0 && i < L) u += uint32_t((uint64_t(c[i]) >> (8 * t)) & 0xFFu);
+    }
+    return u;
+}
+
+__global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) {
+    __shared__ uint32_t s_tile, s_status, s_wA[CARRY_THREADS / 32], s_wB[CARRY_THREADS / 32];
+    __shared__ uint32_t s_warp_cin[CARRY_THREADS / 32];
+    const ProdDesc d = descs[blockIdx.y];
+    const int64_t nz = int64_t(d.na) + d.nb;
+    const int64_t L = nz - 1;
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(&d.st->carry_ticket, 1u);   // tiles in start order
+        int rung;
+        s_status = decide(d.st, &rung);
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t k0 = int64_t(tile) * CARRY_TILE + int64_t(threadIdx.x) * CARRY_PER_THREAD;
+    if (s_status != SSMUL_OK) {
+        // no unverified digit escapes: zero fill, publish a zero carry
+        for (int q = 0; q < CARRY_PER_THREAD; ++q)
+            if (k0 + q < nz) d.z[k0 + q] = 0;
+        if (threadIdx.x == 0) st_release(&d.flags[tile], LB_AGG | LB_INC);
+        return;
+    }
+    // v_k for this thread's positions, and its (generate, propagate) summary
+    uint32_t v[CARRY_PER_THREAD];
+    uint32_t prev_hi = (k0 > 0) ? (digit_byte_sum(d.coeff, L, k0 - 1) >> 8) : 0u;
+    bool G = false, P = true;
+#pragma unroll
+    for (int q = 0; q < CARRY_PER_THREAD; ++q) {
+        const int64_t k = k0 + q;
+        const uint32_t u = (k < nz) ? digit_byte_sum(d.coeff, L, k) : 0u;
+        v[q] = (u & 0xFFu) + prev_hi;
+        prev_hi = u >> 8;
+        const bool g = v[q] >= 256u, p = v[q] == 255u;
+        G = g || (p && G);
+        P = P && p;
+    }
+    // warp: carries into each lane with carry-in 0
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t A = __ballot_sync(0xffffffffu, G || P);
+    const uint32_t B = __ballot_sync(0xffffffffu, G);
+    if (lane == 0) { s_wA[warp] = A; s_wB[warp] = B; }
+    __syncthreads();
+    if (warp == 0) {
+        // warp summaries: generate = carry out with carry-in 0,
+        // propagate = every lane propagates
+        constexpr int NW = CARRY_THREADS / 32;
+        bool wg = false, wp = false;
+        if (lane < NW) {
+            const uint64_t s = uint64_t(s_wA[lane]) + uint64_t(s_wB[lane]);
+            wg = (s >> 32) != 0;
+            wp = (s_wA[lane] == 0xffffffffu) && (s_wB[lane] == 0u);
+        }
+        const uint32_t WA = __ballot_sync(0xffffffffu, wg || wp) & ((1u << NW) - 1u);
+        const uint32_t WB = __ballot_sync(0xffffffffu, wg) & ((1u << NW) - 1u);
+        // tile summary
+        const uint64_t ts = uint64_t(WA) + uint64_t(WB);
+        const bool tg = (ts >> NW) & 1u;
+        const bool tp = WA == ((1u << NW) - 1u) && WB == 0u;
+        uint32_t cin = 0, err = 0;
+        if (lane == 0) {
+            if (tile == 0) {
+                st_release(&d.flags[0], LB_INC | (tg ? LB_G : 0u));
+            } else {
+                st_release(&d.flags[tile], LB_AGG | (tg ? LB_G : 0u) | (tp ? LB_P : 0u));
+                // look back: (rg, rp) summarises tiles pred+1 .. tile-1
+                bool rg = false, rp = true;
+                int64_t pred = int64_t(tile) - 1;
+                while (true) {
+                    uint32_t f = 0;
+                    uint32_t it = 0;
+                    for (; it < SPIN_LIMIT; ++it) {
+                        f = ld_acquire(&d.flags[pred]);
+                        if (f & (LB_AGG | LB_INC)) break;
+                        __nanosleep(64);
+                    }
+                    if (it == SPIN_LIMIT) {
+                        err = LB_ERR;
+                        atomicExch(&d.st->timeout, 1u);
+                        break;
+                    }
+                    err |= (f & LB_ERR);
+                    if (f & LB_INC) {
+                        cin = (rg || (rp && (f & LB_G))) ? 1u : 0u;
+                        break;
+                    }
+                    const bool pg = f & LB_G, pp = f & LB_P;
+                    rg = rg || (rp && pg);
+                    rp = rp && pp;
+                    --pred;
+                }
+                const bool cout = tg || (tp && cin);
+                st_release(&d.flags[tile], LB_AGG | LB_INC | (cout ? LB_G : 0u) | err);
+            }
+        }
+        __syncwarp();
+        cin = __shfl_sync(0xffffffffu, cin, 0);
+        // carry into each warp of the tile
+        const uint32_t carries = uint32_t((uint64_t(WA) + uint64_t(WB) + cin) ^ WA ^ WB);
+        if (lane < NW) s_warp_cin[lane] = (carries >> lane) & 1u;
+    }
+    __syncthreads();
+    const uint32_t wcin = s_warp_cin[warp];
+    const uint32_t carries = uint32_t((uint64_t(A) + uint64_t(B) + wcin) ^ A ^ B);
+    uint32_t c = (carries >> lane) & 1u;
+#pragma unroll
+    for (int q = 0; q < CARRY_PER_THREAD; ++q) {
+        const int64_t k = k0 + q;
+        const uint32_t t = v[q] + c;
+        if (k < nz) d.z[k] = uint8_t(t & 0xFFu);
+        c = t >> 8;
+    }
+}
+
+// Final per-product outcome; zero-fills the digits of a product whose carry
+// scan gave up waiting (the carry kernel already zero-filled the others).
+__global__ void k_finalize(const ProdDesc* descs) {
+    const ProdDesc d = descs[blockIdx.x];
+    __shared__ int s_status;
+    if (threadIdx.x == 0) {
+        int rung;
+        const int status = decide(d.st, &rung);
+        ssmul_result r;
+        r.status = status;
+        r.precision_used = rung == 0 ? SSMUL_PREC_FP32 : SSMUL_PREC_FP64;
+        r.fft_log2 = uint32_t(d.log_n);
+        r.n_unisolated = d.st->unisolated[rung];
+        r.n_empty = d.st->empty[rung];
+        r.reserved = 0;
+        r.max_width = __longlong_as_double((long long)d.st->maxw[rung]);
+        *d.res = r;
+        s_status = status;
+    }
+    __syncthreads();
+    if (s_status == SSMUL_TIMEOUT) {
+        const int64_t nz = int64_t(d.na) + d.nb;
+        for (int64_t k = threadIdx.x; k < nz; k += blockDim.x) d.z[k] = 0;
+    }
+}
+
+}  // namespace ssm

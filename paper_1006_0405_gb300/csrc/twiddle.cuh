@@ -1,0 +1,99 @@
+// twiddle.cuh -- rigorous enclosures of the roots of unity omega_N^j.
+//
+// The DFT of Section 2.2 uses omega = e^{2 pi i / N}; its inverse uses
+// omega^-1.  The plan builds, once, a table of enclosures of
+// cos(2 pi j / Ntab) and sin(2 pi j / Ntab) for the first octant
+// j = 0 .. Ntab/8; every other power of every root omega_N (N <= Ntab, both
+// powers of two) is read from it through exact symmetries of the circle
+// (reflection about pi/4 swaps cos and sin; a quarter turn maps (c, s) to
+// (-s, c); the inverse root conjugates).
+//
+// Each table entry comes from the device's sincospi(2 j / Ntab), whose
+// argument is exact because Ntab is a power of two.  The CUDA Math API
+// documents a maximum error of 2 ulp for the binary64 sincospi; each value
+// is widened outward by TW_WIDEN_ULPS = 4 steps of nextafter (the bound
+// plus margin for the change of ulp size at a power of two), then clamped
+// to what is known exactly on the first octant (cos in [0, 1], sin in
+// [0, 1]).  j = 0 is the exact point (1, 0).  The binary32 table is the
+// binary64 one rounded outward.
+#pragma once
+#include "interval.cuh"
+
+namespace ssm {
+
+constexpr int TW_WIDEN_ULPS = 4;
+constexpr int TW_DOC_ULPS = 2;
+
+template <typename T>
+struct TwEntry {
+    T cl, ch, sl, sh;
+};
+
+struct TwTable {
+    const TwEntry<double>* t64;   // Ntab/8 + 1 entries
+    const TwEntry<float>* t32;    // same, binary32
+    int log_n;                    // log2 Ntab
+};
+
+__global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n) {
+    const int64_t ntab = int64_t(1) << log_n;
+    const int64_t count = ntab / 8 + 1;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
+         j += int64_t(gridDim.x) * blockDim.x) {
+        TwEntry<double> e;
+        if (j == 0) {
+            e = {1.0, 1.0, 0.0, 0.0};
+        } else {
+            // 2 j / ntab is exact: a small integer times a power of two
+            const double x = ldexp(double(2 * j), -log_n);
+            double s, c;
+            sincospi(x, &s, &c);
+            double cl = c, ch = c, sl = s, sh = s;
+            for (int k = 0; k < TW_WIDEN_ULPS; ++k) {
+                cl = nextafter(cl, -1.0e300);
+                ch = nextafter(ch, 1.0e300);
+                sl = nextafter(sl, -1.0e300);
+                sh = nextafter(sh, 1.0e300);
+            }
+            // first octant: 0 < sin <= cos <= 1
+            e = {fmax(cl, 0.0), fmin(ch, 1.0), fmax(sl, 0.0), fmin(sh, 1.0)};
+        }
+        t64[j] = e;
+        t32[j] = {__double2float_rd(e.cl), __double2float_ru(e.ch),
+                  __double2float_rd(e.sl), __double2float_ru(e.sh)};
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ const TwEntry<T>* tw_ptr(const TwTable& tw);
+template <>
+__device__ __forceinline__ const TwEntry<double>* tw_ptr<double>(const TwTable& tw) { return tw.t64; }
+template <>
+__device__ __forceinline__ const TwEntry<float>* tw_ptr<float>(const TwTable& tw) { return tw.t32; }
+
+// Enclosure of omega_Ntab^(sign * j) for any integer j (taken mod Ntab).
+template <typename T, int SIGN>
+__device__ __forceinline__ CI<T> twiddle(const TwTable& tw, uint32_t j) {
+    const int ln = tw.log_n;
+    const uint32_t mask = (1u << ln) - 1u;
+    j &= mask;
+    const uint32_t q = 1u << (ln - 2);               // a quarter turn
+    const uint32_t quad = j >> (ln - 2);
+    const uint32_t r = j & (q - 1u);
+    const bool refl = r > (q >> 1);                  // past pi/4 inside the quadrant
+    const uint32_t jj = refl ? q - r : r;
+    const TwEntry<T> e = tw_ptr<T>(tw)[jj];
+    T cl = refl ? e.sl : e.cl, ch = refl ? e.sh : e.ch;
+    T sl = refl ? e.cl : e.sl, sh = refl ? e.ch : e.sh;
+    CI<T> w;
+    switch (quad) {
+        case 0: w = {cl, ch, sl, sh}; break;
+        case 1: w = {-sh, -sl, cl, ch}; break;        // (c, s) -> (-s, c)
+        case 2: w = {-ch, -cl, -sh, -sl}; break;
+        default: w = {sl, sh, -ch, -cl}; break;       // (c, s) -> (s, -c)
+    }
+    if (SIGN < 0) w = {w.rl, w.rh, -w.ih, -w.il};
+    return w;
+}
+
+}  // namespace ssm
