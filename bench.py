@@ -1,0 +1,426 @@
+"""Benchmark: verified interval-FFT multiplications on one GB300 (or N replicas).
+
+Workload (default): the paper-scale binary64 interval method, products of
+two 75,000-digit base-256 operands (FFT length 2^18).  One step is one
+ssmul_mul_batched call over a batch of B such products (B - 1 with uniform
+random digits, one with every digit 0xFF, the worst case of coefficient
+size), i.e. one pass of the whole path: interval transforms, pointwise
+products, isolation and the carry scan.  Metric: verified multiplies/s
+(status OK and digits equal to the CPU oracle, checked after timing).
+
+Contract: `python bench.py --gpus N --steps K --warmup W` prints one JSON
+line on rank 0.  Under torchrun every rank runs its own batch (products are
+independent: weak scaling, no collective on the data path); value = all
+products of all ranks / the slowest rank's time.  `--impl reference` times
+the CPU oracle (long multiplication, Section 2.1) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "verified multiplies/s at 75k base-256 digits"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--digits", type=int, default=75000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="time budget of the CPU oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---- workload ---------------------------------------------------------------
+
+def make_batch(rank: int, batch: int, n: int):
+    seed = synth.SEED_BASE + 1 + 1000 * rank
+    dists = ["ff" if i == batch - 1 else "uniform" for i in range(batch)]
+    na = [n] * batch
+    return synth.batch_operands(seed, na, na, dists), dists
+
+
+# ---- algorithmic work model ------------------------------------------------------
+#
+# Directed binary64 operations (add, sub, mul, fma: one each) of every kernel
+# for one product, counted from the structure of the kernels:
+#   radix-4 butterfly: 8 complex interval add/sub (4 ops each) = 32, plus
+#     3 twiddle products (8 ops each) unless p = 0
+#   radix-2 butterfly: 8
+#   twiddle product: 8 (4 directed mul + 4 directed fma)
+#   pair product: 2 complex add/sub (8) + general product (12) = 20
+#   half-length packing: 2 add/sub (8) + twiddle (8) + add (4) = 20
+#   scaling: 4 per complex interval; isolation: 1 per coefficient (width)
+
+def _fft_ops(logL: int, nl: int) -> int:
+    L = 1 << logL
+    ops = 0
+    logn, logs = logL, 0
+    while logn >= 2:
+        s = 1 << logs
+        ops += nl * (L // 4) * 32 + nl * (L // 4 - s) * 24
+        logn -= 2
+        logs += 2
+    if logn == 1:
+        ops += nl * (L // 2) * 8
+    return ops
+
+
+def geometry(log_n: int):
+    log_n2 = min((log_n + 1) // 2, 11)
+    log_n1 = log_n - log_n2
+    c = max(0, 11 - log_n1)
+    return log_n1, log_n2, min(c, log_n2), min(c, log_n2 - 1)
+
+
+def kernel_ops(log_n: int) -> dict:
+    """Directed fp64 ops per product for each four-step kernel (log_n > 12)."""
+    n1l, n2l, c1l, c3l = geometry(log_n)
+    N1, N2 = 1 << n1l, 1 << n2l
+    M2 = N2 // 2
+    fwd = (N2 >> c1l) * _fft_ops(n1l, 1 << c1l) + (N1 - 1) * (N2 - 1) * 8
+    rows = 0
+    for k1 in range(N1 // 2 + 1):
+        nl = 1 if k1 == (N1 - k1) % N1 else 2
+        rows += _fft_ops(n2l, nl) + _fft_ops(n2l - 1, nl)
+        rows += (nl * N2 // 2) * 20 + nl * M2 * 20
+        rows += nl * (M2 - 1) * 8 if k1 else 0
+    inv = (M2 >> c3l) * _fft_ops(n1l, 1 << c3l) + (N1 * M2) * (4 + 2)
+    return {"k_fwd_cols<double>": fwd, "k_rows<double>": rows, "k_inv_cols<double>": inv}
+
+
+def fp64_peak_gops(sm_mhz: float) -> float:
+    """152 SMs x 2 binary64 operations per clock (the nominal 1.25 TFLOP/s
+    counts an fma as 2 flops: 152 * 2 * 2 * 2.07 GHz)."""
+    return 152 * 2 * sm_mhz * 1e6 / 1e9
+
+
+# ---- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- CPU oracle ---------------------------------------------------------------
+
+def cpu_oracle_rate(n: int, budget_s: float, rank: int = 0):
+    """Products/s of the CPU oracle (long multiplication: exact convolution
+    sums of Section 2.1 and the carry of Section 2.4) on the host cores."""
+    from oracle import exact as E
+    E.lib()
+    (a_pool, b_pool, a_off, b_off, _), _ = make_batch(rank, 2, n)
+    a, b = a_pool[:n], b_pool[:n]
+    done, t0 = 0, time.perf_counter()
+    while True:
+        E.product(a, b)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return done / el, done, el, E.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import exact as E
+    E.lib()
+    n = args.digits
+    (a_pool, b_pool, *_), _ = make_batch(0, 2, n)
+    a, b = a_pool[:n], b_pool[:n]
+    for _ in range(args.warmup):
+        E.product(a, b)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        E.product(a, b)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "multiplies/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{n}x{n} base-256 digits, uniform bytes; CPU oracle "
+                               f"long multiplication, one product per step"},
+        "cpu_baseline": {"value": v, "unit": "multiplies/s", "cores": E.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} products of {n}x{n} digits"},
+        "e2e": {"value": v, "unit": "multiplies/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm --------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device; the GPU path has no CPU fallback")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1006_0405_gb300 import abi
+    abi.load()
+    n, B = args.digits, args.batch
+    (a_pool, b_pool, a_off, b_off, z_off), dists = make_batch(rank, B, n)
+    nz = 2 * n
+    stream = torch.cuda.Stream(device=dev)
+    plan = abi.ssmul_plan(n, n, B, abi.SSMUL_PREC_FP64, stream.cuda_stream)
+    descs = (abi.ssmul_desc * B)()
+    for i in range(B):
+        descs[i] = abi.ssmul_desc(int(a_off[i]), int(b_off[i]), int(z_off[i]), n, n)
+    da = torch.from_numpy(a_pool).to(dev)
+    db = torch.from_numpy(b_pool).to(dev)
+    dz = torch.zeros(B * nz, dtype=torch.uint8, device=dev)
+    res_bytes = ctypes.sizeof(abi.ssmul_result) * B
+    dres = torch.zeros(res_bytes, dtype=torch.uint8, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(z_target=None, r_target=None):
+        s = abi.ssmul_mul_batched(plan, descs, da.data_ptr(), db.data_ptr(),
+                                  (z_target if z_target is not None else dz).data_ptr(),
+                                  (r_target if r_target is not None else dres).data_ptr())
+        if s != abi.SSMUL_OK:
+            raise RuntimeError(abi.status_string(s))
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        zs = [torch.empty_like(dz) for _ in range(args.steps)]
+        rs = [torch.empty_like(dres) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        abi.ssmul_debug_kernel_stats(plan, True)        # reset; time kernels from here
+        clocks = ClockSampler(local)
+        clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                                 # L2 flushed between timed steps
+            ev[k][0].record(stream)
+            step(zs[k], rs[k])
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - t_wall
+        clk = clocks.stop()
+        _, kstats = abi.ssmul_debug_kernel_stats(plan, False)
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+
+        # end to end through host buffers: pinned H2D, batched call, D2H of
+        # the digits and the per-product outcomes, every step
+        ha = torch.from_numpy(a_pool).pin_memory()
+        hb = torch.from_numpy(b_pool).pin_memory()
+        hz = torch.empty(B * nz, dtype=torch.uint8).pin_memory()
+        hres = torch.empty(res_bytes, dtype=torch.uint8).pin_memory()
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            da.copy_(ha, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            step()
+            hz.copy_(dz, non_blocking=True)
+            hres.copy_(dres, non_blocking=True)
+            stream.synchronize()
+        e2e_s = (time.perf_counter() - te0) / e2e_steps
+    torch.cuda.synchronize()
+
+    # verification of every timed step against the CPU oracle
+    from oracle import exact as E
+    expect = []
+    for i in range(B):
+        a = a_pool[a_off[i]:a_off[i] + n]
+        b = b_pool[b_off[i]:b_off[i] + n]
+        expect.append(E.carry(E.conv_ntt(a, b), nz))
+    verified = 0
+    widths = []
+    statuses = {}
+    for k in range(args.steps):
+        z = zs[k].cpu().numpy()
+        rr = (abi.ssmul_result * B)()
+        host = rs[k].cpu().numpy()
+        ctypes.memmove(rr, host.ctypes.data, res_bytes)
+        for i in range(B):
+            st = rr[i].status
+            statuses[abi.status_string(st)] = statuses.get(abi.status_string(st), 0) + 1
+            ok = st == abi.SSMUL_OK and np.array_equal(z[z_off[i]:z_off[i] + nz], expect[i])
+            verified += int(ok)
+            if k == 0:
+                widths.append((dists[i], rr[i].max_width))
+    hz_np = hz.numpy()
+    e2e_ok = all(np.array_equal(hz_np[z_off[i]:z_off[i] + nz], expect[i]) for i in range(B))
+
+    t_steps = sum(step_ms) / 1e3
+    local_rate = verified / t_steps
+    per_rank_time = t_steps
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([per_rank_time, float(verified), e2e_s], device=dev, dtype=torch.float64)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_verified = sm[1].item()
+        value = total_verified / mx[0].item()
+        e2e_value = world * B / mx[2].item() if e2e_ok else 0.0
+    else:
+        value = local_rate
+        e2e_value = B / e2e_s if e2e_ok else 0.0
+
+    if rank == 0:
+        # roofline of the dominant kernel: binary64 pipe (an ALU bound)
+        ops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length())
+        dom = max(ops, key=lambda k: kstats.get(k, (0, 0.0))[1])
+        launches, ms = kstats[dom]
+        # one launch covers all B products of the batch
+        achieved = ops[dom] * B / (ms / launches * 1e-3) / 1e9 if launches else 0.0
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        peak = fp64_peak_gops(sm_mhz)
+        total_ms = sum(v[1] for v in kstats.values())
+        shares = {k: round(v[1] / total_ms, 4) for k, v in kstats.items() if v[0]}
+        cpu = None
+        if world == 1:
+            cpu_v, cpu_n, cpu_el, cores = cpu_oracle_rate(n, args.cpu_seconds)
+            cpu = {"value": cpu_v, "unit": "multiplies/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{cpu_n} products of {n}x{n} digits in {cpu_el:.1f} s "
+                             f"(long multiplication + carry)"}
+        gpu_launches = sum(v[0] for v in kstats.values())
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "multiplies/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_steps / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{n}x{n} base-256 digits, binary64 inf-sup intervals, "
+                                   f"FFT length 2^18; batch of {B} per step ({B - 1} uniform "
+                                   f"random, 1 all-0xFF) per GPU",
+                       "batch_per_gpu": B, "digits": n, "precision": "fp64",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "verified": f"{verified}/{args.steps * B} per rank 0",
+            "statuses": statuses,
+            "max_width": {"uniform": max(w for d, w in widths if d == "uniform"),
+                          "all_ff": max((w for d, w in widths if d == "ff"), default=None)},
+            "e2e": {"value": e2e_value, "unit": "multiplies/s",
+                    "h2d_bytes_per_step": int(a_pool.nbytes + b_pool.nbytes + ctypes.sizeof(descs)),
+                    "d2h_bytes_per_step": int(B * nz + res_bytes)},
+            "gpu_launches": int(gpu_launches),
+            "kernel_ms_share": shares,
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "fp64 Gop/s", "frac": achieved / peak, "traffic": None,
+                         "peak_note": "binary64 pipe: 152 SMs x 2 ops/clk at the median "
+                                      "sampled SM clock (recipe unit counts and clocks)"},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    abi.ssmul_plan_destroy(plan)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -48,6 +48,27 @@ ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t plan, const uint8_t* d_a, si
 ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double* d_y,
                                double* d_out, size_t n);
 
+/* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays). */
+enum {
+    SSMUL_K_SMALL_F32 = 0, SSMUL_K_SMALL_F64 = 1,
+    SSMUL_K_FWD_COLS_F32 = 2, SSMUL_K_FWD_COLS_F64 = 3,
+    SSMUL_K_ROWS_F32 = 4, SSMUL_K_ROWS_F64 = 5,
+    SSMUL_K_INV_COLS_F32 = 6, SSMUL_K_INV_COLS_F64 = 7,
+    SSMUL_K_CARRY = 8, SSMUL_K_FINALIZE = 9,
+    SSMUL_KERNEL_KINDS = 10
+};
+
+/*
+ * Per-kind kernel statistics of the plan since the previous call: launch
+ * counts always; device time in milliseconds (CUDA events recorded on the
+ * plan's stream around each launch) while timing is enabled.  The call waits
+ * for the recorded events, copies min(cap, SSMUL_KERNEL_KINDS) entries to
+ * ms and launches (host arrays, either may be NULL), resets the
+ * accumulators and then sets timing on (enable != 0) or off.
+ */
+ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t plan, int enable, double* ms,
+                                      unsigned long long* launches, int cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,13 @@ EXPORTS = (
     "ssmul_plan", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched",
     "ssmul_plan_destroy", "ssmul_status_string",
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op",
+    "ssmul_debug_kernel_stats",
 )
+
+#: kernel kinds of ssmul_debug_kernel_stats, in index order
+KERNEL_KINDS = ("k_small<float>", "k_small<double>", "k_fwd_cols<float>", "k_fwd_cols<double>",
+                "k_rows<float>", "k_rows<double>", "k_inv_cols<float>", "k_inv_cols<double>",
+                "k_carry", "k_finalize")
 
 
 class ssmul_result(ctypes.Structure):
@@ -102,6 +108,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_debug_mul_intervals.restype = st
     L.ssmul_debug_ci_op.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, sz]
     L.ssmul_debug_ci_op.restype = st
+    L.ssmul_debug_kernel_stats.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
+    L.ssmul_debug_kernel_stats.restype = st
     _lib = L
     return L
 
@@ -182,3 +190,12 @@ def ssmul_debug_mul_intervals(plan: int, d_a: int, na: int, d_b: int, nb: int, d
 def ssmul_debug_ci_op(op: int, f32: bool, d_x: int, d_y: int, d_out: int, n: int) -> int:
     return load().ssmul_debug_ci_op(op, int(f32), ctypes.c_void_p(d_x), ctypes.c_void_p(d_y),
                                     ctypes.c_void_p(d_out), n)
+
+
+def ssmul_debug_kernel_stats(plan: int, enable: bool):
+    """Returns (status, {kind: (launches, ms)}) since the previous call."""
+    n = len(KERNEL_KINDS)
+    ms = (ctypes.c_double * n)()
+    la = (ctypes.c_ulonglong * n)()
+    s = load().ssmul_debug_kernel_stats(ctypes.c_void_p(plan), int(enable), ms, la, n)
+    return s, {KERNEL_KINDS[i]: (int(la[i]), float(ms[i])) for i in range(n)}

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "kernels.cuh"
@@ -22,6 +23,9 @@ namespace {
 // the isolation limit is reported by the tests and the benchmark)
 constexpr int FP32_MAX_LOG_N = LOG_SMALL;
 constexpr size_t FP32_MAX_MIN_DIGITS = 24;
+
+// largest batch arena a plan allocates (the batch runs in chunks beyond it)
+constexpr size_t ARENA_CAP = size_t(4) << 30;
 
 struct Geom {
     int log_n;       // transform length N = 2^log_n
@@ -96,10 +100,58 @@ struct ssmul_plan_s {
     ssmul_result* h_res = nullptr;      // pinned
     cudaEvent_t desc_free = nullptr;    // h_desc may be rewritten once this fired
     uint8_t* stage = nullptr;           // device staging for ssmul_mul_host
+    // batch workspace: per-product transform buffers are carved from the
+    // arena; a batch larger than the arena runs in stream-ordered chunks
+    unsigned char* arena = nullptr;
+    size_t arena_bytes = 0;
+    std::vector<int> order;             // host scratch of a batched call
+    // optional per-kernel timing (ssmul_debug_kernel_stats)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    double kt_ms[SSMUL_KERNEL_KINDS] = {};
+    unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
     TwTable tw() const { return TwTable{t64, t32, log_tab}; }
 };
 
 namespace {
+
+cudaEvent_t take_event(ssmul_plan_t p) {
+    if (!p->ev_pool.empty()) {
+        cudaEvent_t e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch bookkeeping around every kernel: a launch count always, and a
+// pair of events on the plan's stream when timing is on.
+struct LaunchScope {
+    ssmul_plan_t p;
+    int kind;
+    cudaEvent_t e0 = nullptr;
+    LaunchScope(ssmul_plan_t p_, int kind_) : p(p_), kind(kind_) {
+        p->kt_launches[kind]++;
+        if (p->timing) {
+            e0 = take_event(p);
+            cudaEventRecord(e0, p->stream);
+        }
+    }
+    ~LaunchScope() {
+        if (e0) {
+            cudaEvent_t e1 = take_event(p);
+            cudaEventRecord(e1, p->stream);
+            p->pending.push_back({kind, {e0, e1}});
+        }
+    }
+};
+
+template <typename T> constexpr int kind_off();
+template <> constexpr int kind_off<float>() { return 0; }
+template <> constexpr int kind_off<double>() { return 1; }
 
 template <typename T>
 ssmul_status set_smem_attrs() {
@@ -118,18 +170,30 @@ template <typename T>
 ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
                           int gate) {
     const TwTable tw = p->tw();
+    const int ko = kind_off<T>();
     if (g.small) {
         const int n = 1 << g.log_n;
+        LaunchScope ls(p, SSMUL_K_SMALL_F32 + ko);
         k_small<T><<<count, threads_for(n), n * sizeof(CI<T>), p->stream>>>(d_desc, tw, gate);
     } else {
         const int n1 = 1 << g.log_n1, n2 = 1 << g.log_n2;
         const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
-        k_fwd_cols<T><<<dim3(n2 >> g.log_c1, count), threads_for(e1), e1 * sizeof(CI<T>),
-                        p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
-        k_rows<T><<<dim3(n1 / 2 + 1, count), threads_for(2 * n2), 2 * n2 * sizeof(CI<T>),
-                    p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
-        k_inv_cols<T><<<dim3((n2 / 2) >> g.log_c3, count), threads_for(e3), e3 * sizeof(CI<T>),
-                        p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c3, gate);
+        {
+            LaunchScope ls(p, SSMUL_K_FWD_COLS_F32 + ko);
+            k_fwd_cols<T><<<dim3(n2 >> g.log_c1, count), threads_for(e1), e1 * sizeof(CI<T>),
+                            p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
+        }
+        {
+            LaunchScope ls(p, SSMUL_K_ROWS_F32 + ko);
+            k_rows<T><<<dim3(n1 / 2 + 1, count), threads_for(2 * n2), 2 * n2 * sizeof(CI<T>),
+                        p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
+        }
+        {
+            LaunchScope ls(p, SSMUL_K_INV_COLS_F32 + ko);
+            k_inv_cols<T><<<dim3((n2 / 2) >> g.log_c3, count), threads_for(e3),
+                            e3 * sizeof(CI<T>), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
+                                                             g.log_c3, gate);
+        }
     }
     return cuda_status(cudaGetLastError());
 }
@@ -154,8 +218,14 @@ ssmul_status enqueue_product(ssmul_plan_t p, const ProdDesc* d_desc, size_t na, 
         if (s != SSMUL_OK) return s;
     }
     const size_t tiles = carry_tiles(na + nb);
-    k_carry<<<dim3(unsigned(tiles), 1), CARRY_THREADS, 0, p->stream>>>(d_desc);
-    k_finalize<<<1, 256, 0, p->stream>>>(d_desc);
+    {
+        LaunchScope ls(p, SSMUL_K_CARRY);
+        k_carry<<<dim3(unsigned(tiles), 1), CARRY_THREADS, 0, p->stream>>>(d_desc);
+    }
+    {
+        LaunchScope ls(p, SSMUL_K_FINALIZE);
+        k_finalize<<<1, 256, 0, p->stream>>>(d_desc);
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -210,6 +280,120 @@ ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uin
     return ssmul_status(p->h_res[0].status);
 }
 
+
+// Bytes of arena one product needs (256-byte aligned pieces): the forward
+// spectrum Z (N intervals; the integer coefficients reuse it once it is
+// consumed) and the half-length inverse W (N/2 intervals) for four-step
+// products, the coefficients alone for single-CTA products.
+size_t arena_need(int log_n) {
+    const size_t n = size_t(1) << log_n;
+    if (log_n <= LOG_SMALL) return (n * sizeof(int64_t) + 255) & ~size_t(255);
+    return ((n * sizeof(CI<double>) + 255) & ~size_t(255)) +
+           (((n / 2) * sizeof(CI<double>) + 255) & ~size_t(255));
+}
+
+// A batch: products sorted by transform length (longest first) and, inside
+// one length, binary32-eligible products first, so that every launch covers
+// a contiguous run of descriptors.  Products are packed into the arena in
+// that order; each full arena is one chunk of launches.
+ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
+                           const uint8_t* d_a_pool, const uint8_t* d_b_pool, uint8_t* d_z_pool,
+                           ssmul_result* d_res) {
+    ssmul_status s = SSMUL_OK;
+    std::vector<int>& order = p->order;
+    order.resize(count);
+    std::vector<int> logn(count);
+    std::vector<char> elig(count);
+    for (size_t i = 0; i < count; ++i) {
+        order[i] = int(i);
+        logn[i] = log_n_for(h_desc[i].na, h_desc[i].nb);
+        elig[i] = p->prec == SSMUL_PREC_FP32 ||
+                  (p->prec == SSMUL_PREC_LADDER && fp32_eligible(h_desc[i].na, h_desc[i].nb, logn[i]));
+    }
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        if (logn[x] != logn[y]) return logn[x] > logn[y];
+        if (elig[x] != elig[y]) return elig[x] > elig[y];
+        return x < y;
+    });
+    SS_TRY(cudaEventSynchronize(p->desc_free));
+    for (size_t k = 0; k < count; ++k) {
+        const int i = order[k];
+        const ssmul_desc& h = h_desc[i];
+        ProdDesc d = single_desc(p, d_a_pool + h.a_off, h.na, d_b_pool + h.b_off, h.nb,
+                                 d_z_pool + h.z_off, k);
+        d.res = d_res + i;
+        p->h_desc[k] = d;
+    }
+    SS_TRY(cudaMemsetAsync(p->st, 0, count * sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->flags, 0, count * p->flags_per_product * sizeof(uint32_t),
+                           p->stream));
+    size_t k0 = 0;
+    while (k0 < count) {
+        // pack a chunk into the arena
+        size_t used = 0, k1 = k0;
+        while (k1 < count) {
+            const int ln = logn[order[k1]];
+            const size_t need = arena_need(ln);
+            if (used + need > p->arena_bytes) break;
+            ProdDesc& d = p->h_desc[k1];
+            unsigned char* base = p->arena + used;
+            if (ln <= LOG_SMALL) {
+                d.Z = nullptr;
+                d.W = nullptr;
+                d.coeff = reinterpret_cast<int64_t*>(base);
+            } else {
+                const size_t zb = ((size_t(1) << ln) * sizeof(CI<double>) + 255) & ~size_t(255);
+                d.Z = base;
+                d.W = base + zb;
+                d.coeff = reinterpret_cast<int64_t*>(base);
+            }
+            used += need;
+            ++k1;
+        }
+        if (k1 == k0) return SSMUL_OUT_OF_MEMORY;
+        SS_TRY(cudaMemcpyAsync(p->d_desc + k0, p->h_desc + k0, (k1 - k0) * sizeof(ProdDesc),
+                               cudaMemcpyHostToDevice, p->stream));
+        // launches, one run of equal transform length at a time
+        size_t g0 = k0;
+        while (g0 < k1) {
+            const int ln = logn[order[g0]];
+            size_t g1 = g0;
+            size_t e1 = g0;
+            size_t max_nz = 0;
+            while (g1 < k1 && logn[order[g1]] == ln) {
+                if (elig[order[g1]]) e1 = g1 + 1;
+                const size_t nz = size_t(h_desc[order[g1]].na) + h_desc[order[g1]].nb;
+                if (nz > max_nz) max_nz = nz;
+                ++g1;
+            }
+            const Geom g = geom_for(ln);
+            if (e1 > g0) {
+                s = enqueue_rung<float>(p, p->d_desc + g0, int(e1 - g0), g, 0);
+                if (s != SSMUL_OK) return s;
+            }
+            if (p->prec != SSMUL_PREC_FP32) {
+                s = enqueue_rung<double>(p, p->d_desc + g0, int(g1 - g0), g, e1 > g0 ? 1 : 0);
+                if (s != SSMUL_OK) return s;
+            }
+            {
+                LaunchScope ls(p, SSMUL_K_CARRY);
+                k_carry<<<dim3(unsigned(carry_tiles(max_nz)), unsigned(g1 - g0)), CARRY_THREADS,
+                          0, p->stream>>>(p->d_desc + g0);
+            }
+            SS_TRY(cudaGetLastError());
+            g0 = g1;
+        }
+        {
+            LaunchScope ls(p, SSMUL_K_FINALIZE);
+            k_finalize<<<unsigned(k1 - k0), 256, 0, p->stream>>>(p->d_desc + k0);
+        }
+        SS_TRY(cudaGetLastError());
+        k0 = k1;
+    }
+    SS_TRY(cudaEventRecord(p->desc_free, p->stream));
+    return SSMUL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -244,9 +428,15 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->d_desc);
     cudaFree(p->d_res);
     cudaFree(p->stage);
+    cudaFree(p->arena);
     cudaFreeHost(p->h_desc);
     cudaFreeHost(p->h_res);
     if (p->desc_free) cudaEventDestroy(p->desc_free);
+    for (auto& pe : p->pending) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
 }
@@ -297,6 +487,15 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (e == cudaSuccess) e = cudaMallocHost(&p->h_desc, slots * sizeof(ProdDesc));
     if (e == cudaSuccess) e = cudaMallocHost(&p->h_res, slots * sizeof(ssmul_result));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->desc_free, cudaEventDisableTiming);
+    if (e == cudaSuccess && max_products) {
+        // room for every product at the largest size, capped at ARENA_CAP
+        // bytes (at least one product of the largest size)
+        const size_t one = arena_need(log_n);
+        size_t want = one * max_products;
+        if (want > ARENA_CAP) want = ARENA_CAP > one ? ARENA_CAP : one;
+        p->arena_bytes = want;
+        e = cudaMalloc(&p->arena, want);
+    }
     if (e != cudaSuccess) return fail(cuda_status(e));
 
     if ((s = set_smem_attrs<double>()) != SSMUL_OK) return fail(s);
@@ -351,28 +550,34 @@ ssmul_status ssmul_mul_batched(ssmul_plan_t p, size_t count, const ssmul_desc* h
     if (count == 0) return SSMUL_OK;
     ssmul_status s = check_device(p);
     if (s != SSMUL_OK) return s;
-    SS_TRY(cudaEventSynchronize(p->desc_free));
-    for (size_t i = 0; i < count; ++i) {
-        const ssmul_desc& h = h_desc[i];
-        ProdDesc d = single_desc(p, d_a_pool + h.a_off, h.na, d_b_pool + h.b_off, h.nb,
-                                 d_z_pool + h.z_off, i);
-        d.res = d_res + i;
-        p->h_desc[i] = d;
-    }
-    SS_TRY(cudaMemsetAsync(p->st, 0, count * sizeof(ProdState), p->stream));
-    SS_TRY(cudaMemsetAsync(p->flags, 0, count * p->flags_per_product * sizeof(uint32_t),
-                           p->stream));
-    SS_TRY(cudaMemcpyAsync(p->d_desc, p->h_desc, count * sizeof(ProdDesc),
-                           cudaMemcpyHostToDevice, p->stream));
-    SS_TRY(cudaEventRecord(p->desc_free, p->stream));
-    for (size_t i = 0; i < count; ++i) {
-        s = enqueue_product(p, p->d_desc + i, h_desc[i].na, h_desc[i].nb, p->prec);
-        if (s != SSMUL_OK) return s;
-    }
-    return SSMUL_OK;
+    return enqueue_batch(p, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res);
 }
 
 // ---- inspection entry points (include/ssmul_debug.h) ----------------------------
+
+ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t p, int enable, double* ms,
+                                      unsigned long long* launches, int cap) {
+    if (!p) return SSMUL_INVALID_ARG;
+    ssmul_status s = check_device(p);
+    if (s != SSMUL_OK) return s;
+    for (auto& pe : p->pending) {
+        SS_TRY(cudaEventSynchronize(pe.second.second));
+        float t = 0.f;
+        SS_TRY(cudaEventElapsedTime(&t, pe.second.first, pe.second.second));
+        p->kt_ms[pe.first] += t;
+        p->ev_pool.push_back(pe.second.first);
+        p->ev_pool.push_back(pe.second.second);
+    }
+    p->pending.clear();
+    for (int k = 0; k < SSMUL_KERNEL_KINDS && k < cap; ++k) {
+        if (ms) ms[k] = p->kt_ms[k];
+        if (launches) launches[k] = p->kt_launches[k];
+        p->kt_ms[k] = 0.0;
+        p->kt_launches[k] = 0;
+    }
+    p->timing = enable != 0;
+    return SSMUL_OK;
+}
 
 ssmul_status ssmul_debug_twiddles(ssmul_plan_t p, int f32, double* h_out, size_t cap,
                                   int* log_ntab) {

@@ -74,7 +74,8 @@ def batched(plan: Plan, pairs):
     s = abi.ssmul_mul_batched(plan.h, descs, da.data_ptr(), db.data_ptr(), dz.data_ptr(),
                               dres.data_ptr())
     torch.cuda.synchronize()
-    ctypes.memmove(res, dres.cpu().numpy().ctypes.data, ctypes.sizeof(res))
+    host = dres.cpu().numpy()
+    ctypes.memmove(res, host.ctypes.data, ctypes.sizeof(res))
     z = dz.cpu().numpy()
     digits = [z[z_off[i]:z_off[i] + nz[i]] for i in range(len(pairs))]
     return s, list(res), digits
