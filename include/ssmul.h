@@ -133,6 +133,32 @@ ssmul_status ssmul_mul_batched(ssmul_plan_t plan, size_t count,
                                const uint8_t* d_a_pool, const uint8_t* d_b_pool,
                                uint8_t* d_z_pool, ssmul_result* d_res);
 
+/*
+ * z = a * b without any device allocation, for callers that cannot call
+ * cudaMalloc: for example a process whose device memory is already fully
+ * reserved by another allocator (a framework's caching pool), or a
+ * latency-bound caller that cannot accept the implicit device
+ * synchronisation an allocation may cause.  The paper has no counterpart;
+ * this is a property of the library, not of the method.
+ *
+ * Products with na + nb <= SSMUL_NOALLOC_MAX_DIGITS run the binary64 path
+ * of ssmul_mul with identical results; larger ones return SSMUL_TOO_LARGE.
+ * All scratch memory (twiddle table, descriptor, accumulators, integer
+ * coefficients, carry words, outcome: about 60 KB) is one static device
+ * array of the library, held on every device that loads it until the
+ * process exits.  The first call on a device sets that array up (finds its
+ * address, builds the twiddle table and waits for it); make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * array, so calls that may overlap on the GPU race and must be serialised
+ * by the caller (for example: one stream).  d_a, d_b, d_z: device memory
+ * of the current device; h_res: host memory, may be NULL; cuda_stream: a
+ * cudaStream_t (NULL: legacy default stream).  The call waits for the
+ * product and returns its status; d_z is zero-filled unless SSMUL_OK.
+ */
+#define SSMUL_NOALLOC_MAX_DIGITS 4097
+ssmul_status ssmul_mul_noalloc(const uint8_t* d_a, size_t na, const uint8_t* d_b, size_t nb,
+                               uint8_t* d_z, ssmul_result* h_res, void* cuda_stream);
+
 /* Release everything the plan owns.  NULL is allowed. */
 void ssmul_plan_destroy(ssmul_plan_t plan);
 

@@ -28,7 +28,7 @@ SSMUL_PREC_LADDER = 2
 
 #: every symbol the headers declare
 EXPORTS = (
-    "ssmul_plan", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched",
+    "ssmul_plan", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
     "ssmul_plan_destroy", "ssmul_status_string",
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op",
     "ssmul_debug_kernel_stats",
@@ -95,6 +95,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_mul.restype = st
     L.ssmul_mul_host.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result)]
     L.ssmul_mul_host.restype = st
+    L.ssmul_mul_noalloc.argtypes = [vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result), vp]
+    L.ssmul_mul_noalloc.restype = st
     L.ssmul_mul_batched.argtypes = [vp, sz, ctypes.POINTER(ssmul_desc), vp, vp, vp, vp]
     L.ssmul_mul_batched.restype = st
     L.ssmul_plan_destroy.argtypes = [vp]
@@ -155,6 +157,14 @@ def ssmul_mul_host(plan: int, h_a: int, na: int, h_b: int, nb: int, h_z: int):
     r = ssmul_result()
     s = load().ssmul_mul_host(ctypes.c_void_p(plan), ctypes.c_void_p(h_a), na,
                               ctypes.c_void_p(h_b), nb, ctypes.c_void_p(h_z), ctypes.byref(r))
+    return s, r
+
+
+def ssmul_mul_noalloc(d_a: int, na: int, d_b: int, nb: int, d_z: int, stream: int | None = None):
+    """The allocation-free product (na + nb <= 4097 digits).  Returns (status, ssmul_result)."""
+    r = ssmul_result()
+    s = load().ssmul_mul_noalloc(ctypes.c_void_p(d_a), na, ctypes.c_void_p(d_b), nb,
+                                 ctypes.c_void_p(d_z), ctypes.byref(r), ctypes.c_void_p(stream or 0))
     return s, r
 
 

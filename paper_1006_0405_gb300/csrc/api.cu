@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "kernels.cuh"
@@ -650,4 +651,122 @@ extern "C" ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, co
     SS_TRY(cudaGetLastError());
     SS_TRY(cudaDeviceSynchronize());
     return SSMUL_OK;
+}
+
+// ---- allocation-free entry point (ssmul_mul_noalloc) -----------------------------
+//
+// Everything the one-CTA binary64 path needs beyond the caller's inputs and
+// outputs lives in one file-scope device array: the twiddle table for
+// N <= 4096, the product descriptor, the per-call accumulators, the integer
+// coefficients, the carry look-back words and the outcome.  Host code must
+// not use the array's name as an address; each device's address comes from
+// cudaGetSymbolAddress in noalloc_setup.
+
+namespace {
+
+constexpr int NOALLOC_LOG_N = LOG_SMALL;                         // N <= 4096
+constexpr size_t NOALLOC_N = size_t(1) << NOALLOC_LOG_N;
+constexpr size_t NOALLOC_TAB = NOALLOC_N / 8 + 1;
+constexpr size_t NOALLOC_TILES = (NOALLOC_N + 1 + CARRY_TILE - 1) / CARRY_TILE;
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t NA_OFF_T64 = 0;
+constexpr size_t NA_OFF_T32 = na_align(NA_OFF_T64 + NOALLOC_TAB * sizeof(TwEntry<double>));
+constexpr size_t NA_OFF_DESC = na_align(NA_OFF_T32 + NOALLOC_TAB * sizeof(TwEntry<float>));
+constexpr size_t NA_OFF_ST = na_align(NA_OFF_DESC + sizeof(ProdDesc));
+constexpr size_t NA_OFF_RES = na_align(NA_OFF_ST + sizeof(ProdState));
+constexpr size_t NA_OFF_FLAGS = na_align(NA_OFF_RES + sizeof(ssmul_result));
+constexpr size_t NA_OFF_COEFF = na_align(NA_OFF_FLAGS + NOALLOC_TILES * sizeof(uint32_t));
+constexpr size_t NOALLOC_BYTES = na_align(NA_OFF_COEFF + NOALLOC_N * sizeof(int64_t));
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_dev_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Writes the descriptor and clears what must start at zero: the
+// accumulators, the look-back words and the outcome.
+__global__ void k_noalloc_init(ProdDesc d, unsigned char* base) {
+    if (threadIdx.x == 0) *reinterpret_cast<ProdDesc*>(base + NA_OFF_DESC) = d;
+    unsigned int* st = reinterpret_cast<unsigned int*>(base + NA_OFF_ST);
+    for (size_t i = threadIdx.x; i < sizeof(ProdState) / sizeof(unsigned int); i += blockDim.x)
+        st[i] = 0u;
+    uint32_t* fl = reinterpret_cast<uint32_t*>(base + NA_OFF_FLAGS);
+    for (size_t i = threadIdx.x; i < NOALLOC_TILES; i += blockDim.x) fl[i] = 0u;
+    unsigned char* res = base + NA_OFF_RES;
+    for (size_t i = threadIdx.x; i < sizeof(ssmul_result); i += blockDim.x) res[i] = 0;
+}
+
+// Once per device, with that device current: find the array's device
+// address, build the twiddle table in it and allow the kernel's shared
+// memory size.  Returns the address, or nullptr with *err set.
+unsigned char* noalloc_setup(int dev, cudaStream_t stream, ssmul_status* err) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_dev_ptr[dev]) return g_noalloc_dev_ptr[dev];
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+        *err = cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+        return nullptr;
+    }
+    unsigned char* base = static_cast<unsigned char*>(ptr);
+    e = cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(NOALLOC_N * sizeof(CI<double>)));
+    if (e == cudaSuccess) {
+        k_twiddle_gen<<<int((NOALLOC_TAB + 255) / 256), 256, 0, stream>>>(
+            reinterpret_cast<TwEntry<double>*>(base + NA_OFF_T64),
+            reinterpret_cast<TwEntry<float>*>(base + NA_OFF_T32), NOALLOC_LOG_N);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        *err = cuda_status(e);
+        return nullptr;
+    }
+    g_noalloc_dev_ptr[dev] = base;
+    return base;
+}
+
+}  // namespace
+
+extern "C" ssmul_status ssmul_mul_noalloc(const uint8_t* d_a, size_t na, const uint8_t* d_b,
+                                          size_t nb, uint8_t* d_z, ssmul_result* h_res,
+                                          void* cuda_stream) {
+    if (!d_a || !d_b || !d_z || na == 0 || nb == 0) return SSMUL_INVALID_ARG;
+    if (na + nb > SSMUL_NOALLOC_MAX_DIGITS) return SSMUL_TOO_LARGE;
+    int dev = -1;
+    SS_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SSMUL_CUDA_ERROR;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    ssmul_status err = SSMUL_OK;
+    unsigned char* base = noalloc_setup(dev, stream, &err);
+    if (!base) return err;
+
+    ProdDesc d{};
+    d.a = d_a;
+    d.b = d_b;
+    d.z = d_z;
+    d.na = uint32_t(na);
+    d.nb = uint32_t(nb);
+    d.log_n = log_n_for(na, nb);
+    d.coeff = reinterpret_cast<int64_t*>(base + NA_OFF_COEFF);
+    d.flags = reinterpret_cast<uint32_t*>(base + NA_OFF_FLAGS);
+    d.st = reinterpret_cast<ProdState*>(base + NA_OFF_ST);
+    d.res = reinterpret_cast<ssmul_result*>(base + NA_OFF_RES);
+    const ProdDesc* slot = reinterpret_cast<const ProdDesc*>(base + NA_OFF_DESC);
+    const TwTable tw{reinterpret_cast<const TwEntry<double>*>(base + NA_OFF_T64),
+                     reinterpret_cast<const TwEntry<float>*>(base + NA_OFF_T32), NOALLOC_LOG_N};
+    const int n = 1 << d.log_n;
+
+    k_noalloc_init<<<1, 64, 0, stream>>>(d, base);
+    k_small<double><<<1, threads_for(n), n * sizeof(CI<double>), stream>>>(slot, tw, 0);
+    k_carry<<<unsigned(carry_tiles(na + nb)), CARRY_THREADS, 0, stream>>>(slot);
+    k_finalize<<<1, 256, 0, stream>>>(slot);
+    SS_TRY(cudaGetLastError());
+    ssmul_result r{};
+    SS_TRY(cudaMemcpyAsync(&r, base + NA_OFF_RES, sizeof(r), cudaMemcpyDeviceToHost, stream));
+    SS_TRY(cudaStreamSynchronize(stream));
+    if (h_res) *h_res = r;
+    return ssmul_status(r.status);
 }
