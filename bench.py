@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--digits", type=int, default=75000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="time budget of the CPU oracle sample")
+    ap.add_argument("--workload", default="paper", choices=["paper", "sweep", "ladder", "uneven"],
+                    help="paper: the headline line; sweep / ladder / uneven: report lines of "
+                         "the size sweep, the precision ladder and the uneven batch")
     return ap.parse_args()
 
 
@@ -418,8 +421,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "paper":
         run_ours(args)
+    else:
+        import bench_reports
+        bench_reports.run(args)
 
 
 if __name__ == "__main__":

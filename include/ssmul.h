@@ -85,7 +85,9 @@ typedef struct ssmul_plan_s* ssmul_plan_t;
  * builds the twiddle enclosures omega_N^j = e^{2 pi i j / N} (the DFT root
  * of Section 2.2) on the device for N up to the largest transform length.
  * max_products bounds the count of one ssmul_mul_batched call (0: batches
- * are not used).  prec selects the precision rule.  cuda_stream is a
+ * are not used); for batches the plan also allocates an arena of transform
+ * workspaces, at most 4 GiB (lowered by the environment variable
+ * SSMUL_ARENA_MB), and a batch that does not fit runs in chunks.  prec selects the precision rule.  cuda_stream is a
  * cudaStream_t (NULL: the legacy default stream) on which all work of the
  * plan is ordered.
  * Errors: SSMUL_INVALID_ARG (null out, zero sizes, unknown precision),
@@ -95,6 +97,30 @@ typedef struct ssmul_plan_s* ssmul_plan_t;
 ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb,
                         size_t max_products, ssmul_precision prec,
                         void* cuda_stream);
+
+/* Plan options (ssmul_plan_set_option). */
+typedef enum {
+    /* value != 0: ssmul_mul_batched captures its launches in a CUDA graph and
+     * replays the graph when the next call describes the same batch (same
+     * descriptors, pools and result array); needs a plan stream other than
+     * the legacy default stream, and is ignored on that stream */
+    SSMUL_OPT_GRAPH = 0,
+    /* value != 0: time every candidate four-step geometry (split N = N1 N2,
+     * column tile size) for each transform length of the plan now, and
+     * keep the fastest; results are cached in the file named by the
+     * environment variable SSMUL_TUNE_CACHE when it is set.  0: defaults */
+    SSMUL_OPT_AUTOTUNE = 1,
+    /* under SSMUL_PREC_LADDER, try binary32 only for products whose shorter
+     * operand has at most `value` digits (and N <= 4096); default 24 */
+    SSMUL_OPT_FP32_MAX_DIGITS = 2
+} ssmul_option;
+
+/*
+ * Set a plan option.  Waits for the plan's queued work first.
+ * Errors: SSMUL_INVALID_ARG (null plan, unknown option, negative value),
+ * SSMUL_OUT_OF_MEMORY / SSMUL_CUDA_ERROR from the autotuner.
+ */
+ssmul_status ssmul_plan_set_option(ssmul_plan_t plan, ssmul_option option, long long value);
 
 /*
  * z = a * b for one product (Sections 2.3-2.5 and the carry of Section 2.4).

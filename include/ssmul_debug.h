@@ -69,6 +69,15 @@ enum {
 ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t plan, int enable, double* ms,
                                       unsigned long long* launches, int cap);
 
+/*
+ * The launch geometry the plan uses for transform length 2^log_n: the
+ * four-step split (log2 N1, log2 N2) and log2 of the elements a column CTA
+ * holds; for single-CTA lengths (N <= 4096) *log_n1 = 0 and the others are
+ * log_n.
+ */
+ssmul_status ssmul_debug_geometry(ssmul_plan_t plan, int log_n, int* log_n1, int* log_n2,
+                                  int* log_cta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,11 +28,16 @@ SSMUL_PREC_LADDER = 2
 
 #: every symbol the headers declare
 EXPORTS = (
-    "ssmul_plan", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
+    "ssmul_plan", "ssmul_plan_set_option", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
     "ssmul_plan_destroy", "ssmul_status_string",
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op",
-    "ssmul_debug_kernel_stats",
+    "ssmul_debug_kernel_stats", "ssmul_debug_geometry",
 )
+
+# ssmul_option
+SSMUL_OPT_GRAPH = 0
+SSMUL_OPT_AUTOTUNE = 1
+SSMUL_OPT_FP32_MAX_DIGITS = 2
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = ("k_small<float>", "k_small<double>", "k_fwd_cols<float>", "k_fwd_cols<double>",
@@ -91,6 +96,10 @@ def load(path: str | None = None, build_if_missing: bool = True):
     vp, sz, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
     L.ssmul_plan.argtypes = [ctypes.POINTER(vp), sz, sz, sz, ctypes.c_int, vp]
     L.ssmul_plan.restype = st
+    L.ssmul_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+    L.ssmul_plan_set_option.restype = st
+    L.ssmul_debug_geometry.argtypes = [vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    L.ssmul_debug_geometry.restype = st
     L.ssmul_mul.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result)]
     L.ssmul_mul.restype = st
     L.ssmul_mul_host.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result)]
@@ -139,6 +148,17 @@ def ssmul_plan(max_na: int, max_nb: int, max_products: int = 0,
     _check(load().ssmul_plan(ctypes.byref(h), max_na, max_nb, max_products, prec,
                              ctypes.c_void_p(stream or 0)), "ssmul_plan")
     return h.value
+
+
+def ssmul_plan_set_option(plan: int, option: int, value: int) -> int:
+    return load().ssmul_plan_set_option(ctypes.c_void_p(plan), option, value)
+
+
+def ssmul_debug_geometry(plan: int, log_n: int):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    s = load().ssmul_debug_geometry(ctypes.c_void_p(plan), log_n, ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c))
+    return s, (a.value, b.value, c.value)
 
 
 def ssmul_plan_destroy(plan: int) -> None:

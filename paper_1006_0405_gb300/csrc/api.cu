@@ -1,14 +1,16 @@
 // api.cu -- the C ABI of include/ssmul.h and include/ssmul_debug.h.
 //
 // Host-side orchestration only: argument checks, plan workspace, launch
-// geometry and the precision ladder.  Every arithmetic step of the method
-// runs in the kernels of kernels.cuh.
+// geometry (default or autotuned), the precision ladder, batching (grouped
+// launches over a workspace arena, optionally captured in a CUDA graph).
+// Every arithmetic step of the method runs in the kernels of kernels.cuh.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "kernels.cuh"
@@ -19,9 +21,9 @@ using namespace ssm;
 namespace {
 
 // the binary32 rung is tried when the product's transform is at most this
-// long and the shorter operand has at most this many digits: beyond them a
-// binary32 containment set cannot isolate base-256 coefficients (measured;
-// the isolation limit is reported by the tests and the benchmark)
+// long and the shorter operand has at most this many digits (a plan
+// option): beyond that a binary32 containment set cannot isolate base-256
+// coefficients
 constexpr int FP32_MAX_LOG_N = LOG_SMALL;
 constexpr size_t FP32_MAX_MIN_DIGITS = 24;
 
@@ -33,6 +35,7 @@ struct Geom {
     bool small;      // whole product in one CTA
     int log_n1, log_n2;
     int log_c1, log_c3;
+    int log_cta;     // log2 of the elements a column CTA holds (at least N1)
 };
 
 int log_n_for(size_t na, size_t nb) {
@@ -42,19 +45,33 @@ int log_n_for(size_t na, size_t nb) {
     return k;
 }
 
-Geom geom_for(int log_n) {
+int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+bool geom_valid(int log_n, int log_n2) {
+    const int log_n1 = log_n - log_n2;
+    return log_n2 >= 2 && log_n2 <= LOG_N2_MAX && log_n1 >= 1 && log_n1 <= LOG_N1_MAX;
+}
+
+// four-step split N = N1 * N2 with column CTAs of 2^log_cta elements
+Geom make_geom(int log_n, int log_n2, int log_cta) {
     Geom g{};
     g.log_n = log_n;
     g.small = log_n <= LOG_SMALL;
     if (!g.small) {
-        g.log_n2 = (log_n + 1) / 2 < LOG_N2_MAX ? (log_n + 1) / 2 : LOG_N2_MAX;
-        g.log_n1 = log_n - g.log_n2;
-        int c = LOG_CTA_ELEMS - g.log_n1;
-        if (c < 0) c = 0;
-        g.log_c1 = c < g.log_n2 ? c : g.log_n2;
-        g.log_c3 = c < g.log_n2 - 1 ? c : g.log_n2 - 1;
+        g.log_n2 = log_n2;
+        g.log_n1 = log_n - log_n2;
+        g.log_cta = log_cta;
+        const int c = log_cta - g.log_n1;
+        g.log_c1 = clampi(c, 0, g.log_n2);
+        g.log_c3 = clampi(c, 0, g.log_n2 - 1);
     }
     return g;
+}
+
+Geom default_geom(int log_n) {
+    int log_n2 = (log_n + 1) / 2;
+    if (log_n2 > LOG_N2_MAX) log_n2 = LOG_N2_MAX;
+    return make_geom(log_n, log_n2, LOG_CTA_ELEMS);
 }
 
 int threads_for(int elems) {          // block_fft: nl * L / 8 threads
@@ -77,6 +94,29 @@ ssmul_status cuda_status(cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_status(e_);        \
     } while (0)
 
+// ---- a prepared batch: launch structure computed on the host -------------------
+
+struct BatchGroup {
+    size_t g0, g1;      // descriptor range of one transform length
+    size_t e1;          // [g0, e1) are binary32-eligible
+    int log_n;
+    size_t max_nz;
+};
+
+struct BatchChunk {
+    size_t k0, k1;      // descriptors packed into the arena together
+    std::vector<BatchGroup> groups;
+};
+
+struct GraphEntry {
+    bool valid = false;
+    std::vector<ssmul_desc> key;
+    const void *a = nullptr, *b = nullptr, *z = nullptr, *res = nullptr;
+    std::vector<ProdDesc> prepared;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches[SSMUL_KERNEL_KINDS] = {};
+};
+
 }  // namespace
 
 struct ssmul_plan_s {
@@ -88,6 +128,8 @@ struct ssmul_plan_s {
     int log_tab = 0;
     TwEntry<double>* t64 = nullptr;
     TwEntry<float>* t32 = nullptr;
+    Geom geom[LOG_N_MAX + 1] = {};
+    size_t fp32_max_min_digits = FP32_MAX_MIN_DIGITS;
     // single-product workspace
     void* Z = nullptr;
     void* W = nullptr;
@@ -106,6 +148,12 @@ struct ssmul_plan_s {
     unsigned char* arena = nullptr;
     size_t arena_bytes = 0;
     std::vector<int> order;             // host scratch of a batched call
+    std::vector<BatchChunk> chunks;
+    // CUDA graph of the last batched call (SSMUL_OPT_GRAPH)
+    bool graph = false;
+    bool capturing = false;
+    GraphEntry cached;
+    unsigned long long cap_launches[SSMUL_KERNEL_KINDS] = {};
     // optional per-kernel timing (ssmul_debug_kernel_stats)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -129,12 +177,17 @@ cudaEvent_t take_event(ssmul_plan_t p) {
 }
 
 // Launch bookkeeping around every kernel: a launch count always, and a
-// pair of events on the plan's stream when timing is on.
+// pair of events on the plan's stream when timing is on (not inside a
+// graph capture, whose launches are counted per replay).
 struct LaunchScope {
     ssmul_plan_t p;
     int kind;
     cudaEvent_t e0 = nullptr;
     LaunchScope(ssmul_plan_t p_, int kind_) : p(p_), kind(kind_) {
+        if (p->capturing) {
+            p->cap_launches[kind]++;
+            return;
+        }
         p->kt_launches[kind]++;
         if (p->timing) {
             e0 = take_event(p);
@@ -199,17 +252,18 @@ ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, con
     return cuda_status(cudaGetLastError());
 }
 
-bool fp32_eligible(size_t na, size_t nb, int log_n) {
+bool fp32_eligible(ssmul_plan_t p, size_t na, size_t nb, int log_n) {
     const size_t mn = na < nb ? na : nb;
-    return log_n <= FP32_MAX_LOG_N && mn <= FP32_MAX_MIN_DIGITS;
+    return log_n <= FP32_MAX_LOG_N && mn <= p->fp32_max_min_digits;
 }
 
 // Enqueue one complete product (rungs, carry, outcome) for d_desc[0].
 ssmul_status enqueue_product(ssmul_plan_t p, const ProdDesc* d_desc, size_t na, size_t nb,
                              ssmul_precision prec) {
-    const Geom g = geom_for(log_n_for(na, nb));
+    const Geom& g = p->geom[log_n_for(na, nb)];
     bool ran32 = false;
-    if (prec == SSMUL_PREC_FP32 || (prec == SSMUL_PREC_LADDER && fp32_eligible(na, nb, g.log_n))) {
+    if (prec == SSMUL_PREC_FP32 ||
+        (prec == SSMUL_PREC_LADDER && fp32_eligible(p, na, nb, g.log_n))) {
         ssmul_status s = enqueue_rung<float>(p, d_desc, 1, g, 0);
         if (s != SSMUL_OK) return s;
         ran32 = true;
@@ -281,7 +335,6 @@ ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uin
     return ssmul_status(p->h_res[0].status);
 }
 
-
 // Bytes of arena one product needs (256-byte aligned pieces): the forward
 // spectrum Z (N intervals; the integer coefficients reuse it once it is
 // consumed) and the half-length inverse W (N/2 intervals) for four-step
@@ -293,14 +346,14 @@ size_t arena_need(int log_n) {
            (((n / 2) * sizeof(CI<double>) + 255) & ~size_t(255));
 }
 
-// A batch: products sorted by transform length (longest first) and, inside
-// one length, binary32-eligible products first, so that every launch covers
-// a contiguous run of descriptors.  Products are packed into the arena in
-// that order; each full arena is one chunk of launches.
-ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
+// Host half of a batch: products sorted by transform length (longest
+// first) and, inside one length, binary32-eligible products first, so that
+// every launch covers a contiguous run of descriptors; descriptors written
+// to the pinned array; products packed into the arena in that order, each
+// full arena one chunk of launches.
+ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
                            const uint8_t* d_a_pool, const uint8_t* d_b_pool, uint8_t* d_z_pool,
                            ssmul_result* d_res) {
-    ssmul_status s = SSMUL_OK;
     std::vector<int>& order = p->order;
     order.resize(count);
     std::vector<int> logn(count);
@@ -309,14 +362,14 @@ ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
         order[i] = int(i);
         logn[i] = log_n_for(h_desc[i].na, h_desc[i].nb);
         elig[i] = p->prec == SSMUL_PREC_FP32 ||
-                  (p->prec == SSMUL_PREC_LADDER && fp32_eligible(h_desc[i].na, h_desc[i].nb, logn[i]));
+                  (p->prec == SSMUL_PREC_LADDER &&
+                   fp32_eligible(p, h_desc[i].na, h_desc[i].nb, logn[i]));
     }
     std::sort(order.begin(), order.end(), [&](int x, int y) {
         if (logn[x] != logn[y]) return logn[x] > logn[y];
         if (elig[x] != elig[y]) return elig[x] > elig[y];
         return x < y;
     });
-    SS_TRY(cudaEventSynchronize(p->desc_free));
     for (size_t k = 0; k < count; ++k) {
         const int i = order[k];
         const ssmul_desc& h = h_desc[i];
@@ -325,12 +378,11 @@ ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
         d.res = d_res + i;
         p->h_desc[k] = d;
     }
-    SS_TRY(cudaMemsetAsync(p->st, 0, count * sizeof(ProdState), p->stream));
-    SS_TRY(cudaMemsetAsync(p->flags, 0, count * p->flags_per_product * sizeof(uint32_t),
-                           p->stream));
+    p->chunks.clear();
     size_t k0 = 0;
     while (k0 < count) {
-        // pack a chunk into the arena
+        BatchChunk c;
+        c.k0 = k0;
         size_t used = 0, k1 = k0;
         while (k1 < count) {
             const int ln = logn[order[k1]];
@@ -341,58 +393,288 @@ ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
             if (ln <= LOG_SMALL) {
                 d.Z = nullptr;
                 d.W = nullptr;
-                d.coeff = reinterpret_cast<int64_t*>(base);
             } else {
                 const size_t zb = ((size_t(1) << ln) * sizeof(CI<double>) + 255) & ~size_t(255);
                 d.Z = base;
                 d.W = base + zb;
-                d.coeff = reinterpret_cast<int64_t*>(base);
             }
+            d.coeff = reinterpret_cast<int64_t*>(base);
             used += need;
             ++k1;
         }
         if (k1 == k0) return SSMUL_OUT_OF_MEMORY;
-        SS_TRY(cudaMemcpyAsync(p->d_desc + k0, p->h_desc + k0, (k1 - k0) * sizeof(ProdDesc),
-                               cudaMemcpyHostToDevice, p->stream));
-        // launches, one run of equal transform length at a time
+        c.k1 = k1;
         size_t g0 = k0;
         while (g0 < k1) {
-            const int ln = logn[order[g0]];
+            BatchGroup g;
+            g.g0 = g0;
+            g.log_n = logn[order[g0]];
+            g.e1 = g0;
+            g.max_nz = 0;
             size_t g1 = g0;
-            size_t e1 = g0;
-            size_t max_nz = 0;
-            while (g1 < k1 && logn[order[g1]] == ln) {
-                if (elig[order[g1]]) e1 = g1 + 1;
+            while (g1 < k1 && logn[order[g1]] == g.log_n) {
+                if (elig[order[g1]]) g.e1 = g1 + 1;
                 const size_t nz = size_t(h_desc[order[g1]].na) + h_desc[order[g1]].nb;
-                if (nz > max_nz) max_nz = nz;
+                if (nz > g.max_nz) g.max_nz = nz;
                 ++g1;
             }
-            const Geom g = geom_for(ln);
-            if (e1 > g0) {
-                s = enqueue_rung<float>(p, p->d_desc + g0, int(e1 - g0), g, 0);
+            g.g1 = g1;
+            c.groups.push_back(g);
+            g0 = g1;
+        }
+        p->chunks.push_back(std::move(c));
+        k0 = k1;
+    }
+    return SSMUL_OK;
+}
+
+// Device half of a batch: every stream operation of the prepared batch.
+ssmul_status issue_batch(ssmul_plan_t p, size_t count) {
+    ssmul_status s = SSMUL_OK;
+    SS_TRY(cudaMemsetAsync(p->st, 0, count * sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->flags, 0, count * p->flags_per_product * sizeof(uint32_t),
+                           p->stream));
+    for (const BatchChunk& c : p->chunks) {
+        SS_TRY(cudaMemcpyAsync(p->d_desc + c.k0, p->h_desc + c.k0,
+                               (c.k1 - c.k0) * sizeof(ProdDesc), cudaMemcpyHostToDevice,
+                               p->stream));
+        for (const BatchGroup& g : c.groups) {
+            const Geom& geo = p->geom[g.log_n];
+            if (g.e1 > g.g0) {
+                s = enqueue_rung<float>(p, p->d_desc + g.g0, int(g.e1 - g.g0), geo, 0);
                 if (s != SSMUL_OK) return s;
             }
             if (p->prec != SSMUL_PREC_FP32) {
-                s = enqueue_rung<double>(p, p->d_desc + g0, int(g1 - g0), g, e1 > g0 ? 1 : 0);
+                s = enqueue_rung<double>(p, p->d_desc + g.g0, int(g.g1 - g.g0), geo,
+                                         g.e1 > g.g0 ? 1 : 0);
                 if (s != SSMUL_OK) return s;
             }
             {
                 LaunchScope ls(p, SSMUL_K_CARRY);
-                k_carry<<<dim3(unsigned(carry_tiles(max_nz)), unsigned(g1 - g0)), CARRY_THREADS,
-                          0, p->stream>>>(p->d_desc + g0);
+                k_carry<<<dim3(unsigned(carry_tiles(g.max_nz)), unsigned(g.g1 - g.g0)),
+                          CARRY_THREADS, 0, p->stream>>>(p->d_desc + g.g0);
             }
             SS_TRY(cudaGetLastError());
-            g0 = g1;
         }
         {
             LaunchScope ls(p, SSMUL_K_FINALIZE);
-            k_finalize<<<unsigned(k1 - k0), 256, 0, p->stream>>>(p->d_desc + k0);
+            k_finalize<<<unsigned(c.k1 - c.k0), 256, 0, p->stream>>>(p->d_desc + c.k0);
         }
         SS_TRY(cudaGetLastError());
-        k0 = k1;
     }
+    return SSMUL_OK;
+}
+
+bool graph_key_matches(const GraphEntry& e, size_t count, const ssmul_desc* h_desc,
+                       const void* a, const void* b, const void* z, const void* res) {
+    return e.valid && e.key.size() == count && e.a == a && e.b == b && e.z == z &&
+           e.res == res && std::memcmp(e.key.data(), h_desc, count * sizeof(ssmul_desc)) == 0;
+}
+
+void graph_drop(GraphEntry& e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    e = GraphEntry();
+}
+
+ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
+                           const uint8_t* d_a_pool, const uint8_t* d_b_pool, uint8_t* d_z_pool,
+                           ssmul_result* d_res) {
+    SS_TRY(cudaEventSynchronize(p->desc_free));
+    // a stream capture needs a stream other than the legacy default stream
+    const bool use_graph = p->graph && p->stream != nullptr;
+    if (use_graph &&
+        graph_key_matches(p->cached, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res)) {
+        std::memcpy(p->h_desc, p->cached.prepared.data(), count * sizeof(ProdDesc));
+        SS_TRY(cudaGraphLaunch(p->cached.exec, p->stream));
+        for (int k = 0; k < SSMUL_KERNEL_KINDS; ++k) p->kt_launches[k] += p->cached.launches[k];
+        SS_TRY(cudaEventRecord(p->desc_free, p->stream));
+        return SSMUL_OK;
+    }
+    ssmul_status s = prepare_batch(p, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res);
+    if (s != SSMUL_OK) return s;
+    if (!use_graph) {
+        s = issue_batch(p, count);
+        if (s != SSMUL_OK) return s;
+        SS_TRY(cudaEventRecord(p->desc_free, p->stream));
+        return SSMUL_OK;
+    }
+    graph_drop(p->cached);
+    std::memset(p->cap_launches, 0, sizeof(p->cap_launches));
+    SS_TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    p->capturing = true;
+    s = issue_batch(p, count);
+    p->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->stream, &graph);
+    if (s != SSMUL_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    SS_TRY(ec);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    SS_TRY(ei);
+    GraphEntry& e = p->cached;
+    e.valid = true;
+    e.key.assign(h_desc, h_desc + count);
+    e.a = d_a_pool;
+    e.b = d_b_pool;
+    e.z = d_z_pool;
+    e.res = d_res;
+    e.prepared.assign(p->h_desc, p->h_desc + count);
+    e.exec = exec;
+    std::memcpy(e.launches, p->cap_launches, sizeof(e.launches));
+    SS_TRY(cudaGraphLaunch(exec, p->stream));
+    for (int k = 0; k < SSMUL_KERNEL_KINDS; ++k) p->kt_launches[k] += e.launches[k];
     SS_TRY(cudaEventRecord(p->desc_free, p->stream));
     return SSMUL_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------
+//
+// For every four-step length of the plan the tuner times the binary64 rung
+// of a synthetic batch (all digits 0xA7, count = clamp(2^23 / N, 1, 64))
+// under every candidate geometry: the split log2 N2 in {h-1, h, h+1}
+// (h = ceil(log2 N / 2), where valid) and column CTAs of 2^9, 2^10 or 2^11
+// elements.  The fastest (minimum of 3 timed runs after one warm-up)
+// becomes the plan's geometry.  Results are cached in the text file named
+// by SSMUL_TUNE_CACHE (device name, log2 N, log2 N2, log2 CTA elements).
+
+std::string device_name(int dev) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    std::string s(prop.name);
+    for (char& c : s)
+        if (c == '\t' || c == '\n') c = ' ';
+    return s;
+}
+
+void tune_cache_read(const std::string& dev, std::vector<Geom>& found) {
+    const char* path = std::getenv("SSMUL_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        char* tab = std::strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        int ln, ln2, cta;
+        if (dev == line && std::sscanf(tab + 1, "%d %d %d", &ln, &ln2, &cta) == 3 &&
+            ln > LOG_SMALL && ln <= LOG_N_MAX && geom_valid(ln, ln2) && cta >= 9 && cta <= 12)
+            found.push_back(make_geom(ln, ln2, cta));
+    }
+    std::fclose(f);
+}
+
+void tune_cache_append(const std::string& dev, const Geom& g) {
+    const char* path = std::getenv("SSMUL_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s\t%d %d %d\n", dev.c_str(), g.log_n, g.log_n2, g.log_cta);
+    std::fclose(f);
+}
+
+ssmul_status autotune(ssmul_plan_t p) {
+    const std::string dev = device_name(p->device);
+    std::vector<Geom> cached;
+    tune_cache_read(dev, cached);
+    for (const Geom& g : cached)
+        if (g.log_n <= p->log_n_max) p->geom[g.log_n] = g;
+    std::vector<int> todo;
+    for (int ln = LOG_SMALL + 1; ln <= p->log_n_max; ++ln) {
+        bool have = false;
+        for (const Geom& g : cached) have = have || g.log_n == ln;
+        if (!have) todo.push_back(ln);
+    }
+    if (todo.empty()) return SSMUL_OK;
+    auto batch_count = [](int ln) { return clampi(int((size_t(1) << 23) >> ln), 1, 64); };
+    size_t ws_bytes = 0;
+    for (int ln : todo) {
+        const size_t b = arena_need(ln) * size_t(batch_count(ln));
+        if (b > ws_bytes) ws_bytes = b;
+    }
+    const size_t n_max = size_t(1) << todo.back();
+    void* ws = nullptr;
+    uint8_t* digits = nullptr;
+    ProdDesc* dd = nullptr;
+    ProdState* ds = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ssmul_status s = SSMUL_OK;
+    auto done = [&](ssmul_status r) {
+        cudaStreamSynchronize(p->stream);
+        cudaFree(ws);
+        cudaFree(digits);
+        cudaFree(dd);
+        cudaFree(ds);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return r;
+    };
+    if (cudaMalloc(&ws, ws_bytes) != cudaSuccess ||
+        cudaMalloc(&digits, n_max / 2 + 1) != cudaSuccess ||
+        cudaMalloc(&dd, 64 * sizeof(ProdDesc)) != cudaSuccess ||
+        cudaMalloc(&ds, 64 * sizeof(ProdState)) != cudaSuccess)
+        return done(SSMUL_OUT_OF_MEMORY);
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return done(SSMUL_CUDA_ERROR);
+    if (cudaMemsetAsync(digits, 0xA7, n_max / 2 + 1, p->stream) != cudaSuccess)
+        return done(SSMUL_CUDA_ERROR);
+    const bool was_timing = p->timing;
+    p->timing = false;
+    for (int ln : todo) {
+        const size_t n = size_t(1) << ln;
+        const int cnt = batch_count(ln);
+        std::vector<ProdDesc> hd(cnt);
+        for (int i = 0; i < cnt; ++i) {
+            ProdDesc d{};
+            d.a = digits;
+            d.b = digits;
+            d.na = d.nb = uint32_t(n / 2);
+            d.log_n = ln;
+            unsigned char* base = static_cast<unsigned char*>(ws) + size_t(i) * arena_need(ln);
+            d.Z = base;
+            d.W = base + (((n * sizeof(CI<double>)) + 255) & ~size_t(255));
+            d.coeff = reinterpret_cast<int64_t*>(base);
+            d.st = ds + i;
+            hd[i] = d;
+        }
+        if (cudaMemcpy(dd, hd.data(), cnt * sizeof(ProdDesc), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return done(SSMUL_CUDA_ERROR);
+        const int h = (ln + 1) / 2;
+        float best = 1e30f;
+        Geom best_g = p->geom[ln];
+        for (int ln2 = h - 1; ln2 <= h + 1; ++ln2) {
+            if (!geom_valid(ln, ln2)) continue;
+            for (int cta = 9; cta <= 11; ++cta) {
+                const Geom g = make_geom(ln, ln2, cta);
+                float t_min = 1e30f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    if (cudaMemsetAsync(ds, 0, cnt * sizeof(ProdState), p->stream) != cudaSuccess)
+                        return done(SSMUL_CUDA_ERROR);
+                    cudaEventRecord(e0, p->stream);
+                    s = enqueue_rung<double>(p, dd, cnt, g, 0);
+                    cudaEventRecord(e1, p->stream);
+                    if (s != SSMUL_OK) return done(s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) return done(SSMUL_CUDA_ERROR);
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0 && t < t_min) t_min = t;
+                }
+                if (t_min < best) {
+                    best = t_min;
+                    best_g = g;
+                }
+            }
+        }
+        p->geom[ln] = best_g;
+        tune_cache_append(dev, best_g);
+    }
+    p->timing = was_timing;
+    return done(SSMUL_OK);
 }
 
 }  // namespace
@@ -419,6 +701,8 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    graph_drop(p->cached);
     cudaFree(p->t64);
     cudaFree(p->t32);
     cudaFree(p->Z);
@@ -469,6 +753,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     p->max_products = max_products;
     p->log_n_max = log_n;
     p->log_tab = log_n < 4 ? 4 : log_n;
+    for (int ln = 0; ln <= LOG_N_MAX; ++ln) p->geom[ln] = default_geom(ln);
 
     const size_t n = size_t(1) << log_n;
     const size_t slots = max_products ? max_products : 1;
@@ -491,9 +776,15 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (e == cudaSuccess && max_products) {
         // room for every product at the largest size, capped at ARENA_CAP
         // bytes (at least one product of the largest size)
+        // (the environment variable SSMUL_ARENA_MB lowers the cap)
+        size_t cap = ARENA_CAP;
+        if (const char* env = std::getenv("SSMUL_ARENA_MB")) {
+            const long long mb = std::atoll(env);
+            if (mb > 0 && size_t(mb) << 20 < cap) cap = size_t(mb) << 20;
+        }
         const size_t one = arena_need(log_n);
         size_t want = one * max_products;
-        if (want > ARENA_CAP) want = ARENA_CAP > one ? ARENA_CAP : one;
+        if (want > cap) want = cap > one ? cap : one;
         p->arena_bytes = want;
         e = cudaMalloc(&p->arena, want);
     }
@@ -510,6 +801,33 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
     *out = p;
     return SSMUL_OK;
+}
+
+ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long long value) {
+    if (!p) return SSMUL_INVALID_ARG;
+    ssmul_status s = check_device(p);
+    if (s != SSMUL_OK) return s;
+    switch (option) {
+        case SSMUL_OPT_GRAPH:
+            SS_TRY(cudaStreamSynchronize(p->stream));
+            p->graph = value != 0;
+            graph_drop(p->cached);
+            return SSMUL_OK;
+        case SSMUL_OPT_AUTOTUNE:
+            SS_TRY(cudaStreamSynchronize(p->stream));
+            graph_drop(p->cached);
+            if (value == 0) {
+                for (int ln = 0; ln <= LOG_N_MAX; ++ln) p->geom[ln] = default_geom(ln);
+                return SSMUL_OK;
+            }
+            return autotune(p);
+        case SSMUL_OPT_FP32_MAX_DIGITS:
+            if (value < 0) return SSMUL_INVALID_ARG;
+            graph_drop(p->cached);
+            p->fp32_max_min_digits = size_t(value);
+            return SSMUL_OK;
+    }
+    return SSMUL_INVALID_ARG;
 }
 
 ssmul_status ssmul_mul(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
@@ -577,6 +895,17 @@ ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t p, int enable, double* ms,
         p->kt_launches[k] = 0;
     }
     p->timing = enable != 0;
+    return SSMUL_OK;
+}
+
+ssmul_status ssmul_debug_geometry(ssmul_plan_t p, int log_n, int* log_n1, int* log_n2,
+                                  int* log_cta) {
+    if (!p || log_n < 2 || log_n > LOG_N_MAX || !log_n1 || !log_n2 || !log_cta)
+        return SSMUL_INVALID_ARG;
+    const Geom& g = p->geom[log_n];
+    *log_n1 = g.small ? 0 : g.log_n1;
+    *log_n2 = g.small ? log_n : g.log_n2;
+    *log_cta = g.small ? log_n : g.log_cta;
     return SSMUL_OK;
 }
 

@@ -1,0 +1,130 @@
+"""Batching (grouped launches, CUDA-graph replay), autotuned geometry and the
+ladder's binary32 router, against the CPU oracle."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import exact as E
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1006_0405_gb300 import abi  # noqa: E402
+from tests.gpu_util import Plan, batched, dev  # noqa: E402
+
+OK = abi.SSMUL_OK
+
+
+def _pairs(seed, count, lo, hi):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        na, nb = (int(v) for v in np.exp(rng.uniform(np.log(lo), np.log(hi), 2)).astype(int))
+        out.append(synth.operand_pair(synth.SEED_BASE + seed * 1000 + i, na, nb,
+                                      "ff" if i % 9 == 0 else "uniform"))
+    return out
+
+
+class StreamPlan(Plan):
+    def __init__(self, max_na, max_nb, max_products, prec):
+        self.stream = torch.cuda.Stream()
+        self.h = abi.ssmul_plan(max_na, max_nb, max_products, prec, self.stream.cuda_stream)
+
+
+def _run_batch_on(plan, pairs, pools=None):
+    na = [len(a) for a, _ in pairs]
+    nb = [len(b) for _, b in pairs]
+    a_off = np.concatenate([[0], np.cumsum(na)[:-1]])
+    b_off = np.concatenate([[0], np.cumsum(nb)[:-1]])
+    nz = np.array(na) + np.array(nb)
+    z_off = np.concatenate([[0], np.cumsum(nz)[:-1]])
+    if pools is None:
+        pools = (dev(np.concatenate([a for a, _ in pairs])), dev(np.concatenate([b for _, b in pairs])),
+                 torch.zeros(int(nz.sum()), dtype=torch.uint8, device="cuda"),
+                 torch.zeros(ctypes.sizeof(abi.ssmul_result) * len(pairs), dtype=torch.uint8,
+                             device="cuda"))
+    da, db, dz, dres = pools
+    descs = [(int(a_off[i]), int(b_off[i]), int(z_off[i]), na[i], nb[i]) for i in range(len(pairs))]
+    dz.fill_(0xA5)
+    s = abi.ssmul_mul_batched(plan.h, descs, da.data_ptr(), db.data_ptr(), dz.data_ptr(),
+                              dres.data_ptr())
+    plan.stream.synchronize()
+    res = (abi.ssmul_result * len(pairs))()
+    host = dres.cpu().numpy()
+    ctypes.memmove(res, host.ctypes.data, ctypes.sizeof(res))
+    z = dz.cpu().numpy()
+    return s, list(res), [z[z_off[i]:z_off[i] + nz[i]] for i in range(len(pairs))], pools
+
+
+def test_graph_replay_and_recapture():
+    pairs = _pairs(1, 60, 8, 30000)
+    mx = max(max(len(a), len(b)) for a, b in pairs)
+    expect = [E.product(a, b) for a, b in pairs]
+    with StreamPlan(mx, mx, 80, abi.SSMUL_PREC_LADDER) as p:
+        with torch.cuda.stream(p.stream):
+            assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_GRAPH, 1) == OK
+            pools = None
+            for rep in range(3):                      # capture, then two replays
+                s, res, z, pools = _run_batch_on(p, pairs, pools)
+                assert s == OK
+                for r, zi, ei in zip(res, z, expect):
+                    assert r.status == OK and np.array_equal(zi, ei)
+            other = _pairs(2, 70, 3, 5000)            # a different batch: recaptured
+            s, res, z, _ = _run_batch_on(p, other)
+            assert s == OK
+            for (a, b), r, zi in zip(other, res, z):
+                assert r.status == OK and np.array_equal(zi, E.product(a, b))
+
+
+def test_autotuned_geometry_is_exact(tmp_path):
+    os.environ["SSMUL_TUNE_CACHE"] = str(tmp_path / "tune.txt")
+    try:
+        n = 40000
+        with Plan(n, n) as p:
+            assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_AUTOTUNE, 1) == OK
+            for ln in range(13, 18):
+                s, (l1, l2, lc) = abi.ssmul_debug_geometry(p.h, ln)
+                assert s == OK and l1 + l2 == ln and 1 <= l1 <= 12 and 2 <= l2 <= 11
+            for na, nb in [(n, n), (5000, 4000), (20000, 3)]:
+                a, b = synth.operand_pair(na + nb, na, nb)
+                s, r, z = p.mul(a, b)
+                assert s == OK and np.array_equal(z, E.product(a, b))
+        lines = open(tmp_path / "tune.txt").read().splitlines()
+        assert len(lines) == 5
+        with Plan(n, n) as p:                          # read back from the cache
+            assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_AUTOTUNE, 1) == OK
+            assert len(open(tmp_path / "tune.txt").read().splitlines()) == 5
+    finally:
+        del os.environ["SSMUL_TUNE_CACHE"]
+
+
+def test_fp32_router_option():
+    a, b = synth.operand_pair(5, 40, 40)
+    with Plan(64, 64, 0, abi.SSMUL_PREC_LADDER) as p:
+        s, r, z = p.mul(a, b)                       # 40 digits: above the default threshold
+        assert s == OK and r.precision_used == abi.SSMUL_PREC_FP64
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_MAX_DIGITS, 64) == OK
+        s, r, z = p.mul(a, b)                       # tried in binary32, escalated
+        assert s == OK and np.array_equal(z, E.product(a, b))
+        assert abi.ssmul_plan_set_option(p.h, 99, 1) == abi.SSMUL_INVALID_ARG
+
+
+def test_batched_chunks_beyond_the_arena():
+    # each product of 2^16 digits needs 6 MiB of spectra; a 16 MiB arena
+    # runs the batch of 6 in three chunks
+    pairs = [synth.operand_pair(900 + i, 1 << 16, (1 << 16) - 3 * i) for i in range(6)]
+    os.environ["SSMUL_ARENA_MB"] = "16"
+    try:
+        with Plan(1 << 16, 1 << 16, 6) as p:
+            s, res, digits = batched(p, pairs)
+    finally:
+        del os.environ["SSMUL_ARENA_MB"]
+    assert s == OK
+    for (a, b), r, z in zip(pairs, res, digits):
+        assert r.status == OK and np.array_equal(z, E.product(a, b))
