@@ -47,27 +47,44 @@ typedef enum {
     SSMUL_TOO_LARGE = 4,        /* sizes beyond the plan's maxima */
     SSMUL_CUDA_ERROR = 5,
     SSMUL_OUT_OF_MEMORY = 6,
-    SSMUL_TIMEOUT = 7           /* a bounded device-side wait gave up */
+    SSMUL_TIMEOUT = 7,          /* a bounded device-side wait gave up */
+    /* SSMUL_PREC_NAIVE64 only: digits of the unverified round-to-nearest
+     * transform, returned without any proof of correctness */
+    SSMUL_UNVERIFIED = 8
 } ssmul_status;
 
 typedef enum {
     SSMUL_PREC_FP64 = 0,        /* binary64 inf-sup intervals only */
     SSMUL_PREC_FP32 = 1,        /* binary32 inf-sup intervals only */
-    SSMUL_PREC_LADDER = 2       /* binary32 first; products that do not
+    SSMUL_PREC_LADDER = 2,      /* binary32 first; products that do not
                                  * isolate are redone in binary64 */
+    /* circular containment sets (the paper's Section 4 proposal): discs with
+     * a binary64 centre and a binary32 radius, every rounding error bounded;
+     * half the binary64 work of SSMUL_PREC_FP64 and no wrapping effect */
+    SSMUL_PREC_DISC64 = 3,
+    /* the naive transform of the paper's Section 3: round-to-nearest
+     * binary64 without enclosures, a speed reference; status
+     * SSMUL_UNVERIFIED */
+    SSMUL_PREC_NAIVE64 = 4,
+    /* binary32 rectangles (small products), then binary64 discs, then
+     * binary64 rectangles for what is still unisolated */
+    SSMUL_PREC_LADDER_DISC = 5
 } ssmul_precision;
 
 /* Per-product outcome. */
 typedef struct {
     int32_t  status;            /* ssmul_status of this product */
-    int32_t  precision_used;    /* ssmul_precision of the deciding rung
-                                 * (SSMUL_PREC_FP64 or SSMUL_PREC_FP32) */
+    int32_t  precision_used;    /* ssmul_precision of the deciding rung:
+                                 * SSMUL_PREC_FP32, _FP64, _DISC64 or
+                                 * _NAIVE64 */
     uint32_t fft_log2;          /* log2 of the transform length N */
     uint32_t n_unisolated;      /* coefficients whose set holds >= 2 integers */
     uint32_t n_empty;           /* coefficients whose set holds no integer */
     uint32_t reserved;
     double   max_width;         /* largest coefficient interval width
-                                 * (rounded up), in units of 1 */
+                                 * (rounded up), in units of 1; for
+                                 * SSMUL_PREC_NAIVE64 the largest distance
+                                 * to the nearest integer */
 } ssmul_result;
 
 /* One product of a batch: digits a_pool[a_off .. a_off+na), b_pool[b_off ..

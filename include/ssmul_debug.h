@@ -27,10 +27,11 @@ ssmul_status ssmul_debug_twiddles(ssmul_plan_t plan, int f32, double* h_out, siz
 
 /*
  * One product as ssmul_mul, forced to a single precision rung (prec is
- * SSMUL_PREC_FP64 or SSMUL_PREC_FP32), that also writes the enclosure of
+ * SSMUL_PREC_FP64, _FP32, _DISC64 or _NAIVE64), that also writes the enclosure of
  * every convolution coefficient c_i = sum_j a_j b_{i-j} (Section 2.1) to
  * d_iv (device memory, 2 * (na + nb - 1) doubles: lo_i, hi_i) after the
- * inverse transform and the division by N (Sections 2.3, 2.5).
+ * inverse transform and the division by N (Sections 2.3, 2.5).  For
+ * _NAIVE64 both values are the unverified point result.
  */
 ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t plan, const uint8_t* d_a, size_t na,
                                        const uint8_t* d_b, size_t nb, uint8_t* d_z,
@@ -48,14 +49,29 @@ ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t plan, const uint8_t* d_a, si
 ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double* d_y,
                                double* d_out, size_t n);
 
-/* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays). */
+/*
+ * Elementwise disc operation on n operands (the circular containment sets
+ * of SSMUL_PREC_DISC64), for unit tests of the device arithmetic.  d_x,
+ * d_y, d_out: device arrays of 3 doubles per operand (centre re, centre im,
+ * radius; the radius is used as a binary32 value).  op: 0 add, 1 subtract,
+ * 2 product by a twiddle disc d_y (|centre| <= 1), 3 general product,
+ * 4 scaling by 2^-k with k = (int) d_y[3 i].
+ */
+ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y, double* d_out,
+                                 size_t n);
+
+/* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays):
+ * one per transform kernel and rung (F32 / F64 rectangles, DISC discs,
+ * NAIVE points), then the carry and the finalisation. */
 enum {
-    SSMUL_K_SMALL_F32 = 0, SSMUL_K_SMALL_F64 = 1,
-    SSMUL_K_FWD_COLS_F32 = 2, SSMUL_K_FWD_COLS_F64 = 3,
-    SSMUL_K_ROWS_F32 = 4, SSMUL_K_ROWS_F64 = 5,
-    SSMUL_K_INV_COLS_F32 = 6, SSMUL_K_INV_COLS_F64 = 7,
-    SSMUL_K_CARRY = 8, SSMUL_K_FINALIZE = 9,
-    SSMUL_KERNEL_KINDS = 10
+    SSMUL_K_SMALL_F32 = 0, SSMUL_K_SMALL_F64 = 1, SSMUL_K_SMALL_DISC = 2, SSMUL_K_SMALL_NAIVE = 3,
+    SSMUL_K_FWD_COLS_F32 = 4, SSMUL_K_FWD_COLS_F64 = 5, SSMUL_K_FWD_COLS_DISC = 6,
+    SSMUL_K_FWD_COLS_NAIVE = 7,
+    SSMUL_K_ROWS_F32 = 8, SSMUL_K_ROWS_F64 = 9, SSMUL_K_ROWS_DISC = 10, SSMUL_K_ROWS_NAIVE = 11,
+    SSMUL_K_INV_COLS_F32 = 12, SSMUL_K_INV_COLS_F64 = 13, SSMUL_K_INV_COLS_DISC = 14,
+    SSMUL_K_INV_COLS_NAIVE = 15,
+    SSMUL_K_CARRY = 16, SSMUL_K_FINALIZE = 17,
+    SSMUL_KERNEL_KINDS = 18
 };
 
 /*

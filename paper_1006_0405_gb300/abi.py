@@ -20,17 +20,21 @@ SSMUL_TOO_LARGE = 4
 SSMUL_CUDA_ERROR = 5
 SSMUL_OUT_OF_MEMORY = 6
 SSMUL_TIMEOUT = 7
+SSMUL_UNVERIFIED = 8
 
 # ssmul_precision
 SSMUL_PREC_FP64 = 0
 SSMUL_PREC_FP32 = 1
 SSMUL_PREC_LADDER = 2
+SSMUL_PREC_DISC64 = 3
+SSMUL_PREC_NAIVE64 = 4
+SSMUL_PREC_LADDER_DISC = 5
 
 #: every symbol the headers declare
 EXPORTS = (
     "ssmul_plan", "ssmul_plan_set_option", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
     "ssmul_plan_destroy", "ssmul_status_string",
-    "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op",
+    "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op", "ssmul_debug_disc_op",
     "ssmul_debug_kernel_stats", "ssmul_debug_geometry",
 )
 
@@ -40,9 +44,8 @@ SSMUL_OPT_AUTOTUNE = 1
 SSMUL_OPT_FP32_MAX_DIGITS = 2
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
-KERNEL_KINDS = ("k_small<float>", "k_small<double>", "k_fwd_cols<float>", "k_fwd_cols<double>",
-                "k_rows<float>", "k_rows<double>", "k_inv_cols<float>", "k_inv_cols<double>",
-                "k_carry", "k_finalize")
+KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")
+                     for r in ("float", "double", "disc", "naive")) + ("k_carry", "k_finalize")
 
 
 class ssmul_result(ctypes.Structure):
@@ -119,6 +122,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_debug_mul_intervals.restype = st
     L.ssmul_debug_ci_op.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, sz]
     L.ssmul_debug_ci_op.restype = st
+    L.ssmul_debug_disc_op.argtypes = [ctypes.c_int, vp, vp, vp, sz]
+    L.ssmul_debug_disc_op.restype = st
     L.ssmul_debug_kernel_stats.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.ssmul_debug_kernel_stats.restype = st
     _lib = L
@@ -215,6 +220,11 @@ def ssmul_debug_mul_intervals(plan: int, d_a: int, na: int, d_b: int, nb: int, d
                                          ctypes.c_void_p(d_b), nb, ctypes.c_void_p(d_z),
                                          ctypes.byref(r), prec, ctypes.c_void_p(d_iv))
     return s, r
+
+
+def ssmul_debug_disc_op(op: int, d_x: int, d_y: int, d_out: int, n: int) -> int:
+    return load().ssmul_debug_disc_op(op, ctypes.c_void_p(d_x), ctypes.c_void_p(d_y),
+                                      ctypes.c_void_p(d_out), n)
 
 
 def ssmul_debug_ci_op(op: int, f32: bool, d_x: int, d_y: int, d_out: int, n: int) -> int:

@@ -128,6 +128,7 @@ struct ssmul_plan_s {
     int log_tab = 0;
     TwEntry<double>* t64 = nullptr;
     TwEntry<float>* t32 = nullptr;
+    DiscTw* td = nullptr;
     Geom geom[LOG_N_MAX + 1] = {};
     size_t fp32_max_min_digits = FP32_MAX_MIN_DIGITS;
     // single-product workspace
@@ -160,7 +161,7 @@ struct ssmul_plan_s {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     double kt_ms[SSMUL_KERNEL_KINDS] = {};
     unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
-    TwTable tw() const { return TwTable{t64, t32, log_tab}; }
+    TwTable tw() const { return TwTable{t64, t32, log_tab, td}; }
 };
 
 namespace {
@@ -203,9 +204,7 @@ struct LaunchScope {
     }
 };
 
-template <typename T> constexpr int kind_off();
-template <> constexpr int kind_off<float>() { return 0; }
-template <> constexpr int kind_off<double>() { return 1; }
+template <typename W> constexpr int kind_off() { return VTraits<typename ValOf<W>::type>::rung; }
 
 template <typename T>
 ssmul_status set_smem_attrs() {
@@ -223,30 +222,31 @@ ssmul_status set_smem_attrs() {
 template <typename T>
 ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
                           int gate) {
+    using V = typename ValOf<T>::type;
     const TwTable tw = p->tw();
     const int ko = kind_off<T>();
     if (g.small) {
         const int n = 1 << g.log_n;
         LaunchScope ls(p, SSMUL_K_SMALL_F32 + ko);
-        k_small<T><<<count, threads_for(n), n * sizeof(CI<T>), p->stream>>>(d_desc, tw, gate);
+        k_small<T><<<count, threads_for(n), n * sizeof(V), p->stream>>>(d_desc, tw, gate);
     } else {
         const int n1 = 1 << g.log_n1, n2 = 1 << g.log_n2;
         const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
         {
             LaunchScope ls(p, SSMUL_K_FWD_COLS_F32 + ko);
-            k_fwd_cols<T><<<dim3(n2 >> g.log_c1, count), threads_for(e1), e1 * sizeof(CI<T>),
+            k_fwd_cols<T><<<dim3(n2 >> g.log_c1, count), threads_for(e1), e1 * sizeof(V),
                             p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
         }
         {
             LaunchScope ls(p, SSMUL_K_ROWS_F32 + ko);
-            k_rows<T><<<dim3(n1 / 2 + 1, count), threads_for(2 * n2), 2 * n2 * sizeof(CI<T>),
+            k_rows<T><<<dim3(n1 / 2 + 1, count), threads_for(2 * n2), 2 * n2 * sizeof(V),
                         p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
         }
         {
             LaunchScope ls(p, SSMUL_K_INV_COLS_F32 + ko);
             k_inv_cols<T><<<dim3((n2 / 2) >> g.log_c3, count), threads_for(e3),
-                            e3 * sizeof(CI<T>), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
-                                                             g.log_c3, gate);
+                            e3 * sizeof(V), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
+                                                         g.log_c3, gate);
         }
     }
     return cuda_status(cudaGetLastError());
@@ -257,21 +257,60 @@ bool fp32_eligible(ssmul_plan_t p, size_t na, size_t nb, int log_n) {
     return log_n <= FP32_MAX_LOG_N && mn <= p->fp32_max_min_digits;
 }
 
+bool uses_fp32(ssmul_precision prec) {
+    return prec == SSMUL_PREC_FP32 || prec == SSMUL_PREC_LADDER || prec == SSMUL_PREC_LADDER_DISC;
+}
+
+ssmul_status enqueue_rung_idx(ssmul_plan_t p, int rung, const ProdDesc* d_desc, int count,
+                              const Geom& g, int gate) {
+    switch (rung) {
+        case 0: return enqueue_rung<float>(p, d_desc, count, g, gate);
+        case 1: return enqueue_rung<double>(p, d_desc, count, g, gate);
+        case 2: return enqueue_rung<Disc>(p, d_desc, count, g, gate);
+        default: return enqueue_rung<Pt>(p, d_desc, count, g, gate);
+    }
+}
+
+// The rungs after the binary32 one, in order, for a precision rule.
+int later_rungs(ssmul_precision prec, int* out) {
+    switch (prec) {
+        case SSMUL_PREC_FP32: return 0;
+        case SSMUL_PREC_DISC64: out[0] = 2; return 1;
+        case SSMUL_PREC_NAIVE64: out[0] = 3; return 1;
+        case SSMUL_PREC_LADDER_DISC: out[0] = 2; out[1] = 1; return 2;
+        default: out[0] = 1; return 1;                 // FP64, LADDER
+    }
+}
+
+// Enqueue the rungs of `count` products of one transform length; the first
+// n32 of them try binary32 first.  Each later rung skips the products an
+// earlier rung decided.
+ssmul_status enqueue_rungs(ssmul_plan_t p, ssmul_precision prec, const ProdDesc* d_desc,
+                           int count, int n32, const Geom& g) {
+    int mask = 0;
+    if (n32 > 0) {
+        ssmul_status s = enqueue_rung_idx(p, 0, d_desc, n32, g, 0);
+        if (s != SSMUL_OK) return s;
+        mask |= 1;
+    }
+    int rungs[4];
+    const int nr = later_rungs(prec, rungs);
+    for (int k = 0; k < nr; ++k) {
+        ssmul_status s = enqueue_rung_idx(p, rungs[k], d_desc, count, g, mask);
+        if (s != SSMUL_OK) return s;
+        mask |= 1 << rungs[k];
+    }
+    return SSMUL_OK;
+}
+
 // Enqueue one complete product (rungs, carry, outcome) for d_desc[0].
 ssmul_status enqueue_product(ssmul_plan_t p, const ProdDesc* d_desc, size_t na, size_t nb,
                              ssmul_precision prec) {
     const Geom& g = p->geom[log_n_for(na, nb)];
-    bool ran32 = false;
-    if (prec == SSMUL_PREC_FP32 ||
-        (prec == SSMUL_PREC_LADDER && fp32_eligible(p, na, nb, g.log_n))) {
-        ssmul_status s = enqueue_rung<float>(p, d_desc, 1, g, 0);
-        if (s != SSMUL_OK) return s;
-        ran32 = true;
-    }
-    if (prec == SSMUL_PREC_FP64 || prec == SSMUL_PREC_LADDER) {
-        ssmul_status s = enqueue_rung<double>(p, d_desc, 1, g, ran32 ? 1 : 0);
-        if (s != SSMUL_OK) return s;
-    }
+    const bool try32 = prec == SSMUL_PREC_FP32 ||
+                       (uses_fp32(prec) && fp32_eligible(p, na, nb, g.log_n));
+    ssmul_status s = enqueue_rungs(p, prec, d_desc, 1, try32 ? 1 : 0, g);
+    if (s != SSMUL_OK) return s;
     const size_t tiles = carry_tiles(na + nb);
     {
         LaunchScope ls(p, SSMUL_K_CARRY);
@@ -362,8 +401,7 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
         order[i] = int(i);
         logn[i] = log_n_for(h_desc[i].na, h_desc[i].nb);
         elig[i] = p->prec == SSMUL_PREC_FP32 ||
-                  (p->prec == SSMUL_PREC_LADDER &&
-                   fp32_eligible(p, h_desc[i].na, h_desc[i].nb, logn[i]));
+                  (uses_fp32(p->prec) && fp32_eligible(p, h_desc[i].na, h_desc[i].nb, logn[i]));
     }
     std::sort(order.begin(), order.end(), [&](int x, int y) {
         if (logn[x] != logn[y]) return logn[x] > logn[y];
@@ -440,15 +478,9 @@ ssmul_status issue_batch(ssmul_plan_t p, size_t count) {
                                p->stream));
         for (const BatchGroup& g : c.groups) {
             const Geom& geo = p->geom[g.log_n];
-            if (g.e1 > g.g0) {
-                s = enqueue_rung<float>(p, p->d_desc + g.g0, int(g.e1 - g.g0), geo, 0);
-                if (s != SSMUL_OK) return s;
-            }
-            if (p->prec != SSMUL_PREC_FP32) {
-                s = enqueue_rung<double>(p, p->d_desc + g.g0, int(g.g1 - g.g0), geo,
-                                         g.e1 > g.g0 ? 1 : 0);
-                if (s != SSMUL_OK) return s;
-            }
+            s = enqueue_rungs(p, p->prec, p->d_desc + g.g0, int(g.g1 - g.g0),
+                              int(g.e1 - g.g0), geo);
+            if (s != SSMUL_OK) return s;
             {
                 LaunchScope ls(p, SSMUL_K_CARRY);
                 k_carry<<<dim3(unsigned(carry_tiles(g.max_nz)), unsigned(g.g1 - g.g0)),
@@ -691,6 +723,7 @@ const char* ssmul_status_string(ssmul_status s) {
         case SSMUL_CUDA_ERROR: return "SSMUL_CUDA_ERROR";
         case SSMUL_OUT_OF_MEMORY: return "SSMUL_OUT_OF_MEMORY";
         case SSMUL_TIMEOUT: return "SSMUL_TIMEOUT";
+        case SSMUL_UNVERIFIED: return "SSMUL_UNVERIFIED";
     }
     return "SSMUL_UNKNOWN_STATUS";
 }
@@ -705,6 +738,7 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     graph_drop(p->cached);
     cudaFree(p->t64);
     cudaFree(p->t32);
+    cudaFree(p->td);
     cudaFree(p->Z);
     cudaFree(p->W);
     cudaFree(p->coeff);
@@ -731,7 +765,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (!out) return SSMUL_INVALID_ARG;
     *out = nullptr;
     if (max_na == 0 || max_nb == 0) return SSMUL_INVALID_ARG;
-    if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32 && prec != SSMUL_PREC_LADDER)
+    if (int(prec) < SSMUL_PREC_FP64 || int(prec) > SSMUL_PREC_LADDER_DISC)
         return SSMUL_INVALID_ARG;
     if (max_na > (size_t(1) << LOG_N_MAX) || max_nb > (size_t(1) << LOG_N_MAX))
         return SSMUL_TOO_LARGE;
@@ -762,6 +796,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&p->t64, tab * sizeof(TwEntry<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->t32, tab * sizeof(TwEntry<float>));
+    if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscTw));
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->coeff, n * sizeof(int64_t));
@@ -792,10 +827,13 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
 
     if ((s = set_smem_attrs<double>()) != SSMUL_OK) return fail(s);
     if ((s = set_smem_attrs<float>()) != SSMUL_OK) return fail(s);
+    if ((s = set_smem_attrs<Disc>()) != SSMUL_OK) return fail(s);
+    if ((s = set_smem_attrs<Pt>()) != SSMUL_OK) return fail(s);
 
     const int threads = 256;
     const int blocks = int((tab + threads - 1) / threads);
     k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->t32, p->log_tab);
+    k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->log_tab);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaEventRecord(p->desc_free, p->stream)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
@@ -849,7 +887,7 @@ ssmul_status ssmul_mul_host(ssmul_plan_t p, const uint8_t* h_a, size_t na, const
     SS_TRY(cudaMemcpyAsync(db, h_b, nb, cudaMemcpyHostToDevice, p->stream));
     s = run_single(p, da, na, db, nb, dz, h_res, p->prec, nullptr);
     if (s != SSMUL_OK && s != SSMUL_ISOLATION_FAILED && s != SSMUL_CONTAINMENT_FAILED &&
-        s != SSMUL_TIMEOUT)
+        s != SSMUL_TIMEOUT && s != SSMUL_UNVERIFIED)
         return s;
     SS_TRY(cudaMemcpyAsync(h_z, dz, na + nb, cudaMemcpyDeviceToHost, p->stream));
     SS_TRY(cudaStreamSynchronize(p->stream));
@@ -937,7 +975,9 @@ ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t p, const uint8_t* d_a, size_
                                        ssmul_result* h_res, ssmul_precision prec,
                                        double* d_iv) {
     if (!p || !d_iv) return SSMUL_INVALID_ARG;
-    if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32) return SSMUL_INVALID_ARG;
+    if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32 && prec != SSMUL_PREC_DISC64 &&
+        prec != SSMUL_PREC_NAIVE64)
+        return SSMUL_INVALID_ARG;
     return run_single(p, d_a, na, d_b, nb, d_z, h_res, prec, d_iv);
 }
 
@@ -965,7 +1005,38 @@ __global__ void k_ci_op(int op, const double* x, const double* y, double* out, s
     }
 }
 
+__global__ void k_disc_op(int op, const double* x, const double* y, double* out, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        const Disc a{x[3 * i], x[3 * i + 1], float(x[3 * i + 2]), 0.f};
+        const Disc b{y[3 * i], y[3 * i + 1], float(y[3 * i + 2]), 0.f};
+        Disc r;
+        switch (op) {
+            case 0: r = a + b; break;
+            case 1: r = a - b; break;
+            case 2: r = mul_tw(a, DiscTw{b.x, b.y, b.r, 0.f}); break;
+            case 3: r = mul_ci(a, b); break;
+            default: r = scale_pow2(a, int(y[3 * i])); break;
+        }
+        out[3 * i] = r.x;
+        out[3 * i + 1] = r.y;
+        out[3 * i + 2] = r.r;
+    }
+}
+
 }  // namespace
+
+extern "C" ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y,
+                                            double* d_out, size_t n) {
+    if (op < 0 || op > 4 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
+    if (n == 0) return SSMUL_OK;
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);
+    k_disc_op<<<blocks, threads>>>(op, d_x, d_y, d_out, n);
+    SS_TRY(cudaGetLastError());
+    SS_TRY(cudaDeviceSynchronize());
+    return SSMUL_OK;
+}
 
 extern "C" ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double* d_y,
                                           double* d_out, size_t n) {

@@ -14,27 +14,29 @@
 // products where two radix-2 steps need four, which also means fewer
 // rectangular wrapping effects (Section 2.5) per element.
 //
+// The element type V is any of value.cuh's (inf-sup rectangles, discs or
+// points); twiddles come from get_twiddle<V>.
+//
 // Each step reads all its inputs into registers, synchronises the block,
 // then writes all its outputs in place: the block must hold every
 // butterfly of a step at once, i.e. nl * L / 4 <= 2 * blockDim.x.
 #pragma once
-#include "interval.cuh"
-#include "twiddle.cuh"
+#include "value.cuh"
 
 namespace ssm {
 
-template <typename T, int SIGN>
-__device__ __forceinline__ void bfly4(CI<T>& a, CI<T>& b, CI<T>& c, CI<T>& d) {
-    const CI<T> apc = a + c, amc = a - c, bpd = b + d, bmd = b - d;
-    const CI<T> jb = (SIGN > 0) ? mul_i(bmd) : mul_negi(bmd);
+template <typename V, int SIGN>
+__device__ __forceinline__ void bfly4(V& a, V& b, V& c, V& d) {
+    const V apc = a + c, amc = a - c, bpd = b + d, bmd = b - d;
+    const V jb = (SIGN > 0) ? mul_i(bmd) : mul_negi(bmd);
     a = apc + bpd;   // u = 0
     c = apc - bpd;   // u = 2
     b = amc + jb;    // u = 1
     d = amc - jb;    // u = 3
 }
 
-template <typename T, int SIGN>
-__device__ void block_fft(CI<T>* buf, int logL, int nl, int pitch, const TwTable& tw) {
+template <typename V, int SIGN>
+__device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw) {
     const int L = 1 << logL;
     const int quarter_log = logL - 2;
     int logn = logL, logs = 0;
@@ -42,7 +44,7 @@ __device__ void block_fft(CI<T>* buf, int logL, int nl, int pitch, const TwTable
         const int m = 1 << (logn - 2);          // n / 4
         const int s = 1 << logs;
         const int nbf = nl << (logL - 2);       // butterflies in this step
-        CI<T> v[2][4];
+        V v[2][4];
         int base[2], pp[2];
         bool act[2];
 #pragma unroll
@@ -53,16 +55,16 @@ __device__ void block_fft(CI<T>* buf, int logL, int nl, int pitch, const TwTable
                 const int line = b >> quarter_log;
                 const int bb = b & ((L >> 2) - 1);
                 const int p = bb >> logs, q = bb & (s - 1);
-                CI<T>* x = buf + line * pitch;
+                V* x = buf + line * pitch;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) v[h][t] = x[q + s * (p + t * m)];
-                bfly4<T, SIGN>(v[h][0], v[h][1], v[h][2], v[h][3]);
+                bfly4<V, SIGN>(v[h][0], v[h][1], v[h][2], v[h][3]);
                 if (p != 0) {
                     // omega_n^{p u} = omega_Ntab^{p u Ntab / n}
                     const int sh = tw.log_n - logn;
-                    v[h][1] = mul_tw(v[h][1], twiddle<T, SIGN>(tw, uint32_t(p) << sh));
-                    v[h][2] = mul_tw(v[h][2], twiddle<T, SIGN>(tw, uint32_t(2 * p) << sh));
-                    v[h][3] = mul_tw(v[h][3], twiddle<T, SIGN>(tw, uint32_t(3 * p) << sh));
+                    v[h][1] = mul_tw(v[h][1], get_twiddle<V, SIGN>(tw, uint32_t(p) << sh));
+                    v[h][2] = mul_tw(v[h][2], get_twiddle<V, SIGN>(tw, uint32_t(2 * p) << sh));
+                    v[h][3] = mul_tw(v[h][3], get_twiddle<V, SIGN>(tw, uint32_t(3 * p) << sh));
                 }
                 base[h] = line * pitch + q + s * 4 * p;
                 pp[h] = s;
@@ -86,8 +88,8 @@ __device__ void block_fft(CI<T>* buf, int logL, int nl, int pitch, const TwTable
         const int nbf = nl * half;
         for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
             const int line = b / half, q = b - line * half;
-            CI<T>* x = buf + line * pitch;
-            const CI<T> a = x[q], c = x[q + half];
+            V* x = buf + line * pitch;
+            const V a = x[q], c = x[q + half];
             x[q] = a + c;
             x[q + half] = a - c;
         }

@@ -30,8 +30,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "../../include/ssmul.h"
-#include "interval.cuh"
-#include "twiddle.cuh"
+#include "value.cuh"
 #include "fft.cuh"
 
 namespace ssm {
@@ -46,15 +45,16 @@ constexpr int CARRY_THREADS = 256;
 constexpr int CARRY_PER_THREAD = CARRY_TILE / CARRY_THREADS;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;   // bounded look-back polls
 
-// Per-product accumulators of one call, zeroed before the call.
-// Index 0: binary32 rung, index 1: binary64 rung.
+// Per-product accumulators of one call, zeroed before the call; one entry
+// per rung (value.cuh: 0 binary32 rectangles, 1 binary64 rectangles,
+// 2 binary64 discs, 3 unverified points).
 struct ProdState {
-    unsigned int ran[2];
-    unsigned int unisolated[2];
-    unsigned int empty[2];
+    unsigned int ran[RUNGS];
+    unsigned int unisolated[RUNGS];
+    unsigned int empty[RUNGS];
     unsigned int timeout;
     unsigned int carry_ticket;
-    unsigned long long maxw[2];        // bit pattern of a nonnegative double
+    unsigned long long maxw[RUNGS];    // bit pattern of a nonnegative double
 };
 
 struct ProdDesc {
@@ -75,14 +75,20 @@ struct ProdDesc {
 
 // ---- the rung gate of the precision ladder ------------------------------------
 
-// true when the binary32 rung already decided this product
-__device__ __forceinline__ bool fp32_decided(const ProdState* st) {
-    return st->ran[0] && (st->unisolated[0] == 0 || st->empty[0] != 0);
+// true when a rung in `mask` (bit r: rung r) already decided this product:
+// it ran and either isolated every coefficient or found an empty set
+__device__ __forceinline__ bool decided_by(const ProdState* st, int mask) {
+    for (int r = 0; r < RUNGS; ++r)
+        if (((mask >> r) & 1) && st->ran[r] && (st->unisolated[r] == 0 || st->empty[r] != 0))
+            return true;
+    return false;
 }
 
-template <typename T> struct Rung;
-template <> struct Rung<float> { static constexpr int idx = 0; };
-template <> struct Rung<double> { static constexpr int idx = 1; };
+// kernel template argument -> value type: float and double name the inf-sup
+// rectangles, Disc and Pt themselves
+template <typename W> struct ValOf { using type = W; };
+template <> struct ValOf<float> { using type = CI<float>; };
+template <> struct ValOf<double> { using type = CI<double>; };
 
 // ---- shared-memory stages common to k_small and k_rows -----------------------
 
@@ -91,35 +97,35 @@ template <> struct Rung<double> { static constexpr int idx = 1; };
 // row (N1 - r) mod N1, column (N2 - k2) mod N2 for r = 0 and N2 - 1 - k2
 // otherwise.  With two lines the rows are partners of each other; with
 // one line the row is its own partner.
-template <typename T>
-__device__ void pair_products(CI<T>* sm, int nl, int row0, int logN2) {
+template <typename V>
+__device__ void pair_products(V* sm, int nl, int row0, int logN2) {
     const int N2 = 1 << logN2;
     for (int k2 = threadIdx.x; k2 < N2; k2 += blockDim.x) {
         const int pc = (row0 == 0) ? ((N2 - k2) & (N2 - 1)) : (N2 - 1 - k2);
         if (nl == 1 && k2 > pc) continue;
         const int pi = (nl == 2 ? N2 : 0) + pc;
-        const CI<T> zk = sm[k2];
-        const CI<T> czp = conj(sm[pi]);
-        const CI<T> a2 = zk + czp;                 // 2 A_k
-        const CI<T> b2 = mul_negi(zk - czp);       // 2 B_k
-        const CI<T> c4 = mul_ci(a2, b2);           // 4 C_k
+        const V zk = sm[k2];
+        const V czp = conj(sm[pi]);
+        const V a2 = zk + czp;                     // 2 A_k
+        const V b2 = mul_negi(zk - czp);           // 2 B_k
+        const V c4 = mul_ci(a2, b2);               // 4 C_k
         sm[k2] = c4;
         if (pi != k2) sm[pi] = conj(c4);           // 4 C_{N-k}
     }
 }
 
 // D_k for k2 < N2/2 of each line, written over the first half of the line.
-template <typename T>
-__device__ void pack_half(CI<T>* sm, int nl, const int* rows, int logN1, int logN2,
+template <typename V>
+__device__ void pack_half(V* sm, int nl, const int* rows, int logN1, int logN2,
                           const TwTable& tw) {
     const int N2 = 1 << logN2, M2 = N2 >> 1;
     const int logN = logN1 + logN2;
     for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
         const int l = t >> (logN2 - 1), k2 = t & (M2 - 1);
-        CI<T>* x = sm + l * N2;
-        const CI<T> c0 = x[k2], c1 = x[k2 + M2];
+        V* x = sm + l * N2;
+        const V c0 = x[k2], c1 = x[k2 + M2];
         const uint32_t k = uint32_t(rows[l]) + (uint32_t(k2) << logN1);
-        const CI<T> w = twiddle<T, -1>(tw, k << (tw.log_n - logN));
+        const auto w = get_twiddle<V, -1>(tw, k << (tw.log_n - logN));
         x[k2] = (c0 + c1) + mul_i(mul_tw(c0 - c1, w));
     }
 }
@@ -172,153 +178,206 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
     }
 }
 
+// Both coefficients carried by one complex value: c_{2j} (real part) and
+// c_{2j+1} (imaginary part).
+template <typename T>
+__device__ __forceinline__ void isolate_value(const CI<T>& v, int64_t j, int64_t L,
+                                              int64_t* coeff, IsoAcc& acc, double* iv) {
+    isolate_one(v.rl, v.rh, 2 * j, L, coeff, acc, iv);
+    isolate_one(v.il, v.ih, 2 * j + 1, L, coeff, acc, iv);
+}
+
+__device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, int64_t L,
+                                              int64_t* coeff, IsoAcc& acc, double* iv) {
+    const double r = double(v.r);
+    isolate_one(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, L, coeff, acc, iv);
+    isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, L, coeff, acc, iv);
+}
+
+// the naive transform rounds to the nearest integer without any proof; its
+// "width" statistic is the largest distance to that integer
+__device__ __forceinline__ void naive_one(double v, int64_t idx, int64_t L, int64_t* coeff,
+                                          IsoAcc& acc, double* iv) {
+    const double k = rint(v);
+    const double dist = fabs(v - k);
+    acc.maxw = (dist > acc.maxw || dist != dist) ? dist : acc.maxw;
+    if (iv != nullptr && idx < L) {
+        iv[2 * idx] = v;
+        iv[2 * idx + 1] = v;
+    }
+    if (idx < L) {
+        if (k == k && k >= 0.0) coeff[idx] = int64_t(k);
+        else { coeff[idx] = 0; acc.empty++; }
+    }
+}
+
+__device__ __forceinline__ void isolate_value(const Pt& v, int64_t j, int64_t L, int64_t* coeff,
+                                              IsoAcc& acc, double* iv) {
+    naive_one(v.x, 2 * j, L, coeff, acc, iv);
+    naive_one(v.y, 2 * j + 1, L, coeff, acc, iv);
+}
+
 // ---- k_small: the whole interval convolution of one product in one CTA -----
 
-template <typename T>
+// gate: bit mask of rungs whose decision makes this rung skip the product
+template <typename Tag>
 __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
+    using V = typename ValOf<Tag>::type;
+    constexpr int RUNG = VTraits<V>::rung;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    V* sm = reinterpret_cast<V*>(smem_raw);
     const ProdDesc d = descs[blockIdx.x];
-    if (gate && fp32_decided(d.st)) return;
+    if (gate && decided_by(d.st, gate)) return;
     const int logN = d.log_n, N = 1 << logN;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const T re = j < int(d.na) ? T(d.a[j]) : T(0);
-        const T im = j < int(d.nb) ? T(d.b[j]) : T(0);
-        sm[j] = {re, re, im, im};
+        const int re = j < int(d.na) ? int(d.a[j]) : 0;
+        const int im = j < int(d.nb) ? int(d.b[j]) : 0;
+        sm[j] = make_point<V>(re, im);
     }
     __syncthreads();
-    block_fft<T, +1>(sm, logN, 1, N, tw);
+    block_fft<V, +1>(sm, logN, 1, N, tw);
     pair_products(sm, 1, 0, logN);
     __syncthreads();
     const int rows[2] = {0, 0};
     pack_half(sm, 1, rows, 0, logN, tw);
     __syncthreads();
-    block_fft<T, -1>(sm, logN - 1, 1, N, tw);
-    const T scale = T(ldexp(1.0, -(logN + 2)));
+    block_fft<V, -1>(sm, logN - 1, 1, N, tw);
     const int64_t L = int64_t(d.na) + d.nb - 1;
     IsoAcc acc;
-    for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) {
-        const CI<T> v = scale_out(sm[j], scale);
-        isolate_one(v.rl, v.rh, 2 * int64_t(j), L, d.coeff, acc, d.iv);
-        isolate_one(v.il, v.ih, 2 * int64_t(j) + 1, L, d.coeff, acc, d.iv);
-    }
-    flush_acc(acc, d.st, Rung<T>::idx);
-    if (threadIdx.x == 0) atomicOr(&d.st->ran[Rung<T>::idx], 1u);
+    for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x)
+        isolate_value(scale_pow2(sm[j], logN + 2), j, L, d.coeff, acc, d.iv);
+    flush_acc(acc, d.st, RUNG);
+    if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
 }
 
 // ---- four-step kernels --------------------------------------------------------
 
-template <typename T>
+template <typename Tag>
 __global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
+    using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    V* sm = reinterpret_cast<V*>(smem_raw);
     const ProdDesc d = descs[blockIdx.y];
-    if (gate && fp32_decided(d.st)) return;
+    if (gate && decided_by(d.st, gate)) return;
     const int N1 = 1 << logN1, C = 1 << logC;
     const uint32_t j2_0 = blockIdx.x << logC;
-    CI<T>* Z = reinterpret_cast<CI<T>*>(d.Z);
+    V* Z = reinterpret_cast<V*>(d.Z);
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
         const int c = idx & (C - 1), j1 = idx >> logC;
         const uint32_t j = (uint32_t(j1) << logN2) + j2_0 + c;
-        const T re = j < d.na ? T(d.a[j]) : T(0);
-        const T im = j < d.nb ? T(d.b[j]) : T(0);
-        sm[(c << logN1) + j1] = {re, re, im, im};
+        const int re = j < d.na ? int(d.a[j]) : 0;
+        const int im = j < d.nb ? int(d.b[j]) : 0;
+        sm[(c << logN1) + j1] = make_point<V>(re, im);
     }
     __syncthreads();
-    block_fft<T, +1>(sm, logN1, C, N1, tw);
+    block_fft<V, +1>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
         const int c = idx & (C - 1), k1 = idx >> logC;
         const uint32_t j2 = j2_0 + c;
-        CI<T> v = sm[(c << logN1) + k1];
+        V v = sm[(c << logN1) + k1];
         const uint32_t e = j2 * uint32_t(k1);             // < N
-        if (e) v = mul_tw(v, twiddle<T, +1>(tw, e << (tw.log_n - logN)));
+        if (e) v = mul_tw(v, get_twiddle<V, +1>(tw, e << (tw.log_n - logN)));
         Z[(size_t(k1) << logN2) + j2] = v;
     }
 }
 
-template <typename T>
+template <typename Tag>
 __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
+    using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    V* sm = reinterpret_cast<V*>(smem_raw);
     const ProdDesc d = descs[blockIdx.y];
-    if (gate && fp32_decided(d.st)) return;
+    if (gate && decided_by(d.st, gate)) return;
     const int N1 = 1 << logN1, N2 = 1 << logN2, M2 = N2 >> 1;
     const int k1 = blockIdx.x;                              // 0 .. N1/2
     const int k1b = (N1 - k1) & (N1 - 1);
     const int nl = (k1 == k1b) ? 1 : 2;
     const int rows[2] = {k1, k1b};
-    const CI<T>* Z = reinterpret_cast<const CI<T>*>(d.Z);
-    CI<T>* W = reinterpret_cast<CI<T>*>(d.W);
+    const V* Z = reinterpret_cast<const V*>(d.Z);
+    V* W = reinterpret_cast<V*>(d.W);
     for (int t = threadIdx.x; t < nl * N2; t += blockDim.x) {
         const int l = t >> logN2, k2 = t & (N2 - 1);
         sm[t] = Z[(size_t(rows[l]) << logN2) + k2];
     }
     __syncthreads();
-    block_fft<T, +1>(sm, logN2, nl, N2, tw);
+    block_fft<V, +1>(sm, logN2, nl, N2, tw);
     pair_products(sm, nl, k1, logN2);
     __syncthreads();
     pack_half(sm, nl, rows, logN1, logN2, tw);
     __syncthreads();
-    block_fft<T, -1>(sm, logN2 - 1, nl, N2, tw);
+    block_fft<V, -1>(sm, logN2 - 1, nl, N2, tw);
     const int logM = logN1 + logN2 - 1;
     for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
         const int l = t >> (logN2 - 1), j2 = t & (M2 - 1);
-        CI<T> v = sm[l * N2 + j2];
+        V v = sm[l * N2 + j2];
         const uint32_t e = uint32_t(rows[l]) * uint32_t(j2);    // < N/2
-        if (e) v = mul_tw(v, twiddle<T, -1>(tw, e << (tw.log_n - logM)));
+        if (e) v = mul_tw(v, get_twiddle<V, -1>(tw, e << (tw.log_n - logM)));
         W[(size_t(rows[l]) << (logN2 - 1)) + j2] = v;
     }
 }
 
-template <typename T>
+template <typename Tag>
 __global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
+    using V = typename ValOf<Tag>::type;
+    constexpr int RUNG = VTraits<V>::rung;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CI<T>* sm = reinterpret_cast<CI<T>*>(smem_raw);
+    V* sm = reinterpret_cast<V*>(smem_raw);
     const ProdDesc d = descs[blockIdx.y];
-    if (gate && fp32_decided(d.st)) return;
+    if (gate && decided_by(d.st, gate)) return;
     const int N1 = 1 << logN1, C = 1 << logC;
     const int logM2 = logN2 - 1;
     const uint32_t j2_0 = blockIdx.x << logC;
-    const CI<T>* W = reinterpret_cast<const CI<T>*>(d.W);
+    const V* W = reinterpret_cast<const V*>(d.W);
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
         const int c = idx & (C - 1), k1 = idx >> logC;
         sm[(c << logN1) + k1] = W[(size_t(k1) << logM2) + j2_0 + c];
     }
     __syncthreads();
-    block_fft<T, -1>(sm, logN1, C, N1, tw);
+    block_fft<V, -1>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
-    const T scale = T(ldexp(1.0, -(logN + 2)));
     const int64_t L = int64_t(d.na) + d.nb - 1;
     IsoAcc acc;
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
         const int c = idx & (C - 1), j1 = idx >> logC;
         const int64_t j = (int64_t(j1) << logM2) + j2_0 + c;
-        const CI<T> v = scale_out(sm[(c << logN1) + j1], scale);
-        isolate_one(v.rl, v.rh, 2 * j, L, d.coeff, acc, d.iv);
-        isolate_one(v.il, v.ih, 2 * j + 1, L, d.coeff, acc, d.iv);
+        isolate_value(scale_pow2(sm[(c << logN1) + j1], logN + 2), j, L, d.coeff, acc, d.iv);
     }
-    flush_acc(acc, d.st, Rung<T>::idx);
-    if (threadIdx.x == 0) atomicOr(&d.st->ran[Rung<T>::idx], 1u);
+    flush_acc(acc, d.st, RUNG);
+    if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
 }
 
 // ---- the decision of a product ---------------------------------------------
 
+// The rungs that ran are read in ladder order (binary32 rectangles, binary64
+// discs, binary64 rectangles, unverified points): the first that isolated
+// every coefficient, or found an empty set, decides; otherwise the last one
+// that ran reports its isolation failure.
 __device__ __forceinline__ int decide(const ProdState* st, int* rung) {
-    if (st->timeout) { *rung = 1; return SSMUL_TIMEOUT; }
-    if (st->ran[0]) {
-        if (st->empty[0]) { *rung = 0; return SSMUL_CONTAINMENT_FAILED; }
-        if (st->unisolated[0] == 0) { *rung = 0; return SSMUL_OK; }
+    const int order[RUNGS] = {0, 2, 1, 3};
+    int last = -1;
+    int status = SSMUL_ISOLATION_FAILED;
+    for (int k = 0; k < RUNGS; ++k) {
+        const int r = order[k];
+        if (!st->ran[r]) continue;
+        last = r;
+        if (r == 3) { status = SSMUL_UNVERIFIED; break; }
+        if (st->empty[r]) { status = SSMUL_CONTAINMENT_FAILED; break; }
+        if (st->unisolated[r] == 0) { status = SSMUL_OK; break; }
     }
-    if (st->ran[1]) {
-        *rung = 1;
-        if (st->empty[1]) return SSMUL_CONTAINMENT_FAILED;
-        return st->unisolated[1] ? SSMUL_ISOLATION_FAILED : SSMUL_OK;
+    *rung = last < 0 ? 1 : last;
+    return st->timeout ? SSMUL_TIMEOUT : status;
+}
+
+__device__ __forceinline__ int rung_precision(int rung) {
+    switch (rung) {
+        case 0: return SSMUL_PREC_FP32;
+        case 2: return SSMUL_PREC_DISC64;
+        case 3: return SSMUL_PREC_NAIVE64;
+        default: return SSMUL_PREC_FP64;
     }
-    *rung = 0;
-    return SSMUL_ISOLATION_FAILED;
 }
 
 // ---- carry (Section 2.4) as a parallel carry-lookahead scan ------------------
@@ -371,7 +430,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
     __syncthreads();
     const uint32_t tile = s_tile;
     const int64_t k0 = int64_t(tile) * CARRY_TILE + int64_t(threadIdx.x) * CARRY_PER_THREAD;
-    if (s_status != SSMUL_OK) {
+    if (s_status != SSMUL_OK && s_status != SSMUL_UNVERIFIED) {
         // no unverified digit escapes: zero fill, publish a zero carry
         for (int q = 0; q < CARRY_PER_THREAD; ++q)
             if (k0 + q < nz) d.z[k0 + q] = 0;
@@ -479,7 +538,7 @@ __global__ void k_finalize(const ProdDesc* descs) {
         const int status = decide(d.st, &rung);
         ssmul_result r;
         r.status = status;
-        r.precision_used = rung == 0 ? SSMUL_PREC_FP32 : SSMUL_PREC_FP64;
+        r.precision_used = rung_precision(rung);
         r.fft_log2 = uint32_t(d.log_n);
         r.n_unisolated = d.st->unisolated[rung];
         r.n_empty = d.st->empty[rung];

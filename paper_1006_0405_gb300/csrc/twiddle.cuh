@@ -18,6 +18,7 @@
 // binary64 one rounded outward.
 #pragma once
 #include "interval.cuh"
+#include "disc.cuh"
 
 namespace ssm {
 
@@ -33,6 +34,7 @@ struct TwTable {
     const TwEntry<double>* t64;   // Ntab/8 + 1 entries
     const TwEntry<float>* t32;    // same, binary32
     int log_n;                    // log2 Ntab
+    const DiscTw* td;             // same, as discs (centre, radius)
 };
 
 __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n) {
@@ -62,6 +64,45 @@ __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log
         t32[j] = {__double2float_rd(e.cl), __double2float_ru(e.ch),
                   __double2float_rd(e.sl), __double2float_ru(e.sh)};
     }
+}
+
+// The disc form of each enclosure: centre = the rounded midpoint of each
+// component's interval, radius >= (distance of the centre to either end,
+// rounded up) summed over the two components, which bounds the complex
+// distance to any point of the rectangle.
+__global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscTw* td, int log_n) {
+    const int64_t count = (int64_t(1) << log_n) / 8 + 1;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
+         j += int64_t(gridDim.x) * blockDim.x) {
+        const TwEntry<double> e = t64[j];
+        const double c = __dadd_rn(0.5 * e.cl, 0.5 * e.ch);
+        const double s = __dadd_rn(0.5 * e.sl, 0.5 * e.sh);
+        const double ec = fmax(__dsub_ru(c, e.cl), __dsub_ru(e.ch, c));
+        const double es = fmax(__dsub_ru(s, e.sl), __dsub_ru(e.sh, s));
+        td[j] = {c, s, __double2float_ru(__dadd_ru(ec, es)), 0.f};
+    }
+}
+
+// Disc enclosure of omega_Ntab^(sign * j): the same symmetries as twiddle();
+// they move the centre exactly and keep the radius.
+template <int SIGN>
+__device__ __forceinline__ DiscTw twiddle_disc(const TwTable& tw, uint32_t j) {
+    const int ln = tw.log_n;
+    j &= (1u << ln) - 1u;
+    const uint32_t q = 1u << (ln - 2);
+    const uint32_t quad = j >> (ln - 2);
+    const uint32_t r = j & (q - 1u);
+    const bool refl = r > (q >> 1);
+    const DiscTw e = tw.td[refl ? q - r : r];
+    double c = refl ? e.s : e.c, s = refl ? e.c : e.s;
+    double wc, ws;
+    switch (quad) {
+        case 0: wc = c; ws = s; break;
+        case 1: wc = -s; ws = c; break;
+        case 2: wc = -c; ws = -s; break;
+        default: wc = s; ws = -c; break;
+    }
+    return {wc, SIGN < 0 ? -ws : ws, e.rho, 0.f};
 }
 
 template <typename T>

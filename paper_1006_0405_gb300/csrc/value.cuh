@@ -1,0 +1,83 @@
+// value.cuh -- the value types the transform kernels are instantiated for.
+//
+//   CI<float>   rung 0: binary32 inf-sup rectangles (Section 2.5)
+//   CI<double>  rung 1: binary64 inf-sup rectangles (Section 2.5)
+//   Disc        rung 2: binary64 midpoint-radius discs (Section 4's
+//               circular containment sets)
+//   Pt          rung 3: unverified round-to-nearest binary64 points (the
+//               naive transform of Section 3, a speed reference)
+//
+// Each type provides +, -, mul_i, mul_negi, conj, mul_tw (by its twiddle
+// type), mul_ci, scale_pow2, make_point, get_twiddle and the isolation of
+// its two components.
+#pragma once
+#include "interval.cuh"
+#include "disc.cuh"
+#include "twiddle.cuh"
+
+namespace ssm {
+
+constexpr int RUNGS = 4;
+
+template <typename V> struct VTraits;
+template <> struct VTraits<CI<float>> { using Tw = CI<float>; static constexpr int rung = 0; };
+template <> struct VTraits<CI<double>> { using Tw = CI<double>; static constexpr int rung = 1; };
+template <> struct VTraits<Disc> { using Tw = DiscTw; static constexpr int rung = 2; };
+template <> struct VTraits<Pt> { using Tw = DiscTw; static constexpr int rung = 3; };
+
+template <typename V, int SIGN>
+__device__ __forceinline__ typename VTraits<V>::Tw get_twiddle(const TwTable& tw, uint32_t j);
+template <>
+__device__ __forceinline__ CI<float> get_twiddle<CI<float>, 1>(const TwTable& tw, uint32_t j) {
+    return twiddle<float, 1>(tw, j);
+}
+template <>
+__device__ __forceinline__ CI<float> get_twiddle<CI<float>, -1>(const TwTable& tw, uint32_t j) {
+    return twiddle<float, -1>(tw, j);
+}
+template <>
+__device__ __forceinline__ CI<double> get_twiddle<CI<double>, 1>(const TwTable& tw, uint32_t j) {
+    return twiddle<double, 1>(tw, j);
+}
+template <>
+__device__ __forceinline__ CI<double> get_twiddle<CI<double>, -1>(const TwTable& tw, uint32_t j) {
+    return twiddle<double, -1>(tw, j);
+}
+template <>
+__device__ __forceinline__ DiscTw get_twiddle<Disc, 1>(const TwTable& tw, uint32_t j) {
+    return twiddle_disc<1>(tw, j);
+}
+template <>
+__device__ __forceinline__ DiscTw get_twiddle<Disc, -1>(const TwTable& tw, uint32_t j) {
+    return twiddle_disc<-1>(tw, j);
+}
+template <>
+__device__ __forceinline__ DiscTw get_twiddle<Pt, 1>(const TwTable& tw, uint32_t j) {
+    return twiddle_disc<1>(tw, j);
+}
+template <>
+__device__ __forceinline__ DiscTw get_twiddle<Pt, -1>(const TwTable& tw, uint32_t j) {
+    return twiddle_disc<-1>(tw, j);
+}
+
+// a digit pair as an exact point (small integers are exact in every type)
+template <typename V> __device__ __forceinline__ V make_point(int re, int im);
+template <> __device__ __forceinline__ CI<float> make_point<CI<float>>(int re, int im) {
+    return {float(re), float(re), float(im), float(im)};
+}
+template <> __device__ __forceinline__ CI<double> make_point<CI<double>>(int re, int im) {
+    return {double(re), double(re), double(im), double(im)};
+}
+template <> __device__ __forceinline__ Disc make_point<Disc>(int re, int im) {
+    return {double(re), double(im), 0.f, 0.f};
+}
+template <> __device__ __forceinline__ Pt make_point<Pt>(int re, int im) {
+    return {double(re), double(im)};
+}
+
+template <typename T>
+__device__ __forceinline__ CI<T> scale_pow2(const CI<T>& a, int k) {
+    return scale_out(a, T(ldexp(1.0, -k)));
+}
+
+}  // namespace ssm
