@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "disc64", "naive64"],
                     help="rung of the paper workload: binary64 rectangles (default), binary64 "
                          "discs, or the unverified naive transform")
+    ap.add_argument("--balanced", action="store_true",
+                    help="balanced digits (the transforms carry digit - 128)")
     ap.add_argument("--workload", default="paper", choices=["paper", "sweep", "ladder", "uneven"],
                     help="paper: the headline line; sweep / ladder / uneven: report lines of "
                          "the size sweep, the precision ladder and the uneven batch")
@@ -261,6 +263,8 @@ def run_ours(args):
     prec = {"fp64": abi.SSMUL_PREC_FP64, "disc64": abi.SSMUL_PREC_DISC64,
             "naive64": abi.SSMUL_PREC_NAIVE64}[args.precision]
     plan = abi.ssmul_plan(n, n, B, prec, stream.cuda_stream)
+    if args.balanced:
+        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
     descs = (abi.ssmul_desc * B)()
     for i in range(B):
         descs[i] = abi.ssmul_desc(int(a_off[i]), int(b_off[i]), int(z_off[i]), n, n)
@@ -399,6 +403,7 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f64",
             "precision": args.precision,
+            "balanced_digits": bool(args.balanced),
             "data": "synthetic",
             "config": {"workload": f"{n}x{n} base-256 digits, "
                                    f"{ {'fp64': 'binary64 inf-sup intervals', 'disc64': 'binary64 midpoint-radius discs', 'naive64': 'unverified binary64 points'}[args.precision]}, "

@@ -129,7 +129,13 @@ typedef enum {
     SSMUL_OPT_AUTOTUNE = 1,
     /* under SSMUL_PREC_LADDER, try binary32 only for products whose shorter
      * operand has at most `value` digits (and N <= 4096); default 24 */
-    SSMUL_OPT_FP32_MAX_DIGITS = 2
+    SSMUL_OPT_FP32_MAX_DIGITS = 2,
+    /* value != 0: balanced digits.  The transforms carry a_j - 128 and
+     * b_j - 128 instead of the digits, so their values (and the widths of
+     * the containment sets) are much smaller; the isolated coefficients are
+     * corrected exactly with integer window sums of the digits.  The
+     * product is the same.  Default 0 (the paper's digits 0..255). */
+    SSMUL_OPT_BALANCED = 3
 } ssmul_option;
 
 /*

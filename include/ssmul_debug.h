@@ -62,7 +62,8 @@ ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y, d
 
 /* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays):
  * one per transform kernel and rung (F32 / F64 rectangles, DISC discs,
- * NAIVE points), then the carry and the finalisation. */
+ * NAIVE points), then the carry, the finalisation and the digit prefix
+ * sums of balanced digits. */
 enum {
     SSMUL_K_SMALL_F32 = 0, SSMUL_K_SMALL_F64 = 1, SSMUL_K_SMALL_DISC = 2, SSMUL_K_SMALL_NAIVE = 3,
     SSMUL_K_FWD_COLS_F32 = 4, SSMUL_K_FWD_COLS_F64 = 5, SSMUL_K_FWD_COLS_DISC = 6,
@@ -70,8 +71,8 @@ enum {
     SSMUL_K_ROWS_F32 = 8, SSMUL_K_ROWS_F64 = 9, SSMUL_K_ROWS_DISC = 10, SSMUL_K_ROWS_NAIVE = 11,
     SSMUL_K_INV_COLS_F32 = 12, SSMUL_K_INV_COLS_F64 = 13, SSMUL_K_INV_COLS_DISC = 14,
     SSMUL_K_INV_COLS_NAIVE = 15,
-    SSMUL_K_CARRY = 16, SSMUL_K_FINALIZE = 17,
-    SSMUL_KERNEL_KINDS = 18
+    SSMUL_K_CARRY = 16, SSMUL_K_FINALIZE = 17, SSMUL_K_PREFIX = 18,
+    SSMUL_KERNEL_KINDS = 19
 };
 
 /*

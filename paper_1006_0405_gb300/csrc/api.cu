@@ -82,6 +82,12 @@ int threads_for(int elems) {          // block_fft: nl * L / 8 threads
 
 size_t carry_tiles(size_t nz) { return (nz + CARRY_TILE - 1) / CARRY_TILE; }
 
+// words of a balanced-digit prefix array (see k_prefix): local sums and tile offsets
+size_t pre_words(size_t n) { return n + 1 + (n + PRE_TILE - 1) / PRE_TILE; }
+size_t pre_bytes(size_t na, size_t nb) {
+    return ((pre_words(na) + pre_words(nb)) * sizeof(uint32_t) + 255) & ~size_t(255);
+}
+
 ssmul_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SSMUL_OK;
     if (e == cudaErrorMemoryAllocation) return SSMUL_OUT_OF_MEMORY;
@@ -131,6 +137,8 @@ struct ssmul_plan_s {
     DiscTw* td = nullptr;
     Geom geom[LOG_N_MAX + 1] = {};
     size_t fp32_max_min_digits = FP32_MAX_MIN_DIGITS;
+    bool balanced = false;
+    uint32_t* pre = nullptr;            // balanced: digit prefix sums of one product
     // single-product workspace
     void* Z = nullptr;
     void* W = nullptr;
@@ -303,10 +311,29 @@ ssmul_status enqueue_rungs(ssmul_plan_t p, ssmul_precision prec, const ProdDesc*
     return SSMUL_OK;
 }
 
+// Digit prefix sums of `count` products (balanced digits only).
+ssmul_status enqueue_prefix(ssmul_plan_t p, const ProdDesc* d_desc, int count, size_t max_n) {
+    if (!p->balanced) return SSMUL_OK;
+    {
+        LaunchScope ls(p, SSMUL_K_PREFIX);
+        k_prefix<<<dim3(unsigned((max_n + PRE_TILE - 1) / PRE_TILE), unsigned(count), 2),
+                   PRE_THREADS, 0, p->stream>>>(d_desc);
+    }
+    {
+        LaunchScope ls(p, SSMUL_K_PREFIX);
+        k_prefix_tiles<<<dim3(unsigned(count), 2), 32, 0, p->stream>>>(d_desc);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
 // Enqueue one complete product (rungs, carry, outcome) for d_desc[0].
 ssmul_status enqueue_product(ssmul_plan_t p, const ProdDesc* d_desc, size_t na, size_t nb,
                              ssmul_precision prec) {
     const Geom& g = p->geom[log_n_for(na, nb)];
+    {
+        ssmul_status s0 = enqueue_prefix(p, d_desc, 1, na > nb ? na : nb);
+        if (s0 != SSMUL_OK) return s0;
+    }
     const bool try32 = prec == SSMUL_PREC_FP32 ||
                        (uses_fp32(prec) && fp32_eligible(p, na, nb, g.log_n));
     ssmul_status s = enqueue_rungs(p, prec, d_desc, 1, try32 ? 1 : 0, g);
@@ -346,6 +373,9 @@ ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t*
     d.st = p->st + slot;
     d.res = p->d_res + slot;
     d.iv = nullptr;
+    d.balanced = p->balanced ? 1 : 0;
+    d.pre_a = p->pre;
+    d.pre_b = p->pre + pre_words(p->max_na);
     return d;
 }
 
@@ -424,10 +454,16 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
         size_t used = 0, k1 = k0;
         while (k1 < count) {
             const int ln = logn[order[k1]];
-            const size_t need = arena_need(ln);
+            const ssmul_desc& hd = h_desc[order[k1]];
+            const size_t pb = p->balanced ? pre_bytes(hd.na, hd.nb) : 0;
+            const size_t need = arena_need(ln) + pb;
             if (used + need > p->arena_bytes) break;
             ProdDesc& d = p->h_desc[k1];
             unsigned char* base = p->arena + used;
+            if (pb) {
+                d.pre_a = reinterpret_cast<uint32_t*>(base + arena_need(ln));
+                d.pre_b = d.pre_a + pre_words(hd.na);
+            }
             if (ln <= LOG_SMALL) {
                 d.Z = nullptr;
                 d.W = nullptr;
@@ -476,6 +512,9 @@ ssmul_status issue_batch(ssmul_plan_t p, size_t count) {
         SS_TRY(cudaMemcpyAsync(p->d_desc + c.k0, p->h_desc + c.k0,
                                (c.k1 - c.k0) * sizeof(ProdDesc), cudaMemcpyHostToDevice,
                                p->stream));
+        s = enqueue_prefix(p, p->d_desc + c.k0, int(c.k1 - c.k0),
+                           p->max_na > p->max_nb ? p->max_na : p->max_nb);
+        if (s != SSMUL_OK) return s;
         for (const BatchGroup& g : c.groups) {
             const Geom& geo = p->geom[g.log_n];
             s = enqueue_rungs(p, p->prec, p->d_desc + g.g0, int(g.g1 - g.g0),
@@ -747,6 +786,7 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->d_desc);
     cudaFree(p->d_res);
     cudaFree(p->stage);
+    cudaFree(p->pre);
     cudaFree(p->arena);
     cudaFreeHost(p->h_desc);
     cudaFreeHost(p->h_res);
@@ -805,6 +845,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, slots * sizeof(ProdDesc));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_res, slots * sizeof(ssmul_result));
     if (e == cudaSuccess) e = cudaMalloc(&p->stage, 2 * (max_na + max_nb));
+    if (e == cudaSuccess) e = cudaMalloc(&p->pre, pre_bytes(max_na, max_nb));
     if (e == cudaSuccess) e = cudaMallocHost(&p->h_desc, slots * sizeof(ProdDesc));
     if (e == cudaSuccess) e = cudaMallocHost(&p->h_res, slots * sizeof(ssmul_result));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->desc_free, cudaEventDisableTiming);
@@ -817,7 +858,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
             const long long mb = std::atoll(env);
             if (mb > 0 && size_t(mb) << 20 < cap) cap = size_t(mb) << 20;
         }
-        const size_t one = arena_need(log_n);
+        const size_t one = arena_need(log_n) + pre_bytes(max_na, max_nb);
         size_t want = one * max_products;
         if (want > cap) want = cap > one ? cap : one;
         p->arena_bytes = want;
@@ -863,6 +904,11 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
             if (value < 0) return SSMUL_INVALID_ARG;
             graph_drop(p->cached);
             p->fp32_max_min_digits = size_t(value);
+            return SSMUL_OK;
+        case SSMUL_OPT_BALANCED:
+            SS_TRY(cudaStreamSynchronize(p->stream));
+            graph_drop(p->cached);
+            p->balanced = value != 0;
             return SSMUL_OK;
     }
     return SSMUL_INVALID_ARG;

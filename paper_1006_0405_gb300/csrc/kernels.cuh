@@ -63,7 +63,7 @@ struct ProdDesc {
     uint8_t* z;
     uint32_t na, nb;
     int32_t log_n;                     // transform length N = 2^log_n
-    int32_t pad0;
+    int32_t balanced;                  // digits enter the transform as x_j - 128
     void* Z;                           // four-step workspace, N intervals
     void* W;                           // four-step workspace, N/2 intervals
     int64_t* coeff;                    // N integer coefficients
@@ -71,7 +71,100 @@ struct ProdDesc {
     ProdState* st;
     ssmul_result* res;
     double* iv;                        // optional: coefficient enclosures (tests)
+    uint32_t* pre_a;                   // balanced: prefix sums of a (see k_prefix)
+    uint32_t* pre_b;                   // balanced: prefix sums of b
 };
+
+// ---- balanced digits --------------------------------------------------------
+//
+// With balanced digits a'_j = a_j - 128, b'_j = b_j - 128 (zero past the
+// operands) the transforms carry far smaller values.  The product is
+// unchanged: with u the all-ones vectors,
+//   a * b = a' * b' + 128 (u_a * b + a * u_b) - 16384 u_a * u_b,
+// so c_i = c'_i + 128 (Wa_i + Wb_i) - 16384 cnt_i, where Wa_i and Wb_i are
+// the sums of the digits of a and b that meet in coefficient i and cnt_i
+// the number of such pairs.  The window sums come from prefix sums of the
+// digits: for tile size PRE_TILE, local[k] (k = 1 .. n) is the sum of the
+// digits from the start of the tile of digit k-1 up to digit k-1, and
+// off[t] the sum of all digits before tile t.
+
+constexpr int PRE_LOG_TILE = 11;
+constexpr int PRE_TILE = 1 << PRE_LOG_TILE;
+constexpr int PRE_THREADS = 256;
+
+__device__ __forceinline__ uint32_t prefix_at(const uint32_t* pre, uint32_t n, uint32_t k) {
+    if (k == 0) return 0u;
+    return pre[n + 1 + ((k - 1) >> PRE_LOG_TILE)] + pre[k];
+}
+
+// the exact term that turns c'_i into c_i
+__device__ __forceinline__ int64_t balance_corr(const ProdDesc& d, int64_t i) {
+    const int64_t na = d.na, nb = d.nb;
+    const int64_t ja_lo = i - nb + 1 > 0 ? i - nb + 1 : 0, ja_hi = i < na - 1 ? i : na - 1;
+    const int64_t jb_lo = i - na + 1 > 0 ? i - na + 1 : 0, jb_hi = i < nb - 1 ? i : nb - 1;
+    const int64_t wa = int64_t(prefix_at(d.pre_a, d.na, uint32_t(ja_hi + 1))) -
+                       int64_t(prefix_at(d.pre_a, d.na, uint32_t(ja_lo)));
+    const int64_t wb = int64_t(prefix_at(d.pre_b, d.nb, uint32_t(jb_hi + 1))) -
+                       int64_t(prefix_at(d.pre_b, d.nb, uint32_t(jb_lo)));
+    return 128 * (wa + wb) - 16384 * (ja_hi - ja_lo + 1);
+}
+
+// tile-local inclusive sums and tile totals; blockIdx.z: 0 for a, 1 for b
+__global__ void __launch_bounds__(PRE_THREADS) k_prefix(const ProdDesc* descs) {
+    __shared__ uint32_t s_warp[PRE_THREADS / 32];
+    const ProdDesc d = descs[blockIdx.y];
+    if (!d.balanced) return;
+    const bool isb = blockIdx.z != 0;
+    const uint32_t n = isb ? d.nb : d.na;
+    const uint8_t* x = isb ? d.b : d.a;
+    uint32_t* pre = isb ? d.pre_b : d.pre_a;
+    const uint32_t base = blockIdx.x << PRE_LOG_TILE;
+    if (base >= n) return;
+    constexpr int PER = PRE_TILE / PRE_THREADS;
+    const uint32_t k0 = base + threadIdx.x * PER;
+    uint32_t v[PER];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        v[q] = (k0 + q < n) ? uint32_t(x[k0 + q]) : 0u;
+        sum += v[q];
+    }
+    // exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += s_warp[w];
+    uint32_t run = wbase + inc - sum;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        run += v[q];
+        if (k0 + q < n) pre[k0 + q + 1] = run;
+    }
+    if (threadIdx.x == PRE_THREADS - 1) pre[n + 1 + blockIdx.x] = run;   // tile total
+    if (blockIdx.x == 0 && threadIdx.x == 0) pre[0] = 0u;
+}
+
+// exclusive scan of the tile totals, in place; blockIdx.y: 0 for a, 1 for b
+__global__ void k_prefix_tiles(const ProdDesc* descs) {
+    const ProdDesc d = descs[blockIdx.x];
+    if (!d.balanced || threadIdx.x != 0) return;
+    const bool isb = blockIdx.y != 0;
+    const uint32_t n = isb ? d.nb : d.na;
+    uint32_t* off = (isb ? d.pre_b : d.pre_a) + n + 1;
+    const uint32_t tiles = (n + PRE_TILE - 1) >> PRE_LOG_TILE;
+    uint32_t acc = 0;
+    for (uint32_t t = 0; t < tiles; ++t) {
+        const uint32_t tot = off[t];
+        off[t] = acc;
+        acc += tot;
+    }
+}
 
 // ---- the rung gate of the precision ladder ------------------------------------
 
@@ -138,27 +231,33 @@ struct IsoAcc {
 };
 
 // Decide coefficient `idx` from its enclosure [lo, hi]; L = na + nb - 1.
+// Decide coefficient idx from the enclosure [lo, hi] of c_idx (of c'_idx
+// with balanced digits, corrected here to c_idx); L = na + nb - 1.  The
+// exact coefficient is a nonnegative integer: an isolated negative value is
+// a containment failure like an empty set.
 template <typename T>
-__device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, int64_t L,
-                                            int64_t* coeff, IsoAcc& acc, double* iv) {
+__device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdDesc& d,
+                                            IsoAcc& acc) {
+    const int64_t L = int64_t(d.na) + d.nb - 1;
     const double dl = double(lo), dh = double(hi);    // exact widening
-    if (iv != nullptr && idx < L) {
-        iv[2 * idx] = dl;
-        iv[2 * idx + 1] = dh;
-    }
     const double w = __dsub_ru(dh, dl);
     acc.maxw = (w > acc.maxw || w != w) ? w : acc.maxw;
     if (idx < L) {
+        const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
+        if (d.iv != nullptr) {
+            d.iv[2 * idx] = __dadd_rd(dl, double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(dh, double(corr));
+        }
         const double kl = ceil(dl), kh = floor(dh);
         int64_t v = 0;
-        if (kl == kh && kl >= 0.0) {
-            v = int64_t(kl);
+        if (kl == kh && fabs(kl) < 4.0e15 && int64_t(kl) + corr >= 0) {
+            v = int64_t(kl) + corr;
         } else if (kl < kh) {
             acc.unisolated++;
         } else {
             acc.empty++;           // no integer, a negative one, or NaN
         }
-        coeff[idx] = v;
+        d.coeff[idx] = v;
     } else {
         if (!(dl <= 0.0 && 0.0 <= dh)) acc.empty++;   // exact value is 0
     }
@@ -181,40 +280,42 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
 // Both coefficients carried by one complex value: c_{2j} (real part) and
 // c_{2j+1} (imaginary part).
 template <typename T>
-__device__ __forceinline__ void isolate_value(const CI<T>& v, int64_t j, int64_t L,
-                                              int64_t* coeff, IsoAcc& acc, double* iv) {
-    isolate_one(v.rl, v.rh, 2 * j, L, coeff, acc, iv);
-    isolate_one(v.il, v.ih, 2 * j + 1, L, coeff, acc, iv);
+__device__ __forceinline__ void isolate_value(const CI<T>& v, int64_t j, const ProdDesc& d,
+                                              IsoAcc& acc) {
+    isolate_one(v.rl, v.rh, 2 * j, d, acc);
+    isolate_one(v.il, v.ih, 2 * j + 1, d, acc);
 }
 
-__device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, int64_t L,
-                                              int64_t* coeff, IsoAcc& acc, double* iv) {
+__device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, const ProdDesc& d,
+                                              IsoAcc& acc) {
     const double r = double(v.r);
-    isolate_one(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, L, coeff, acc, iv);
-    isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, L, coeff, acc, iv);
+    isolate_one(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, d, acc);
+    isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc);
 }
 
 // the naive transform rounds to the nearest integer without any proof; its
 // "width" statistic is the largest distance to that integer
-__device__ __forceinline__ void naive_one(double v, int64_t idx, int64_t L, int64_t* coeff,
-                                          IsoAcc& acc, double* iv) {
+__device__ __forceinline__ void naive_one(double v, int64_t idx, const ProdDesc& d,
+                                          IsoAcc& acc) {
+    const int64_t L = int64_t(d.na) + d.nb - 1;
     const double k = rint(v);
     const double dist = fabs(v - k);
     acc.maxw = (dist > acc.maxw || dist != dist) ? dist : acc.maxw;
-    if (iv != nullptr && idx < L) {
-        iv[2 * idx] = v;
-        iv[2 * idx + 1] = v;
-    }
     if (idx < L) {
-        if (k == k && k >= 0.0) coeff[idx] = int64_t(k);
-        else { coeff[idx] = 0; acc.empty++; }
+        const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
+        if (d.iv != nullptr) {
+            d.iv[2 * idx] = v + double(corr);
+            d.iv[2 * idx + 1] = v + double(corr);
+        }
+        if (fabs(k) < 4.0e15 && int64_t(k) + corr >= 0) d.coeff[idx] = int64_t(k) + corr;
+        else { d.coeff[idx] = 0; acc.empty++; }
     }
 }
 
-__device__ __forceinline__ void isolate_value(const Pt& v, int64_t j, int64_t L, int64_t* coeff,
-                                              IsoAcc& acc, double* iv) {
-    naive_one(v.x, 2 * j, L, coeff, acc, iv);
-    naive_one(v.y, 2 * j + 1, L, coeff, acc, iv);
+__device__ __forceinline__ void isolate_value(const Pt& v, int64_t j, const ProdDesc& d,
+                                              IsoAcc& acc) {
+    naive_one(v.x, 2 * j, d, acc);
+    naive_one(v.y, 2 * j + 1, d, acc);
 }
 
 // ---- k_small: the whole interval convolution of one product in one CTA -----
@@ -230,8 +331,9 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     if (gate && decided_by(d.st, gate)) return;
     const int logN = d.log_n, N = 1 << logN;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const int re = j < int(d.na) ? int(d.a[j]) : 0;
-        const int im = j < int(d.nb) ? int(d.b[j]) : 0;
+        const int bias = d.balanced ? 128 : 0;
+        const int re = j < int(d.na) ? int(d.a[j]) - bias : 0;
+        const int im = j < int(d.nb) ? int(d.b[j]) - bias : 0;
         sm[j] = make_point<V>(re, im);
     }
     __syncthreads();
@@ -242,10 +344,9 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     pack_half(sm, 1, rows, 0, logN, tw);
     __syncthreads();
     block_fft<V, -1>(sm, logN - 1, 1, N, tw);
-    const int64_t L = int64_t(d.na) + d.nb - 1;
     IsoAcc acc;
     for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x)
-        isolate_value(scale_pow2(sm[j], logN + 2), j, L, d.coeff, acc, d.iv);
+        isolate_value(scale_pow2(sm[j], logN + 2), j, d, acc);
     flush_acc(acc, d.st, RUNG);
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
 }
@@ -266,8 +367,9 @@ __global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
         const int c = idx & (C - 1), j1 = idx >> logC;
         const uint32_t j = (uint32_t(j1) << logN2) + j2_0 + c;
-        const int re = j < d.na ? int(d.a[j]) : 0;
-        const int im = j < d.nb ? int(d.b[j]) : 0;
+        const int bias = d.balanced ? 128 : 0;
+        const int re = j < d.na ? int(d.a[j]) - bias : 0;
+        const int im = j < d.nb ? int(d.b[j]) - bias : 0;
         sm[(c << logN1) + j1] = make_point<V>(re, im);
     }
     __syncthreads();
@@ -338,12 +440,11 @@ __global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
     __syncthreads();
     block_fft<V, -1>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
-    const int64_t L = int64_t(d.na) + d.nb - 1;
     IsoAcc acc;
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
         const int c = idx & (C - 1), j1 = idx >> logC;
         const int64_t j = (int64_t(j1) << logM2) + j2_0 + c;
-        isolate_value(scale_pow2(sm[(c << logN1) + j1], logN + 2), j, L, d.coeff, acc, d.iv);
+        isolate_value(scale_pow2(sm[(c << logN1) + j1], logN + 2), j, d, acc);
     }
     flush_acc(acc, d.st, RUNG);
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
