@@ -127,15 +127,23 @@ typedef enum {
      * keep the fastest; results are cached in the file named by the
      * environment variable SSMUL_TUNE_CACHE when it is set.  0: defaults */
     SSMUL_OPT_AUTOTUNE = 1,
-    /* under SSMUL_PREC_LADDER, try binary32 only for products whose shorter
-     * operand has at most `value` digits (and N <= 4096); default 24 */
+    /* under the ladders, try binary32 only for products with
+     * na + nb <= value digits (and N <= 4096); default 32 */
     SSMUL_OPT_FP32_MAX_DIGITS = 2,
     /* value != 0: balanced digits.  The transforms carry a_j - 128 and
      * b_j - 128 instead of the digits, so their values (and the widths of
      * the containment sets) are much smaller; the isolated coefficients are
      * corrected exactly with integer window sums of the digits.  The
      * product is the same.  Default 0 (the paper's digits 0..255). */
-    SSMUL_OPT_BALANCED = 3
+    SSMUL_OPT_BALANCED = 3,
+    /* value m >= 1024: ssmul_mul / ssmul_mul_host cut a product whose longer
+     * operand has more than m digits into parts of at most m digits per
+     * operand, run each part's interval convolution (which isolates at
+     * sizes the whole product would not), and add the parts' exact integer
+     * coefficients before one carry: the way past the isolation limit that
+     * Section 1 names ("use a different algorithm").  The status is the
+     * worst of the parts'.  0 (default): off.  Batched calls do not split. */
+    SSMUL_OPT_SPLIT_DIGITS = 4
 } ssmul_option;
 
 /*

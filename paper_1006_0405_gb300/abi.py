@@ -43,6 +43,7 @@ SSMUL_OPT_GRAPH = 0
 SSMUL_OPT_AUTOTUNE = 1
 SSMUL_OPT_FP32_MAX_DIGITS = 2
 SSMUL_OPT_BALANCED = 3
+SSMUL_OPT_SPLIT_DIGITS = 4
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")

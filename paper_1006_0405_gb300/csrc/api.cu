@@ -20,12 +20,12 @@ using namespace ssm;
 
 namespace {
 
-// the binary32 rung is tried when the product's transform is at most this
-// long and the shorter operand has at most this many digits (a plan
-// option): beyond that a binary32 containment set cannot isolate base-256
-// coefficients
+// the binary32 rung is tried when the product has at most this many digits
+// in total (na + nb, a plan option): binary32 rectangles were measured to
+// isolate every uniform square product up to 16 x 16 digits, and the width
+// grows with the transform length
 constexpr int FP32_MAX_LOG_N = LOG_SMALL;
-constexpr size_t FP32_MAX_MIN_DIGITS = 24;
+constexpr size_t FP32_MAX_DIGITS = 32;
 
 // largest batch arena a plan allocates (the batch runs in chunks beyond it)
 constexpr size_t ARENA_CAP = size_t(4) << 30;
@@ -136,9 +136,16 @@ struct ssmul_plan_s {
     TwEntry<float>* t32 = nullptr;
     DiscTw* td = nullptr;
     Geom geom[LOG_N_MAX + 1] = {};
-    size_t fp32_max_min_digits = FP32_MAX_MIN_DIGITS;
+    size_t fp32_max_digits = FP32_MAX_DIGITS;
     bool balanced = false;
     uint32_t* pre = nullptr;            // balanced: digit prefix sums of one product
+    // split products (SSMUL_OPT_SPLIT_DIGITS)
+    size_t split_digits = 0;
+    size_t split_slots = 0;
+    int64_t* coeff_total = nullptr;     // max_na + max_nb coefficients
+    ProdState* split_st = nullptr;      // split_slots entries
+    ProdDesc* d_split = nullptr;        // split_slots entries
+    ProdDesc* h_split = nullptr;        // pinned
     // single-product workspace
     void* Z = nullptr;
     void* W = nullptr;
@@ -261,8 +268,7 @@ ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, con
 }
 
 bool fp32_eligible(ssmul_plan_t p, size_t na, size_t nb, int log_n) {
-    const size_t mn = na < nb ? na : nb;
-    return log_n <= FP32_MAX_LOG_N && mn <= p->fp32_max_min_digits;
+    return log_n <= FP32_MAX_LOG_N && na + nb <= p->fp32_max_digits;
 }
 
 bool uses_fp32(ssmul_precision prec) {
@@ -379,6 +385,72 @@ ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t*
     return d;
 }
 
+// One product cut into parts of at most m digits per operand (see
+// k_split_accumulate); waits for the result.
+ssmul_status run_split(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
+                       size_t nb, uint8_t* d_z, ssmul_result* h_res, ssmul_precision prec) {
+    const size_t m = p->split_digits;
+    const size_t ka = (na + m - 1) / m, kb = (nb + m - 1) / m;
+    if (ka * kb > p->split_slots) return SSMUL_TOO_LARGE;
+    SS_TRY(cudaEventSynchronize(p->desc_free));
+    ProdDesc parent = single_desc(p, d_a, na, d_b, nb, d_z, 0);
+    parent.coeff = p->coeff_total;
+    p->h_desc[0] = parent;
+    size_t np = 0;
+    for (size_t k = 0; k < ka; ++k) {
+        for (size_t l = 0; l < kb; ++l, ++np) {
+            const size_t la = (k + 1) * m <= na ? m : na - k * m;
+            const size_t lb = (l + 1) * m <= nb ? m : nb - l * m;
+            ProdDesc d = single_desc(p, d_a + k * m, la, d_b + l * m, lb, nullptr, 0);
+            d.st = p->split_st + np;
+            d.res = nullptr;
+            d.flags = nullptr;
+            p->h_split[np] = d;
+        }
+    }
+    SS_TRY(cudaMemsetAsync(p->st, 0, sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->split_st, 0, np * sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->coeff_total, 0, (na + nb) * sizeof(int64_t), p->stream));
+    SS_TRY(cudaMemsetAsync(p->flags, 0, carry_tiles(na + nb) * sizeof(uint32_t), p->stream));
+    SS_TRY(cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ProdDesc), cudaMemcpyHostToDevice,
+                           p->stream));
+    SS_TRY(cudaMemcpyAsync(p->d_split, p->h_split, np * sizeof(ProdDesc), cudaMemcpyHostToDevice,
+                           p->stream));
+    SS_TRY(cudaEventRecord(p->desc_free, p->stream));
+    ssmul_status s = SSMUL_OK;
+    np = 0;
+    for (size_t k = 0; k < ka; ++k) {
+        for (size_t l = 0; l < kb; ++l, ++np) {
+            const ProdDesc& hd = p->h_split[np];
+            const Geom& g = p->geom[hd.log_n];
+            s = enqueue_prefix(p, p->d_split + np, 1, hd.na > hd.nb ? hd.na : hd.nb);
+            if (s != SSMUL_OK) return s;
+            const bool try32 = prec == SSMUL_PREC_FP32 ||
+                               (uses_fp32(prec) && fp32_eligible(p, hd.na, hd.nb, g.log_n));
+            s = enqueue_rungs(p, prec, p->d_split + np, 1, try32 ? 1 : 0, g);
+            if (s != SSMUL_OK) return s;
+            const size_t L = size_t(hd.na) + hd.nb - 1;
+            k_split_accumulate<<<unsigned((L + 255) / 256 < 1024 ? (L + 255) / 256 : 1024), 256, 0,
+                                 p->stream>>>(p->d_split + np, p->coeff_total, (k + l) * m, p->st);
+            SS_TRY(cudaGetLastError());
+        }
+    }
+    {
+        LaunchScope ls(p, SSMUL_K_CARRY);
+        k_carry<<<dim3(unsigned(carry_tiles(na + nb)), 1), CARRY_THREADS, 0, p->stream>>>(p->d_desc);
+    }
+    {
+        LaunchScope ls(p, SSMUL_K_FINALIZE);
+        k_finalize<<<1, 256, 0, p->stream>>>(p->d_desc);
+    }
+    SS_TRY(cudaGetLastError());
+    SS_TRY(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(ssmul_result), cudaMemcpyDeviceToHost,
+                           p->stream));
+    SS_TRY(cudaStreamSynchronize(p->stream));
+    if (h_res) *h_res = p->h_res[0];
+    return ssmul_status(p->h_res[0].status);
+}
+
 // one product on device buffers; fills h_res; waits for the result
 ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
                         size_t nb, uint8_t* d_z, ssmul_result* h_res, ssmul_precision prec,
@@ -387,6 +459,8 @@ ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uin
     if (na > p->max_na || nb > p->max_nb) return SSMUL_TOO_LARGE;
     ssmul_status s = check_device(p);
     if (s != SSMUL_OK) return s;
+    if (p->split_digits && d_iv == nullptr && (na > p->split_digits || nb > p->split_digits))
+        return run_split(p, d_a, na, d_b, nb, d_z, h_res, prec);
     SS_TRY(cudaEventSynchronize(p->desc_free));
     p->h_desc[0] = single_desc(p, d_a, na, d_b, nb, d_z, 0);
     p->h_desc[0].iv = d_iv;
@@ -788,6 +862,10 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->stage);
     cudaFree(p->pre);
     cudaFree(p->arena);
+    cudaFree(p->coeff_total);
+    cudaFree(p->split_st);
+    cudaFree(p->d_split);
+    cudaFreeHost(p->h_split);
     cudaFreeHost(p->h_desc);
     cudaFreeHost(p->h_res);
     if (p->desc_free) cudaEventDestroy(p->desc_free);
@@ -903,13 +981,38 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
         case SSMUL_OPT_FP32_MAX_DIGITS:
             if (value < 0) return SSMUL_INVALID_ARG;
             graph_drop(p->cached);
-            p->fp32_max_min_digits = size_t(value);
+            p->fp32_max_digits = size_t(value);
             return SSMUL_OK;
         case SSMUL_OPT_BALANCED:
             SS_TRY(cudaStreamSynchronize(p->stream));
             graph_drop(p->cached);
             p->balanced = value != 0;
             return SSMUL_OK;
+        case SSMUL_OPT_SPLIT_DIGITS: {
+            if (value < 0 || (value > 0 && value < 1024)) return SSMUL_INVALID_ARG;
+            SS_TRY(cudaStreamSynchronize(p->stream));
+            cudaFree(p->coeff_total);
+            cudaFree(p->split_st);
+            cudaFree(p->d_split);
+            cudaFreeHost(p->h_split);
+            p->coeff_total = nullptr;
+            p->split_st = nullptr;
+            p->d_split = nullptr;
+            p->h_split = nullptr;
+            p->split_digits = 0;
+            p->split_slots = 0;
+            if (value == 0) return SSMUL_OK;
+            const size_t m = size_t(value);
+            const size_t slots = ((p->max_na + m - 1) / m) * ((p->max_nb + m - 1) / m);
+            cudaError_t e = cudaMalloc(&p->coeff_total, (p->max_na + p->max_nb) * sizeof(int64_t));
+            if (e == cudaSuccess) e = cudaMalloc(&p->split_st, slots * sizeof(ProdState));
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_split, slots * sizeof(ProdDesc));
+            if (e == cudaSuccess) e = cudaMallocHost(&p->h_split, slots * sizeof(ProdDesc));
+            if (e != cudaSuccess) return cuda_status(e);
+            p->split_digits = m;
+            p->split_slots = slots;
+            return SSMUL_OK;
+        }
     }
     return SSMUL_INVALID_ARG;
 }

@@ -55,6 +55,8 @@ struct ProdState {
     unsigned int timeout;
     unsigned int carry_ticket;
     unsigned long long maxw[RUNGS];    // bit pattern of a nonnegative double
+    unsigned int forced;               // split products: worst status of a part
+    unsigned int pad;
 };
 
 struct ProdDesc {
@@ -469,6 +471,7 @@ __device__ __forceinline__ int decide(const ProdState* st, int* rung) {
         if (st->unisolated[r] == 0) { status = SSMUL_OK; break; }
     }
     *rung = last < 0 ? 1 : last;
+    if (st->forced) status = int(st->forced);
     return st->timeout ? SSMUL_TIMEOUT : status;
 }
 
@@ -626,6 +629,35 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
         const uint32_t t = v[q] + c;
         if (k < nz) d.z[k] = uint8_t(t & 0xFFu);
         c = t >> 8;
+    }
+}
+
+// ---- products split into parts (past the isolation limit) -------------------
+//
+// A product whose operands are cut into parts a = sum_k a_k 256^{k m},
+// b = sum_l b_l 256^{l m} has the coefficients
+//   c_i = sum_{k,l} c(a_k, b_l)_{i - (k + l) m},
+// exact integer sums of the parts' isolated coefficients (Section 2.1's
+// product identity applied block-wise).  Each part runs the interval
+// convolution on its own; this kernel adds its coefficients into the
+// parent's array at offset (k + l) m and folds its outcome into the
+// parent's accumulators (the parts run one after another on one stream).
+__global__ void k_split_accumulate(const ProdDesc* part, int64_t* total, uint64_t shift,
+                                   ProdState* parent) {
+    const ProdDesc d = *part;
+    const int64_t L = int64_t(d.na) + d.nb - 1;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < L;
+         i += int64_t(gridDim.x) * blockDim.x)
+        total[shift + i] += d.coeff[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int rung;
+        const int status = decide(d.st, &rung);
+        parent->ran[rung] = 1u;
+        parent->unisolated[rung] += d.st->unisolated[rung];
+        parent->empty[rung] += d.st->empty[rung];
+        if (d.st->maxw[rung] > parent->maxw[rung]) parent->maxw[rung] = d.st->maxw[rung];
+        if (status != SSMUL_OK && unsigned(status) > parent->forced) parent->forced = unsigned(status);
+        if (d.st->timeout) parent->timeout = 1u;
     }
 }
 

@@ -107,9 +107,9 @@ def test_autotuned_geometry_is_exact(tmp_path):
 def test_fp32_router_option():
     a, b = synth.operand_pair(5, 40, 40)
     with Plan(64, 64, 0, abi.SSMUL_PREC_LADDER) as p:
-        s, r, z = p.mul(a, b)                       # 40 digits: above the default threshold
+        s, r, z = p.mul(a, b)                       # 80 digits: above the default threshold
         assert s == OK and r.precision_used == abi.SSMUL_PREC_FP64
-        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_MAX_DIGITS, 64) == OK
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_MAX_DIGITS, 100) == OK
         s, r, z = p.mul(a, b)                       # tried in binary32, escalated
         assert s == OK and np.array_equal(z, E.product(a, b))
         assert abi.ssmul_plan_set_option(p.h, 99, 1) == abi.SSMUL_INVALID_ARG
