@@ -74,8 +74,21 @@ Geom default_geom(int log_n) {
     return make_geom(log_n, log_n2, LOG_CTA_ELEMS);
 }
 
-int threads_for(int elems) {          // block_fft: nl * L / 8 threads
+int threads_for(int elems) {          // block_fft with 2 butterflies per thread
     int t = elems / 8;
+    if (t < 32) t = 32;
+    return t;
+}
+
+// radix-4 butterflies per thread the plan's launches use: one for the
+// binary64 types (half the registers, twice the warps to cover the binary64
+// pipe's latency), two for binary32
+template <typename V> constexpr int plan_bpt() { return 1; }
+template <> constexpr int plan_bpt<CI<float>>() { return 2; }
+
+template <typename V>
+int fft_threads(int elems) {          // block_fft: nl * L / (4 BPT) threads
+    int t = elems / (4 * plan_bpt<V>());
     if (t < 32) t = 32;
     return t;
 }
@@ -223,11 +236,12 @@ template <typename W> constexpr int kind_off() { return VTraits<typename ValOf<W
 
 template <typename T>
 ssmul_status set_smem_attrs() {
+    constexpr int B = plan_bpt<typename ValOf<T>::type>();
     const int big = 160 * 1024;
-    SS_TRY(cudaFuncSetAttribute(k_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_small<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_rows<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return SSMUL_OK;
 }
 
@@ -238,28 +252,29 @@ template <typename T>
 ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
                           int gate) {
     using V = typename ValOf<T>::type;
+    constexpr int B = plan_bpt<V>();
     const TwTable tw = p->tw();
     const int ko = kind_off<T>();
     if (g.small) {
         const int n = 1 << g.log_n;
         LaunchScope ls(p, SSMUL_K_SMALL_F32 + ko);
-        k_small<T><<<count, threads_for(n), n * sizeof(V), p->stream>>>(d_desc, tw, gate);
+        k_small<T, B><<<count, fft_threads<V>(n), n * sizeof(V), p->stream>>>(d_desc, tw, gate);
     } else {
         const int n1 = 1 << g.log_n1, n2 = 1 << g.log_n2;
         const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
         {
             LaunchScope ls(p, SSMUL_K_FWD_COLS_F32 + ko);
-            k_fwd_cols<T><<<dim3(n2 >> g.log_c1, count), threads_for(e1), e1 * sizeof(V),
+            k_fwd_cols<T, B><<<dim3(n2 >> g.log_c1, count), fft_threads<V>(e1), e1 * sizeof(V),
                             p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
         }
         {
             LaunchScope ls(p, SSMUL_K_ROWS_F32 + ko);
-            k_rows<T><<<dim3(n1 / 2 + 1, count), threads_for(2 * n2), 2 * n2 * sizeof(V),
+            k_rows<T, B><<<dim3(n1 / 2 + 1, count), fft_threads<V>(2 * n2), 2 * n2 * sizeof(V),
                         p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
         }
         {
             LaunchScope ls(p, SSMUL_K_INV_COLS_F32 + ko);
-            k_inv_cols<T><<<dim3((n2 / 2) >> g.log_c3, count), threads_for(e3),
+            k_inv_cols<T, B><<<dim3((n2 / 2) >> g.log_c3, count), fft_threads<V>(e3),
                             e3 * sizeof(V), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
                                                          g.log_c3, gate);
         }

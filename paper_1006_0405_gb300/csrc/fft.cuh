@@ -19,7 +19,9 @@
 //
 // Each step reads all its inputs into registers, synchronises the block,
 // then writes all its outputs in place: the block must hold every
-// butterfly of a step at once, i.e. nl * L / 4 <= 2 * blockDim.x.
+// butterfly of a step at once, i.e. nl * L / 4 <= BPT * blockDim.x, with
+// BPT butterflies per thread (1 or 2; with 1 a thread holds half the
+// registers, so more warps can cover the binary64 pipe's latency).
 #pragma once
 #include "value.cuh"
 
@@ -35,7 +37,7 @@ __device__ __forceinline__ void bfly4(V& a, V& b, V& c, V& d) {
     d = amc - jb;    // u = 3
 }
 
-template <typename V, int SIGN>
+template <typename V, int SIGN, int BPT = 2>
 __device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw) {
     const int L = 1 << logL;
     const int quarter_log = logL - 2;
@@ -44,11 +46,11 @@ __device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw
         const int m = 1 << (logn - 2);          // n / 4
         const int s = 1 << logs;
         const int nbf = nl << (logL - 2);       // butterflies in this step
-        V v[2][4];
-        int base[2], pp[2];
-        bool act[2];
+        V v[BPT][4];
+        int base[BPT], pp[BPT];
+        bool act[BPT];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < BPT; ++h) {
             const int b = threadIdx.x + h * blockDim.x;
             act[h] = b < nbf;
             if (act[h]) {
@@ -72,7 +74,7 @@ __device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw
         }
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < BPT; ++h) {
             if (act[h]) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) buf[base[h] + u * pp[h]] = v[h][u];

@@ -322,8 +322,10 @@ __device__ __forceinline__ void isolate_value(const Pt& v, int64_t j, const Prod
 
 // ---- k_small: the whole interval convolution of one product in one CTA -----
 
-// gate: bit mask of rungs whose decision makes this rung skip the product
-template <typename Tag>
+// gate: bit mask of rungs whose decision makes this rung skip the product;
+// BPT: radix-4 butterflies per thread in block_fft (the launch gives
+// nl * L / (4 BPT) threads)
+template <typename Tag, int BPT = 2>
 __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     using V = typename ValOf<Tag>::type;
     constexpr int RUNG = VTraits<V>::rung;
@@ -339,13 +341,13 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
         sm[j] = make_point<V>(re, im);
     }
     __syncthreads();
-    block_fft<V, +1>(sm, logN, 1, N, tw);
+    block_fft<V, +1, BPT>(sm, logN, 1, N, tw);
     pair_products(sm, 1, 0, logN);
     __syncthreads();
     const int rows[2] = {0, 0};
     pack_half(sm, 1, rows, 0, logN, tw);
     __syncthreads();
-    block_fft<V, -1>(sm, logN - 1, 1, N, tw);
+    block_fft<V, -1, BPT>(sm, logN - 1, 1, N, tw);
     IsoAcc acc;
     for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x)
         isolate_value(scale_pow2(sm[j], logN + 2), j, d, acc);
@@ -355,7 +357,7 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
 
 // ---- four-step kernels --------------------------------------------------------
 
-template <typename Tag>
+template <typename Tag, int BPT = 2>
 __global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
     using V = typename ValOf<Tag>::type;
@@ -375,7 +377,7 @@ __global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
         sm[(c << logN1) + j1] = make_point<V>(re, im);
     }
     __syncthreads();
-    block_fft<V, +1>(sm, logN1, C, N1, tw);
+    block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
         const int c = idx & (C - 1), k1 = idx >> logC;
@@ -387,7 +389,7 @@ __global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
     }
 }
 
-template <typename Tag>
+template <typename Tag, int BPT = 2>
 __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -406,12 +408,12 @@ __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, 
         sm[t] = Z[(size_t(rows[l]) << logN2) + k2];
     }
     __syncthreads();
-    block_fft<V, +1>(sm, logN2, nl, N2, tw);
+    block_fft<V, +1, BPT>(sm, logN2, nl, N2, tw);
     pair_products(sm, nl, k1, logN2);
     __syncthreads();
     pack_half(sm, nl, rows, logN1, logN2, tw);
     __syncthreads();
-    block_fft<V, -1>(sm, logN2 - 1, nl, N2, tw);
+    block_fft<V, -1, BPT>(sm, logN2 - 1, nl, N2, tw);
     const int logM = logN1 + logN2 - 1;
     for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
         const int l = t >> (logN2 - 1), j2 = t & (M2 - 1);
@@ -422,7 +424,7 @@ __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, 
     }
 }
 
-template <typename Tag>
+template <typename Tag, int BPT = 2>
 __global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
     using V = typename ValOf<Tag>::type;
@@ -440,7 +442,7 @@ __global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
         sm[(c << logN1) + k1] = W[(size_t(k1) << logM2) + j2_0 + c];
     }
     __syncthreads();
-    block_fft<V, -1>(sm, logN1, C, N1, tw);
+    block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
     IsoAcc acc;
     for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
