@@ -80,11 +80,10 @@ int threads_for(int elems) {          // block_fft with 2 butterflies per thread
     return t;
 }
 
-// radix-4 butterflies per thread the plan's launches use: one for the
-// binary64 types (half the registers, twice the warps to cover the binary64
-// pipe's latency), two for binary32
-template <typename V> constexpr int plan_bpt() { return 1; }
-template <> constexpr int plan_bpt<CI<float>>() { return 2; }
+// radix-4 butterflies per thread the plan's launches use: two (one
+// butterfly per thread halves the registers but measured slower on GB300,
+// and leaves too few registers at 1024 threads)
+template <typename V> constexpr int plan_bpt() { return 2; }
 
 template <typename V>
 int fft_threads(int elems) {          // block_fft: nl * L / (4 BPT) threads

@@ -85,8 +85,8 @@ constexpr float TW_MOD_UP = 1.00000012f;
 
 __device__ __forceinline__ Disc operator+(const Disc& a, const Disc& b) {
     Disc z;
-    z.x = __dadd_rn(a.x, b.x);
-    z.y = __dadd_rn(a.y, b.y);
+    z.x = add_rn(a.x, b.x);
+    z.y = add_rn(a.y, b.y);
     z.r = __fadd_ru(__fadd_ru(a.r, b.r), err2(z.x, z.y));
     z.pad = 0.f;
     return z;
@@ -94,8 +94,8 @@ __device__ __forceinline__ Disc operator+(const Disc& a, const Disc& b) {
 
 __device__ __forceinline__ Disc operator-(const Disc& a, const Disc& b) {
     Disc z;
-    z.x = __dsub_rn(a.x, b.x);
-    z.y = __dsub_rn(a.y, b.y);
+    z.x = sub_rn(a.x, b.x);
+    z.y = sub_rn(a.y, b.y);
     z.r = __fadd_ru(__fadd_ru(a.r, b.r), err2(z.x, z.y));
     z.pad = 0.f;
     return z;
@@ -110,9 +110,9 @@ __device__ __forceinline__ Disc conj(const Disc& a) { return {a.x, -a.y, a.r, 0.
 // x = RN(fma(ax, c, -RN(ay s))) errs by <= hu(t1) + hu(x), likewise y.
 __device__ __forceinline__ Disc mul_tw(const Disc& a, const DiscTw& w) {
     Disc z;
-    const double t1 = __dmul_rn(a.y, w.s);
+    const double t1 = mul_rn(a.y, w.s);
     z.x = __fma_rn(a.x, w.c, -t1);
-    const double t2 = __dmul_rn(a.y, w.c);
+    const double t2 = mul_rn(a.y, w.c);
     z.y = __fma_rn(a.x, w.s, t2);
     const float rnd = __fadd_ru(err2(t1, z.x), err2(t2, z.y));
     const float prop = __fmaf_ru(a.r, __fadd_ru(TW_MOD_UP, w.rho), __fmul_ru(mod_up(a.x, a.y), w.rho));
@@ -124,9 +124,9 @@ __device__ __forceinline__ Disc mul_tw(const Disc& a, const DiscTw& w) {
 // general product (pointwise step): |a b - a_c b_c| <= |a_c| rb + |b_c| ra + ra rb
 __device__ __forceinline__ Disc mul_ci(const Disc& a, const Disc& b) {
     Disc z;
-    const double t1 = __dmul_rn(a.y, b.y);
+    const double t1 = mul_rn(a.y, b.y);
     z.x = __fma_rn(a.x, b.x, -t1);
-    const double t2 = __dmul_rn(a.y, b.x);
+    const double t2 = mul_rn(a.y, b.x);
     z.y = __fma_rn(a.x, b.y, t2);
     const float rnd = __fadd_ru(err2(t1, z.x), err2(t2, z.y));
     const float ma = mod_up(a.x, a.y), mb = mod_up(b.x, b.y);
@@ -141,8 +141,8 @@ __device__ __forceinline__ Disc mul_ci(const Disc& a, const Disc& b) {
 __device__ __forceinline__ Disc scale_pow2(const Disc& a, int k) {
     const double s = ldexp(1.0, -k);
     Disc z;
-    z.x = __dmul_rn(a.x, s);
-    z.y = __dmul_rn(a.y, s);
+    z.x = mul_rn(a.x, s);
+    z.y = mul_rn(a.y, s);
     z.r = __fadd_ru(__fmul_ru(a.r, __int_as_float((127 - k) << 23)), err2(z.x, z.y));
     z.pad = 0.f;
     return z;
@@ -151,23 +151,23 @@ __device__ __forceinline__ Disc scale_pow2(const Disc& a, int k) {
 // ---- naive point arithmetic (unverified) -------------------------------------------
 
 __device__ __forceinline__ Pt operator+(const Pt& a, const Pt& b) {
-    return {__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)};
+    return {add_rn(a.x, b.x), add_rn(a.y, b.y)};
 }
 __device__ __forceinline__ Pt operator-(const Pt& a, const Pt& b) {
-    return {__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)};
+    return {sub_rn(a.x, b.x), sub_rn(a.y, b.y)};
 }
 __device__ __forceinline__ Pt mul_i(const Pt& a) { return {-a.y, a.x}; }
 __device__ __forceinline__ Pt mul_negi(const Pt& a) { return {a.y, -a.x}; }
 __device__ __forceinline__ Pt conj(const Pt& a) { return {a.x, -a.y}; }
 __device__ __forceinline__ Pt mul_tw(const Pt& a, const DiscTw& w) {
-    return {__fma_rn(a.x, w.c, -__dmul_rn(a.y, w.s)), __fma_rn(a.x, w.s, __dmul_rn(a.y, w.c))};
+    return {__fma_rn(a.x, w.c, -mul_rn(a.y, w.s)), __fma_rn(a.x, w.s, mul_rn(a.y, w.c))};
 }
 __device__ __forceinline__ Pt mul_ci(const Pt& a, const Pt& b) {
-    return {__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x))};
+    return {__fma_rn(a.x, b.x, -mul_rn(a.y, b.y)), __fma_rn(a.x, b.y, mul_rn(a.y, b.x))};
 }
 __device__ __forceinline__ Pt scale_pow2(const Pt& a, int k) {
     const double s = ldexp(1.0, -k);
-    return {__dmul_rn(a.x, s), __dmul_rn(a.y, s)};
+    return {mul_rn(a.x, s), mul_rn(a.y, s)};
 }
 
 }  // namespace ssm
