@@ -26,26 +26,16 @@ struct CI {
 };
 
 // ---- directed rounding --------------------------------------------------------
-//
-// Binary64 sums and products are issued as fused multiply-adds, a*1 + b and
-// a*b + 0: the exact value is the same, so the correctly rounded result is
-// the same (up to the sign of a zero result, which no bound depends on).  On
-// GB300 the binary64 pipe retires a directed fma at 2 per clock per SM but a
-// directed add or multiply at about 1.66 (measured).  The constants sit in
-// constant memory, so the compiler cannot fold the fma back into an add.
 
-static __constant__ double k_fma_one = 1.0;
-static __constant__ double k_fma_zero = 0.0;
-
-__device__ __forceinline__ double add_dn(double a, double b) { return __fma_rd(a, k_fma_one, b); }
-__device__ __forceinline__ double add_up(double a, double b) { return __fma_ru(a, k_fma_one, b); }
-__device__ __forceinline__ double sub_dn(double a, double b) { return __fma_rd(b, -k_fma_one, a); }
-__device__ __forceinline__ double sub_up(double a, double b) { return __fma_ru(b, -k_fma_one, a); }
-__device__ __forceinline__ double mul_dn(double a, double b) { return __fma_rd(a, b, k_fma_zero); }
-__device__ __forceinline__ double mul_up(double a, double b) { return __fma_ru(a, b, k_fma_zero); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __fma_rn(a, k_fma_one, b); }
-__device__ __forceinline__ double sub_rn(double a, double b) { return __fma_rn(b, -k_fma_one, a); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __fma_rn(a, b, k_fma_zero); }
+__device__ __forceinline__ double add_dn(double a, double b) { return __dadd_rd(a, b); }
+__device__ __forceinline__ double add_up(double a, double b) { return __dadd_ru(a, b); }
+__device__ __forceinline__ double sub_dn(double a, double b) { return __dsub_rd(a, b); }
+__device__ __forceinline__ double sub_up(double a, double b) { return __dsub_ru(a, b); }
+__device__ __forceinline__ double mul_dn(double a, double b) { return __dmul_rd(a, b); }
+__device__ __forceinline__ double mul_up(double a, double b) { return __dmul_ru(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double fma_dn(double a, double b, double c) { return __fma_rd(a, b, c); }
 __device__ __forceinline__ double fma_up(double a, double b, double c) { return __fma_ru(a, b, c); }
 
