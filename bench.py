@@ -40,16 +40,18 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--digits", type=int, default=75000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="time budget of the CPU oracle sample")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "disc64", "naive64"],
                     help="rung of the paper workload: binary64 rectangles (default), binary64 "
                          "discs, or the unverified naive transform")
+    ap.add_argument("--no-alternates", action="store_true",
+                    help="skip the extra lines for the other rungs (disc64, naive64)")
     ap.add_argument("--balanced", action="store_true",
                     help="balanced digits (the transforms carry digit - 128)")
     ap.add_argument("--workload", default="paper", choices=["paper", "sweep", "ladder", "uneven"],
@@ -151,7 +153,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -160,11 +162,15 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken between t0 and t1 (perf_counter
+        seconds; sampling lags by up to one period, so the window is widened
+        by 0.15 s at its end); all samples when no window is given."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -172,7 +178,12 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = [ln for t, ln in self.lines
+                 if t0 is None or (t0 <= t <= t1 + 0.15)]
+        if not lines and self.lines:
+            # nearest sample to the window
+            lines = [min(self.lines, key=lambda x: abs(x[0] - (t0 or 0)))[1]]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -187,6 +198,27 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- multi-rank aggregation -------------------------------------------------------
+
+def aggregate_ranks(step_seconds: float, verified: int, e2e_seconds: float, products: int,
+                    world: int, device):
+    """Whole-job numbers from every rank's own measurement (products are
+    independent: no collective on the data path, only these three numbers):
+    value = all verified products / the slowest rank's timed seconds,
+    e2e = all products / the slowest rank's end-to-end seconds per step."""
+    if world == 1:
+        return verified / step_seconds, products / e2e_seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([step_seconds, float(verified), e2e_seconds], dtype=torch.float64,
+                     device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return sm[1].item() / mx[0].item(), world * products / mx[2].item()
 
 
 # ---- CPU oracle ---------------------------------------------------------------
@@ -260,8 +292,9 @@ def run_ours(args):
     (a_pool, b_pool, a_off, b_off, z_off), dists = make_batch(rank, B, n)
     nz = 2 * n
     stream = torch.cuda.Stream(device=dev)
-    prec = {"fp64": abi.SSMUL_PREC_FP64, "disc64": abi.SSMUL_PREC_DISC64,
-            "naive64": abi.SSMUL_PREC_NAIVE64}[args.precision]
+    PRECS = {"fp64": abi.SSMUL_PREC_FP64, "disc64": abi.SSMUL_PREC_DISC64,
+             "naive64": abi.SSMUL_PREC_NAIVE64}
+    prec = PRECS[args.precision]
     plan = abi.ssmul_plan(n, n, B, prec, stream.cuda_stream)
     if args.balanced:
         abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
@@ -293,6 +326,7 @@ def run_ours(args):
         abi.ssmul_debug_kernel_stats(plan, True)        # reset; time kernels from here
         clocks = ClockSampler(local)
         clocks.start()
+        time.sleep(0.5)                                   # sampler running before timing
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -305,8 +339,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        wall = time.perf_counter() - t_wall
-        clk = clocks.stop()
+        t_end = time.perf_counter()
+        wall = t_end - t_wall
+        clk = clocks.stop(t_wall, t_end)
         _, kstats = abi.ssmul_debug_kernel_stats(plan, False)
         step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
 
@@ -355,22 +390,59 @@ def run_ours(args):
     hz_np = hz.numpy()
     e2e_ok = all(np.array_equal(hz_np[z_off[i]:z_off[i] + nz], expect[i]) for i in range(B))
 
+    # the other rungs on the same batch (context for the headline rung)
+    alternatives = {}
+    if world == 1 and not args.no_alternates:
+        for alt in ("fp64", "disc64", "naive64"):
+            if alt == args.precision:
+                continue
+            aplan = abi.ssmul_plan(n, n, B, PRECS[alt], stream.cuda_stream)
+            if args.balanced:
+                abi.ssmul_plan_set_option(aplan, abi.SSMUL_OPT_BALANCED, 1)
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    s_ = abi.ssmul_mul_batched(aplan, descs, da.data_ptr(), db.data_ptr(),
+                                               dz.data_ptr(), dres.data_ptr())
+                stream.synchronize()
+                abi.ssmul_debug_kernel_stats(aplan, True)
+                aev = []
+                for k in range(args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s_ = abi.ssmul_mul_batched(aplan, descs, da.data_ptr(), db.data_ptr(),
+                                               zs[k].data_ptr(), rs[k].data_ptr())
+                    e1.record(stream)
+                    aev.append((e0, e1))
+                stream.synchronize()
+                _, akst = abi.ssmul_debug_kernel_stats(aplan, False)
+            abi.ssmul_plan_destroy(aplan)
+            a_ok, a_w = 0, 0.0
+            for k in range(args.steps):
+                z = zs[k].cpu().numpy()
+                rr = (abi.ssmul_result * B)()
+                host = rs[k].cpu().numpy()
+                ctypes.memmove(rr, host.ctypes.data, res_bytes)
+                for i in range(B):
+                    if rr[i].status in (abi.SSMUL_OK, abi.SSMUL_UNVERIFIED) and \
+                            np.array_equal(z[z_off[i]:z_off[i] + nz], expect[i]):
+                        a_ok += 1
+                    a_w = max(a_w, rr[i].max_width)
+            a_t = sum(e0.elapsed_time(e1) for e0, e1 in aev) / 1e3
+            aops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length(), alt)
+            adom = max(aops, key=lambda kk: akst.get(kk, (0, 0.0))[1])
+            ala, ams = akst[adom]
+            aach = aops[adom] * B / (ams / ala * 1e-3) / 1e9 if ala else 0.0
+            alternatives[alt] = {
+                "value": a_ok / a_t, "unit": "multiplies/s", "ms_per_step": 1e3 * a_t / args.steps,
+                "verified": f"{a_ok}/{args.steps * B}", "max_width": a_w,
+                "status": "unverified digits (naive transform)" if alt == "naive64" else "verified",
+                "dominant_kernel": adom, "fp64_gops": aach}
+
     t_steps = sum(step_ms) / 1e3
-    local_rate = verified / t_steps
-    per_rank_time = t_steps
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([per_rank_time, float(verified), e2e_s], device=dev, dtype=torch.float64)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_verified = sm[1].item()
-        value = total_verified / mx[0].item()
-        e2e_value = world * B / mx[2].item() if e2e_ok else 0.0
-    else:
-        value = local_rate
-        e2e_value = B / e2e_s if e2e_ok else 0.0
+    value, e2e_value = aggregate_ranks(t_steps, verified, e2e_s, B, world, dev)
+    if not e2e_ok:
+        e2e_value = 0.0
 
     if rank == 0:
         # roofline of the dominant kernel: binary64 pipe (an ALU bound)
@@ -420,6 +492,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(a_pool.nbytes + b_pool.nbytes + ctypes.sizeof(descs)),
                     "d2h_bytes_per_step": int(B * nz + res_bytes)},
             "gpu_launches": int(gpu_launches),
+            "alternatives": alternatives,
             "kernel_ms_share": shares,
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "fp64 Gop/s", "frac": achieved / peak, "traffic": None,
