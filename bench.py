@@ -131,6 +131,17 @@ def kernel_ops(log_n: int, precision: str = "fp64") -> dict:
     return {f"k_fwd_cols<{tag}>": fwd, f"k_rows<{tag}>": rows, f"k_inv_cols<{tag}>": inv}
 
 
+# DRAM bytes per product of one launch of the dominant kernels, from the
+# ncu capture of profiles/fp64_kernels_75k_full.md and
+# profiles/disc_kernels_75k_full.md (16 products of 75k x 75k digits per
+# launch, spectra larger than L2): dram__bytes_read.sum + dram__bytes_write.sum
+# divided by 16.  Only valid for the 75k workload and these kernels.
+NCU_TRAFFIC_PER_PRODUCT = {
+    "k_rows<double>": (135.336448e6 + 35.300096e6) / 16,
+    "k_rows<disc>": (101.512960e6 + 18.267904e6) / 16,
+}
+
+
 def fp64_peak_gops(sm_mhz: float) -> float:
     """152 SMs x 2 binary64 operations per clock (the nominal 1.25 TFLOP/s
     counts an fma as 2 flops: 152 * 2 * 2 * 2.07 GHz)."""
@@ -495,7 +506,11 @@ def run_ours(args):
             "alternatives": alternatives,
             "kernel_ms_share": shares,
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "fp64 Gop/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "fp64 Gop/s", "frac": achieved / peak,
+                         "traffic": (NCU_TRAFFIC_PER_PRODUCT[dom] * B
+                                     if n == 75000 and dom in NCU_TRAFFIC_PER_PRODUCT else None),
+                         "traffic_note": "bytes per launch: ncu DRAM bytes of a 16-product launch "
+                                         "scaled to the B products of this launch",
                          "peak_note": "binary64 pipe: 152 SMs x 2 ops/clk at the median "
                                       "sampled SM clock (recipe unit counts and clocks)"},
             "cpu_baseline": cpu,
