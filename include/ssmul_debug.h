@@ -87,6 +87,19 @@ ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t plan, int enable, double* ms,
                                       unsigned long long* launches, int cap);
 
 /*
+ * Faults for tests of the failure paths, set on the host; nothing faults
+ * or traps the device.  kind 0: clear all.  kind 1: the enclosures rung
+ * `value` produces (0 binary32 rectangles, 1 binary64 rectangles, 2 discs,
+ * 3 points) are widened by 4 before isolation, so that rung cannot isolate
+ * and the ladder must escalate (the sets still contain the exact values).
+ * kind 2: carry tile `value` (4096 digits each) of every product never
+ * publishes its look-back word, so later tiles give up after their bounded
+ * wait (about a second) and the product reports SSMUL_TIMEOUT with its
+ * digits zero-filled.  Applies to the plan's later calls.
+ */
+ssmul_status ssmul_debug_set_fault(ssmul_plan_t plan, int kind, long long value);
+
+/*
  * The launch geometry the plan uses for transform length 2^log_n: the
  * four-step split (log2 N1, log2 N2) and log2 of the elements a column CTA
  * holds; for single-CTA lengths (N <= 4096) *log_n1 = 0 and the others are

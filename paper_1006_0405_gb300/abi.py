@@ -35,7 +35,7 @@ EXPORTS = (
     "ssmul_plan", "ssmul_plan_set_option", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
     "ssmul_plan_destroy", "ssmul_status_string",
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op", "ssmul_debug_disc_op",
-    "ssmul_debug_kernel_stats", "ssmul_debug_geometry",
+    "ssmul_debug_kernel_stats", "ssmul_debug_geometry", "ssmul_debug_set_fault",
 )
 
 # ssmul_option
@@ -106,6 +106,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_plan_set_option.restype = st
     L.ssmul_debug_geometry.argtypes = [vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
     L.ssmul_debug_geometry.restype = st
+    L.ssmul_debug_set_fault.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+    L.ssmul_debug_set_fault.restype = st
     L.ssmul_mul.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result)]
     L.ssmul_mul.restype = st
     L.ssmul_mul_host.argtypes = [vp, vp, sz, vp, sz, vp, ctypes.POINTER(ssmul_result)]
@@ -160,6 +162,10 @@ def ssmul_plan(max_na: int, max_nb: int, max_products: int = 0,
 
 def ssmul_plan_set_option(plan: int, option: int, value: int) -> int:
     return load().ssmul_plan_set_option(ctypes.c_void_p(plan), option, value)
+
+
+def ssmul_debug_set_fault(plan: int, kind: int, value: int = 0) -> int:
+    return load().ssmul_debug_set_fault(ctypes.c_void_p(plan), kind, value)
 
 
 def ssmul_debug_geometry(plan: int, log_n: int):

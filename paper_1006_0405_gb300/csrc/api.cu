@@ -151,6 +151,7 @@ struct ssmul_plan_s {
     size_t fp32_max_digits = FP32_MAX_DIGITS;
     bool balanced = false;
     uint32_t* pre = nullptr;            // balanced: digit prefix sums of one product
+    int fault_widen = 0, fault_stall = 0;   // ssmul_debug_set_fault
     // split products (SSMUL_OPT_SPLIT_DIGITS)
     size_t split_digits = 0;
     size_t split_slots = 0;
@@ -394,6 +395,8 @@ ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t*
     d.res = p->d_res + slot;
     d.iv = nullptr;
     d.balanced = p->balanced ? 1 : 0;
+    d.fault_widen = p->fault_widen;
+    d.fault_stall = p->fault_stall;
     d.pre_a = p->pre;
     d.pre_b = p->pre + pre_words(p->max_na);
     return d;
@@ -1097,6 +1100,23 @@ ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t p, int enable, double* ms,
     }
     p->timing = enable != 0;
     return SSMUL_OK;
+}
+
+ssmul_status ssmul_debug_set_fault(ssmul_plan_t p, int kind, long long value) {
+    if (!p) return SSMUL_INVALID_ARG;
+    graph_drop(p->cached);
+    switch (kind) {
+        case 0: p->fault_widen = 0; p->fault_stall = 0; return SSMUL_OK;
+        case 1:
+            if (value < 0 || value >= RUNGS) return SSMUL_INVALID_ARG;
+            p->fault_widen = int(value) + 1;
+            return SSMUL_OK;
+        case 2:
+            if (value < 0) return SSMUL_INVALID_ARG;
+            p->fault_stall = int(value) + 1;
+            return SSMUL_OK;
+    }
+    return SSMUL_INVALID_ARG;
 }
 
 ssmul_status ssmul_debug_geometry(ssmul_plan_t p, int log_n, int* log_n1, int* log_n2,

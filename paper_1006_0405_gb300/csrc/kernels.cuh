@@ -43,7 +43,7 @@ constexpr int LOG_CTA_ELEMS = 11;      // column kernels hold >= 2^11 elements
 constexpr int CARRY_TILE = 4096;       // digits per carry CTA
 constexpr int CARRY_THREADS = 256;
 constexpr int CARRY_PER_THREAD = CARRY_TILE / CARRY_THREADS;
-constexpr uint32_t SPIN_LIMIT = 1u << 22;   // bounded look-back polls
+constexpr uint32_t SPIN_LIMIT = 1u << 20;   // bounded look-back polls (about a second)
 
 // Per-product accumulators of one call, zeroed before the call; one entry
 // per rung (value.cuh: 0 binary32 rectangles, 1 binary64 rectangles,
@@ -75,6 +75,10 @@ struct ProdDesc {
     double* iv;                        // optional: coefficient enclosures (tests)
     uint32_t* pre_a;                   // balanced: prefix sums of a (see k_prefix)
     uint32_t* pre_b;                   // balanced: prefix sums of b
+    // test faults set on the host (0: off): rung + 1 whose enclosures are
+    // widened by 4 so it cannot isolate; carry tile + 1 that never publishes
+    int32_t fault_widen;
+    int32_t fault_stall;
 };
 
 // ---- balanced digits --------------------------------------------------------
@@ -239,9 +243,13 @@ struct IsoAcc {
 // a containment failure like an empty set.
 template <typename T>
 __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdDesc& d,
-                                            IsoAcc& acc) {
+                                            IsoAcc& acc, int rung) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
-    const double dl = double(lo), dh = double(hi);    // exact widening
+    double dl = double(lo), dh = double(hi);          // exact widening
+    if (d.fault_widen == rung + 1) {                  // test fault: still an enclosure
+        dl = __dsub_rd(dl, 4.0);
+        dh = __dadd_ru(dh, 4.0);
+    }
     const double w = __dsub_ru(dh, dl);
     acc.maxw = (w > acc.maxw || w != w) ? w : acc.maxw;
     if (idx < L) {
@@ -284,15 +292,16 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
 template <typename T>
 __device__ __forceinline__ void isolate_value(const CI<T>& v, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
-    isolate_one(v.rl, v.rh, 2 * j, d, acc);
-    isolate_one(v.il, v.ih, 2 * j + 1, d, acc);
+    constexpr int R = VTraits<CI<T>>::rung;
+    isolate_one(v.rl, v.rh, 2 * j, d, acc, R);
+    isolate_one(v.il, v.ih, 2 * j + 1, d, acc, R);
 }
 
 __device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
     const double r = double(v.r);
-    isolate_one(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, d, acc);
-    isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc);
+    isolate_one(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, d, acc, 2);
+    isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc, 2);
 }
 
 // the naive transform rounds to the nearest integer without any proof; its
@@ -540,9 +549,11 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
         // no unverified digit escapes: zero fill, publish a zero carry
         for (int q = 0; q < CARRY_PER_THREAD; ++q)
             if (k0 + q < nz) d.z[k0 + q] = 0;
-        if (threadIdx.x == 0) st_release(&d.flags[tile], LB_AGG | LB_INC);
+        if (threadIdx.x == 0 && d.fault_stall != int32_t(tile) + 1)
+            st_release(&d.flags[tile], LB_AGG | LB_INC);
         return;
     }
+    const bool publish = d.fault_stall != int32_t(tile) + 1;   // test fault
     // v_k for this thread's positions, and its (generate, propagate) summary
     uint32_t v[CARRY_PER_THREAD];
     uint32_t prev_hi = (k0 > 0) ? (digit_byte_sum(d.coeff, L, k0 - 1) >> 8) : 0u;
@@ -582,9 +593,10 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
         uint32_t cin = 0, err = 0;
         if (lane == 0) {
             if (tile == 0) {
-                st_release(&d.flags[0], LB_INC | (tg ? LB_G : 0u));
+                if (publish) st_release(&d.flags[0], LB_INC | (tg ? LB_G : 0u));
             } else {
-                st_release(&d.flags[tile], LB_AGG | (tg ? LB_G : 0u) | (tp ? LB_P : 0u));
+                if (publish)
+                    st_release(&d.flags[tile], LB_AGG | (tg ? LB_G : 0u) | (tp ? LB_P : 0u));
                 // look back: (rg, rp) summarises tiles pred+1 .. tile-1
                 bool rg = false, rp = true;
                 int64_t pred = int64_t(tile) - 1;
@@ -612,7 +624,8 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
                     --pred;
                 }
                 const bool cout = tg || (tp && cin);
-                st_release(&d.flags[tile], LB_AGG | LB_INC | (cout ? LB_G : 0u) | err);
+                if (publish)
+                    st_release(&d.flags[tile], LB_AGG | LB_INC | (cout ? LB_G : 0u) | err);
             }
         }
         __syncwarp();
