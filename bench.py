@@ -34,6 +34,19 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "verified multiplies/s at 75k base-256 digits"
+
+
+def _hbm_peak() -> float:
+    """Measured HBM copy bandwidth (GB/s) of the GB300s, else the
+    fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak()
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -140,6 +153,14 @@ NCU_TRAFFIC_PER_PRODUCT = {
     "k_rows<double>": (135.336448e6 + 35.300096e6) / 16,
     "k_rows<disc>": (101.512960e6 + 18.267904e6) / 16,
 }
+
+
+def algorithmic_bytes(n: int) -> float:
+    """HBM bytes one product's passes must move at minimum (binary64
+    rectangles, N = 2^18 for 75k digits): digits in, Z written and read,
+    W written and read, coefficients written and read, digits out."""
+    N = 1 << max(2, (2 * n - 2).bit_length())
+    return 2 * n + 32 * N * 2 + 16 * N * 2 + 8 * N * 2 + 2 * n
 
 
 def fp64_peak_gops(sm_mhz: float) -> float:
@@ -513,6 +534,11 @@ def run_ours(args):
                                          "scaled to the B products of this launch",
                          "peak_note": "binary64 pipe: 152 SMs x 2 ops/clk at the median "
                                       "sampled SM clock (recipe unit counts and clocks)"},
+            "hbm_roofline": {"achieved_gbs": value * algorithmic_bytes(n) / 1e9,
+                             "peak_gbs": HBM_PEAK_GBS,
+                             "frac": value * algorithmic_bytes(n) / 1e9 / HBM_PEAK_GBS,
+                             "note": "minimum pass traffic per product x products/s over the "
+                                     "measured copy bandwidth; the path is binary64-pipe bound"},
             "cpu_baseline": cpu,
             "clocks": clk,
             "wall_s": wall,

@@ -25,13 +25,13 @@
 
 namespace ssm {
 
-struct Disc {
+struct alignas(8) Disc {
     double x, y;     // centre
     float r;         // radius (rounded up)
     float pad;
 };
 
-struct Pt {
+struct alignas(16) Pt {
     double x, y;
 };
 

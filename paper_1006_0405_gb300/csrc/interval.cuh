@@ -20,8 +20,10 @@
 
 namespace ssm {
 
+// aligned to its size (16 B for binary32, 32 B for binary64) so that global
+// and shared memory accesses move it with 128-bit vector instructions
 template <typename T>
-struct CI {
+struct alignas(4 * sizeof(T)) CI {
     T rl, rh, il, ih;   // [rl, rh] + i [il, ih]
 };
 
