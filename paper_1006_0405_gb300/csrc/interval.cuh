@@ -56,6 +56,14 @@ __device__ __forceinline__ float fma_up(float a, float b, float c) { return __fm
 __device__ __forceinline__ bool neg(double x) { return __double2hiint(x) < 0; }
 __device__ __forceinline__ bool neg(float x) { return __float_as_int(x) < 0; }
 
+// Exact negation by flipping the sign bit on the integer pipe: for values
+// that are selected or stored rather than fed straight into an arithmetic
+// operation (where the compiler folds a negation into an operand modifier).
+__device__ __forceinline__ double flip(double x) {
+    return __hiloint2double(__double2hiint(x) ^ int(0x80000000), __double2loint(x));
+}
+__device__ __forceinline__ float flip(float x) { return __int_as_float(__float_as_int(x) ^ int(0x80000000)); }
+
 // ---- complex interval add / subtract (sharp, Section 2.5) --------------------
 
 template <typename T>
@@ -75,6 +83,11 @@ template <typename T>
 __device__ __forceinline__ CI<T> mul_negi(const CI<T>& a) { return {a.il, a.ih, -a.rh, -a.rl}; }
 template <typename T>
 __device__ __forceinline__ CI<T> conj(const CI<T>& a) { return {a.rl, a.rh, -a.ih, -a.il}; }
+// the same, with the negations on the integer pipe, for a value that is stored
+template <typename T>
+__device__ __forceinline__ CI<T> conj_flip(const CI<T>& a) {
+    return {a.rl, a.rh, flip(a.ih), flip(a.il)};
+}
 
 // ---- product by a twiddle ------------------------------------------------------
 //

@@ -209,7 +209,7 @@ __device__ void pair_products(V* sm, int nl, int row0, int logN2) {
         const V b2 = mul_negi(zk - czp);           // 2 B_k
         const V c4 = mul_ci(a2, b2);               // 4 C_k
         sm[k2] = c4;
-        if (pi != k2) sm[pi] = conj(c4);           // 4 C_{N-k}
+        if (pi != k2) sm[pi] = conj_flip(c4);      // 4 C_{N-k}
     }
 }
 

@@ -94,15 +94,12 @@ __device__ __forceinline__ DiscTw twiddle_disc(const TwTable& tw, uint32_t j) {
     const uint32_t r = j & (q - 1u);
     const bool refl = r > (q >> 1);
     const DiscTw e = tw.td[refl ? q - r : r];
-    double c = refl ? e.s : e.c, s = refl ? e.c : e.s;
-    double wc, ws;
-    switch (quad) {
-        case 0: wc = c; ws = s; break;
-        case 1: wc = -s; ws = c; break;
-        case 2: wc = -c; ws = -s; break;
-        default: wc = s; ws = -c; break;
-    }
-    return {wc, SIGN < 0 ? -ws : ws, e.rho, 0.f};
+    const double c = refl ? e.s : e.c, s = refl ? e.c : e.s;
+    const bool swap = quad & 1u;
+    const double wc = swap ? s : c, ws = swap ? c : s;
+    const bool negr = quad == 1u || quad == 2u;
+    const bool negi = (quad >= 2u) != (SIGN < 0);
+    return {negr ? flip(wc) : wc, negi ? flip(ws) : ws, e.rho, 0.f};
 }
 
 template <typename T>
@@ -124,16 +121,21 @@ __device__ __forceinline__ CI<T> twiddle(const TwTable& tw, uint32_t j) {
     const bool refl = r > (q >> 1);                  // past pi/4 inside the quadrant
     const uint32_t jj = refl ? q - r : r;
     const TwEntry<T> e = tw_ptr<T>(tw)[jj];
-    T cl = refl ? e.sl : e.cl, ch = refl ? e.sh : e.ch;
-    T sl = refl ? e.cl : e.sl, sh = refl ? e.ch : e.sh;
+    const T cl = refl ? e.sl : e.cl, ch = refl ? e.sh : e.ch;
+    const T sl = refl ? e.cl : e.sl, sh = refl ? e.ch : e.sh;
+    // a quarter turn maps (c, s) to (-s, c); the negations are sign-bit
+    // flips on the integer pipe (the interval -[l, h] is [-h, -l])
+    const bool swap = quad & 1u;                       // quadrants 1 and 3
+    const bool negr = quad == 1u || quad == 2u;        // real part negated
+    const bool negi = quad >= 2u;                      // imaginary part negated
+    T rl = swap ? sl : cl, rh = swap ? sh : ch;        // real part before sign
+    T il = swap ? cl : sl, ih = swap ? ch : sh;        // imaginary part before sign
     CI<T> w;
-    switch (quad) {
-        case 0: w = {cl, ch, sl, sh}; break;
-        case 1: w = {-sh, -sl, cl, ch}; break;        // (c, s) -> (-s, c)
-        case 2: w = {-ch, -cl, -sh, -sl}; break;
-        default: w = {sl, sh, -ch, -cl}; break;       // (c, s) -> (s, -c)
-    }
-    if (SIGN < 0) w = {w.rl, w.rh, -w.ih, -w.il};
+    w.rl = negr ? flip(rh) : rl;
+    w.rh = negr ? flip(rl) : rh;
+    const bool ni = negi != (SIGN < 0);                // the inverse conjugates
+    w.il = ni ? flip(ih) : il;
+    w.ih = ni ? flip(il) : ih;
     return w;
 }
 
