@@ -105,6 +105,7 @@ __device__ __forceinline__ Disc mul_i(const Disc& a) { return {-a.y, a.x, a.r, 0
 __device__ __forceinline__ Disc mul_negi(const Disc& a) { return {a.y, -a.x, a.r, 0.f}; }
 __device__ __forceinline__ Disc conj(const Disc& a) { return {a.x, -a.y, a.r, 0.f}; }
 __device__ __forceinline__ Disc conj_flip(const Disc& a) { return {a.x, flip(a.y), a.r, 0.f}; }
+__device__ __forceinline__ Disc mul_negi_flip(const Disc& a) { return {a.y, flip(a.x), a.r, 0.f}; }
 
 // a * w for a twiddle disc w = D(c + i s, rho):
 // |a w - a_c w_c| <= r (|w_c| + rho) + |a_c| rho, plus the centre rounding:
@@ -161,6 +162,7 @@ __device__ __forceinline__ Pt mul_i(const Pt& a) { return {-a.y, a.x}; }
 __device__ __forceinline__ Pt mul_negi(const Pt& a) { return {a.y, -a.x}; }
 __device__ __forceinline__ Pt conj(const Pt& a) { return {a.x, -a.y}; }
 __device__ __forceinline__ Pt conj_flip(const Pt& a) { return {a.x, flip(a.y)}; }
+__device__ __forceinline__ Pt mul_negi_flip(const Pt& a) { return {a.y, flip(a.x)}; }
 __device__ __forceinline__ Pt mul_tw(const Pt& a, const DiscTw& w) {
     return {__fma_rn(a.x, w.c, -mul_rn(a.y, w.s)), __fma_rn(a.x, w.s, mul_rn(a.y, w.c))};
 }

@@ -64,6 +64,18 @@ __device__ __forceinline__ double flip(double x) {
 }
 __device__ __forceinline__ float flip(float x) { return __int_as_float(__float_as_int(x) ^ int(0x80000000)); }
 
+// Exact binary64 value of an integer |v| < 2^31 built from its bits on the
+// integer pipe (an int-to-double conversion would occupy the binary64 pipe).
+__device__ __forceinline__ double int_to_double(int v) {
+    const unsigned int a = v < 0 ? 0u - unsigned(v) : unsigned(v);
+    const int e = 31 - __clz(int(a | 1u));                 // floor(log2 a) for a >= 1
+    const unsigned long long mant = (static_cast<unsigned long long>(a) << (52 - e)) &
+                                    ((1ull << 52) - 1ull);
+    const unsigned long long bits = (static_cast<unsigned long long>(1023 + e) << 52) | mant |
+                                    (v < 0 ? (1ull << 63) : 0ull);
+    return __longlong_as_double(a == 0u ? 0ll : static_cast<long long>(bits));
+}
+
 // ---- complex interval add / subtract (sharp, Section 2.5) --------------------
 
 template <typename T>
@@ -87,6 +99,10 @@ __device__ __forceinline__ CI<T> conj(const CI<T>& a) { return {a.rl, a.rh, -a.i
 template <typename T>
 __device__ __forceinline__ CI<T> conj_flip(const CI<T>& a) {
     return {a.rl, a.rh, flip(a.ih), flip(a.il)};
+}
+template <typename T>
+__device__ __forceinline__ CI<T> mul_negi_flip(const CI<T>& a) {
+    return {a.il, a.ih, flip(a.rh), flip(a.rl)};
 }
 
 // ---- product by a twiddle ------------------------------------------------------

@@ -206,7 +206,7 @@ __device__ void pair_products(V* sm, int nl, int row0, int logN2) {
         const V zk = sm[k2];
         const V czp = conj(sm[pi]);
         const V a2 = zk + czp;                     // 2 A_k
-        const V b2 = mul_negi(zk - czp);           // 2 B_k
+        const V b2 = mul_negi_flip(zk - czp);      // 2 B_k
         const V c4 = mul_ci(a2, b2);               // 4 C_k
         sm[k2] = c4;
         if (pi != k2) sm[pi] = conj_flip(c4);      // 4 C_{N-k}
@@ -233,14 +233,18 @@ __device__ void pack_half(V* sm, int nl, const int* rows, int logN1, int logN2,
 
 struct IsoAcc {
     unsigned int unisolated = 0, empty = 0;
-    double maxw = 0.0;
+    unsigned long long maxw_bits = 0;   // bit pattern of the largest width (>= 0)
 };
 
 // Decide coefficient `idx` from its enclosure [lo, hi]; L = na + nb - 1.
 // Decide coefficient idx from the enclosure [lo, hi] of c_idx (of c'_idx
 // with balanced digits, corrected here to c_idx); L = na + nb - 1.  The
-// exact coefficient is a nonnegative integer: an isolated negative value is
-// a containment failure like an empty set.
+// decision is integer arithmetic on kl = ceil(lo) and kh = floor(hi),
+// obtained by conversions to int64 that round up / round down and saturate:
+// one integer lies in [lo, hi] iff kl == kh.  A NaN converts to the most
+// negative value, and |k| >= 2^53 (an overflowed or infinite bound) is
+// never accepted.  The exact coefficient is a nonnegative integer: an
+// isolated negative value is a containment failure like an empty set.
 template <typename T>
 __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdDesc& d,
                                             IsoAcc& acc, int rung) {
@@ -250,26 +254,28 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
         dl = __dsub_rd(dl, 4.0);
         dh = __dadd_ru(dh, 4.0);
     }
-    const double w = __dsub_ru(dh, dl);
-    acc.maxw = (w > acc.maxw || w != w) ? w : acc.maxw;
+    const unsigned long long wb = (unsigned long long)__double_as_longlong(__dsub_ru(dh, dl));
+    acc.maxw_bits = wb > acc.maxw_bits ? wb : acc.maxw_bits;   // widths are >= 0 (or NaN)
+    const long long kl = __double2ll_ru(dl);
+    const long long kh = __double2ll_rd(dh);
+    constexpr long long KMAX = 1ll << 53;
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
         if (d.iv != nullptr) {
             d.iv[2 * idx] = __dadd_rd(dl, double(corr));
             d.iv[2 * idx + 1] = __dadd_ru(dh, double(corr));
         }
-        const double kl = ceil(dl), kh = floor(dh);
         int64_t v = 0;
-        if (kl == kh && fabs(kl) < 4.0e15 && int64_t(kl) + corr >= 0) {
-            v = int64_t(kl) + corr;
+        if (kl == kh && kl > -KMAX && kl < KMAX && kl + corr >= 0) {
+            v = kl + corr;
         } else if (kl < kh) {
             acc.unisolated++;
         } else {
-            acc.empty++;           // no integer, a negative one, or NaN
+            acc.empty++;           // no integer, a negative one, NaN or overflow
         }
         d.coeff[idx] = v;
     } else {
-        if (!(dl <= 0.0 && 0.0 <= dh)) acc.empty++;   // exact value is 0
+        if (!(kl <= 0 && kh >= 0)) acc.empty++;      // the exact value is 0
     }
 }
 
@@ -277,13 +283,13 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
     for (int o = 16; o > 0; o >>= 1) {
         acc.unisolated += __shfl_xor_sync(0xffffffffu, acc.unisolated, o);
         acc.empty += __shfl_xor_sync(0xffffffffu, acc.empty, o);
-        const double w = __shfl_xor_sync(0xffffffffu, acc.maxw, o);
-        acc.maxw = (w > acc.maxw || w != w) ? w : acc.maxw;
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, acc.maxw_bits, o);
+        acc.maxw_bits = w > acc.maxw_bits ? w : acc.maxw_bits;
     }
     if ((threadIdx.x & 31) == 0) {
         if (acc.unisolated) atomicAdd(&st->unisolated[rung], acc.unisolated);
         if (acc.empty) atomicAdd(&st->empty[rung], acc.empty);
-        atomicMax(&st->maxw[rung], (unsigned long long)__double_as_longlong(acc.maxw));
+        atomicMax(&st->maxw[rung], acc.maxw_bits);
     }
 }
 
@@ -311,7 +317,8 @@ __device__ __forceinline__ void naive_one(double v, int64_t idx, const ProdDesc&
     const int64_t L = int64_t(d.na) + d.nb - 1;
     const double k = rint(v);
     const double dist = fabs(v - k);
-    acc.maxw = (dist > acc.maxw || dist != dist) ? dist : acc.maxw;
+    const unsigned long long db = (unsigned long long)__double_as_longlong(dist);
+    acc.maxw_bits = db > acc.maxw_bits ? db : acc.maxw_bits;
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
         if (d.iv != nullptr) {

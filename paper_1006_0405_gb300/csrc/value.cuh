@@ -66,13 +66,14 @@ template <> __device__ __forceinline__ CI<float> make_point<CI<float>>(int re, i
     return {float(re), float(re), float(im), float(im)};
 }
 template <> __device__ __forceinline__ CI<double> make_point<CI<double>>(int re, int im) {
-    return {double(re), double(re), double(im), double(im)};
+    const double r = int_to_double(re), i = int_to_double(im);
+    return {r, r, i, i};
 }
 template <> __device__ __forceinline__ Disc make_point<Disc>(int re, int im) {
-    return {double(re), double(im), 0.f, 0.f};
+    return {int_to_double(re), int_to_double(im), 0.f, 0.f};
 }
 template <> __device__ __forceinline__ Pt make_point<Pt>(int re, int im) {
-    return {double(re), double(im)};
+    return {int_to_double(re), int_to_double(im)};
 }
 
 template <typename T>
