@@ -141,7 +141,7 @@ __device__ __forceinline__ Disc mul_ci(const Disc& a, const Disc& b) {
 // scaling by 2^-k (k >= 0): exact for normal results; the half-ulp terms
 // cover a result that falls into the subnormal range
 __device__ __forceinline__ Disc scale_pow2(const Disc& a, int k) {
-    const double s = ldexp(1.0, -k);
+    const double s = pow2_neg(k);
     Disc z;
     z.x = mul_rn(a.x, s);
     z.y = mul_rn(a.y, s);
@@ -170,7 +170,7 @@ __device__ __forceinline__ Pt mul_ci(const Pt& a, const Pt& b) {
     return {__fma_rn(a.x, b.x, -mul_rn(a.y, b.y)), __fma_rn(a.x, b.y, mul_rn(a.y, b.x))};
 }
 __device__ __forceinline__ Pt scale_pow2(const Pt& a, int k) {
-    const double s = ldexp(1.0, -k);
+    const double s = pow2_neg(k);
     return {mul_rn(a.x, s), mul_rn(a.y, s)};
 }
 

@@ -64,6 +64,11 @@ __device__ __forceinline__ double flip(double x) {
 }
 __device__ __forceinline__ float flip(float x) { return __int_as_float(__float_as_int(x) ^ int(0x80000000)); }
 
+// 2^-k for 0 <= k <= 1022, built from its exponent bits
+__device__ __forceinline__ double pow2_neg(int k) {
+    return __longlong_as_double(static_cast<long long>(1023 - k) << 52);
+}
+
 // Exact binary64 value of an integer |v| < 2^31 built from its bits on the
 // integer pipe (an int-to-double conversion would occupy the binary64 pipe).
 __device__ __forceinline__ double int_to_double(int v) {

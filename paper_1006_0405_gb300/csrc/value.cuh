@@ -76,9 +76,11 @@ template <> __device__ __forceinline__ Pt make_point<Pt>(int re, int im) {
     return {int_to_double(re), int_to_double(im)};
 }
 
-template <typename T>
-__device__ __forceinline__ CI<T> scale_pow2(const CI<T>& a, int k) {
-    return scale_out(a, T(ldexp(1.0, -k)));
+__device__ __forceinline__ CI<double> scale_pow2(const CI<double>& a, int k) {
+    return scale_out(a, pow2_neg(k));
+}
+__device__ __forceinline__ CI<float> scale_pow2(const CI<float>& a, int k) {
+    return scale_out(a, __int_as_float((127 - k) << 23));     // 2^-k, k <= 126
 }
 
 }  // namespace ssm
