@@ -68,15 +68,22 @@ typedef enum {
     SSMUL_PREC_NAIVE64 = 4,
     /* binary32 rectangles (small products), then binary64 discs, then
      * binary64 rectangles for what is still unisolated */
-    SSMUL_PREC_LADDER_DISC = 5
+    SSMUL_PREC_LADDER_DISC = 5,
+    /* circular containment sets whose centres are pairs of binary32 numbers
+     * (about 48 bits) with every rounding error bounded: the binary32 pipe
+     * does all the work; wider sets than SSMUL_PREC_DISC64 */
+    SSMUL_PREC_DISC32X2 = 6,
+    /* binary32 rectangles (small products), then double-binary32 discs,
+     * then binary64 discs, then binary64 rectangles */
+    SSMUL_PREC_LADDER_FAST = 7
 } ssmul_precision;
 
 /* Per-product outcome. */
 typedef struct {
     int32_t  status;            /* ssmul_status of this product */
     int32_t  precision_used;    /* ssmul_precision of the deciding rung:
-                                 * SSMUL_PREC_FP32, _FP64, _DISC64 or
-                                 * _NAIVE64 */
+                                 * SSMUL_PREC_FP32, _FP64, _DISC64,
+                                 * _DISC32X2 or _NAIVE64 */
     uint32_t fft_log2;          /* log2 of the transform length N */
     uint32_t n_unisolated;      /* coefficients whose set holds >= 2 integers */
     uint32_t n_empty;           /* coefficients whose set holds no integer */

@@ -27,7 +27,7 @@ ssmul_status ssmul_debug_twiddles(ssmul_plan_t plan, int f32, double* h_out, siz
 
 /*
  * One product as ssmul_mul, forced to a single precision rung (prec is
- * SSMUL_PREC_FP64, _FP32, _DISC64 or _NAIVE64), that also writes the enclosure of
+ * SSMUL_PREC_FP64, _FP32, _DISC64, _DISC32X2 or _NAIVE64), that also writes the enclosure of
  * every convolution coefficient c_i = sum_j a_j b_{i-j} (Section 2.1) to
  * d_iv (device memory, 2 * (na + nb - 1) doubles: lo_i, hi_i) after the
  * inverse transform and the division by N (Sections 2.3, 2.5).  For
@@ -60,19 +60,24 @@ ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double*
 ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y, double* d_out,
                                  size_t n);
 
+/*
+ * The same for discs with double-binary32 centres (SSMUL_PREC_DISC32X2):
+ * 5 doubles per operand (centre re as hi, lo; centre im as hi, lo; radius),
+ * every value a binary32 number, pairs normalised (|lo| <= 2^-24 |hi|).
+ * op 2 takes d_y as a twiddle disc (|centre| <= 1); op 4 scales by 2^-k
+ * with k = (int) d_y[5 i].
+ */
+ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y, double* d_out,
+                                  size_t n);
+
 /* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays):
- * one per transform kernel and rung (F32 / F64 rectangles, DISC discs,
- * NAIVE points), then the carry, the finalisation and the digit prefix
- * sums of balanced digits. */
+ * kernel * 5 + rung for the four transform kernels (rungs: 0 F32 and 1 F64
+ * rectangles, 2 DISC binary64 discs, 3 NAIVE points, 4 DISC32X2 discs),
+ * then the carry, the finalisation and the balanced-digit prefix sums. */
 enum {
-    SSMUL_K_SMALL_F32 = 0, SSMUL_K_SMALL_F64 = 1, SSMUL_K_SMALL_DISC = 2, SSMUL_K_SMALL_NAIVE = 3,
-    SSMUL_K_FWD_COLS_F32 = 4, SSMUL_K_FWD_COLS_F64 = 5, SSMUL_K_FWD_COLS_DISC = 6,
-    SSMUL_K_FWD_COLS_NAIVE = 7,
-    SSMUL_K_ROWS_F32 = 8, SSMUL_K_ROWS_F64 = 9, SSMUL_K_ROWS_DISC = 10, SSMUL_K_ROWS_NAIVE = 11,
-    SSMUL_K_INV_COLS_F32 = 12, SSMUL_K_INV_COLS_F64 = 13, SSMUL_K_INV_COLS_DISC = 14,
-    SSMUL_K_INV_COLS_NAIVE = 15,
-    SSMUL_K_CARRY = 16, SSMUL_K_FINALIZE = 17, SSMUL_K_PREFIX = 18,
-    SSMUL_KERNEL_KINDS = 19
+    SSMUL_K_SMALL = 0, SSMUL_K_FWD_COLS = 5, SSMUL_K_ROWS = 10, SSMUL_K_INV_COLS = 15,
+    SSMUL_K_CARRY = 20, SSMUL_K_FINALIZE = 21, SSMUL_K_PREFIX = 22,
+    SSMUL_KERNEL_KINDS = 23
 };
 
 /*
@@ -89,8 +94,8 @@ ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t plan, int enable, double* ms,
 /*
  * Faults for tests of the failure paths, set on the host; nothing faults
  * or traps the device.  kind 0: clear all.  kind 1: the enclosures rung
- * `value` produces (0 binary32 rectangles, 1 binary64 rectangles, 2 discs,
- * 3 points) are widened by 4 before isolation, so that rung cannot isolate
+ * `value` produces (0 binary32 rectangles, 1 binary64 rectangles, 2 binary64
+ * discs, 3 points, 4 double-binary32 discs) are widened by 4 before isolation, so that rung cannot isolate
  * and the ladder must escalate (the sets still contain the exact values).
  * kind 2: carry tile `value` (4096 digits each) of every product never
  * publishes its look-back word, so later tiles give up after their bounded

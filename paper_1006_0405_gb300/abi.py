@@ -29,12 +29,15 @@ SSMUL_PREC_LADDER = 2
 SSMUL_PREC_DISC64 = 3
 SSMUL_PREC_NAIVE64 = 4
 SSMUL_PREC_LADDER_DISC = 5
+SSMUL_PREC_DISC32X2 = 6
+SSMUL_PREC_LADDER_FAST = 7
 
 #: every symbol the headers declare
 EXPORTS = (
     "ssmul_plan", "ssmul_plan_set_option", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
     "ssmul_plan_destroy", "ssmul_status_string",
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op", "ssmul_debug_disc_op",
+    "ssmul_debug_ddisc_op",
     "ssmul_debug_kernel_stats", "ssmul_debug_geometry", "ssmul_debug_set_fault",
 )
 
@@ -47,8 +50,8 @@ SSMUL_OPT_SPLIT_DIGITS = 4
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")
-                     for r in ("float", "double", "disc", "naive")) + ("k_carry", "k_finalize",
-                                                                       "k_prefix")
+                     for r in ("float", "double", "disc", "naive", "disc32x2")) + (
+    "k_carry", "k_finalize", "k_prefix")
 
 
 class ssmul_result(ctypes.Structure):
@@ -129,6 +132,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_debug_ci_op.restype = st
     L.ssmul_debug_disc_op.argtypes = [ctypes.c_int, vp, vp, vp, sz]
     L.ssmul_debug_disc_op.restype = st
+    L.ssmul_debug_ddisc_op.argtypes = [ctypes.c_int, vp, vp, vp, sz]
+    L.ssmul_debug_ddisc_op.restype = st
     L.ssmul_debug_kernel_stats.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.ssmul_debug_kernel_stats.restype = st
     _lib = L
@@ -234,6 +239,11 @@ def ssmul_debug_mul_intervals(plan: int, d_a: int, na: int, d_b: int, nb: int, d
 def ssmul_debug_disc_op(op: int, d_x: int, d_y: int, d_out: int, n: int) -> int:
     return load().ssmul_debug_disc_op(op, ctypes.c_void_p(d_x), ctypes.c_void_p(d_y),
                                       ctypes.c_void_p(d_out), n)
+
+
+def ssmul_debug_ddisc_op(op: int, d_x: int, d_y: int, d_out: int, n: int) -> int:
+    return load().ssmul_debug_ddisc_op(op, ctypes.c_void_p(d_x), ctypes.c_void_p(d_y),
+                                       ctypes.c_void_p(d_out), n)
 
 
 def ssmul_debug_ci_op(op: int, f32: bool, d_x: int, d_y: int, d_out: int, n: int) -> int:

@@ -147,6 +147,7 @@ struct ssmul_plan_s {
     TwEntry<double>* t64 = nullptr;
     TwEntry<float>* t32 = nullptr;
     DiscTw* td = nullptr;
+    DDiscTw* tdd = nullptr;
     Geom geom[LOG_N_MAX + 1] = {};
     size_t fp32_max_digits = FP32_MAX_DIGITS;
     bool balanced = false;
@@ -189,7 +190,7 @@ struct ssmul_plan_s {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     double kt_ms[SSMUL_KERNEL_KINDS] = {};
     unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
-    TwTable tw() const { return TwTable{t64, t32, log_tab, td}; }
+    TwTable tw() const { return TwTable{t64, t32, log_tab, td, tdd}; }
 };
 
 namespace {
@@ -257,23 +258,23 @@ ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, con
     const int ko = kind_off<T>();
     if (g.small) {
         const int n = 1 << g.log_n;
-        LaunchScope ls(p, SSMUL_K_SMALL_F32 + ko);
+        LaunchScope ls(p, SSMUL_K_SMALL + ko);
         k_small<T, B><<<count, fft_threads<V>(n), n * sizeof(V), p->stream>>>(d_desc, tw, gate);
     } else {
         const int n1 = 1 << g.log_n1, n2 = 1 << g.log_n2;
         const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
         {
-            LaunchScope ls(p, SSMUL_K_FWD_COLS_F32 + ko);
+            LaunchScope ls(p, SSMUL_K_FWD_COLS + ko);
             k_fwd_cols<T, B><<<dim3(n2 >> g.log_c1, count), fft_threads<V>(e1), e1 * sizeof(V),
                             p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
         }
         {
-            LaunchScope ls(p, SSMUL_K_ROWS_F32 + ko);
+            LaunchScope ls(p, SSMUL_K_ROWS + ko);
             k_rows<T, B><<<dim3(n1 / 2 + 1, count), fft_threads<V>(2 * n2), 2 * n2 * sizeof(V),
                         p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
         }
         {
-            LaunchScope ls(p, SSMUL_K_INV_COLS_F32 + ko);
+            LaunchScope ls(p, SSMUL_K_INV_COLS + ko);
             k_inv_cols<T, B><<<dim3((n2 / 2) >> g.log_c3, count), fft_threads<V>(e3),
                             e3 * sizeof(V), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
                                                          g.log_c3, gate);
@@ -287,7 +288,8 @@ bool fp32_eligible(ssmul_plan_t p, size_t na, size_t nb, int log_n) {
 }
 
 bool uses_fp32(ssmul_precision prec) {
-    return prec == SSMUL_PREC_FP32 || prec == SSMUL_PREC_LADDER || prec == SSMUL_PREC_LADDER_DISC;
+    return prec == SSMUL_PREC_FP32 || prec == SSMUL_PREC_LADDER ||
+           prec == SSMUL_PREC_LADDER_DISC || prec == SSMUL_PREC_LADDER_FAST;
 }
 
 ssmul_status enqueue_rung_idx(ssmul_plan_t p, int rung, const ProdDesc* d_desc, int count,
@@ -296,6 +298,7 @@ ssmul_status enqueue_rung_idx(ssmul_plan_t p, int rung, const ProdDesc* d_desc, 
         case 0: return enqueue_rung<float>(p, d_desc, count, g, gate);
         case 1: return enqueue_rung<double>(p, d_desc, count, g, gate);
         case 2: return enqueue_rung<Disc>(p, d_desc, count, g, gate);
+        case 4: return enqueue_rung<DDisc>(p, d_desc, count, g, gate);
         default: return enqueue_rung<Pt>(p, d_desc, count, g, gate);
     }
 }
@@ -307,6 +310,8 @@ int later_rungs(ssmul_precision prec, int* out) {
         case SSMUL_PREC_DISC64: out[0] = 2; return 1;
         case SSMUL_PREC_NAIVE64: out[0] = 3; return 1;
         case SSMUL_PREC_LADDER_DISC: out[0] = 2; out[1] = 1; return 2;
+        case SSMUL_PREC_DISC32X2: out[0] = 4; return 1;
+        case SSMUL_PREC_LADDER_FAST: out[0] = 4; out[1] = 2; out[2] = 1; return 3;
         default: out[0] = 1; return 1;                 // FP64, LADDER
     }
 }
@@ -869,6 +874,7 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->t64);
     cudaFree(p->t32);
     cudaFree(p->td);
+    cudaFree(p->tdd);
     cudaFree(p->Z);
     cudaFree(p->W);
     cudaFree(p->coeff);
@@ -900,7 +906,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (!out) return SSMUL_INVALID_ARG;
     *out = nullptr;
     if (max_na == 0 || max_nb == 0) return SSMUL_INVALID_ARG;
-    if (int(prec) < SSMUL_PREC_FP64 || int(prec) > SSMUL_PREC_LADDER_DISC)
+    if (int(prec) < SSMUL_PREC_FP64 || int(prec) > SSMUL_PREC_LADDER_FAST)
         return SSMUL_INVALID_ARG;
     if (max_na > (size_t(1) << LOG_N_MAX) || max_nb > (size_t(1) << LOG_N_MAX))
         return SSMUL_TOO_LARGE;
@@ -932,6 +938,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (e == cudaSuccess) e = cudaMalloc(&p->t64, tab * sizeof(TwEntry<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->t32, tab * sizeof(TwEntry<float>));
     if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscTw));
+    if (e == cudaSuccess) e = cudaMalloc(&p->tdd, tab * sizeof(DDiscTw));
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->coeff, n * sizeof(int64_t));
@@ -965,11 +972,13 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if ((s = set_smem_attrs<float>()) != SSMUL_OK) return fail(s);
     if ((s = set_smem_attrs<Disc>()) != SSMUL_OK) return fail(s);
     if ((s = set_smem_attrs<Pt>()) != SSMUL_OK) return fail(s);
+    if ((s = set_smem_attrs<DDisc>()) != SSMUL_OK) return fail(s);
 
     const int threads = 256;
     const int blocks = int((tab + threads - 1) / threads);
     k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->t32, p->log_tab);
     k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->log_tab);
+    k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->td, p->tdd, p->log_tab);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaEventRecord(p->desc_free, p->stream)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
@@ -1159,7 +1168,7 @@ ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t p, const uint8_t* d_a, size_
                                        double* d_iv) {
     if (!p || !d_iv) return SSMUL_INVALID_ARG;
     if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32 && prec != SSMUL_PREC_DISC64 &&
-        prec != SSMUL_PREC_NAIVE64)
+        prec != SSMUL_PREC_NAIVE64 && prec != SSMUL_PREC_DISC32X2)
         return SSMUL_INVALID_ARG;
     return run_single(p, d_a, na, d_b, nb, d_z, h_res, prec, d_iv);
 }
@@ -1207,7 +1216,43 @@ __global__ void k_disc_op(int op, const double* x, const double* y, double* out,
     }
 }
 
+__global__ void k_ddisc_op(int op, const double* x, const double* y, double* out, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        const double* a5 = x + 5 * i;
+        const double* b5 = y + 5 * i;
+        const DDisc a{float(a5[0]), float(a5[1]), float(a5[2]), float(a5[3]), float(a5[4]), 0.f};
+        const DDisc b{float(b5[0]), float(b5[1]), float(b5[2]), float(b5[3]), float(b5[4]), 0.f};
+        DDisc r;
+        switch (op) {
+            case 0: r = a + b; break;
+            case 1: r = a - b; break;
+            case 2: r = mul_tw(a, DDiscTw{b.xh, b.xl, b.yh, b.yl, b.r, 0.f}); break;
+            case 3: r = mul_ci(a, b); break;
+            default: r = scale_pow2(a, int(b5[0])); break;
+        }
+        double* o = out + 5 * i;
+        o[0] = r.xh;
+        o[1] = r.xl;
+        o[2] = r.yh;
+        o[3] = r.yl;
+        o[4] = r.r;
+    }
+}
+
 }  // namespace
+
+extern "C" ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y,
+                                             double* d_out, size_t n) {
+    if (op < 0 || op > 4 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
+    if (n == 0) return SSMUL_OK;
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);
+    k_ddisc_op<<<blocks, threads>>>(op, d_x, d_y, d_out, n);
+    SS_TRY(cudaGetLastError());
+    SS_TRY(cudaDeviceSynchronize());
+    return SSMUL_OK;
+}
 
 extern "C" ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y,
                                             double* d_out, size_t n) {

@@ -1,0 +1,186 @@
+// ddisc.cuh -- circular containment sets with double-binary32 centres.
+//
+// On GB300 the binary32 pipe retires about 73 times as many operations as
+// the binary64 pipe, so the cheapest way to carry ~48 significant bits is a
+// pair of binary32 numbers x = h + l with |l| <= u |h| (u = 2^-24): the
+// error-free transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and
+// TwoProduct via a fused multiply-add give the exact error of a binary32 sum
+// and product.  A DDisc is the disc {z : |z - (x + i y)| <= r} with such
+// pair centres and a binary32 radius rounded upward, i.e. the circular sets
+// of the paper's Section 4 in another machine format; the enclosure
+// property holds because every operation adds to the radius a proved bound
+// of its own rounding error (derivations beside each rule):
+//
+//   pair sum     (s, e) = TwoSum(xh, yh); v = RN(e + RN(xl + yl));
+//                z = TwoSum(s, v).  |z - (x + y)| <= u |RN(xl + yl)| + u |v|
+//                <= u^2 (|xh| + |yh|) (2 + u) + u^2 (1 + u) (|xh| + |yh|)
+//                <= 3.0001 u^2 (|xh| + |yh|).
+//   pair product p = RN(xh wh); pe = fma(xh, wh, -p) (exact);
+//                r = RN(xl wh + RN(xh wl + pe)); z = FastTwoSum(p, r) (exact,
+//                |r| <= 3u|p|).  The dropped xl wl and the two roundings give
+//                |z - x w| <= 6.001 u^2 |xh| |wh|.
+//   complex product: each component is two pair products and one pair sum:
+//                error <= 9.01 u^2 (|axh| + |ayh|)(|bxh| + |byh|) for both
+//                components together.
+//
+// Each bound also gets ETA = 2^-126, far above the error of any operation
+// whose result falls into the binary32 subnormal range.  All arithmetic
+// uses explicit round-to-nearest intrinsics, so nothing is contracted or
+// reassociated.
+#pragma once
+#include <cstdint>
+#include "interval.cuh"
+#include "disc.cuh"
+
+namespace ssm {
+
+struct alignas(8) DDisc {
+    float xh, xl, yh, yl;   // centre (xh + xl) + i (yh + yl)
+    float r;                // radius (rounded up)
+    float pad;
+};
+
+struct alignas(8) DDiscTw {
+    float ch, cl, sh, sl;   // centre (ch + cl) + i (sh + sl)
+    float rho;
+    float pad;
+};
+
+constexpr float DD_U2 = 5.9604645e-8f * 5.9604645e-8f;      // u^2 = 2^-48 (exact)
+constexpr float DD_ADD = 3.0001f * DD_U2;
+constexpr float DD_MUL = 9.01f * DD_U2;
+constexpr float DD_ETA = 1.17549435e-38f;                     // 2^-126
+constexpr float DD_ONE_U = 1.00000024f;                      // >= 1 + 2u: |h + l| <= (1+u)|h|
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// exact when |a| >= |b| or a == 0
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void pair_add(float xh, float xl, float yh, float yl, float& zh,
+                                         float& zl) {
+    float s, e;
+    two_sum(xh, yh, s, e);
+    const float v = __fadd_rn(e, __fadd_rn(xl, yl));
+    two_sum(s, v, zh, zl);
+}
+
+__device__ __forceinline__ void pair_mul(float xh, float xl, float wh, float wl, float& zh,
+                                         float& zl) {
+    const float p = __fmul_rn(xh, wh);
+    const float pe = __fmaf_rn(xh, wh, -p);
+    const float q = __fmaf_rn(xh, wl, pe);
+    const float r = __fmaf_rn(xl, wh, q);
+    fast_two_sum(p, r, zh, zl);
+}
+
+// upper bound on |centre| from the high parts: (|xh| + |yh|)(1 + 2u)
+__device__ __forceinline__ float dd_mod_up(float xh, float yh) {
+    return __fmul_ru(__fadd_ru(fabsf(xh), fabsf(yh)), DD_ONE_U);
+}
+
+__device__ __forceinline__ DDisc operator+(const DDisc& a, const DDisc& b) {
+    DDisc z;
+    pair_add(a.xh, a.xl, b.xh, b.xl, z.xh, z.xl);
+    pair_add(a.yh, a.yl, b.yh, b.yl, z.yh, z.yl);
+    const float m = __fadd_ru(__fadd_ru(fabsf(a.xh), fabsf(b.xh)),
+                              __fadd_ru(fabsf(a.yh), fabsf(b.yh)));
+    z.r = __fadd_ru(__fadd_ru(a.r, b.r), __fmaf_ru(DD_ADD, m, 2.f * DD_ETA));
+    z.pad = 0.f;
+    return z;
+}
+
+__device__ __forceinline__ DDisc operator-(const DDisc& a, const DDisc& b) {
+    DDisc z;
+    pair_add(a.xh, a.xl, -b.xh, -b.xl, z.xh, z.xl);
+    pair_add(a.yh, a.yl, -b.yh, -b.yl, z.yh, z.yl);
+    const float m = __fadd_ru(__fadd_ru(fabsf(a.xh), fabsf(b.xh)),
+                              __fadd_ru(fabsf(a.yh), fabsf(b.yh)));
+    z.r = __fadd_ru(__fadd_ru(a.r, b.r), __fmaf_ru(DD_ADD, m, 2.f * DD_ETA));
+    z.pad = 0.f;
+    return z;
+}
+
+__device__ __forceinline__ DDisc mul_i(const DDisc& a) { return {-a.yh, -a.yl, a.xh, a.xl, a.r, 0.f}; }
+__device__ __forceinline__ DDisc mul_negi(const DDisc& a) { return {a.yh, a.yl, -a.xh, -a.xl, a.r, 0.f}; }
+__device__ __forceinline__ DDisc conj(const DDisc& a) { return {a.xh, a.xl, -a.yh, -a.yl, a.r, 0.f}; }
+__device__ __forceinline__ DDisc conj_flip(const DDisc& a) {
+    return {a.xh, a.xl, flip(a.yh), flip(a.yl), a.r, 0.f};
+}
+__device__ __forceinline__ DDisc mul_negi_flip(const DDisc& a) {
+    return {a.yh, a.yl, flip(a.xh), flip(a.xl), a.r, 0.f};
+}
+
+// centre of a * b and the bound of its rounding error
+__device__ __forceinline__ void pair_cmul(float axh, float axl, float ayh, float ayl, float bxh,
+                                          float bxl, float byh, float byl, DDisc& z,
+                                          float& err) {
+    float p1h, p1l, p2h, p2l, p3h, p3l, p4h, p4l;
+    pair_mul(axh, axl, bxh, bxl, p1h, p1l);     // ax bx
+    pair_mul(ayh, ayl, byh, byl, p2h, p2l);     // ay by
+    pair_mul(axh, axl, byh, byl, p3h, p3l);     // ax by
+    pair_mul(ayh, ayl, bxh, bxl, p4h, p4l);     // ay bx
+    pair_add(p1h, p1l, -p2h, -p2l, z.xh, z.xl);
+    pair_add(p3h, p3l, p4h, p4l, z.yh, z.yl);
+    const float ma = __fadd_ru(fabsf(axh), fabsf(ayh));
+    const float mb = __fadd_ru(fabsf(bxh), fabsf(byh));
+    err = __fmaf_ru(__fmul_ru(DD_MUL, ma), mb, 6.f * DD_ETA);
+}
+
+// a * w for a twiddle disc: |a w - a_c w_c| <= r (|w_c| + rho) + |a_c| rho
+__device__ __forceinline__ DDisc mul_tw(const DDisc& a, const DDiscTw& w) {
+    DDisc z;
+    float err;
+    pair_cmul(a.xh, a.xl, a.yh, a.yl, w.ch, w.cl, w.sh, w.sl, z, err);
+    const float prop = __fmaf_ru(a.r, __fadd_ru(TW_MOD_UP, w.rho), __fmul_ru(dd_mod_up(a.xh, a.yh), w.rho));
+    z.r = __fadd_ru(prop, err);
+    z.pad = 0.f;
+    return z;
+}
+
+// general product (pointwise step): |a b - a_c b_c| <= |a_c| rb + |b_c| ra + ra rb
+__device__ __forceinline__ DDisc mul_ci(const DDisc& a, const DDisc& b) {
+    DDisc z;
+    float err;
+    pair_cmul(a.xh, a.xl, a.yh, a.yl, b.xh, b.xl, b.yh, b.yl, z, err);
+    const float ma = dd_mod_up(a.xh, a.yh), mb = dd_mod_up(b.xh, b.yh);
+    const float prop = __fmaf_ru(ma, b.r, __fmaf_ru(mb, a.r, __fmul_ru(a.r, b.r)));
+    z.r = __fadd_ru(prop, err);
+    z.pad = 0.f;
+    return z;
+}
+
+// scaling by 2^-k (0 <= k <= 126): exact unless a part becomes subnormal
+__device__ __forceinline__ DDisc scale_pow2(const DDisc& a, int k) {
+    const float s = __int_as_float((127 - k) << 23);
+    DDisc z{__fmul_rn(a.xh, s), __fmul_rn(a.xl, s), __fmul_rn(a.yh, s), __fmul_rn(a.yl, s),
+            0.f, 0.f};
+    z.r = __fadd_ru(__fmul_ru(a.r, s), 4.f * DD_ETA);
+    return z;
+}
+
+// twiddle discs from the binary64 disc table: c = ch + cl with
+// ch = RN32(c), cl = RN32(c - ch) (c - ch exact in binary64), so
+// |c - ch - cl| <= u |cl| <= 2^-48 for |c| <= 1; the radius grows by the
+// two components' errors
+__global__ void k_ddisc_tw_gen(const DiscTw* td, DDiscTw* tdd, int log_n) {
+    const int64_t count = (int64_t(1) << log_n) / 8 + 1;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
+         j += int64_t(gridDim.x) * blockDim.x) {
+        const DiscTw e = td[j];
+        const float ch = __double2float_rn(e.c);
+        const float cl = __double2float_rn(e.c - double(ch));
+        const float sh = __double2float_rn(e.s);
+        const float sl = __double2float_rn(e.s - double(sh));
+        tdd[j] = {ch, cl, sh, sl, __fadd_ru(e.rho, 2.f * DD_U2 + DD_ETA), 0.f};
+    }
+}
+
+}  // namespace ssm

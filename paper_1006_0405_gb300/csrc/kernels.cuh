@@ -47,7 +47,7 @@ constexpr uint32_t SPIN_LIMIT = 1u << 20;   // bounded look-back polls (about a 
 
 // Per-product accumulators of one call, zeroed before the call; one entry
 // per rung (value.cuh: 0 binary32 rectangles, 1 binary64 rectangles,
-// 2 binary64 discs, 3 unverified points).
+// 2 binary64 discs, 3 unverified points, 4 double-binary32 discs).
 struct ProdState {
     unsigned int ran[RUNGS];
     unsigned int unisolated[RUNGS];
@@ -310,6 +310,15 @@ __device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, const Pr
     isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc, 2);
 }
 
+__device__ __forceinline__ void isolate_value(const DDisc& v, int64_t j, const ProdDesc& d,
+                                              IsoAcc& acc) {
+    const double r = double(v.r);
+    const double xl = __dadd_rd(double(v.xh), double(v.xl)), xh = __dadd_ru(double(v.xh), double(v.xl));
+    const double yl = __dadd_rd(double(v.yh), double(v.yl)), yh = __dadd_ru(double(v.yh), double(v.yl));
+    isolate_one(__dsub_rd(xl, r), __dadd_ru(xh, r), 2 * j, d, acc, 4);
+    isolate_one(__dsub_rd(yl, r), __dadd_ru(yh, r), 2 * j + 1, d, acc, 4);
+}
+
 // the naive transform rounds to the nearest integer without any proof; its
 // "width" statistic is the largest distance to that integer
 __device__ __forceinline__ void naive_one(double v, int64_t idx, const ProdDesc& d,
@@ -472,12 +481,13 @@ __global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
 
 // ---- the decision of a product ---------------------------------------------
 
-// The rungs that ran are read in ladder order (binary32 rectangles, binary64
-// discs, binary64 rectangles, unverified points): the first that isolated
+// The rungs that ran are read in ladder order (binary32 rectangles,
+// double-binary32 discs, binary64 discs, binary64 rectangles, unverified
+// points): the first that isolated
 // every coefficient, or found an empty set, decides; otherwise the last one
 // that ran reports its isolation failure.
 __device__ __forceinline__ int decide(const ProdState* st, int* rung) {
-    const int order[RUNGS] = {0, 2, 1, 3};
+    const int order[RUNGS] = {0, 4, 2, 1, 3};
     int last = -1;
     int status = SSMUL_ISOLATION_FAILED;
     for (int k = 0; k < RUNGS; ++k) {
@@ -498,6 +508,7 @@ __device__ __forceinline__ int rung_precision(int rung) {
         case 0: return SSMUL_PREC_FP32;
         case 2: return SSMUL_PREC_DISC64;
         case 3: return SSMUL_PREC_NAIVE64;
+        case 4: return SSMUL_PREC_DISC32X2;
         default: return SSMUL_PREC_FP64;
     }
 }

@@ -35,6 +35,7 @@ struct TwTable {
     const TwEntry<float>* t32;    // same, binary32
     int log_n;                    // log2 Ntab
     const DiscTw* td;             // same, as discs (centre, radius)
+    const struct DDiscTw* tdd;    // same, as discs with double-binary32 centres
 };
 
 __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n) {

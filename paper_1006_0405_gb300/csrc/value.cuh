@@ -6,6 +6,8 @@
 //               circular containment sets)
 //   Pt          rung 3: unverified round-to-nearest binary64 points (the
 //               naive transform of Section 3, a speed reference)
+//   DDisc       rung 4: midpoint-radius discs with double-binary32 centres
+//               (the circular sets on the binary32 pipe)
 //
 // Each type provides +, -, mul_i, mul_negi, conj, mul_tw (by its twiddle
 // type), mul_ci, scale_pow2, make_point, get_twiddle and the isolation of
@@ -13,17 +15,19 @@
 #pragma once
 #include "interval.cuh"
 #include "disc.cuh"
+#include "ddisc.cuh"
 #include "twiddle.cuh"
 
 namespace ssm {
 
-constexpr int RUNGS = 4;
+constexpr int RUNGS = 5;
 
 template <typename V> struct VTraits;
 template <> struct VTraits<CI<float>> { using Tw = CI<float>; static constexpr int rung = 0; };
 template <> struct VTraits<CI<double>> { using Tw = CI<double>; static constexpr int rung = 1; };
 template <> struct VTraits<Disc> { using Tw = DiscTw; static constexpr int rung = 2; };
 template <> struct VTraits<Pt> { using Tw = DiscTw; static constexpr int rung = 3; };
+template <> struct VTraits<DDisc> { using Tw = DDiscTw; static constexpr int rung = 4; };
 
 template <typename V, int SIGN>
 __device__ __forceinline__ typename VTraits<V>::Tw get_twiddle(const TwTable& tw, uint32_t j);
@@ -60,6 +64,35 @@ __device__ __forceinline__ DiscTw get_twiddle<Pt, -1>(const TwTable& tw, uint32_
     return twiddle_disc<-1>(tw, j);
 }
 
+// disc twiddle with double-binary32 centre: the symmetries of twiddle_disc
+template <int SIGN>
+__device__ __forceinline__ DDiscTw twiddle_ddisc(const TwTable& tw, uint32_t j) {
+    const int ln = tw.log_n;
+    j &= (1u << ln) - 1u;
+    const uint32_t q = 1u << (ln - 2);
+    const uint32_t quad = j >> (ln - 2);
+    const uint32_t r = j & (q - 1u);
+    const bool refl = r > (q >> 1);
+    const DDiscTw e = tw.tdd[refl ? q - r : r];
+    const float ch = refl ? e.sh : e.ch, cl = refl ? e.sl : e.cl;
+    const float sh = refl ? e.ch : e.sh, sl = refl ? e.cl : e.sl;
+    const bool swap = quad & 1u;
+    const float wch = swap ? sh : ch, wcl = swap ? sl : cl;
+    const float wsh = swap ? ch : sh, wsl = swap ? cl : sl;
+    const bool negr = quad == 1u || quad == 2u;
+    const bool negi = (quad >= 2u) != (SIGN < 0);
+    return {negr ? flip(wch) : wch, negr ? flip(wcl) : wcl, negi ? flip(wsh) : wsh,
+            negi ? flip(wsl) : wsl, e.rho, 0.f};
+}
+template <>
+__device__ __forceinline__ DDiscTw get_twiddle<DDisc, 1>(const TwTable& tw, uint32_t j) {
+    return twiddle_ddisc<1>(tw, j);
+}
+template <>
+__device__ __forceinline__ DDiscTw get_twiddle<DDisc, -1>(const TwTable& tw, uint32_t j) {
+    return twiddle_ddisc<-1>(tw, j);
+}
+
 // a digit pair as an exact point (small integers are exact in every type)
 template <typename V> __device__ __forceinline__ V make_point(int re, int im);
 template <> __device__ __forceinline__ CI<float> make_point<CI<float>>(int re, int im) {
@@ -74,6 +107,9 @@ template <> __device__ __forceinline__ Disc make_point<Disc>(int re, int im) {
 }
 template <> __device__ __forceinline__ Pt make_point<Pt>(int re, int im) {
     return {int_to_double(re), int_to_double(im)};
+}
+template <> __device__ __forceinline__ DDisc make_point<DDisc>(int re, int im) {
+    return {float(re), 0.f, float(im), 0.f, 0.f, 0.f};
 }
 
 __device__ __forceinline__ CI<double> scale_pow2(const CI<double>& a, int k) {

@@ -1,0 +1,148 @@
+"""Discs with double-binary32 centres (SSMUL_PREC_DISC32X2) and the fast
+ladder (SSMUL_PREC_LADDER_FAST) against exact rational arithmetic and the
+CPU oracle.  A pair-disc operation must contain the exact result for points
+spread over its operand discs; products must be bit-exact whenever the
+status is SSMUL_OK, and a product that does not isolate must say so."""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import exact as E
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1006_0405_gb300 import abi  # noqa: E402
+from tests.gpu_util import Plan, batched, dev  # noqa: E402
+
+OK = abi.SSMUL_OK
+UNIT = [(Fr(0), Fr(0)), (Fr(1), Fr(0)), (Fr(-1), Fr(0)), (Fr(0), Fr(1)), (Fr(0), Fr(-1)),
+        (Fr(3, 5), Fr(4, 5)), (Fr(-4, 5), Fr(3, 5)), (Fr(5, 13), Fr(-12, 13))]
+
+
+def _pairs_of(v):
+    h = v.astype(np.float32).astype(np.float64)
+    lo = (v - h).astype(np.float32).astype(np.float64)
+    return h, lo
+
+
+def _rand(rng, n, tw=False):
+    if tw:
+        ang = rng.uniform(0, 2 * np.pi, n)
+        x, y = np.cos(ang), np.sin(ang)
+        r = np.full(n, 2.0 ** -46)
+    else:
+        x = rng.standard_normal(n) * 10.0 ** rng.integers(-3, 8, n)
+        y = rng.standard_normal(n) * 10.0 ** rng.integers(-3, 8, n)
+        r = (np.abs(x) + np.abs(y)) * 10.0 ** rng.integers(-13, -4, n)
+        x[:3], y[:3], r[:3] = [0, 3, -7], [0, 0, 5], [0, 0, 1]
+    xh, xl = _pairs_of(x)
+    yh, yl = _pairs_of(y)
+    r = r.astype(np.float32).astype(np.float64)
+    return np.stack([xh, xl, yh, yl, r], 1)
+
+
+def _op(op, a, b):
+    da, db = dev(a.ravel()), dev(b.ravel())
+    out = torch.zeros_like(da)
+    assert abi.ssmul_debug_ddisc_op(op, da.data_ptr(), db.data_ptr(), out.data_ptr(), len(a)) == OK
+    return out.cpu().numpy().reshape(-1, 5)
+
+
+def _centre(row):
+    return (Fr(float(row[0])) + Fr(float(row[1])), Fr(float(row[2])) + Fr(float(row[3])),
+            Fr(float(row[4])))
+
+
+@pytest.mark.parametrize("op", [0, 1, 2, 3])
+def test_pair_disc_ops_contain_exact_results(op):
+    rng = np.random.default_rng(70 + op)
+    a = _rand(rng, 300)
+    b = _rand(rng, 300, tw=(op == 2))
+    out = _op(op, a, b)
+    for i in range(0, 300, 3):
+        ax, ay, ar = _centre(a[i])
+        bx, by, br = _centre(b[i])
+        ox, oy, orr = _centre(out[i])
+        # results stay normalised pairs
+        assert abs(out[i, 1]) <= 2.0 ** -24 * abs(out[i, 0]) and abs(out[i, 3]) <= 2.0 ** -24 * abs(out[i, 2])
+        for (p, q) in UNIT[:5]:
+            for (s, t) in UNIT[::2]:
+                u = (ax + ar * p, ay + ar * q)
+                v = (bx + br * s, by + br * t)
+                if op == 0:
+                    re, im = u[0] + v[0], u[1] + v[1]
+                elif op == 1:
+                    re, im = u[0] - v[0], u[1] - v[1]
+                else:
+                    re, im = u[0] * v[0] - u[1] * v[1], u[0] * v[1] + u[1] * v[0]
+                assert (re - ox) ** 2 + (im - oy) ** 2 <= orr * orr, (op, i)
+
+
+def test_pair_disc_scale_contains():
+    rng = np.random.default_rng(6)
+    a = _rand(rng, 100)
+    k = np.zeros((100, 5))
+    k[:, 0] = rng.integers(0, 26, 100)
+    out = _op(4, a, k)
+    for i in range(100):
+        s = Fr(1, 2 ** int(k[i, 0]))
+        ax, ay, ar = _centre(a[i])
+        ox, oy, orr = _centre(out[i])
+        for (p, q) in UNIT:
+            re, im = (ax + ar * p) * s, (ay + ar * q) * s
+            assert (re - ox) ** 2 + (im - oy) ** 2 <= orr * orr
+
+
+@pytest.mark.parametrize("na,nb", [(1, 1), (2, 3), (31, 33), (1000, 999), (2049, 2048), (9000, 7000),
+                                   (30000, 30000)])
+def test_pair_disc_products(na, nb):
+    a, b = synth.operand_pair(synth.SEED_BASE + 17 * na + nb, na, nb)
+    with Plan(na, nb, 0, abi.SSMUL_PREC_DISC32X2) as p:
+        s, r, z = p.mul(a, b)
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_BALANCED, 1) == OK
+        s2, r2, z2 = p.mul(a, b)
+    expect = E.product(a, b)
+    for st, rr, zz in ((s, r, z), (s2, r2, z2)):
+        assert st in (OK, abi.SSMUL_ISOLATION_FAILED), abi.status_string(st)
+        if st == OK:
+            assert rr.precision_used == abi.SSMUL_PREC_DISC32X2
+            assert np.array_equal(zz, expect)
+        else:
+            assert not zz.any()
+    if na * nb <= 9000 * 7000:
+        assert s == OK                                  # well inside the rung's reach
+
+
+@pytest.mark.parametrize("na,nb", [(300, 200), (4096, 4096), (20000, 20000)])
+def test_pair_disc_intervals_contain_exact(na, nb):
+    a, b = synth.operand_pair(synth.SEED_BASE + na, na, nb)
+    with Plan(na, nb) as p:
+        s, r, z, lo, hi = p.mul_intervals(a, b, abi.SSMUL_PREC_DISC32X2)
+    c = E.conv(a, b).astype(np.float64)
+    assert np.all((lo <= c) & (c <= hi))
+    assert r.n_empty == 0
+
+
+def test_fast_ladder_escalates_and_stays_exact():
+    pairs = [synth.operand_pair(synth.SEED_BASE + 800 + i, na, nb) for i, (na, nb) in
+             enumerate([(5, 4), (300, 200), (5000, 6000), (75000, 75000), (200000, 150000)])]
+    with Plan(200000, 200000, 8, abi.SSMUL_PREC_LADDER_FAST) as p:
+        used = []
+        for a, b in pairs:
+            s, r, z = p.mul(a, b)
+            assert s == OK, abi.status_string(s)
+            assert np.array_equal(z, E.product(a, b))
+            used.append(r.precision_used)
+        assert used[0] == abi.SSMUL_PREC_FP32
+        assert used[1] == abi.SSMUL_PREC_DISC32X2
+        s, res, digits = batched(p, pairs)
+        assert s == OK
+        for (a, b), rr, zz, u in zip(pairs, res, digits, used):
+            assert rr.status == OK and rr.precision_used == u
+            assert np.array_equal(zz, E.product(a, b))
