@@ -47,7 +47,7 @@ def test_plan_argument_checks_without_device():
     L = abi.load()
     assert L.ssmul_plan(None, 1, 1, 0, 0, None) == abi.SSMUL_INVALID_ARG
     assert L.ssmul_plan(ctypes.byref(h), 0, 1, 0, 0, None) == abi.SSMUL_INVALID_ARG
-    assert L.ssmul_plan(ctypes.byref(h), 1, 1, 0, 7, None) == abi.SSMUL_INVALID_ARG
+    assert L.ssmul_plan(ctypes.byref(h), 1, 1, 0, 99, None) == abi.SSMUL_INVALID_ARG
     assert L.ssmul_plan(ctypes.byref(h), 1 << 24, 1 << 24, 0, 0, None) == abi.SSMUL_TOO_LARGE
     assert L.ssmul_mul(None, None, 1, None, 1, None, None) == abi.SSMUL_INVALID_ARG
 
