@@ -60,9 +60,11 @@ def parse():
     ap.add_argument("--digits", type=int, default=75000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="time budget of the CPU oracle sample")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "disc64", "naive64"],
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "disc64", "naive64", "disc32x2", "ladder_fast"],
                     help="rung of the paper workload: binary64 rectangles (default), binary64 "
-                         "discs, or the unverified naive transform")
+                         "discs, the unverified naive transform, double-binary32 discs, or the "
+                         "fast ladder (double-binary32 discs, escalating to binary64)")
     ap.add_argument("--no-alternates", action="store_true",
                     help="skip the extra lines for the other rungs (disc64, naive64)")
     ap.add_argument("--balanced", action="store_true",
@@ -99,7 +101,12 @@ COSTS = {
     "fp64": dict(add=4, tw=8, mul=12, scale=4, iso=1),
     "disc64": dict(add=2, tw=4, mul=4, scale=2, iso=3),
     "naive64": dict(add=2, tw=4, mul=4, scale=2, iso=0),
+    # double-binary32 discs count binary32 operations: a complex add is two
+    # pair sums (2 x 14) and its radius (6); a complex product four pair
+    # products (4 x 7), two pair sums and its radius
+    "disc32x2": dict(add=34, tw=65, mul=67, scale=6, iso=0),
 }
+TAGS = {"fp64": "double", "disc64": "disc", "naive64": "naive", "disc32x2": "disc32x2"}
 
 
 def _fft_ops(logL: int, nl: int, c: dict) -> int:
@@ -129,7 +136,7 @@ def kernel_ops(log_n: int, precision: str = "fp64") -> dict:
     2 adds; pair product = 2 adds + 1 general product; packing = 3 adds +
     1 twiddle product; four-step twiddles; scaling and isolation."""
     c = COSTS[precision]
-    tag = {"fp64": "double", "disc64": "disc", "naive64": "naive"}[precision]
+    tag = TAGS[precision]
     n1l, n2l, c1l, c3l = geometry(log_n)
     N1, N2 = 1 << n1l, 1 << n2l
     M2 = N2 // 2
@@ -167,6 +174,11 @@ def fp64_peak_gops(sm_mhz: float) -> float:
     """152 SMs x 2 binary64 operations per clock (the nominal 1.25 TFLOP/s
     counts an fma as 2 flops: 152 * 2 * 2 * 2.07 GHz)."""
     return 152 * 2 * sm_mhz * 1e6 / 1e9
+
+
+def fp32_peak_gops(sm_mhz: float) -> float:
+    """152 SMs x 128 binary32 lanes per clock."""
+    return 152 * 128 * sm_mhz * 1e6 / 1e9
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -325,7 +337,8 @@ def run_ours(args):
     nz = 2 * n
     stream = torch.cuda.Stream(device=dev)
     PRECS = {"fp64": abi.SSMUL_PREC_FP64, "disc64": abi.SSMUL_PREC_DISC64,
-             "naive64": abi.SSMUL_PREC_NAIVE64}
+             "naive64": abi.SSMUL_PREC_NAIVE64, "disc32x2": abi.SSMUL_PREC_DISC32X2,
+             "ladder_fast": abi.SSMUL_PREC_LADDER_FAST}
     prec = PRECS[args.precision]
     plan = abi.ssmul_plan(n, n, B, prec, stream.cuda_stream)
     if args.balanced:
@@ -425,7 +438,7 @@ def run_ours(args):
     # the other rungs on the same batch (context for the headline rung)
     alternatives = {}
     if world == 1 and not args.no_alternates:
-        for alt in ("fp64", "disc64", "naive64"):
+        for alt in ("fp64", "disc64", "naive64", "disc32x2", "ladder_fast"):
             if alt == args.precision:
                 continue
             aplan = abi.ssmul_plan(n, n, B, PRECS[alt], stream.cuda_stream)
@@ -461,7 +474,8 @@ def run_ours(args):
                         a_ok += 1
                     a_w = max(a_w, rr[i].max_width)
             a_t = sum(e0.elapsed_time(e1) for e0, e1 in aev) / 1e3
-            aops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length(), alt)
+            amodel = "disc32x2" if alt == "ladder_fast" else alt
+            aops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length(), amodel)
             adom = max(aops, key=lambda kk: akst.get(kk, (0, 0.0))[1])
             ala, ams = akst[adom]
             aach = aops[adom] * B / (ams / ala * 1e-3) / 1e9 if ala else 0.0
@@ -469,7 +483,8 @@ def run_ours(args):
                 "value": a_ok / a_t, "unit": "multiplies/s", "ms_per_step": 1e3 * a_t / args.steps,
                 "verified": f"{a_ok}/{args.steps * B}", "max_width": a_w,
                 "status": "unverified digits (naive transform)" if alt == "naive64" else "verified",
-                "dominant_kernel": adom, "fp64_gops": aach}
+                "dominant_kernel": adom,
+                ("fp32_gops" if amodel == "disc32x2" else "fp64_gops"): aach}
 
     t_steps = sum(step_ms) / 1e3
     value, e2e_value = aggregate_ranks(t_steps, verified, e2e_s, B, world, dev)
@@ -478,13 +493,14 @@ def run_ours(args):
 
     if rank == 0:
         # roofline of the dominant kernel: binary64 pipe (an ALU bound)
-        ops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length(), args.precision)
+        model = "disc32x2" if args.precision == "ladder_fast" else args.precision
+        ops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length(), model)
         dom = max(ops, key=lambda k: kstats.get(k, (0, 0.0))[1])
         launches, ms = kstats[dom]
         # one launch covers all B products of the batch
         achieved = ops[dom] * B / (ms / launches * 1e-3) / 1e9 if launches else 0.0
         sm_mhz = clk.get("sm_mhz") or 2070.0
-        peak = fp64_peak_gops(sm_mhz)
+        peak = fp32_peak_gops(sm_mhz) if model == "disc32x2" else fp64_peak_gops(sm_mhz)
         total_ms = sum(v[1] for v in kstats.values())
         shares = {k: round(v[1] / total_ms, 4) for k, v in kstats.items() if v[0]}
         cpu = None
@@ -510,7 +526,7 @@ def run_ours(args):
             "balanced_digits": bool(args.balanced),
             "data": "synthetic",
             "config": {"workload": f"{n}x{n} base-256 digits, "
-                                   f"{ {'fp64': 'binary64 inf-sup intervals', 'disc64': 'binary64 midpoint-radius discs', 'naive64': 'unverified binary64 points'}[args.precision]}, "
+                                   f"{ {'fp64': 'binary64 inf-sup intervals', 'disc64': 'binary64 midpoint-radius discs', 'naive64': 'unverified binary64 points', 'disc32x2': 'double-binary32 midpoint-radius discs', 'ladder_fast': 'ladder of double-binary32 then binary64 discs'}[args.precision]}, "
                                    f"FFT length 2^18; batch of {B} per step ({B - 1} uniform "
                                    f"random, 1 all-0xFF) per GPU",
                        "batch_per_gpu": B, "digits": n, "precision": args.precision,
@@ -527,7 +543,8 @@ def run_ours(args):
             "alternatives": alternatives,
             "kernel_ms_share": shares,
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "fp64 Gop/s", "frac": achieved / peak,
+                         "unit": "fp32 Gop/s" if model == "disc32x2" else "fp64 Gop/s",
+                         "frac": achieved / peak,
                          "traffic": (NCU_TRAFFIC_PER_PRODUCT[dom] * B
                                      if n == 75000 and dom in NCU_TRAFFIC_PER_PRODUCT else None),
                          "traffic_note": "bytes per launch: ncu DRAM bytes of a 16-product launch "

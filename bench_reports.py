@@ -146,7 +146,8 @@ def sweep(args):
     abi.load()
     sizes = [(1 << k, 1 << k) for k in range(10, 23)] + [(1 << 20, 1 << 12)]
     prec = {"fp64": abi.SSMUL_PREC_FP64, "disc64": abi.SSMUL_PREC_DISC64,
-            "naive64": abi.SSMUL_PREC_NAIVE64}[args.precision]
+            "naive64": abi.SSMUL_PREC_NAIVE64, "disc32x2": abi.SSMUL_PREC_DISC32X2,
+            "ladder_fast": abi.SSMUL_PREC_LADDER_FAST}[args.precision]
     rows = []
     largest = None
     for na, nb in sizes:
@@ -211,14 +212,18 @@ def ladder(args):
     stream = torch.cuda.Stream()
     expect = _expected(batch)
     out = {"report": "ladder", "count": batch.count, "digits_total": int(batch.nz.sum())}
-    for name, prec in (("ladder_batched", abi.SSMUL_PREC_LADDER), ("fp64_batched", abi.SSMUL_PREC_FP64)):
+    for name, prec in (("ladder_batched", abi.SSMUL_PREC_LADDER), ("fp64_batched", abi.SSMUL_PREC_FP64),
+                       ("ladder_fast_batched", abi.SSMUL_PREC_LADDER_FAST)):
         plan = abi.ssmul_plan(max_n, max_n, batch.count, prec, stream.cuda_stream)
         abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 1)
         t = _time_batch(torch, plan, batch, 3, stream)
         rs, zs = batch.results(), batch.digits()
         ok = _verify_full(rs, zs, expect)
         fp32 = sum(1 for r in rs if r.status == 0 and r.precision_used == abi.SSMUL_PREC_FP32)
-        out[name] = {"s_per_batch": t, "verified": ok,
+        used = {}
+        for r in rs:
+            used[r.precision_used] = used.get(r.precision_used, 0) + 1
+        out[name] = {"s_per_batch": t, "verified": ok, "precision_used": used,
                      "verified_digits_per_s": float(sum(batch.nz[i] for i in range(batch.count)
                                                         if rs[i].status == 0)) / t,
                      "resolved_fp32": fp32, "fraction_fp32": fp32 / batch.count}
@@ -242,7 +247,24 @@ def uneven(args):
     max_n = int(max(na.max(), nb.max()))
     stream = torch.cuda.Stream()
     out = {"report": "uneven", "count": batch.count, "digits_total": int(batch.nz.sum())}
-    plan = abi.ssmul_plan(max_n, max_n, batch.count, abi.SSMUL_PREC_LADDER, stream.cuda_stream)
+    for name, prec in (("ladder_graph_batched", abi.SSMUL_PREC_LADDER),
+                       ("ladder_fast_graph_batched", abi.SSMUL_PREC_LADDER_FAST)):
+        out[name] = _uneven_batched(torch, abi, batch, max_n, prec, stream, seed)
+    el, outs = _one_at_a_time(torch, abi, batch, max_n, abi.SSMUL_PREC_FP64)
+    zs = batch.digits()
+    rs1 = [type("R", (), {"status": s})() for s, _ in outs]
+    ok1 = _verify_residues(batch, rs1, zs)
+    out["fp64_one_at_a_time"] = {"s_total": el,
+                                 "verified_digits_per_s": float(sum(batch.nz[i] for i in range(batch.count) if ok1[i])) / el,
+                                 "residue_verified": int(ok1.sum())}
+    for name in ("ladder_graph_batched", "ladder_fast_graph_batched"):
+        out["speedup_" + name] = out[name]["verified_digits_per_s"] / \
+            out["fp64_one_at_a_time"]["verified_digits_per_s"]
+    print(json.dumps(out), flush=True)
+
+
+def _uneven_batched(torch, abi, batch, max_n, prec, stream, seed):
+    plan = abi.ssmul_plan(max_n, max_n, batch.count, prec, stream.cuda_stream)
     abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 1)
     abi.ssmul_debug_kernel_stats(plan, False)
     t = _time_batch(torch, plan, batch, 3, stream)
@@ -258,22 +280,14 @@ def uneven(args):
         k = abi.status_string(r.status)
         statuses[k] = statuses.get(k, 0) + 1
     ver_digits = float(sum(batch.nz[i] for i in range(batch.count) if res_ok[i]))
-    out["ladder_graph_batched"] = {
+    used = {}
+    for r in rs:
+        used[r.precision_used] = used.get(r.precision_used, 0) + 1
+    return {
         "s_per_batch": t, "verified_digits_per_s": ver_digits / t, "statuses": statuses,
         "residue_verified": int(res_ok.sum()), "full_sample": len(sample),
-        "full_sample_verified": full_ok,
-        "resolved_fp32": sum(1 for r in rs if r.status == 0 and r.precision_used == abi.SSMUL_PREC_FP32),
+        "full_sample_verified": full_ok, "precision_used": used,
         "launches_per_batch": {k: v[0] // 4 for k, v in kst.items() if v[0]}}
-    el, outs = _one_at_a_time(torch, abi, batch, max_n, abi.SSMUL_PREC_FP64)
-    zs = batch.digits()
-    rs1 = [type("R", (), {"status": s})() for s, _ in outs]
-    ok1 = _verify_residues(batch, rs1, zs)
-    out["fp64_one_at_a_time"] = {"s_total": el,
-                                 "verified_digits_per_s": float(sum(batch.nz[i] for i in range(batch.count) if ok1[i])) / el,
-                                 "residue_verified": int(ok1.sum())}
-    out["speedup_digits_per_s"] = out["ladder_graph_batched"]["verified_digits_per_s"] / \
-        out["fp64_one_at_a_time"]["verified_digits_per_s"]
-    print(json.dumps(out), flush=True)
 
 
 def run(args):
