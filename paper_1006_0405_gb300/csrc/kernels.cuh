@@ -539,17 +539,20 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 // bit 2 generate / carry-out, bit 3 propagate, bit 4 timed out upstream
 constexpr uint32_t LB_AGG = 1u, LB_INC = 2u, LB_G = 4u, LB_P = 8u, LB_ERR = 16u;
 
-__device__ __forceinline__ uint32_t digit_byte_sum(const int64_t* c, int64_t L, int64_t k) {
+// byte sum u_k of digit position k from the coefficients staged in shared
+// memory: sc[i] holds c[k0_tile - CARRY_HALO + i]
+constexpr int CARRY_HALO = 8;
+
+__device__ __forceinline__ uint32_t digit_byte_sum_s(const int64_t* sc, int rel) {
     uint32_t u = 0;
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-        const int64_t i = k - t;
-        if (i >= 0 && i < L) u += uint32_t((uint64_t(c[i]) >> (8 * t)) & 0xFFu);
-    }
+    for (int t = 0; t < 6; ++t)
+        u += uint32_t((uint64_t(sc[CARRY_HALO + rel - t]) >> (8 * t)) & 0xFFu);
     return u;
 }
 
 __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) {
+    __shared__ int64_t s_c[CARRY_TILE + CARRY_HALO];
     __shared__ uint32_t s_tile, s_status, s_wA[CARRY_THREADS / 32], s_wB[CARRY_THREADS / 32];
     __shared__ uint32_t s_warp_cin[CARRY_THREADS / 32];
     const ProdDesc d = descs[blockIdx.y];
@@ -572,14 +575,22 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
         return;
     }
     const bool publish = d.fault_stall != int32_t(tile) + 1;   // test fault
+    // stage c[tile start - CARRY_HALO .. tile end) with coalesced loads
+    const int64_t kt = int64_t(tile) * CARRY_TILE;
+    for (int i = threadIdx.x; i < CARRY_TILE + CARRY_HALO; i += CARRY_THREADS) {
+        const int64_t idx = kt - CARRY_HALO + i;
+        s_c[i] = (idx >= 0 && idx < L) ? d.coeff[idx] : 0;
+    }
+    __syncthreads();
     // v_k for this thread's positions, and its (generate, propagate) summary
+    const int rel0 = int(k0 - kt);
     uint32_t v[CARRY_PER_THREAD];
-    uint32_t prev_hi = (k0 > 0) ? (digit_byte_sum(d.coeff, L, k0 - 1) >> 8) : 0u;
+    uint32_t prev_hi = (k0 > 0) ? (digit_byte_sum_s(s_c, rel0 - 1) >> 8) : 0u;
     bool G = false, P = true;
 #pragma unroll
     for (int q = 0; q < CARRY_PER_THREAD; ++q) {
         const int64_t k = k0 + q;
-        const uint32_t u = (k < nz) ? digit_byte_sum(d.coeff, L, k) : 0u;
+        const uint32_t u = (k < nz) ? digit_byte_sum_s(s_c, rel0 + q) : 0u;
         v[q] = (u & 0xFFu) + prev_hi;
         prev_hi = u >> 8;
         const bool g = v[q] >= 256u, p = v[q] == 255u;
