@@ -620,42 +620,54 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
         const bool tg = (ts >> NW) & 1u;
         const bool tp = WA == ((1u << NW) - 1u) && WB == 0u;
         uint32_t cin = 0, err = 0;
-        if (lane == 0) {
-            if (tile == 0) {
-                if (publish) st_release(&d.flags[0], LB_INC | (tg ? LB_G : 0u));
-            } else {
-                if (publish)
-                    st_release(&d.flags[tile], LB_AGG | (tg ? LB_G : 0u) | (tp ? LB_P : 0u));
-                // look back: (rg, rp) summarises tiles pred+1 .. tile-1
-                bool rg = false, rp = true;
-                int64_t pred = int64_t(tile) - 1;
-                while (true) {
-                    uint32_t f = 0;
+        if (tile == 0) {
+            if (lane == 0 && publish) st_release(&d.flags[0], LB_INC | (tg ? LB_G : 0u));
+        } else {
+            if (lane == 0 && publish)
+                st_release(&d.flags[tile], LB_AGG | (tg ? LB_G : 0u) | (tp ? LB_P : 0u));
+            // warp-wide look-back: lane i polls tile (base - i); the closest
+            // tile with an inclusive carry ends the walk, and the aggregates
+            // of the tiles before it (nearest first) fold into (rg, rp)
+            bool rg = false, rp = true;
+            int64_t base = int64_t(tile) - 1;
+            bool done = false;
+            while (!done) {
+                const int64_t t = base - lane;
+                uint32_t f = LB_INC;                  // before tile 0: carry 0
+                if (t >= 0) {
                     uint32_t it = 0;
                     for (; it < SPIN_LIMIT; ++it) {
-                        f = ld_acquire(&d.flags[pred]);
+                        f = ld_acquire(&d.flags[t]);
                         if (f & (LB_AGG | LB_INC)) break;
                         __nanosleep(64);
                     }
                     if (it == SPIN_LIMIT) {
-                        err = LB_ERR;
+                        f = LB_INC | LB_ERR;          // gave up: carry 0, flagged
                         atomicExch(&d.st->timeout, 1u);
-                        break;
                     }
-                    err |= (f & LB_ERR);
-                    if (f & LB_INC) {
-                        cin = (rg || (rp && (f & LB_G))) ? 1u : 0u;
-                        break;
-                    }
-                    const bool pg = f & LB_G, pp = f & LB_P;
+                }
+                const uint32_t inc = __ballot_sync(0xffffffffu, (f & LB_INC) != 0u);
+                const uint32_t gm = __ballot_sync(0xffffffffu, (f & LB_G) != 0u);
+                const uint32_t pm = __ballot_sync(0xffffffffu, (f & LB_P) != 0u);
+                const uint32_t em = __ballot_sync(0xffffffffu, (f & LB_ERR) != 0u);
+                const int j = inc ? __ffs(int(inc)) - 1 : 32;
+                for (int i = 0; i < j; ++i) {
+                    const bool pg = (gm >> i) & 1u, pp = (pm >> i) & 1u;
                     rg = rg || (rp && pg);
                     rp = rp && pp;
-                    --pred;
                 }
-                const bool cout = tg || (tp && cin);
-                if (publish)
-                    st_release(&d.flags[tile], LB_AGG | LB_INC | (cout ? LB_G : 0u) | err);
+                if (j < 32) {
+                    cin = (rg || (rp && ((gm >> j) & 1u))) ? 1u : 0u;
+                    err |= (em & ((2u << j) - 1u)) ? LB_ERR : 0u;
+                    done = true;
+                } else {
+                    err |= em ? LB_ERR : 0u;
+                    base -= 32;
+                }
             }
+            const bool cout = tg || (tp && cin);
+            if (lane == 0 && publish)
+                st_release(&d.flags[tile], LB_AGG | LB_INC | (cout ? LB_G : 0u) | err);
         }
         __syncwarp();
         cin = __shfl_sync(0xffffffffu, cin, 0);
