@@ -552,7 +552,12 @@ __device__ __forceinline__ uint32_t digit_byte_sum_s(const int64_t* sc, int rel)
 }
 
 __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) {
+    // coefficients of the tile (later reused for its output digits) and the
+    // byte sums u_k, padded by one entry per 16 so that a thread's 16
+    // consecutive entries fall into distinct banks
     __shared__ int64_t s_c[CARRY_TILE + CARRY_HALO];
+    __shared__ uint16_t s_u[CARRY_TILE + CARRY_TILE / 16];
+    __shared__ uint32_t s_uprev;
     __shared__ uint32_t s_tile, s_status, s_wA[CARRY_THREADS / 32], s_wB[CARRY_THREADS / 32];
     __shared__ uint32_t s_warp_cin[CARRY_THREADS / 32];
     const ProdDesc d = descs[blockIdx.y];
@@ -582,15 +587,21 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
         s_c[i] = (idx >= 0 && idx < L) ? d.coeff[idx] : 0;
     }
     __syncthreads();
+    // byte sums u_k, one position per thread at a time (consecutive lanes,
+    // consecutive coefficients)
+    for (int kr = threadIdx.x; kr < CARRY_TILE; kr += CARRY_THREADS)
+        s_u[kr + (kr >> 4)] = uint16_t((kt + kr < nz) ? digit_byte_sum_s(s_c, kr) : 0u);
+    if (threadIdx.x == 0) s_uprev = (kt > 0) ? digit_byte_sum_s(s_c, -1) : 0u;
+    __syncthreads();
     // v_k for this thread's positions, and its (generate, propagate) summary
     const int rel0 = int(k0 - kt);
     uint32_t v[CARRY_PER_THREAD];
-    uint32_t prev_hi = (k0 > 0) ? (digit_byte_sum_s(s_c, rel0 - 1) >> 8) : 0u;
+    uint32_t prev_hi = (rel0 == 0) ? (s_uprev >> 8)
+                                   : (uint32_t(s_u[(rel0 - 1) + ((rel0 - 1) >> 4)]) >> 8);
     bool G = false, P = true;
 #pragma unroll
     for (int q = 0; q < CARRY_PER_THREAD; ++q) {
-        const int64_t k = k0 + q;
-        const uint32_t u = (k < nz) ? digit_byte_sum_s(s_c, rel0 + q) : 0u;
+        const uint32_t u = s_u[(rel0 + q) + ((rel0 + q) >> 4)];
         v[q] = (u & 0xFFu) + prev_hi;
         prev_hi = u >> 8;
         const bool g = v[q] >= 256u, p = v[q] == 255u;
@@ -679,13 +690,18 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
     const uint32_t wcin = s_warp_cin[warp];
     const uint32_t carries = uint32_t((uint64_t(A) + uint64_t(B) + wcin) ^ A ^ B);
     uint32_t c = (carries >> lane) & 1u;
+    // digits staged in shared memory (the coefficients are no longer
+    // needed), then written with consecutive lanes on consecutive bytes
+    uint8_t* s_z = reinterpret_cast<uint8_t*>(s_c);
 #pragma unroll
     for (int q = 0; q < CARRY_PER_THREAD; ++q) {
-        const int64_t k = k0 + q;
         const uint32_t t = v[q] + c;
-        if (k < nz) d.z[k] = uint8_t(t & 0xFFu);
+        s_z[rel0 + q] = uint8_t(t & 0xFFu);
         c = t >> 8;
     }
+    __syncthreads();
+    for (int kr = threadIdx.x; kr < CARRY_TILE; kr += CARRY_THREADS)
+        if (kt + kr < nz) d.z[kt + kr] = s_z[kr];
 }
 
 // ---- products split into parts (past the isolation limit) -------------------
