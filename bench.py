@@ -521,7 +521,7 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64",
+            "dtype": {"disc32x2": "f32", "ladder_fast": "f32+f64"}.get(args.precision, "f64"),
             "precision": args.precision,
             "balanced_digits": bool(args.balanced),
             "data": "synthetic",
@@ -549,13 +549,17 @@ def run_ours(args):
                                      if n == 75000 and dom in NCU_TRAFFIC_PER_PRODUCT else None),
                          "traffic_note": "bytes per launch: ncu DRAM bytes of a 16-product launch "
                                          "scaled to the B products of this launch",
-                         "peak_note": "binary64 pipe: 152 SMs x 2 ops/clk at the median "
-                                      "sampled SM clock (recipe unit counts and clocks)"},
+                         "peak_note": ("binary32 pipe: 152 SMs x 128 lanes/clk"
+                                       if model == "disc32x2" else
+                                       "binary64 pipe: 152 SMs x 2 ops/clk")
+                                      + " at the median sampled SM clock (recipe unit counts "
+                                        "and clocks)"},
             "hbm_roofline": {"achieved_gbs": value * algorithmic_bytes(n) / 1e9,
                              "peak_gbs": HBM_PEAK_GBS,
                              "frac": value * algorithmic_bytes(n) / 1e9 / HBM_PEAK_GBS,
                              "note": "minimum pass traffic per product x products/s over the "
-                                     "measured copy bandwidth; the path is binary64-pipe bound"},
+                                     "measured copy bandwidth; the path is arithmetic-pipe "
+                                     "bound"},
             "cpu_baseline": cpu,
             "clocks": clk,
             "wall_s": wall,

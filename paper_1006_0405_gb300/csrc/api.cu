@@ -146,8 +146,14 @@ struct ssmul_plan_s {
     int log_tab = 0;
     TwEntry<double>* t64 = nullptr;
     TwEntry<float>* t32 = nullptr;
-    DiscTw* td = nullptr;
-    DDiscTw* tdd = nullptr;
+    DiscC* td = nullptr;
+    DDiscC* tdd = nullptr;
+    float* rho = nullptr;               // device: the radii of td and tdd
+    float rho_d = 0.f, rho_dd = 0.f;
+    CI<double>* s64 = nullptr;          // step-ordered twiddles (STEP_TAB x 3 each)
+    CI<float>* s32 = nullptr;
+    DiscC* sd = nullptr;
+    DDiscC* sdd = nullptr;
     Geom geom[LOG_N_MAX + 1] = {};
     size_t fp32_max_digits = FP32_MAX_DIGITS;
     bool balanced = false;
@@ -190,7 +196,9 @@ struct ssmul_plan_s {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     double kt_ms[SSMUL_KERNEL_KINDS] = {};
     unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
-    TwTable tw() const { return TwTable{t64, t32, log_tab, td, tdd}; }
+    TwTable tw() const {
+        return TwTable{t64, t32, log_tab, td, tdd, rho_d, rho_dd, s64, s32, sd, sdd};
+    }
 };
 
 namespace {
@@ -875,6 +883,11 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->t32);
     cudaFree(p->td);
     cudaFree(p->tdd);
+    cudaFree(p->rho);
+    cudaFree(p->s64);
+    cudaFree(p->s32);
+    cudaFree(p->sd);
+    cudaFree(p->sdd);
     cudaFree(p->Z);
     cudaFree(p->W);
     cudaFree(p->coeff);
@@ -937,8 +950,13 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&p->t64, tab * sizeof(TwEntry<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->t32, tab * sizeof(TwEntry<float>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscTw));
-    if (e == cudaSuccess) e = cudaMalloc(&p->tdd, tab * sizeof(DDiscTw));
+    if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscC));
+    if (e == cudaSuccess) e = cudaMalloc(&p->tdd, tab * sizeof(DDiscC));
+    if (e == cudaSuccess) e = cudaMalloc(&p->rho, 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&p->s64, 3 * STEP_TAB * sizeof(CI<double>));
+    if (e == cudaSuccess) e = cudaMalloc(&p->s32, 3 * STEP_TAB * sizeof(CI<float>));
+    if (e == cudaSuccess) e = cudaMalloc(&p->sd, 3 * STEP_TAB * sizeof(DiscC));
+    if (e == cudaSuccess) e = cudaMalloc(&p->sdd, 3 * STEP_TAB * sizeof(DDiscC));
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->coeff, n * sizeof(int64_t));
@@ -976,12 +994,29 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
 
     const int threads = 256;
     const int blocks = int((tab + threads - 1) / threads);
+    if ((e = cudaMemsetAsync(p->rho, 0, 2 * sizeof(float), p->stream)) != cudaSuccess)
+        return fail(cuda_status(e));
     k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->t32, p->log_tab);
-    k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->log_tab);
-    k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->td, p->tdd, p->log_tab);
+    k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->rho, p->log_tab);
+    k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->td, p->rho, p->tdd, p->log_tab);
+    {
+        TwTable octant = p->tw();
+        octant.s64 = nullptr;
+        octant.s32 = nullptr;
+        octant.sd = nullptr;
+        octant.sdd = nullptr;
+        k_step_tw_gen<<<(3 * STEP_TAB + threads - 1) / threads, threads, 0, p->stream>>>(
+            octant, p->s64, p->s32, p->sd, p->sdd);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_status(e));
+    float h_rho[2] = {0.f, 0.f};
+    if ((e = cudaMemcpyAsync(h_rho, p->rho, sizeof(h_rho), cudaMemcpyDeviceToHost, p->stream)) !=
+        cudaSuccess)
+        return fail(cuda_status(e));
     if ((e = cudaEventRecord(p->desc_free, p->stream)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
+    p->rho_d = h_rho[0];
+    p->rho_dd = h_rho[1];
     *out = p;
     return SSMUL_OK;
 }

@@ -46,6 +46,11 @@ struct alignas(8) DDiscTw {
     float pad;
 };
 
+// twiddle table entry: the centre only (the table's radius is shared)
+struct alignas(16) DDiscC {
+    float ch, cl, sh, sl;
+};
+
 constexpr float DD_U2 = 5.9604645e-8f * 5.9604645e-8f;      // u^2 = 2^-48 (exact)
 constexpr float DD_ADD = 3.0001f * DD_U2;
 constexpr float DD_MUL = 9.01f * DD_U2;
@@ -169,18 +174,19 @@ __device__ __forceinline__ DDisc scale_pow2(const DDisc& a, int k) {
 // twiddle discs from the binary64 disc table: c = ch + cl with
 // ch = RN32(c), cl = RN32(c - ch) (c - ch exact in binary64), so
 // |c - ch - cl| <= u |cl| <= 2^-48 for |c| <= 1; the radius grows by the
-// two components' errors
-__global__ void k_ddisc_tw_gen(const DiscTw* td, DDiscTw* tdd, int log_n) {
+// two components' errors: rho[1] = rho[0] + 2u^2 + ETA, rounded up
+__global__ void k_ddisc_tw_gen(const DiscC* td, float* rho, DDiscC* tdd, int log_n) {
     const int64_t count = (int64_t(1) << log_n) / 8 + 1;
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
-        const DiscTw e = td[j];
+        const DiscC e = td[j];
         const float ch = __double2float_rn(e.c);
         const float cl = __double2float_rn(e.c - double(ch));
         const float sh = __double2float_rn(e.s);
         const float sl = __double2float_rn(e.s - double(sh));
-        tdd[j] = {ch, cl, sh, sl, __fadd_ru(e.rho, 2.f * DD_U2 + DD_ETA), 0.f};
+        tdd[j] = {ch, cl, sh, sl};
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rho[1] = __fadd_ru(rho[0], 2.f * DD_U2 + DD_ETA);
 }
 
 }  // namespace ssm

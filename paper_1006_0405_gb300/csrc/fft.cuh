@@ -15,7 +15,7 @@
 // rectangular wrapping effects (Section 2.5) per element.
 //
 // The element type V is any of value.cuh's (inf-sup rectangles, discs or
-// points); twiddles come from get_twiddle<V>.
+// points); twiddles come from step_twiddle<V>.
 //
 // Each step reads all its inputs into registers, synchronises the block,
 // then writes all its outputs in place: the block must hold every
@@ -62,11 +62,10 @@ __device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw
                 for (int t = 0; t < 4; ++t) v[h][t] = x[q + s * (p + t * m)];
                 bfly4<V, SIGN>(v[h][0], v[h][1], v[h][2], v[h][3]);
                 if (p != 0) {
-                    // omega_n^{p u} = omega_Ntab^{p u Ntab / n}
-                    const int sh = tw.log_n - logn;
-                    v[h][1] = mul_tw(v[h][1], get_twiddle<V, SIGN>(tw, uint32_t(p) << sh));
-                    v[h][2] = mul_tw(v[h][2], get_twiddle<V, SIGN>(tw, uint32_t(2 * p) << sh));
-                    v[h][3] = mul_tw(v[h][3], get_twiddle<V, SIGN>(tw, uint32_t(3 * p) << sh));
+                    // omega_n^{p u}
+                    v[h][1] = mul_tw(v[h][1], step_twiddle<V, SIGN>(tw, logn, p, 1));
+                    v[h][2] = mul_tw(v[h][2], step_twiddle<V, SIGN>(tw, logn, p, 2));
+                    v[h][3] = mul_tw(v[h][3], step_twiddle<V, SIGN>(tw, logn, p, 3));
                 }
                 base[h] = line * pitch + q + s * 4 * p;
                 pp[h] = s;

@@ -215,7 +215,7 @@ __device__ void pair_products(V* sm, int nl, int row0, int logN2) {
 
 // D_k for k2 < N2/2 of each line, written over the first half of the line.
 template <typename V>
-__device__ void pack_half(V* sm, int nl, const int* rows, int logN1, int logN2,
+__device__ void pack_half(V* sm, int nl, int row0, int row1, int logN1, int logN2,
                           const TwTable& tw) {
     const int N2 = 1 << logN2, M2 = N2 >> 1;
     const int logN = logN1 + logN2;
@@ -223,7 +223,7 @@ __device__ void pack_half(V* sm, int nl, const int* rows, int logN1, int logN2,
         const int l = t >> (logN2 - 1), k2 = t & (M2 - 1);
         V* x = sm + l * N2;
         const V c0 = x[k2], c1 = x[k2 + M2];
-        const uint32_t k = uint32_t(rows[l]) + (uint32_t(k2) << logN1);
+        const uint32_t k = uint32_t(l ? row1 : row0) + (uint32_t(k2) << logN1);
         const auto w = get_twiddle<V, -1>(tw, k << (tw.log_n - logN));
         x[k2] = (c0 + c1) + mul_i(mul_tw(c0 - c1, w));
     }
@@ -234,6 +234,7 @@ __device__ void pack_half(V* sm, int nl, const int* rows, int logN1, int logN2,
 struct IsoAcc {
     unsigned int unisolated = 0, empty = 0;
     unsigned long long maxw_bits = 0;   // bit pattern of the largest width (>= 0)
+    unsigned int maxw_f32 = 0;          // the same for widths held in binary32
 };
 
 // Decide coefficient `idx` from its enclosure [lo, hi]; L = na + nb - 1.
@@ -280,6 +281,12 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
 }
 
 __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
+    if (acc.maxw_f32) {
+        // binary32 -> binary64 is exact and keeps the order (NaN stays the largest)
+        const unsigned long long w =
+            (unsigned long long)__double_as_longlong(double(__uint_as_float(acc.maxw_f32)));
+        acc.maxw_bits = w > acc.maxw_bits ? w : acc.maxw_bits;
+    }
     for (int o = 16; o > 0; o >>= 1) {
         acc.unisolated += __shfl_xor_sync(0xffffffffu, acc.unisolated, o);
         acc.empty += __shfl_xor_sync(0xffffffffu, acc.empty, o);
@@ -310,13 +317,89 @@ __device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, const Pr
     isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc, 2);
 }
 
+// rint(x) for |x| < 2^23 (x + 2^23 sign(x) has ulp 1), x itself otherwise
+// (then x is an integer, inf or NaN)
+__device__ __forceinline__ float rint_f32(float x) {
+    const float S = __int_as_float(0x4B000000 | (__float_as_int(x) & int(0x80000000)));
+    return fabsf(x) < 8388608.f ? __fsub_rn(__fadd_rn(x, S), S) : x;
+}
+
+// the integer value of an integer-valued binary32 x with |x| < 2^53, on the
+// integer pipe
+__device__ __forceinline__ long long int_of_f32(float x) {
+    const int b = __float_as_int(x);
+    const int ef = (b >> 23) & 0xFF;
+    const long long m = (b & 0x7FFFFF) | 0x800000;
+    const int e = ef - 150;                                    // x = m 2^e
+    long long v = e >= 0 ? (m << (e > 40 ? 40 : e)) : (m >> (-e > 31 ? 31 : -e));
+    v = ef == 0 ? 0ll : v;
+    return b < 0 ? -v : v;
+}
+
+// The decision of isolate_one for a component held as a double-binary32
+// centre h + l and a binary32 radius r, on the binary32 and integer pipes
+// only.  With k0 = rint(h), k1 = rint(l) (exact) the remainders t = h - k0
+// and t' = l - k1 are exact and |t + t'| <= 1, so the component lies in
+// [k0 + k1 + lo, k0 + k1 + hi] with lo = RD(RD(t + t') - r) and
+// hi = RU(RU(t + t') + r).  While |lo|, |hi| < 2^22, ceil(lo) and floor(hi)
+// are read off RU(lo + 1.5 2^23) and RD(hi + 1.5 2^23), whose ulp is 1.
+// Beyond that r > 2^21 (the set holds many integers) unless a part is NaN
+// or infinite (no integer: empty); a centre with |h| >= 2^53 cannot hold a
+// coefficient (they are below 2^53) and is empty unless it is wide.
+__device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t idx,
+                                             const ProdDesc& d, IsoAcc& acc, int rung) {
+    const int64_t L = int64_t(d.na) + d.nb - 1;
+    if (d.fault_widen == rung + 1) r = __fadd_ru(r, 4.f);     // test fault: still an enclosure
+    const float k0 = rint_f32(h), k1 = rint_f32(l);
+    const float t = __fsub_rn(h, k0), t2 = __fsub_rn(l, k1);
+    const float lo = __fsub_rd(__fadd_rd(t, t2), r);
+    const float hi = __fadd_ru(__fadd_ru(t, t2), r);
+    const unsigned int wb = __float_as_uint(__fsub_ru(hi, lo));
+    acc.maxw_f32 = wb > acc.maxw_f32 ? wb : acc.maxw_f32;
+    constexpr float M = 12582912.f;                            // 1.5 2^23
+    const bool fits = fabsf(lo) < 4194304.f && fabsf(hi) < 4194304.f;   // false for NaN
+    const bool bad = (__float_as_int(h) & 0x7F800000) == 0x7F800000 ||
+                     (__float_as_int(l) & 0x7F800000) == 0x7F800000 || r != r;
+    const bool big = fabsf(h) >= 9007199254740992.f;            // 2^53
+    const int cl = __float_as_int(__fadd_ru(lo, M)) - __float_as_int(M);
+    const int fh = __float_as_int(__fadd_rd(hi, M)) - __float_as_int(M);
+    const long long K = big ? 0ll : int_of_f32(k0) + int_of_f32(k1);
+    if (idx < L) {
+        const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
+        if (d.iv != nullptr) {
+            // the enclosure as binary64 bounds (test output)
+            const double dr = double(r);
+            const double dl = __dsub_rd(__dadd_rd(double(h), double(l)), dr);
+            const double dh = __dadd_ru(__dadd_ru(double(h), double(l)), dr);
+            d.iv[2 * idx] = __dadd_rd(dl, double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(dh, double(corr));
+        }
+        int64_t v = 0;
+        if (bad) {
+            acc.empty++;
+        } else if (!fits) {
+            acc.unisolated++;
+        } else if (cl == fh && !big && K + cl + corr >= 0) {
+            v = K + cl + corr;
+        } else if (cl < fh) {
+            acc.unisolated++;
+        } else {
+            acc.empty++;           // no integer, a negative one or overflow
+        }
+        d.coeff[idx] = v;
+    } else {
+        // the exact value is 0; for a wide or far centre, 0 is outside when
+        // |h| - |l| > r (a lower bound on |h + l| exceeds the radius)
+        const bool excl = (fits && !big) ? !(K + cl <= 0 && K + fh >= 0)
+                                         : __fsub_rd(__fsub_rd(fabsf(h), fabsf(l)), r) > 0.f;
+        if (bad || excl) acc.empty++;
+    }
+}
+
 __device__ __forceinline__ void isolate_value(const DDisc& v, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
-    const double r = double(v.r);
-    const double xl = __dadd_rd(double(v.xh), double(v.xl)), xh = __dadd_ru(double(v.xh), double(v.xl));
-    const double yl = __dadd_rd(double(v.yh), double(v.yl)), yh = __dadd_ru(double(v.yh), double(v.yl));
-    isolate_one(__dsub_rd(xl, r), __dadd_ru(xh, r), 2 * j, d, acc, 4);
-    isolate_one(__dsub_rd(yl, r), __dadd_ru(yh, r), 2 * j + 1, d, acc, 4);
+    isolate_pair(v.xh, v.xl, v.r, 2 * j, d, acc, 4);
+    isolate_pair(v.yh, v.yl, v.r, 2 * j + 1, d, acc, 4);
 }
 
 // the naive transform rounds to the nearest integer without any proof; its
@@ -369,8 +452,7 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     block_fft<V, +1, BPT>(sm, logN, 1, N, tw);
     pair_products(sm, 1, 0, logN);
     __syncthreads();
-    const int rows[2] = {0, 0};
-    pack_half(sm, 1, rows, 0, logN, tw);
+    pack_half(sm, 1, 0, 0, 0, logN, tw);
     __syncthreads();
     block_fft<V, -1, BPT>(sm, logN - 1, 1, N, tw);
     IsoAcc acc;
@@ -425,27 +507,27 @@ __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, 
     const int k1 = blockIdx.x;                              // 0 .. N1/2
     const int k1b = (N1 - k1) & (N1 - 1);
     const int nl = (k1 == k1b) ? 1 : 2;
-    const int rows[2] = {k1, k1b};
     const V* Z = reinterpret_cast<const V*>(d.Z);
     V* W = reinterpret_cast<V*>(d.W);
     for (int t = threadIdx.x; t < nl * N2; t += blockDim.x) {
         const int l = t >> logN2, k2 = t & (N2 - 1);
-        sm[t] = Z[(size_t(rows[l]) << logN2) + k2];
+        sm[t] = Z[(size_t(l ? k1b : k1) << logN2) + k2];
     }
     __syncthreads();
     block_fft<V, +1, BPT>(sm, logN2, nl, N2, tw);
     pair_products(sm, nl, k1, logN2);
     __syncthreads();
-    pack_half(sm, nl, rows, logN1, logN2, tw);
+    pack_half(sm, nl, k1, k1b, logN1, logN2, tw);
     __syncthreads();
     block_fft<V, -1, BPT>(sm, logN2 - 1, nl, N2, tw);
     const int logM = logN1 + logN2 - 1;
     for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
         const int l = t >> (logN2 - 1), j2 = t & (M2 - 1);
         V v = sm[l * N2 + j2];
-        const uint32_t e = uint32_t(rows[l]) * uint32_t(j2);    // < N/2
+        const int row = l ? k1b : k1;
+        const uint32_t e = uint32_t(row) * uint32_t(j2);        // < N/2
         if (e) v = mul_tw(v, get_twiddle<V, -1>(tw, e << (tw.log_n - logM)));
-        W[(size_t(rows[l]) << (logN2 - 1)) + j2] = v;
+        W[(size_t(row) << (logN2 - 1)) + j2] = v;
     }
 }
 

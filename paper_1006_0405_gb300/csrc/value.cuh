@@ -73,7 +73,7 @@ __device__ __forceinline__ DDiscTw twiddle_ddisc(const TwTable& tw, uint32_t j) 
     const uint32_t quad = j >> (ln - 2);
     const uint32_t r = j & (q - 1u);
     const bool refl = r > (q >> 1);
-    const DDiscTw e = tw.tdd[refl ? q - r : r];
+    const DDiscC e = tw.tdd[refl ? q - r : r];
     const float ch = refl ? e.sh : e.ch, cl = refl ? e.sl : e.cl;
     const float sh = refl ? e.ch : e.sh, sl = refl ? e.cl : e.sl;
     const bool swap = quad & 1u;
@@ -82,7 +82,7 @@ __device__ __forceinline__ DDiscTw twiddle_ddisc(const TwTable& tw, uint32_t j) 
     const bool negr = quad == 1u || quad == 2u;
     const bool negi = (quad >= 2u) != (SIGN < 0);
     return {negr ? flip(wch) : wch, negr ? flip(wcl) : wcl, negi ? flip(wsh) : wsh,
-            negi ? flip(wsl) : wsl, e.rho, 0.f};
+            negi ? flip(wsl) : wsl, tw.rho_dd, 0.f};
 }
 template <>
 __device__ __forceinline__ DDiscTw get_twiddle<DDisc, 1>(const TwTable& tw, uint32_t j) {
@@ -91,6 +91,84 @@ __device__ __forceinline__ DDiscTw get_twiddle<DDisc, 1>(const TwTable& tw, uint
 template <>
 __device__ __forceinline__ DDiscTw get_twiddle<DDisc, -1>(const TwTable& tw, uint32_t j) {
     return twiddle_ddisc<-1>(tw, j);
+}
+
+// ---- step-ordered twiddles -------------------------------------------------------
+//
+// omega_n^(SIGN u p) for the radix-4 step of sub-length n = 2^logn: the
+// step table's entry (a forward twiddle; the inverse root is its conjugate,
+// a sign-bit flip), or the octant table's when the plan has no step tables.
+// Both give the same bits.
+
+__device__ __forceinline__ CI<double> tw_conj(const CI<double>& w) { return conj_flip(w); }
+__device__ __forceinline__ CI<float> tw_conj(const CI<float>& w) { return conj_flip(w); }
+__device__ __forceinline__ DiscTw tw_conj(const DiscTw& w) { return {w.c, flip(w.s), w.rho, 0.f}; }
+__device__ __forceinline__ DDiscTw tw_conj(const DDiscTw& w) {
+    return {w.ch, w.cl, flip(w.sh), flip(w.sl), w.rho, 0.f};
+}
+
+template <typename V> struct StepOf;
+template <> struct StepOf<CI<double>> {
+    static __device__ __forceinline__ const CI<double>* table(const TwTable& tw) { return tw.s64; }
+    static __device__ __forceinline__ CI<double> load(const CI<double>* t, int i, const TwTable&) {
+        return t[i];
+    }
+};
+template <> struct StepOf<CI<float>> {
+    static __device__ __forceinline__ const CI<float>* table(const TwTable& tw) { return tw.s32; }
+    static __device__ __forceinline__ CI<float> load(const CI<float>* t, int i, const TwTable&) {
+        return t[i];
+    }
+};
+template <> struct StepOf<Disc> {
+    static __device__ __forceinline__ const DiscC* table(const TwTable& tw) { return tw.sd; }
+    static __device__ __forceinline__ DiscTw load(const DiscC* t, int i, const TwTable& tw) {
+        const DiscC e = t[i];
+        return {e.c, e.s, tw.rho_d, 0.f};
+    }
+};
+template <> struct StepOf<Pt> : StepOf<Disc> {};
+template <> struct StepOf<DDisc> {
+    static __device__ __forceinline__ const DDiscC* table(const TwTable& tw) { return tw.sdd; }
+    static __device__ __forceinline__ DDiscTw load(const DDiscC* t, int i, const TwTable& tw) {
+        const DDiscC e = t[i];
+        return {e.ch, e.cl, e.sh, e.sl, tw.rho_dd, 0.f};
+    }
+};
+
+template <typename V, int SIGN>
+__device__ __forceinline__ typename VTraits<V>::Tw step_twiddle(const TwTable& tw, int logn, int p,
+                                                                int u) {
+    const auto* t = StepOf<V>::table(tw);
+    if (t == nullptr) return get_twiddle<V, SIGN>(tw, uint32_t(u * p) << (tw.log_n - logn));
+    const auto w = StepOf<V>::load(t, (u - 1) * STEP_TAB + (1 << (logn - 2)) + p, tw);
+    return SIGN > 0 ? w : tw_conj(w);
+}
+
+// Fills the step tables from the octant tables (rho of the disc tables is
+// not needed: the step tables of discs hold centres).
+__global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscC* sd,
+                              DDiscC* sdd) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * STEP_TAB;
+         i += gridDim.x * blockDim.x) {
+        const int u = i / STEP_TAB + 1, pos = i % STEP_TAB;
+        const int lq = pos < 2 ? -1 : 31 - __clz(pos);        // log2(n/4)
+        const int logn = lq + 2;
+        if (lq < 1 || logn > tw.log_n) {
+            s64[i] = {};
+            s32[i] = {};
+            sd[i] = {};
+            sdd[i] = {};
+            continue;
+        }
+        const uint32_t j = uint32_t(u * (pos - (1 << lq))) << (tw.log_n - logn);
+        s64[i] = twiddle<double, 1>(tw, j);
+        s32[i] = twiddle<float, 1>(tw, j);
+        const DiscTw d = twiddle_disc<1>(tw, j);
+        sd[i] = {d.c, d.s};
+        const DDiscTw dd = twiddle_ddisc<1>(tw, j);
+        sdd[i] = {dd.ch, dd.cl, dd.sh, dd.sl};
+    }
 }
 
 // a digit pair as an exact point (small integers are exact in every type)
