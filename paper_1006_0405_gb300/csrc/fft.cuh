@@ -2,7 +2,8 @@
 //
 // Computes X_k = sum_j x_j omega_L^{SIGN j k} (the DFT of Section 2.2 for
 // SIGN = +1, the unscaled inverse for SIGN = -1) for `nl` lines of length
-// L = 2^logL, line l at buf[l * pitch ...], natural order in and out.
+// L = 2^logL, line l at buf[l * pitch ...], natural order in and out (the
+// indices are SBuf's, before its swizzle).
 //
 // The paper's transform is the radix-2 Cooley-Tukey recursion.  Here the
 // same DFT is evaluated by the Stockham autosort factorisation in radix 4
@@ -38,7 +39,7 @@ __device__ __forceinline__ void bfly4(V& a, V& b, V& c, V& d) {
 }
 
 template <typename V, int SIGN, int BPT = 2>
-__device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw) {
+__device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTable& tw) {
     const int L = 1 << logL;
     const int quarter_log = logL - 2;
     int logn = logL, logs = 0;
@@ -57,9 +58,9 @@ __device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw
                 const int line = b >> quarter_log;
                 const int bb = b & ((L >> 2) - 1);
                 const int p = bb >> logs, q = bb & (s - 1);
-                V* x = buf + line * pitch;
+                const int x = line * pitch + q;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) v[h][t] = x[q + s * (p + t * m)];
+                for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
                 bfly4<V, SIGN>(v[h][0], v[h][1], v[h][2], v[h][3]);
                 if (p != 0) {
                     // omega_n^{p u}
@@ -89,10 +90,10 @@ __device__ void block_fft(V* buf, int logL, int nl, int pitch, const TwTable& tw
         const int nbf = nl * half;
         for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
             const int line = b / half, q = b - line * half;
-            V* x = buf + line * pitch;
-            const V a = x[q], c = x[q + half];
-            x[q] = a + c;
-            x[q + half] = a - c;
+            const int x = line * pitch + q;
+            const V a = buf[x], c = buf[x + half];
+            buf[x] = a + c;
+            buf[x + half] = a - c;
         }
         __syncthreads();
     }

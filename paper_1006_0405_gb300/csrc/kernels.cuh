@@ -197,7 +197,7 @@ template <> struct ValOf<double> { using type = CI<double>; };
 // otherwise.  With two lines the rows are partners of each other; with
 // one line the row is its own partner.
 template <typename V>
-__device__ void pair_products(V* sm, int nl, int row0, int logN2) {
+__device__ void pair_products(SBuf<V> sm, int nl, int row0, int logN2) {
     const int N2 = 1 << logN2;
     for (int k2 = threadIdx.x; k2 < N2; k2 += blockDim.x) {
         const int pc = (row0 == 0) ? ((N2 - k2) & (N2 - 1)) : (N2 - 1 - k2);
@@ -215,17 +215,17 @@ __device__ void pair_products(V* sm, int nl, int row0, int logN2) {
 
 // D_k for k2 < N2/2 of each line, written over the first half of the line.
 template <typename V>
-__device__ void pack_half(V* sm, int nl, int row0, int row1, int logN1, int logN2,
+__device__ void pack_half(SBuf<V> sm, int nl, int row0, int row1, int logN1, int logN2,
                           const TwTable& tw) {
     const int N2 = 1 << logN2, M2 = N2 >> 1;
     const int logN = logN1 + logN2;
     for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
         const int l = t >> (logN2 - 1), k2 = t & (M2 - 1);
-        V* x = sm + l * N2;
-        const V c0 = x[k2], c1 = x[k2 + M2];
+        const int x = l * N2 + k2;
+        const V c0 = sm[x], c1 = sm[x + M2];
         const uint32_t k = uint32_t(l ? row1 : row0) + (uint32_t(k2) << logN1);
         const auto w = get_twiddle<V, -1>(tw, k << (tw.log_n - logN));
-        x[k2] = (c0 + c1) + mul_i(mul_tw(c0 - c1, w));
+        sm[x] = (c0 + c1) + mul_i(mul_tw(c0 - c1, w));
     }
 }
 
@@ -428,6 +428,24 @@ __device__ __forceinline__ void isolate_value(const Pt& v, int64_t j, const Prod
     naive_one(v.y, 2 * j + 1, d, acc);
 }
 
+// Global -> shared staging of `total` elements: a thread issues all of its
+// (up to EPT) loads before its first store, so their latencies overlap.
+template <int EPT, typename T, typename Load, typename Store>
+__device__ __forceinline__ void stage(int total, Load load, Store store) {
+    T v[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+        if (i < total) v[k] = load(i);
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+        if (i < total) store(i, v[k]);
+    }
+    for (int i = threadIdx.x + EPT * blockDim.x; i < total; i += blockDim.x) store(i, load(i));
+}
+
 // ---- k_small: the whole interval convolution of one product in one CTA -----
 
 // gate: bit mask of rungs whose decision makes this rung skip the product;
@@ -438,16 +456,18 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     using V = typename ValOf<Tag>::type;
     constexpr int RUNG = VTraits<V>::rung;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* sm = reinterpret_cast<V*>(smem_raw);
+    const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
     const ProdDesc d = descs[blockIdx.x];
     if (gate && decided_by(d.st, gate)) return;
     const int logN = d.log_n, N = 1 << logN;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const int bias = d.balanced ? 128 : 0;
-        const int re = j < int(d.na) ? int(d.a[j]) - bias : 0;
-        const int im = j < int(d.nb) ? int(d.b[j]) - bias : 0;
-        sm[j] = make_point<V>(re, im);
-    }
+    const int bias = d.balanced ? 128 : 0;
+    stage<4 * BPT, int2>(
+        N,
+        [&](int j) {
+            return make_int2(j < int(d.na) ? int(d.a[j]) - bias : 0,
+                             j < int(d.nb) ? int(d.b[j]) - bias : 0);
+        },
+        [&](int j, int2 v) { sm[j] = make_point<V>(v.x, v.y); });
     __syncthreads();
     block_fft<V, +1, BPT>(sm, logN, 1, N, tw);
     pair_products(sm, 1, 0, logN);
@@ -469,20 +489,22 @@ __global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
                            int gate) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* sm = reinterpret_cast<V*>(smem_raw);
+    const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
     const ProdDesc d = descs[blockIdx.y];
     if (gate && decided_by(d.st, gate)) return;
     const int N1 = 1 << logN1, C = 1 << logC;
     const uint32_t j2_0 = blockIdx.x << logC;
     V* Z = reinterpret_cast<V*>(d.Z);
-    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
-        const int c = idx & (C - 1), j1 = idx >> logC;
-        const uint32_t j = (uint32_t(j1) << logN2) + j2_0 + c;
-        const int bias = d.balanced ? 128 : 0;
-        const int re = j < d.na ? int(d.a[j]) - bias : 0;
-        const int im = j < d.nb ? int(d.b[j]) - bias : 0;
-        sm[(c << logN1) + j1] = make_point<V>(re, im);
-    }
+    const int bias = d.balanced ? 128 : 0;
+    stage<4 * BPT, int2>(
+        C << logN1,
+        [&](int idx) {
+            const uint32_t j = (uint32_t(idx >> logC) << logN2) + j2_0 + (idx & (C - 1));
+            return make_int2(j < d.na ? int(d.a[j]) - bias : 0, j < d.nb ? int(d.b[j]) - bias : 0);
+        },
+        [&](int idx, int2 v) {
+            sm[((idx & (C - 1)) << logN1) + (idx >> logC)] = make_point<V>(v.x, v.y);
+        });
     __syncthreads();
     block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
@@ -500,7 +522,7 @@ template <typename Tag, int BPT = 2>
 __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* sm = reinterpret_cast<V*>(smem_raw);
+    const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
     const ProdDesc d = descs[blockIdx.y];
     if (gate && decided_by(d.st, gate)) return;
     const int N1 = 1 << logN1, N2 = 1 << logN2, M2 = N2 >> 1;
@@ -509,10 +531,10 @@ __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, 
     const int nl = (k1 == k1b) ? 1 : 2;
     const V* Z = reinterpret_cast<const V*>(d.Z);
     V* W = reinterpret_cast<V*>(d.W);
-    for (int t = threadIdx.x; t < nl * N2; t += blockDim.x) {
-        const int l = t >> logN2, k2 = t & (N2 - 1);
-        sm[t] = Z[(size_t(l ? k1b : k1) << logN2) + k2];
-    }
+    stage<4 * BPT, V>(
+        nl * N2,
+        [&](int t) { return Z[(size_t((t >> logN2) ? k1b : k1) << logN2) + (t & (N2 - 1))]; },
+        [&](int t, const V& v) { sm[t] = v; });
     __syncthreads();
     block_fft<V, +1, BPT>(sm, logN2, nl, N2, tw);
     pair_products(sm, nl, k1, logN2);
@@ -537,17 +559,17 @@ __global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
     using V = typename ValOf<Tag>::type;
     constexpr int RUNG = VTraits<V>::rung;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* sm = reinterpret_cast<V*>(smem_raw);
+    const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
     const ProdDesc d = descs[blockIdx.y];
     if (gate && decided_by(d.st, gate)) return;
     const int N1 = 1 << logN1, C = 1 << logC;
     const int logM2 = logN2 - 1;
     const uint32_t j2_0 = blockIdx.x << logC;
     const V* W = reinterpret_cast<const V*>(d.W);
-    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
-        const int c = idx & (C - 1), k1 = idx >> logC;
-        sm[(c << logN1) + k1] = W[(size_t(k1) << logM2) + j2_0 + c];
-    }
+    stage<4 * BPT, V>(
+        C << logN1,
+        [&](int idx) { return W[(size_t(idx >> logC) << logM2) + j2_0 + (idx & (C - 1))]; },
+        [&](int idx, const V& v) { sm[((idx & (C - 1)) << logN1) + (idx >> logC)] = v; });
     __syncthreads();
     block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;

@@ -22,12 +22,43 @@ namespace ssm {
 
 constexpr int RUNGS = 5;
 
+// sw_src, sw_mask: the shared-memory swizzle of SBuf for the type's size
 template <typename V> struct VTraits;
-template <> struct VTraits<CI<float>> { using Tw = CI<float>; static constexpr int rung = 0; };
-template <> struct VTraits<CI<double>> { using Tw = CI<double>; static constexpr int rung = 1; };
-template <> struct VTraits<Disc> { using Tw = DiscTw; static constexpr int rung = 2; };
-template <> struct VTraits<Pt> { using Tw = DiscTw; static constexpr int rung = 3; };
-template <> struct VTraits<DDisc> { using Tw = DDiscTw; static constexpr int rung = 4; };
+template <> struct VTraits<CI<float>> {
+    using Tw = CI<float>;
+    static constexpr int rung = 0, sw_src = 3, sw_mask = 3;
+};
+template <> struct VTraits<CI<double>> {
+    using Tw = CI<double>;
+    static constexpr int rung = 1, sw_src = 2, sw_mask = 3;
+};
+template <> struct VTraits<Disc> {
+    using Tw = DiscTw;
+    static constexpr int rung = 2, sw_src = 3, sw_mask = 7;
+};
+template <> struct VTraits<Pt> {
+    using Tw = DiscTw;
+    static constexpr int rung = 3, sw_src = 3, sw_mask = 3;
+};
+template <> struct VTraits<DDisc> {
+    using Tw = DDiscTw;
+    static constexpr int rung = 4, sw_src = 3, sw_mask = 7;
+};
+
+// A transform buffer in shared memory.  Element i lives in slot
+// i ^ ((i >> sw_src) & sw_mask): the swizzle permutes each aligned group of
+// sw_mask + 1 elements, so it maps [0, n) onto itself for every n that is a
+// multiple of that group or smaller than 2^sw_src.  It spreads the strided
+// accesses of the radix-4 steps (stride 4 s for s < 32) over more banks
+// (16-, 24- and 32-byte elements each take the variant with the fewest
+// shared-memory wavefronts over the steps of the transform lengths in use).
+template <typename V>
+struct SBuf {
+    V* p;
+    __device__ __forceinline__ V& operator[](int i) const {
+        return p[i ^ ((i >> VTraits<V>::sw_src) & VTraits<V>::sw_mask)];
+    }
+};
 
 template <typename V, int SIGN>
 __device__ __forceinline__ typename VTraits<V>::Tw get_twiddle(const TwTable& tw, uint32_t j);
