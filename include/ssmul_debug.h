@@ -70,6 +70,22 @@ ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y, d
 ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y, double* d_out,
                                   size_t n);
 
+/*
+ * The isolation decision (Section 1: accept a coefficient only when its
+ * enclosure holds exactly one integer) for one component of a
+ * double-binary32 disc, n of them independently.  Row i of d_x (device,
+ * 4 doubles, the first three binary32 values) is (h, l, r, pad): the
+ * enclosure [h + l - r, h + l + r]; pad != 0 makes it a value past the
+ * product's last coefficient, which must contain 0.  path 0: the rung's
+ * decision on the binary32 and integer pipes; path 1: the same set bounded
+ * in binary64 and decided there.  Outputs (device): d_class[i] = 0
+ * isolated (d_value[i] = the integer), 1 not isolated, 2 empty (no
+ * integer, a negative one, NaN, a centre beyond 2^53, or for pad rows a
+ * set that excludes 0); d_value[i] = 0 otherwise.
+ */
+ssmul_status ssmul_debug_isolate(int path, const double* d_x, int64_t* d_value, int* d_class,
+                                 size_t n);
+
 /* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays):
  * kernel * 5 + rung for the four transform kernels (rungs: 0 F32 and 1 F64
  * rectangles, 2 DISC binary64 discs, 3 NAIVE points, 4 DISC32X2 discs),
@@ -100,7 +116,10 @@ ssmul_status ssmul_debug_kernel_stats(ssmul_plan_t plan, int enable, double* ms,
  * kind 2: carry tile `value` (4096 digits each) of every product never
  * publishes its look-back word, so later tiles give up after their bounded
  * wait (about a second) and the product reports SSMUL_TIMEOUT with its
- * digits zero-filled.  Applies to the plan's later calls.
+ * digits zero-filled.  kind 3 (not a fault): value != 0 makes the
+ * transforms read every twiddle from the octant tables instead of the
+ * step-ordered copies, which must give the same bits.  Applies to the
+ * plan's later calls.
  */
 ssmul_status ssmul_debug_set_fault(ssmul_plan_t plan, int kind, long long value);
 

@@ -159,6 +159,7 @@ struct ssmul_plan_s {
     bool balanced = false;
     uint32_t* pre = nullptr;            // balanced: digit prefix sums of one product
     int fault_widen = 0, fault_stall = 0;   // ssmul_debug_set_fault
+    bool octant_only = false;           // transforms read the octant tables (a test)
     // split products (SSMUL_OPT_SPLIT_DIGITS)
     size_t split_digits = 0;
     size_t split_slots = 0;
@@ -197,6 +198,8 @@ struct ssmul_plan_s {
     double kt_ms[SSMUL_KERNEL_KINDS] = {};
     unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
     TwTable tw() const {
+        if (octant_only)
+            return TwTable{t64, t32, log_tab, td, tdd, rho_d, rho_dd, nullptr, nullptr, nullptr, nullptr};
         return TwTable{t64, t32, log_tab, td, tdd, rho_d, rho_dd, s64, s32, sd, sdd};
     }
 };
@@ -1000,11 +1003,9 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->rho, p->log_tab);
     k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->td, p->rho, p->tdd, p->log_tab);
     {
-        TwTable octant = p->tw();
-        octant.s64 = nullptr;
-        octant.s32 = nullptr;
-        octant.sd = nullptr;
-        octant.sdd = nullptr;
+        p->octant_only = true;
+        const TwTable octant = p->tw();
+        p->octant_only = false;
         k_step_tw_gen<<<(3 * STEP_TAB + threads - 1) / threads, threads, 0, p->stream>>>(
             octant, p->s64, p->s32, p->sd, p->sdd);
     }
@@ -1150,7 +1151,14 @@ ssmul_status ssmul_debug_set_fault(ssmul_plan_t p, int kind, long long value) {
     if (!p) return SSMUL_INVALID_ARG;
     graph_drop(p->cached);
     switch (kind) {
-        case 0: p->fault_widen = 0; p->fault_stall = 0; return SSMUL_OK;
+        case 0:
+            p->fault_widen = 0;
+            p->fault_stall = 0;
+            p->octant_only = false;
+            return SSMUL_OK;
+        case 3:
+            p->octant_only = value != 0;
+            return SSMUL_OK;
         case 1:
             if (value < 0 || value >= RUNGS) return SSMUL_INVALID_ARG;
             p->fault_widen = int(value) + 1;
@@ -1275,7 +1283,44 @@ __global__ void k_ddisc_op(int op, const double* x, const double* y, double* out
     }
 }
 
+// one coefficient per thread: row i of x is (h, l, r, pad); pad != 0 puts
+// the value past the product's last coefficient (it must contain 0)
+__global__ void k_iso_op(int path, const double* x, int64_t* value, int* cls, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        const double* r4 = x + 4 * i;
+        const float h = float(r4[0]), l = float(r4[1]), r = float(r4[2]);
+        ProdDesc d{};
+        d.na = 1;
+        d.nb = 1;                           // one coefficient: index 0
+        d.coeff = value + i;
+        const int64_t idx = r4[3] != 0.0 ? 1 : 0;
+        value[i] = 0;
+        IsoAcc acc;
+        if (path == 0) {
+            isolate_pair(h, l, r, idx, d, acc, 4);
+        } else {
+            const double dr = double(r);
+            isolate_one(__dsub_rd(__dadd_rd(double(h), double(l)), dr),
+                        __dadd_ru(__dadd_ru(double(h), double(l)), dr), idx, d, acc, 4);
+        }
+        cls[i] = acc.empty ? 2 : (acc.unisolated ? 1 : 0);
+    }
+}
+
 }  // namespace
+
+extern "C" ssmul_status ssmul_debug_isolate(int path, const double* d_x, int64_t* d_value,
+                                            int* d_class, size_t n) {
+    if (path < 0 || path > 1 || (n && (!d_x || !d_value || !d_class))) return SSMUL_INVALID_ARG;
+    if (n == 0) return SSMUL_OK;
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);
+    k_iso_op<<<blocks, threads>>>(path, d_x, d_value, d_class, n);
+    SS_TRY(cudaGetLastError());
+    SS_TRY(cudaDeviceSynchronize());
+    return SSMUL_OK;
+}
 
 extern "C" ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y,
                                              double* d_out, size_t n) {
