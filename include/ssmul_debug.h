@@ -65,7 +65,10 @@ ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y, d
  * 5 doubles per operand (centre re as hi, lo; centre im as hi, lo; radius),
  * every value a binary32 number, pairs normalised (|lo| <= 2^-24 |hi|).
  * op 2 takes d_y as a twiddle disc (|centre| <= 1); op 4 scales by 2^-k
- * with k = (int) d_y[5 i].
+ * with k = (int) d_y[5 i].  op 5 (6): the radix-4 butterfly of the
+ * transform (the inverse's) on the four discs d_x[20 i .. 20 i + 20), its
+ * four outputs at d_out[20 i ..] sharing one radius; d_y is not read and
+ * may be NULL.
  */
 ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y, double* d_out,
                                   size_t n);

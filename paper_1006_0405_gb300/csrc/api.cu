@@ -1262,6 +1262,25 @@ __global__ void k_disc_op(int op, const double* x, const double* y, double* out,
 __global__ void k_ddisc_op(int op, const double* x, const double* y, double* out, size_t n) {
     for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
          i += size_t(gridDim.x) * blockDim.x) {
+        if (op >= 5) {
+            // radix-4 butterfly of the four discs x[20 i ..] (SIGN +1 for op 5, -1 for op 6)
+            DDisc v[4];
+            for (int t = 0; t < 4; ++t) {
+                const double* e = x + 20 * i + 5 * t;
+                v[t] = {float(e[0]), float(e[1]), float(e[2]), float(e[3]), float(e[4]), 0.f};
+            }
+            if (op == 5) bfly4_dd<1>(v[0], v[1], v[2], v[3]);
+            else bfly4_dd<-1>(v[0], v[1], v[2], v[3]);
+            for (int t = 0; t < 4; ++t) {
+                double* o = out + 20 * i + 5 * t;
+                o[0] = v[t].xh;
+                o[1] = v[t].xl;
+                o[2] = v[t].yh;
+                o[3] = v[t].yl;
+                o[4] = v[t].r;
+            }
+            continue;
+        }
         const double* a5 = x + 5 * i;
         const double* b5 = y + 5 * i;
         const DDisc a{float(a5[0]), float(a5[1]), float(a5[2]), float(a5[3]), float(a5[4]), 0.f};
@@ -1324,7 +1343,7 @@ extern "C" ssmul_status ssmul_debug_isolate(int path, const double* d_x, int64_t
 
 extern "C" ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y,
                                              double* d_out, size_t n) {
-    if (op < 0 || op > 4 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
+    if (op < 0 || op > 6 || (n && (!d_x || !d_out || (op < 5 && !d_y)))) return SSMUL_INVALID_ARG;
     if (n == 0) return SSMUL_OK;
     const int threads = 256;
     const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);

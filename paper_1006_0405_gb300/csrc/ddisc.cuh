@@ -113,6 +113,62 @@ __device__ __forceinline__ DDisc operator-(const DDisc& a, const DDisc& b) {
     return z;
 }
 
+// ---- radix-4 butterfly with one radius for its four outputs -----------------------
+//
+// The two levels of sums of a radix-4 butterfly (a +- c, b +- d, then their
+// sums and differences, one of them times +-i) give every output the radius
+// r_a + r_b + r_c + r_d plus the rounding of one first-level and one
+// second-level sum of each component.  With M the sum of |xh| + |yh| over
+// the four inputs: the first-level sums feeding an output err by at most
+// DD_ADD (M_ac + M_bd) = DD_ADD M (+ 4 ETA); a first-level result z of, say,
+// a.x + c.x has |z| <= (|a.xh| + |c.xh|)(1 + u + 3.0001 u^2) and its high
+// part |zh| <= |z| / (1 - u), so the second-level operands' high parts sum
+// to at most M (1 + 3u) and that sum errs by at most DD_ADD M (1 + 3u)
+// (+ 2 ETA).  Every output therefore lies within
+//   r = r_a + r_b + r_c + r_d + DD_ADD (2 + 3u) M + 6 ETA
+// of its computed centre; DD_BFLY >= DD_ADD (2 + 3u).  One radius costs 13
+// operations where eight per-sum radii cost 48.
+constexpr float DD_BFLY = 6.0003f * DD_U2;
+
+__device__ __forceinline__ DDisc centre_add(const DDisc& a, const DDisc& b) {
+    DDisc z;
+    pair_add(a.xh, a.xl, b.xh, b.xl, z.xh, z.xl);
+    pair_add(a.yh, a.yl, b.yh, b.yl, z.yh, z.yl);
+    z.r = 0.f;
+    z.pad = 0.f;
+    return z;
+}
+
+__device__ __forceinline__ DDisc centre_sub(const DDisc& a, const DDisc& b) {
+    DDisc z;
+    pair_add(a.xh, a.xl, -b.xh, -b.xl, z.xh, z.xl);
+    pair_add(a.yh, a.yl, -b.yh, -b.yl, z.yh, z.yl);
+    z.r = 0.f;
+    z.pad = 0.f;
+    return z;
+}
+
+template <int SIGN>
+__device__ __forceinline__ void bfly4_dd(DDisc& a, DDisc& b, DDisc& c, DDisc& d) {
+    const float m = __fadd_ru(__fadd_ru(__fadd_ru(fabsf(a.xh), fabsf(a.yh)), __fadd_ru(fabsf(b.xh), fabsf(b.yh))),
+                              __fadd_ru(__fadd_ru(fabsf(c.xh), fabsf(c.yh)), __fadd_ru(fabsf(d.xh), fabsf(d.yh))));
+    const float rs = __fadd_ru(__fadd_ru(a.r, b.r), __fadd_ru(c.r, d.r));
+    const float r = __fmaf_ru(DD_BFLY, m, __fadd_ru(rs, 6.f * DD_ETA));
+    const DDisc apc = centre_add(a, c), amc = centre_sub(a, c);
+    const DDisc bpd = centre_add(b, d), bmd = centre_sub(b, d);
+    // jb = (SIGN i) bmd, exact
+    const DDisc jb = SIGN > 0 ? DDisc{-bmd.yh, -bmd.yl, bmd.xh, bmd.xl, 0.f, 0.f}
+                              : DDisc{bmd.yh, bmd.yl, -bmd.xh, -bmd.xl, 0.f, 0.f};
+    a = centre_add(apc, bpd);
+    c = centre_sub(apc, bpd);
+    b = centre_add(amc, jb);
+    d = centre_sub(amc, jb);
+    a.r = r;
+    b.r = r;
+    c.r = r;
+    d.r = r;
+}
+
 __device__ __forceinline__ DDisc mul_i(const DDisc& a) { return {-a.yh, -a.yl, a.xh, a.xl, a.r, 0.f}; }
 __device__ __forceinline__ DDisc mul_negi(const DDisc& a) { return {a.yh, a.yl, -a.xh, -a.xl, a.r, 0.f}; }
 __device__ __forceinline__ DDisc conj(const DDisc& a) { return {a.xh, a.xl, -a.yh, -a.yl, a.r, 0.f}; }
@@ -123,10 +179,10 @@ __device__ __forceinline__ DDisc mul_negi_flip(const DDisc& a) {
     return {a.yh, a.yl, flip(a.xh), flip(a.xl), a.r, 0.f};
 }
 
-// centre of a * b and the bound of its rounding error
+// centre of a * b (its rounding error is at most DD_MUL ma mb + 6 ETA with
+// ma = |axh| + |ayh|, mb = |bxh| + |byh|)
 __device__ __forceinline__ void pair_cmul(float axh, float axl, float ayh, float ayl, float bxh,
-                                          float bxl, float byh, float byl, DDisc& z,
-                                          float& err) {
+                                          float bxl, float byh, float byl, DDisc& z) {
     float p1h, p1l, p2h, p2l, p3h, p3l, p4h, p4l;
     pair_mul(axh, axl, bxh, bxl, p1h, p1l);     // ax bx
     pair_mul(ayh, ayl, byh, byl, p2h, p2l);     // ay by
@@ -134,18 +190,19 @@ __device__ __forceinline__ void pair_cmul(float axh, float axl, float ayh, float
     pair_mul(ayh, ayl, bxh, bxl, p4h, p4l);     // ay bx
     pair_add(p1h, p1l, -p2h, -p2l, z.xh, z.xl);
     pair_add(p3h, p3l, p4h, p4l, z.yh, z.yl);
-    const float ma = __fadd_ru(fabsf(axh), fabsf(ayh));
-    const float mb = __fadd_ru(fabsf(bxh), fabsf(byh));
-    err = __fmaf_ru(__fmul_ru(DD_MUL, ma), mb, 6.f * DD_ETA);
 }
 
 // a * w for a twiddle disc: |a w - a_c w_c| <= r (|w_c| + rho) + |a_c| rho
+// with |a_c| <= ma (1 + 2u), plus the centre's rounding DD_MUL ma mb + 6 ETA,
+// gathered as r (TW_MOD_UP + rho) + ma (DD_MUL mb + (1 + 2u) rho) + 6 ETA
+// (the terms in rho alone are the same for every twiddle of a table)
 __device__ __forceinline__ DDisc mul_tw(const DDisc& a, const DDiscTw& w) {
     DDisc z;
-    float err;
-    pair_cmul(a.xh, a.xl, a.yh, a.yl, w.ch, w.cl, w.sh, w.sl, z, err);
-    const float prop = __fmaf_ru(a.r, __fadd_ru(TW_MOD_UP, w.rho), __fmul_ru(dd_mod_up(a.xh, a.yh), w.rho));
-    z.r = __fadd_ru(prop, err);
+    pair_cmul(a.xh, a.xl, a.yh, a.yl, w.ch, w.cl, w.sh, w.sl, z);
+    const float ma = __fadd_ru(fabsf(a.xh), fabsf(a.yh));
+    const float mb = __fadd_ru(fabsf(w.ch), fabsf(w.sh));
+    const float k = __fmaf_ru(DD_MUL, mb, __fmul_ru(DD_ONE_U, w.rho));
+    z.r = __fmaf_ru(a.r, __fadd_ru(TW_MOD_UP, w.rho), __fmaf_ru(ma, k, 6.f * DD_ETA));
     z.pad = 0.f;
     return z;
 }
@@ -153,8 +210,9 @@ __device__ __forceinline__ DDisc mul_tw(const DDisc& a, const DDiscTw& w) {
 // general product (pointwise step): |a b - a_c b_c| <= |a_c| rb + |b_c| ra + ra rb
 __device__ __forceinline__ DDisc mul_ci(const DDisc& a, const DDisc& b) {
     DDisc z;
-    float err;
-    pair_cmul(a.xh, a.xl, a.yh, a.yl, b.xh, b.xl, b.yh, b.yl, z, err);
+    pair_cmul(a.xh, a.xl, a.yh, a.yl, b.xh, b.xl, b.yh, b.yl, z);
+    const float err = __fmaf_ru(__fmul_ru(DD_MUL, __fadd_ru(fabsf(a.xh), fabsf(a.yh))),
+                                __fadd_ru(fabsf(b.xh), fabsf(b.yh)), 6.f * DD_ETA);
     const float ma = dd_mod_up(a.xh, a.yh), mb = dd_mod_up(b.xh, b.yh);
     const float prop = __fmaf_ru(ma, b.r, __fmaf_ru(mb, a.r, __fmul_ru(a.r, b.r)));
     z.r = __fadd_ru(prop, err);

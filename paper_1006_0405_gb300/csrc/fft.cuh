@@ -24,18 +24,23 @@
 // BPT butterflies per thread (1 or 2; with 1 a thread holds half the
 // registers, so more warps can cover the binary64 pipe's latency).
 #pragma once
+#include <type_traits>
 #include "value.cuh"
 
 namespace ssm {
 
 template <typename V, int SIGN>
 __device__ __forceinline__ void bfly4(V& a, V& b, V& c, V& d) {
-    const V apc = a + c, amc = a - c, bpd = b + d, bmd = b - d;
-    const V jb = (SIGN > 0) ? mul_i(bmd) : mul_negi(bmd);
-    a = apc + bpd;   // u = 0
-    c = apc - bpd;   // u = 2
-    b = amc + jb;    // u = 1
-    d = amc - jb;    // u = 3
+    if constexpr (std::is_same<V, DDisc>::value) {
+        bfly4_dd<SIGN>(a, b, c, d);      // one radius bound for the four outputs
+    } else {
+        const V apc = a + c, amc = a - c, bpd = b + d, bmd = b - d;
+        const V jb = (SIGN > 0) ? mul_i(bmd) : mul_negi(bmd);
+        a = apc + bpd;   // u = 0
+        c = apc - bpd;   // u = 2
+        b = amc + jb;    // u = 1
+        d = amc - jb;    // u = 3
+    }
 }
 
 template <typename V, int SIGN, int BPT = 2>

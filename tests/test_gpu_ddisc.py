@@ -146,3 +146,36 @@ def test_fast_ladder_escalates_and_stays_exact():
         for (a, b), rr, zz, u in zip(pairs, res, digits, used):
             assert rr.status == OK and rr.precision_used == u
             assert np.array_equal(zz, E.product(a, b))
+
+
+@pytest.mark.parametrize("op", [5, 6])
+def test_pair_disc_butterfly_contains(op):
+    """The radix-4 butterfly gives its four outputs one radius: every output
+    must contain the exact butterfly of any points of the four input discs."""
+    rng = np.random.default_rng(80 + op)
+    n = 120
+    x = np.stack([_rand(rng, 4) for _ in range(n)])          # (n, 4, 5)
+    x[n // 2:, :, 4] = 0.0                                     # point inputs too
+    dx = dev(x.ravel())
+    out = torch.zeros_like(dx)
+    assert abi.ssmul_debug_ddisc_op(op, dx.data_ptr(), 0, out.data_ptr(), n) == OK
+    o = out.cpu().numpy().reshape(n, 4, 5)
+    j = Fr(1) if op == 5 else Fr(-1)                            # SIGN
+    for i in range(0, n, 2):
+        ins = [_centre(x[i, t]) for t in range(4)]
+        outs = [_centre(o[i, t]) for t in range(4)]
+        assert len({float(q[2]) for q in outs}) == 1             # one shared radius
+        for pick in range(6):
+            pts = []
+            for t, (cx, cy, cr) in enumerate(ins):
+                p, q = UNIT[(pick + 2 * t) % len(UNIT)]
+                pts.append((cx + cr * p, cy + cr * q))
+            (ax, ay), (bx, by), (cx, cy), (dx_, dy) = pts
+            # y_u = sum_t x_t (SIGN i)^{t u}
+            ex = [(ax + bx + cx + dx_, ay + by + cy + dy),
+                  (ax - j * by - cx + j * dy, ay + j * bx - cy - j * dx_),
+                  (ax - bx + cx - dx_, ay - by + cy - dy),
+                  (ax + j * by - cx - j * dy, ay - j * bx - cy + j * dx_)]
+            for u in range(4):
+                ox, oy, orr = outs[u]
+                assert (ex[u][0] - ox) ** 2 + (ex[u][1] - oy) ** 2 <= orr * orr, (op, i, u)
