@@ -98,13 +98,17 @@ def make_batch(rank: int, batch: int, n: int):
 # 1 per coefficient width) and discs / points (2, 4, 4, 2; isolation of a
 # disc: 2 bounds + 1 width per coefficient)
 COSTS = {
-    "fp64": dict(add=4, tw=8, mul=12, scale=4, iso=1),
-    "disc64": dict(add=2, tw=4, mul=4, scale=2, iso=3),
-    "naive64": dict(add=2, tw=4, mul=4, scale=2, iso=0),
+    "fp64": dict(add=4, bfly=32, tw=8, mul=12, scale=4, iso=1),
+    "disc64": dict(add=2, bfly=16, tw=4, mul=4, scale=2, iso=3),
+    "naive64": dict(add=2, bfly=16, tw=4, mul=4, scale=2, iso=0),
     # double-binary32 discs count binary32 operations: a complex add is two
-    # pair sums (2 x 14) and its radius (6); a complex product four pair
-    # products (4 x 7), two pair sums and its radius
-    "disc32x2": dict(add=34, tw=65, mul=67, scale=6, iso=0),
+    # pair sums (2 x 14) and its radius (6); the radix-4 butterfly's eight
+    # sums share one radius (8 x 28 + 13); a twiddle product is four pair
+    # products (4 x 7), two pair sums and 5 radius operations (the terms in
+    # the table's radius alone are loop invariants); a general product 56 + 10;
+    # the binary32 isolation of a component 12 (two roundings to integers,
+    # the remainders' sum and its bounds, the width, two magic-number roundings)
+    "disc32x2": dict(add=34, bfly=237, tw=61, mul=66, scale=6, iso=12),
 }
 TAGS = {"fp64": "double", "disc64": "disc", "naive64": "naive", "disc32x2": "disc32x2"}
 
@@ -115,7 +119,7 @@ def _fft_ops(logL: int, nl: int, c: dict) -> int:
     logn, logs = logL, 0
     while logn >= 2:
         s = 1 << logs
-        ops += nl * (L // 4) * 8 * c["add"] + nl * (L // 4 - s) * 3 * c["tw"]
+        ops += nl * (L // 4) * c["bfly"] + nl * (L // 4 - s) * 3 * c["tw"]
         logn -= 2
         logs += 2
     if logn == 1:
@@ -131,8 +135,8 @@ def geometry(log_n: int):
 
 
 def kernel_ops(log_n: int, precision: str = "fp64") -> dict:
-    """binary64 operations per product of each four-step kernel (log_n > 12):
-    radix-4 butterfly = 8 adds + 3 twiddle products unless p = 0; radix-2 =
+    """arithmetic operations per product of each four-step kernel (log_n > 12):
+    radix-4 butterfly (8 adds) + 3 twiddle products unless p = 0; radix-2 =
     2 adds; pair product = 2 adds + 1 general product; packing = 3 adds +
     1 twiddle product; four-step twiddles; scaling and isolation."""
     c = COSTS[precision]
