@@ -156,13 +156,15 @@ def kernel_ops(log_n: int, precision: str = "fp64") -> dict:
 
 
 # DRAM bytes per product of one launch of the dominant kernels, from the
-# ncu capture of profiles/fp64_kernels_75k_full.md and
-# profiles/disc_kernels_75k_full.md (16 products of 75k x 75k digits per
-# launch, spectra larger than L2): dram__bytes_read.sum + dram__bytes_write.sum
-# divided by 16.  Only valid for the 75k workload and these kernels.
+# ncu captures of profiles/fp64_kernels_75k_full.md,
+# profiles/disc_kernels_75k_full.md and profiles/ddisc_kernels_75k_full.md
+# (16 products of 75k x 75k digits per launch, spectra larger than L2):
+# dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  Only valid for
+# the 75k workload and these kernels.
 NCU_TRAFFIC_PER_PRODUCT = {
-    "k_rows<double>": (135.336448e6 + 35.300096e6) / 16,
-    "k_rows<disc>": (101.512960e6 + 18.267904e6) / 16,
+    "k_rows<double>": (135.372288e6 + 35.084288e6) / 16,
+    "k_rows<disc>": (101.266432e6 + 17.150720e6) / 16,
+    "k_rows<disc32x2>": (101.279232e6 + 14.916352e6) / 16,
 }
 
 
