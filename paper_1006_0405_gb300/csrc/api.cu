@@ -146,13 +146,13 @@ struct ssmul_plan_s {
     int log_tab = 0;
     TwEntry<double>* t64 = nullptr;
     TwEntry<float>* t32 = nullptr;
-    DiscC* td = nullptr;
+    DiscTw* td = nullptr;
     DDiscC* tdd = nullptr;
-    float* rho = nullptr;               // device: the radii of td and tdd
-    float rho_d = 0.f, rho_dd = 0.f;
+    float* rho = nullptr;               // device: the largest radius of td; the radius of tdd
+    float rho_dd = 0.f;
     CI<double>* s64 = nullptr;          // step-ordered twiddles (STEP_TAB x 3 each)
     CI<float>* s32 = nullptr;
-    DiscC* sd = nullptr;
+    DiscTw* sd = nullptr;
     DDiscC* sdd = nullptr;
     Geom geom[LOG_N_MAX + 1] = {};
     size_t fp32_max_digits = FP32_MAX_DIGITS;
@@ -199,8 +199,8 @@ struct ssmul_plan_s {
     unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
     TwTable tw() const {
         if (octant_only)
-            return TwTable{t64, t32, log_tab, td, tdd, rho_d, rho_dd, nullptr, nullptr, nullptr, nullptr};
-        return TwTable{t64, t32, log_tab, td, tdd, rho_d, rho_dd, s64, s32, sd, sdd};
+            return TwTable{t64, t32, log_tab, td, tdd, rho_dd, nullptr, nullptr, nullptr, nullptr};
+        return TwTable{t64, t32, log_tab, td, tdd, rho_dd, s64, s32, sd, sdd};
     }
 };
 
@@ -953,12 +953,12 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&p->t64, tab * sizeof(TwEntry<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->t32, tab * sizeof(TwEntry<float>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscC));
+    if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscTw));
     if (e == cudaSuccess) e = cudaMalloc(&p->tdd, tab * sizeof(DDiscC));
     if (e == cudaSuccess) e = cudaMalloc(&p->rho, 2 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&p->s64, 3 * STEP_TAB * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->s32, 3 * STEP_TAB * sizeof(CI<float>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->sd, 3 * STEP_TAB * sizeof(DiscC));
+    if (e == cudaSuccess) e = cudaMalloc(&p->sd, 3 * STEP_TAB * sizeof(DiscTw));
     if (e == cudaSuccess) e = cudaMalloc(&p->sdd, 3 * STEP_TAB * sizeof(DDiscC));
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
@@ -1016,7 +1016,6 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
         return fail(cuda_status(e));
     if ((e = cudaEventRecord(p->desc_free, p->stream)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
-    p->rho_d = h_rho[0];
     p->rho_dd = h_rho[1];
     *out = p;
     return SSMUL_OK;

@@ -46,7 +46,9 @@ struct alignas(8) DDiscTw {
     float pad;
 };
 
-// twiddle table entry: the centre only (the table's radius is shared)
+// twiddle table entry: the centre only.  Every entry of a table shares one
+// radius, so that a scattered read moves 16 bytes; it costs nothing here, as
+// the pair split's 2u^2 dominates every entry's radius.
 struct alignas(16) DDiscC {
     float ch, cl, sh, sl;
 };
@@ -233,11 +235,11 @@ __device__ __forceinline__ DDisc scale_pow2(const DDisc& a, int k) {
 // ch = RN32(c), cl = RN32(c - ch) (c - ch exact in binary64), so
 // |c - ch - cl| <= u |cl| <= 2^-48 for |c| <= 1; the radius grows by the
 // two components' errors: rho[1] = rho[0] + 2u^2 + ETA, rounded up
-__global__ void k_ddisc_tw_gen(const DiscC* td, float* rho, DDiscC* tdd, int log_n) {
+__global__ void k_ddisc_tw_gen(const DiscTw* td, float* rho, DDiscC* tdd, int log_n) {
     const int64_t count = (int64_t(1) << log_n) / 8 + 1;
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
-        const DiscC e = td[j];
+        const DiscTw e = td[j];
         const float ch = __double2float_rn(e.c);
         const float cl = __double2float_rn(e.c - double(ch));
         const float sh = __double2float_rn(e.s);

@@ -42,13 +42,6 @@ struct DiscTw {
     float pad;
 };
 
-// Disc twiddle table entry: the centre only.  Every entry of a table shares
-// one radius (the largest of its entries' radii), so that a scattered read
-// moves 16 bytes.
-struct alignas(16) DiscC {
-    double c, s;
-};
-
 // ---- bounds from the bit patterns (integer pipe) ----------------------------------
 
 // An upper bound (binary32) on half an ulp of the binary64 value x, i.e. on

@@ -45,14 +45,14 @@ struct TwTable {
     const TwEntry<double>* t64;   // Ntab/8 + 1 entries
     const TwEntry<float>* t32;    // same, binary32
     int log_n;                    // log2 Ntab
-    const DiscC* td;              // same, as disc centres
+    const DiscTw* td;             // same, as discs (centre, radius)
     const DDiscC* tdd;            // same, as double-binary32 disc centres
-    float rho_d, rho_dd;          // the radius of every entry of td / tdd
+    float rho_dd;                 // the radius of every entry of tdd
     // step-ordered copies (3 STEP_TAB entries each), or all null: then the
     // transforms read the octant tables
     const CI<double>* s64;
     const CI<float>* s32;
-    const DiscC* sd;
+    const DiscTw* sd;
     const DDiscC* sdd;
 };
 
@@ -88,10 +88,10 @@ __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log
 // The disc form of each enclosure: centre = the rounded midpoint of each
 // component's interval, radius >= (distance of the centre to either end,
 // rounded up) summed over the two components, which bounds the complex
-// distance to any point of the rectangle.  The table's radius *rho (zero on
-// entry) becomes the largest of these (nonnegative binary32 values order
-// like their bit patterns).
-__global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscC* td, float* rho, int log_n) {
+// distance to any point of the rectangle.  *rho (zero on entry) becomes the
+// largest of these radii (nonnegative binary32 values order like their bit
+// patterns), the radius the double-binary32 table shares.
+__global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscTw* td, float* rho, int log_n) {
     const int64_t count = (int64_t(1) << log_n) / 8 + 1;
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
@@ -100,8 +100,9 @@ __global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscC* td, float* rho,
         const double s = __dadd_rn(0.5 * e.sl, 0.5 * e.sh);
         const double ec = fmax(__dsub_ru(c, e.cl), __dsub_ru(e.ch, c));
         const double es = fmax(__dsub_ru(s, e.sl), __dsub_ru(e.sh, s));
-        td[j] = {c, s};
-        atomicMax(reinterpret_cast<int*>(rho), __float_as_int(__double2float_ru(__dadd_ru(ec, es))));
+        const float r = __double2float_ru(__dadd_ru(ec, es));
+        td[j] = {c, s, r, 0.f};
+        atomicMax(reinterpret_cast<int*>(rho), __float_as_int(r));
     }
 }
 
@@ -115,13 +116,13 @@ __device__ __forceinline__ DiscTw twiddle_disc(const TwTable& tw, uint32_t j) {
     const uint32_t quad = j >> (ln - 2);
     const uint32_t r = j & (q - 1u);
     const bool refl = r > (q >> 1);
-    const DiscC e = tw.td[refl ? q - r : r];
+    const DiscTw e = tw.td[refl ? q - r : r];
     const double c = refl ? e.s : e.c, s = refl ? e.c : e.s;
     const bool swap = quad & 1u;
     const double wc = swap ? s : c, ws = swap ? c : s;
     const bool negr = quad == 1u || quad == 2u;
     const bool negi = (quad >= 2u) != (SIGN < 0);
-    return {negr ? flip(wc) : wc, negi ? flip(ws) : ws, tw.rho_d, 0.f};
+    return {negr ? flip(wc) : wc, negi ? flip(ws) : ws, e.rho, 0.f};
 }
 
 template <typename T>

@@ -152,10 +152,9 @@ template <> struct StepOf<CI<float>> {
     }
 };
 template <> struct StepOf<Disc> {
-    static __device__ __forceinline__ const DiscC* table(const TwTable& tw) { return tw.sd; }
-    static __device__ __forceinline__ DiscTw load(const DiscC* t, int i, const TwTable& tw) {
-        const DiscC e = t[i];
-        return {e.c, e.s, tw.rho_d, 0.f};
+    static __device__ __forceinline__ const DiscTw* table(const TwTable& tw) { return tw.sd; }
+    static __device__ __forceinline__ DiscTw load(const DiscTw* t, int i, const TwTable&) {
+        return t[i];
     }
 };
 template <> struct StepOf<Pt> : StepOf<Disc> {};
@@ -176,9 +175,9 @@ __device__ __forceinline__ typename VTraits<V>::Tw step_twiddle(const TwTable& t
     return SIGN > 0 ? w : tw_conj(w);
 }
 
-// Fills the step tables from the octant tables (rho of the disc tables is
-// not needed: the step tables of discs hold centres).
-__global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscC* sd,
+// Fills the step tables from the octant tables (the pair-disc step table
+// holds centres: its radius is the table's).
+__global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscTw* sd,
                               DDiscC* sdd) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * STEP_TAB;
          i += gridDim.x * blockDim.x) {
@@ -195,8 +194,7 @@ __global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscC
         const uint32_t j = uint32_t(u * (pos - (1 << lq))) << (tw.log_n - logn);
         s64[i] = twiddle<double, 1>(tw, j);
         s32[i] = twiddle<float, 1>(tw, j);
-        const DiscTw d = twiddle_disc<1>(tw, j);
-        sd[i] = {d.c, d.s};
+        sd[i] = twiddle_disc<1>(tw, j);
         const DDiscTw dd = twiddle_ddisc<1>(tw, j);
         sdd[i] = {dd.ch, dd.cl, dd.sh, dd.sl};
     }
