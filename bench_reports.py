@@ -269,6 +269,16 @@ def _uneven_batched(torch, abi, batch, max_n, prec, stream, seed):
     abi.ssmul_debug_kernel_stats(plan, False)
     t = _time_batch(torch, plan, batch, 3, stream)
     _, kst = abi.ssmul_debug_kernel_stats(plan, False)
+    # the same batch once more without the graph and with every launch timed:
+    # the summed kernel time against the graph-replayed wall time shows how
+    # much of a batched call the GPU spends outside the kernels
+    abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 0)
+    abi.ssmul_debug_kernel_stats(plan, True)
+    with torch.cuda.stream(stream):
+        batch.run(plan)
+        stream.synchronize()
+    _, kt = abi.ssmul_debug_kernel_stats(plan, False)
+    kernel_s = sum(ms for _, ms in kt.values()) / 1e3
     abi.ssmul_plan_destroy(plan)
     rs, zs = batch.results(), batch.digits()
     res_ok = _verify_residues(batch, rs, zs)
@@ -287,7 +297,8 @@ def _uneven_batched(torch, abi, batch, max_n, prec, stream, seed):
         "s_per_batch": t, "verified_digits_per_s": ver_digits / t, "statuses": statuses,
         "residue_verified": int(res_ok.sum()), "full_sample": len(sample),
         "full_sample_verified": full_ok, "precision_used": used,
-        "launches_per_batch": {k: v[0] // 4 for k, v in kst.items() if v[0]}}
+        "launches_per_batch": {k: v[0] // 4 for k, v in kst.items() if v[0]},
+        "kernel_s_per_batch": kernel_s, "kernel_time_fraction": kernel_s / t}
 
 
 def run(args):
