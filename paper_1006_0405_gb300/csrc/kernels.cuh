@@ -485,7 +485,7 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
 // ---- four-step kernels --------------------------------------------------------
 
 template <typename Tag, int BPT = 2>
-__global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
+__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -519,7 +519,7 @@ __global__ void k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int log
 }
 
 template <typename Tag, int BPT = 2>
-__global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
+__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_rows) k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
@@ -554,7 +554,7 @@ __global__ void k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, 
 }
 
 template <typename Tag, int BPT = 2>
-__global__ void k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
+__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
     using V = typename ValOf<Tag>::type;
     constexpr int RUNG = VTraits<V>::rung;

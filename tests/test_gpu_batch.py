@@ -128,3 +128,38 @@ def test_batched_chunks_beyond_the_arena():
     assert s == OK
     for (a, b), r, z in zip(pairs, res, digits):
         assert r.status == OK and np.array_equal(z, E.product(a, b))
+
+
+@pytest.mark.parametrize("prec", [abi.SSMUL_PREC_FP64, abi.SSMUL_PREC_DISC64,
+                                  abi.SSMUL_PREC_DISC32X2, abi.SSMUL_PREC_LADDER_FAST])
+def test_bench_configuration_75k(prec):
+    """The launch configuration bench.py times, at the paper's size: one
+    ssmul_mul_batched call over products of two 75,000-digit operands from
+    the bench's own generator (uniform bytes, the last product all 0xFF),
+    on the plan's stream, twice in a row; every product bit-exact."""
+    import bench
+    B, n = 16, 75000
+    (a_pool, b_pool, a_off, b_off, z_off), dists = bench.make_batch(0, B, n)
+    expect = [E.product(a_pool[a_off[i]:a_off[i] + n], b_pool[b_off[i]:b_off[i] + n])
+              for i in range(B)]
+    with StreamPlan(n, n, B, prec) as p:
+        with torch.cuda.stream(p.stream):
+            descs = [(int(a_off[i]), int(b_off[i]), int(z_off[i]), n, n) for i in range(B)]
+            da, db = dev(a_pool), dev(b_pool)
+            dres = torch.zeros(ctypes.sizeof(abi.ssmul_result) * B, dtype=torch.uint8, device="cuda")
+            outs = []
+            for _ in range(2):
+                dz = torch.full((B * 2 * n,), 0xA5, dtype=torch.uint8, device="cuda")
+                assert abi.ssmul_mul_batched(p.h, descs, da.data_ptr(), db.data_ptr(), dz.data_ptr(),
+                                             dres.data_ptr()) == OK
+                p.stream.synchronize()
+                res = (abi.ssmul_result * B)()
+                host = dres.cpu().numpy()
+                ctypes.memmove(res, host.ctypes.data, ctypes.sizeof(res))
+                outs.append((list(res), dz.cpu().numpy()))
+    for res, z in outs:
+        for i in range(B):
+            assert res[i].status == OK, (i, abi.status_string(res[i].status))
+            assert np.array_equal(z[z_off[i]:z_off[i] + 2 * n], expect[i]), i
+            assert 0.0 <= res[i].max_width < 1.0
+    assert np.array_equal(outs[0][1], outs[1][1])
