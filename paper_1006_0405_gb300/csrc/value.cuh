@@ -23,14 +23,15 @@ namespace ssm {
 constexpr int RUNGS = 5;
 
 // sw_src, sw_mask: the shared-memory swizzle of SBuf for the type's size;
-// reg_rows, reg_cols: register caps of k_rows and of the column kernels
-// (binary64 rectangles: 96 and 80 registers let 5 and 3 CTAs share an SM,
-// which hides more binary64 latency than the few spills cost)
+// reg_rows, reg_cols: register caps of k_rows and of the column kernels,
+// chosen so that one more CTA shares an SM than the natural register count
+// allows (an explicit cap for every type: a cap of 255 is not the same as
+// none)
 template <typename V> struct VTraits;
 template <> struct VTraits<CI<float>> {
     using Tw = CI<float>;
     static constexpr int rung = 0, sw_src = 3, sw_mask = 3;
-    static constexpr int reg_rows = 255, reg_cols = 255;
+    static constexpr int reg_rows = 64, reg_cols = 72;
 };
 template <> struct VTraits<CI<double>> {
     using Tw = CI<double>;
@@ -40,17 +41,17 @@ template <> struct VTraits<CI<double>> {
 template <> struct VTraits<Disc> {
     using Tw = DiscTw;
     static constexpr int rung = 2, sw_src = 3, sw_mask = 7;
-    static constexpr int reg_rows = 255, reg_cols = 255;
+    static constexpr int reg_rows = 80, reg_cols = 80;
 };
 template <> struct VTraits<Pt> {
     using Tw = DiscTw;
     static constexpr int rung = 3, sw_src = 3, sw_mask = 3;
-    static constexpr int reg_rows = 255, reg_cols = 255;
+    static constexpr int reg_rows = 64, reg_cols = 72;
 };
 template <> struct VTraits<DDisc> {
     using Tw = DDiscTw;
     static constexpr int rung = 4, sw_src = 3, sw_mask = 7;
-    static constexpr int reg_rows = 255, reg_cols = 255;
+    static constexpr int reg_rows = 64, reg_cols = 64;
 };
 
 // A transform buffer in shared memory.  Element i lives in slot
