@@ -1,7 +1,7 @@
 """Benchmark: verified interval-FFT multiplications on one GB300 (or N replicas).
 
 Workload (default): the paper-scale binary64 interval method, products of
-two 75,000-digit base-256 operands (FFT length 2^18).  One step is one
+two 75,000-digit base-256 operands (FFT length 3 2^16).  One step is one
 ssmul_mul_batched call over a batch of B such products (B - 1 with uniform
 random digits, one with every digit 0xFF, the worst case of coefficient
 size), i.e. one pass of the whole path: interval transforms, pointwise
@@ -127,53 +127,93 @@ def _fft_ops(logL: int, nl: int, c: dict) -> int:
     return ops
 
 
-def geometry(log_n: int):
-    log_n2 = min((log_n + 1) // 2, 11)
-    log_n1 = log_n - log_n2
-    c = max(0, 11 - log_n1)
-    return log_n1, log_n2, min(c, log_n2), min(c, log_n2 - 1)
+def _fft3_ops(loga: int, nl: int, c: dict) -> int:
+    """lines of length 3 2^loga (loga even): radix-4 steps, then one radix-3
+    step of 6 adds, a scaling by 1/2 and one twiddle product per butterfly"""
+    L = 3 << loga
+    ops = 0
+    logn2, logs = loga, 0
+    while logn2 >= 2:
+        s = 1 << logs
+        ops += nl * (L // 4) * c["bfly"] + nl * (L // 4 - s) * 3 * c["tw"]
+        logn2 -= 2
+        logs += 2
+    return ops + nl * (L // 3) * (6 * c["add"] + c["scale"] + c["tw"])
 
 
-def kernel_ops(log_n: int, precision: str = "fp64") -> dict:
-    """arithmetic operations per product of each four-step kernel (log_n > 12):
+def length_code(na: int, nb: int) -> tuple[int, int]:
+    """(R, k): the transform length R 2^k the library picks (SSMUL_OPT_RADIX3 on)."""
+    L = na + nb - 1
+    k = max(2, (L - 1).bit_length())
+    j = k - 2
+    if 11 <= j <= 21 and (3 << j) >= L:
+        return 3, j
+    return 1, k
+
+
+def geometry(R: int, k: int):
+    """(R, log2 N1 / R, log2 N2, log2 C1, log2 C3) of the default four-step split"""
+    if R == 1:
+        b = min((k + 1) // 2, 11)
+        a = k - b
+        c = max(0, 11 - a)
+    else:
+        b = (k + 1) // 2
+        a = k - b
+        if a & 1:
+            a, b = a - 1, b + 1
+        while b > 11:
+            a, b = a + 2, b - 2
+        while a > 10:
+            a, b = a - 2, b + 2
+        c = max(0, 11 - a - 1)
+    return a, b, min(c, b), min(c, b - 1)
+
+
+def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
+    """arithmetic operations per product of each four-step kernel (N > 4096):
     radix-4 butterfly (8 adds) + 3 twiddle products unless p = 0; radix-2 =
-    2 adds; pair product = 2 adds + 1 general product; packing = 3 adds +
-    1 twiddle product; four-step twiddles; scaling and isolation."""
+    2 adds; radix-3 = 6 adds + 1 scaling + 1 twiddle product; pair product =
+    2 adds + 1 general product; packing = 3 adds + 1 twiddle product;
+    four-step twiddles; scaling and isolation."""
     c = COSTS[precision]
     tag = TAGS[precision]
-    n1l, n2l, c1l, c3l = geometry(log_n)
-    N1, N2 = 1 << n1l, 1 << n2l
+    R, k = length_code(na, nb)
+    n1l, n2l, c1l, c3l = geometry(R, k)
+    N1, N2 = R << n1l, 1 << n2l
     M2 = N2 // 2
-    fwd = (N2 >> c1l) * _fft_ops(n1l, 1 << c1l, c) + (N1 - 1) * (N2 - 1) * c["tw"]
+    col = (lambda nl: _fft_ops(n1l, nl, c)) if R == 1 else (lambda nl: _fft3_ops(n1l, nl, c))
+    fwd = (N2 >> c1l) * col(1 << c1l) + (N1 - 1) * (N2 - 1) * c["tw"]
     rows = 0
     for k1 in range(N1 // 2 + 1):
         nl = 1 if k1 == (N1 - k1) % N1 else 2
         rows += _fft_ops(n2l, nl, c) + _fft_ops(n2l - 1, nl, c)
         rows += (nl * N2 // 2) * (2 * c["add"] + c["mul"]) + nl * M2 * (3 * c["add"] + c["tw"])
         rows += nl * (M2 - 1) * c["tw"] if k1 else 0
-    inv = (M2 >> c3l) * _fft_ops(n1l, 1 << c3l, c) + (N1 * M2) * (c["scale"] + 2 * c["iso"])
+    inv = (M2 >> c3l) * col(1 << c3l) + (N1 * M2) * (c["scale"] + 2 * c["iso"])
     return {f"k_fwd_cols<{tag}>": fwd, f"k_rows<{tag}>": rows, f"k_inv_cols<{tag}>": inv}
 
 
-# DRAM bytes per product of one launch of the dominant kernels, from the
-# ncu captures of profiles/fp64_kernels_75k_full.md,
-# profiles/disc_kernels_75k_full.md and profiles/ddisc_kernels_75k_full.md
-# (16 products of 75k x 75k digits per launch, spectra larger than L2):
-# dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  Only valid for
-# the 75k workload and these kernels.
-NCU_TRAFFIC_PER_PRODUCT = {
-    "k_rows<double>": (135.372288e6 + 35.084288e6) / 16,
-    "k_rows<disc>": (101.266432e6 + 17.150720e6) / 16,
-    "k_rows<disc32x2>": (101.279232e6 + 14.916352e6) / 16,
-}
+# DRAM bytes per product of one launch of the dominant kernels, from ncu
+# captures (16 products of 75k x 75k digits per launch, spectra larger than
+# L2): dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  Only
+# valid for the 75k workload and the kernels as captured; empty when the
+# kernels changed since.
+NCU_TRAFFIC_PER_PRODUCT: dict = {}
 
 
 def algorithmic_bytes(n: int) -> float:
     """HBM bytes one product's passes must move at minimum (binary64
-    rectangles, N = 2^18 for 75k digits): digits in, Z written and read,
+    rectangles, N = 3 2^16 for 75k digits): digits in, Z written and read,
     W written and read, coefficients written and read, digits out."""
-    N = 1 << max(2, (2 * n - 2).bit_length())
+    R, k = length_code(n, n)
+    N = R << k
     return 2 * n + 32 * N * 2 + 16 * N * 2 + 8 * N * 2 + 2 * n
+
+
+def fft_len_str(n: int) -> str:
+    R, k = length_code(n, n)
+    return f"2^{k}" if R == 1 else f"3*2^{k}"
 
 
 def fp64_peak_gops(sm_mhz: float) -> float:
@@ -481,7 +521,7 @@ def run_ours(args):
                     a_w = max(a_w, rr[i].max_width)
             a_t = sum(e0.elapsed_time(e1) for e0, e1 in aev) / 1e3
             amodel = "disc32x2" if alt == "ladder_fast" else alt
-            aops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length(), amodel)
+            aops = kernel_ops(n, n, amodel)
             adom = max(aops, key=lambda kk: akst.get(kk, (0, 0.0))[1])
             ala, ams = akst[adom]
             aach = aops[adom] * B / (ams / ala * 1e-3) / 1e9 if ala else 0.0
@@ -500,7 +540,7 @@ def run_ours(args):
     if rank == 0:
         # roofline of the dominant kernel: binary64 pipe (an ALU bound)
         model = "disc32x2" if args.precision == "ladder_fast" else args.precision
-        ops = kernel_ops(18 if n == 75000 else (2 * n - 1).bit_length(), model)
+        ops = kernel_ops(n, n, model)
         dom = max(ops, key=lambda k: kstats.get(k, (0, 0.0))[1])
         launches, ms = kstats[dom]
         # one launch covers all B products of the batch
@@ -533,7 +573,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"{n}x{n} base-256 digits, "
                                    f"{ {'fp64': 'binary64 inf-sup intervals', 'disc64': 'binary64 midpoint-radius discs', 'naive64': 'unverified binary64 points', 'disc32x2': 'double-binary32 midpoint-radius discs', 'ladder_fast': 'ladder of double-binary32 then binary64 discs'}[args.precision]}, "
-                                   f"FFT length 2^18; batch of {B} per step ({B - 1} uniform "
+                                   f"FFT length {fft_len_str(n)}; batch of {B} per step ({B - 1} uniform "
                                    f"random, 1 all-0xFF) per GPU",
                        "batch_per_gpu": B, "digits": n, "precision": args.precision,
                        "l2": "flushed between timed steps (256 MiB write)",

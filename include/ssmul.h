@@ -84,10 +84,11 @@ typedef struct {
     int32_t  precision_used;    /* ssmul_precision of the deciding rung:
                                  * SSMUL_PREC_FP32, _FP64, _DISC64,
                                  * _DISC32X2 or _NAIVE64 */
-    uint32_t fft_log2;          /* log2 of the transform length N */
+    uint32_t fft_log2;          /* the transform length is
+                                 * N = (fft_times3 ? 3 : 1) << fft_log2 */
     uint32_t n_unisolated;      /* coefficients whose set holds >= 2 integers */
     uint32_t n_empty;           /* coefficients whose set holds no integer */
-    uint32_t reserved;
+    uint32_t fft_times3;        /* 1: N = 3 * 2^fft_log2 (SSMUL_OPT_RADIX3) */
     double   max_width;         /* largest coefficient interval width
                                  * (rounded up), in units of 1; for
                                  * SSMUL_PREC_NAIVE64 the largest distance
@@ -150,7 +151,16 @@ typedef enum {
      * coefficients before one carry: the way past the isolation limit that
      * Section 1 names ("use a different algorithm").  The status is the
      * worst of the parts'.  0 (default): off.  Batched calls do not split. */
-    SSMUL_OPT_SPLIT_DIGITS = 4
+    SSMUL_OPT_SPLIT_DIGITS = 4,
+    /* value != 0 (default): a product whose na + nb - 1 coefficients fit in
+     * 3 * 2^k < 2^ceil(log2(na + nb - 1)) points (and 3 * 2^k > 4096) uses
+     * the transform length N = 3 * 2^k: the zero padding of Section 2.3 to
+     * the next length of either family, a quarter less work than the next
+     * power of two.  The column transforms then take one radix-3 step, the
+     * roots of unity come from a second table (Ntab = 3 * 2^K), and the
+     * 1/N scaling leaves a factor 1/3 that the isolation applies exactly to
+     * the integer bounds.  0: powers of two only (the paper's 2^k). */
+    SSMUL_OPT_RADIX3 = 5
 } ssmul_option;
 
 /*

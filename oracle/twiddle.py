@@ -12,7 +12,9 @@ pi, Taylor series for sin and cos on [0, pi/4]), each with a proved bound
 on its error in units of 2^-PREC, and the resulting rational enclosure is
 rounded outward to binary64 (or binary32).  Exact values (0, +-1) give
 point intervals.  Symmetries of the circle map j to the first octant
-without error because N is a power of two.
+without error whenever N is a multiple of 8 (powers of two >= 8 and the
+lengths 3 2^k, k >= 3): the quarter turn N/4 and the octant N/8 are then
+whole steps.
 
 Pins (tests/test_oracle_twiddle.py): pi against its published decimal
 expansion, cos^2 + sin^2 = 1 on the exact rational bounds, containment of
@@ -125,8 +127,8 @@ def octant_table(N: int, f32: bool = False):
     """Enclosures of cos and sin of 2 pi j / N for j = 0 .. N/8 (N >= 8).
 
     Returns four float64 arrays (cos_lo, cos_hi, sin_lo, sin_hi)."""
-    if N < 8 or N & (N - 1):
-        raise ValueError("N must be a power of two >= 8")
+    if N < 8 or N % 8:
+        raise ValueError("N must be a multiple of 8")
     m = N // 8
     out = np.zeros((4, m + 1))
     for jj in range(m + 1):

@@ -31,17 +31,36 @@ constexpr size_t FP32_MAX_DIGITS = 32;
 constexpr size_t ARENA_CAP = size_t(4) << 30;
 
 struct Geom {
-    int log_n;       // transform length N = 2^log_n
+    int log_n;       // transform length code (N = 2^log_n, or 3 2^(log_n - LEN3))
     bool small;      // whole product in one CTA
+    int r;           // 1, or 3: columns of 3 2^log_n1 (four-step only)
     int log_n1, log_n2;
     int log_c1, log_c3;
     int log_cta;     // log2 of the elements a column CTA holds (at least N1)
 };
 
+constexpr int GEOM_CODES = LEN3 + LOG3_MAX + 1;
+
+// the transform length of a length code
+size_t len_of(int code) {
+    return code >= LEN3 ? size_t(3) << (code - LEN3) : size_t(1) << code;
+}
+
 int log_n_for(size_t na, size_t nb) {
     const size_t L = na + nb - 1;
     int k = 2;                          // N >= 4: the half-length inverse needs N/2 >= 2
     while ((size_t(1) << k) < L) ++k;
+    return k;
+}
+
+// The length code of a product: the next power of two N >= na + nb - 1, or
+// 3 2^(k-2) = 3N/4 when that is long enough and allowed (the only length
+// of the other family between N/2 and N).
+int length_code(size_t na, size_t nb, bool radix3) {
+    const int k = log_n_for(na, nb);
+    const int j = k - 2;
+    if (radix3 && j >= LOG3_MIN && j <= LOG3_MAX && (size_t(3) << j) >= na + nb - 1)
+        return LEN3 + j;
     return k;
 }
 
@@ -56,6 +75,7 @@ bool geom_valid(int log_n, int log_n2) {
 Geom make_geom(int log_n, int log_n2, int log_cta) {
     Geom g{};
     g.log_n = log_n;
+    g.r = 1;
     g.small = log_n <= LOG_SMALL;
     if (!g.small) {
         g.log_n2 = log_n2;
@@ -72,6 +92,41 @@ Geom default_geom(int log_n) {
     int log_n2 = (log_n + 1) / 2;
     if (log_n2 > LOG_N2_MAX) log_n2 = LOG_N2_MAX;
     return make_geom(log_n, log_n2, LOG_CTA_ELEMS);
+}
+
+// N = 3 2^j = N1 N2 with N1 = 3 2^a (a even: the radix-4 steps of a column
+// end at length 3), N2 = 2^log_n2
+bool geom3_valid(int j, int log_n2) {
+    const int a = j - log_n2;
+    return j >= LOG3_MIN && j <= LOG3_MAX && log_n2 >= 2 && log_n2 <= LOG_N2_MAX && a >= 2 &&
+           a <= 10 && (a & 1) == 0;
+}
+
+// column CTAs hold C 3 2^a >= 1.5 2^log_cta elements
+Geom make_geom3(int j, int log_n2, int log_cta) {
+    Geom g{};
+    g.log_n = LEN3 + j;
+    g.r = 3;
+    g.small = false;
+    g.log_n2 = log_n2;
+    g.log_n1 = j - log_n2;
+    g.log_cta = log_cta;
+    const int c = log_cta - g.log_n1 - 1;
+    g.log_c1 = clampi(c, 0, g.log_n2);
+    g.log_c3 = clampi(c, 0, g.log_n2 - 1);
+    return g;
+}
+
+Geom default_geom3(int j) {
+    int b = (j + 1) / 2, a = j - b;
+    if (a & 1) { --a; ++b; }
+    while (b > LOG_N2_MAX) { b -= 2; a += 2; }
+    while (a > 10) { a -= 2; b += 2; }
+    return make_geom3(j, b, LOG_CTA_ELEMS);
+}
+
+Geom default_geom_code(int code) {
+    return code >= LEN3 ? default_geom3(code - LEN3) : default_geom(code);
 }
 
 int threads_for(int elems) {          // block_fft with 2 butterflies per thread
@@ -154,7 +209,19 @@ struct ssmul_plan_s {
     CI<float>* s32 = nullptr;
     DiscTw* sd = nullptr;
     DDiscC* sdd = nullptr;
-    Geom geom[LOG_N_MAX + 1] = {};
+    // the family Ntab3 = 3 2^log_tab3 (lengths 3 2^j; 0 when the plan has none)
+    int log_tab3 = 0;
+    TwEntry<double>* t64_3 = nullptr;
+    TwEntry<float>* t32_3 = nullptr;
+    DiscTw* td_3 = nullptr;
+    DDiscC* tdd_3 = nullptr;
+    float rho_dd3 = 0.f;
+    CI<double>* s64_3 = nullptr;        // step-ordered twiddles for n = 3 2^j
+    CI<float>* s32_3 = nullptr;
+    DiscTw* sd_3 = nullptr;
+    DDiscC* sdd_3 = nullptr;
+    Geom geom[GEOM_CODES] = {};           // by length code
+    bool radix3 = true;                 // SSMUL_OPT_RADIX3
     size_t fp32_max_digits = FP32_MAX_DIGITS;
     bool balanced = false;
     uint32_t* pre = nullptr;            // balanced: digit prefix sums of one product
@@ -199,8 +266,19 @@ struct ssmul_plan_s {
     unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
     TwTable tw() const {
         if (octant_only)
-            return TwTable{t64, t32, log_tab, td, tdd, rho_dd, nullptr, nullptr, nullptr, nullptr};
-        return TwTable{t64, t32, log_tab, td, tdd, rho_dd, s64, s32, sd, sdd};
+            return TwTable{t64, t32, log_tab, td, tdd, rho_dd, nullptr, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, nullptr, nullptr};
+        return TwTable{t64, t32, log_tab, td, tdd, rho_dd, s64, s32, sd, sdd,
+                       nullptr, nullptr, nullptr, nullptr};
+    }
+    // the table of the family 3 2^K (its power-of-two step tables are the
+    // first family's: the same enclosed values)
+    TwTable tw3() const {
+        if (octant_only)
+            return TwTable{t64_3, t32_3, log_tab3, td_3, tdd_3, rho_dd3, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, nullptr, nullptr, nullptr};
+        return TwTable{t64_3, t32_3, log_tab3, td_3, tdd_3, rho_dd3, s64, s32, sd, sdd,
+                       s64_3, s32_3, sd_3, sdd_3};
     }
 };
 
@@ -254,7 +332,37 @@ ssmul_status set_smem_attrs() {
     SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SS_TRY(cudaFuncSetAttribute(k_rows<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return SSMUL_OK;
+}
+
+// The three four-step launches of one transform length of family R.
+template <typename T, int R>
+void enqueue_four_step(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g, int gate,
+                       const TwTable& tw) {
+    using V = typename ValOf<T>::type;
+    constexpr int B = plan_bpt<V>();
+    const int ko = kind_off<T>();
+    const int n1 = R << g.log_n1, n2 = 1 << g.log_n2;
+    const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
+    {
+        LaunchScope ls(p, SSMUL_K_FWD_COLS + ko);
+        k_fwd_cols<T, B, R><<<dim3(n2 >> g.log_c1, count), fft_threads<V>(e1), e1 * sizeof(V),
+                              p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
+    }
+    {
+        LaunchScope ls(p, SSMUL_K_ROWS + ko);
+        k_rows<T, B, R><<<dim3(n1 / 2 + 1, count), fft_threads<V>(2 * n2), 2 * n2 * sizeof(V),
+                          p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
+    }
+    {
+        LaunchScope ls(p, SSMUL_K_INV_COLS + ko);
+        k_inv_cols<T, B, R><<<dim3((n2 / 2) >> g.log_c3, count), fft_threads<V>(e3),
+                              e3 * sizeof(V), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
+                                                           g.log_c3, gate);
+    }
 }
 
 // Enqueue the interval convolution of `count` products that share one
@@ -271,25 +379,10 @@ ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, con
         const int n = 1 << g.log_n;
         LaunchScope ls(p, SSMUL_K_SMALL + ko);
         k_small<T, B><<<count, fft_threads<V>(n), n * sizeof(V), p->stream>>>(d_desc, tw, gate);
+    } else if (g.r == 3) {
+        enqueue_four_step<T, 3>(p, d_desc, count, g, gate, p->tw3());
     } else {
-        const int n1 = 1 << g.log_n1, n2 = 1 << g.log_n2;
-        const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
-        {
-            LaunchScope ls(p, SSMUL_K_FWD_COLS + ko);
-            k_fwd_cols<T, B><<<dim3(n2 >> g.log_c1, count), fft_threads<V>(e1), e1 * sizeof(V),
-                            p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
-        }
-        {
-            LaunchScope ls(p, SSMUL_K_ROWS + ko);
-            k_rows<T, B><<<dim3(n1 / 2 + 1, count), fft_threads<V>(2 * n2), 2 * n2 * sizeof(V),
-                        p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
-        }
-        {
-            LaunchScope ls(p, SSMUL_K_INV_COLS + ko);
-            k_inv_cols<T, B><<<dim3((n2 / 2) >> g.log_c3, count), fft_threads<V>(e3),
-                            e3 * sizeof(V), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
-                                                         g.log_c3, gate);
-        }
+        enqueue_four_step<T, 1>(p, d_desc, count, g, gate, tw);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -366,7 +459,7 @@ ssmul_status enqueue_prefix(ssmul_plan_t p, const ProdDesc* d_desc, int count, s
 // Enqueue one complete product (rungs, carry, outcome) for d_desc[0].
 ssmul_status enqueue_product(ssmul_plan_t p, const ProdDesc* d_desc, size_t na, size_t nb,
                              ssmul_precision prec) {
-    const Geom& g = p->geom[log_n_for(na, nb)];
+    const Geom& g = p->geom[length_code(na, nb, p->radix3)];
     {
         ssmul_status s0 = enqueue_prefix(p, d_desc, 1, na > nb ? na : nb);
         if (s0 != SSMUL_OK) return s0;
@@ -402,7 +495,7 @@ ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t*
     d.z = z;
     d.na = uint32_t(na);
     d.nb = uint32_t(nb);
-    d.log_n = log_n_for(na, nb);
+    d.log_n = length_code(na, nb, p->radix3);
     d.Z = p->Z;
     d.W = p->W;
     d.coeff = p->coeff;
@@ -516,7 +609,7 @@ ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uin
 // consumed) and the half-length inverse W (N/2 intervals) for four-step
 // products, the coefficients alone for single-CTA products.
 size_t arena_need(int log_n) {
-    const size_t n = size_t(1) << log_n;
+    const size_t n = len_of(log_n);
     if (log_n <= LOG_SMALL) return (n * sizeof(int64_t) + 255) & ~size_t(255);
     return ((n * sizeof(CI<double>) + 255) & ~size_t(255)) +
            (((n / 2) * sizeof(CI<double>) + 255) & ~size_t(255));
@@ -536,7 +629,7 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
     std::vector<char> elig(count);
     for (size_t i = 0; i < count; ++i) {
         order[i] = int(i);
-        logn[i] = log_n_for(h_desc[i].na, h_desc[i].nb);
+        logn[i] = length_code(h_desc[i].na, h_desc[i].nb, p->radix3);
         elig[i] = p->prec == SSMUL_PREC_FP32 ||
                   (uses_fp32(p->prec) && fp32_eligible(p, h_desc[i].na, h_desc[i].nb, logn[i]));
     }
@@ -575,7 +668,7 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
                 d.Z = nullptr;
                 d.W = nullptr;
             } else {
-                const size_t zb = ((size_t(1) << ln) * sizeof(CI<double>) + 255) & ~size_t(255);
+                const size_t zb = (len_of(ln) * sizeof(CI<double>) + 255) & ~size_t(255);
                 d.Z = base;
                 d.W = base + zb;
             }
@@ -740,8 +833,12 @@ void tune_cache_read(const std::string& dev, std::vector<Geom>& found) {
         *tab = 0;
         int ln, ln2, cta;
         if (dev == line && std::sscanf(tab + 1, "%d %d %d", &ln, &ln2, &cta) == 3 &&
-            ln > LOG_SMALL && ln <= LOG_N_MAX && geom_valid(ln, ln2) && cta >= 9 && cta <= 12)
-            found.push_back(make_geom(ln, ln2, cta));
+            cta >= 9 && cta <= 12) {
+            if (ln > LOG_SMALL && ln <= LOG_N_MAX && geom_valid(ln, ln2))
+                found.push_back(make_geom(ln, ln2, cta));
+            else if (ln >= LEN3 && geom3_valid(ln - LEN3, ln2))
+                found.push_back(make_geom3(ln - LEN3, ln2, cta));
+        }
     }
     std::fclose(f);
 }
@@ -759,22 +856,29 @@ ssmul_status autotune(ssmul_plan_t p) {
     const std::string dev = device_name(p->device);
     std::vector<Geom> cached;
     tune_cache_read(dev, cached);
-    for (const Geom& g : cached)
-        if (g.log_n <= p->log_n_max) p->geom[g.log_n] = g;
+    // the length codes the plan can use
+    std::vector<int> codes;
+    for (int ln = LOG_SMALL + 1; ln <= p->log_n_max; ++ln) codes.push_back(ln);
+    for (int j = LOG3_MIN; p->log_tab3 && j <= p->log_tab3; ++j) codes.push_back(LEN3 + j);
     std::vector<int> todo;
-    for (int ln = LOG_SMALL + 1; ln <= p->log_n_max; ++ln) {
+    for (int ln : codes) {
         bool have = false;
-        for (const Geom& g : cached) have = have || g.log_n == ln;
+        for (const Geom& g : cached) {
+            if (g.log_n == ln) {
+                p->geom[ln] = g;
+                have = true;
+            }
+        }
         if (!have) todo.push_back(ln);
     }
     if (todo.empty()) return SSMUL_OK;
-    auto batch_count = [](int ln) { return clampi(int((size_t(1) << 23) >> ln), 1, 64); };
-    size_t ws_bytes = 0;
+    auto batch_count = [](int ln) { return clampi(int((size_t(1) << 23) / len_of(ln)), 1, 64); };
+    size_t ws_bytes = 0, n_max = 0;
     for (int ln : todo) {
         const size_t b = arena_need(ln) * size_t(batch_count(ln));
         if (b > ws_bytes) ws_bytes = b;
+        if (len_of(ln) > n_max) n_max = len_of(ln);
     }
-    const size_t n_max = size_t(1) << todo.back();
     void* ws = nullptr;
     uint8_t* digits = nullptr;
     ProdDesc* dd = nullptr;
@@ -803,7 +907,7 @@ ssmul_status autotune(ssmul_plan_t p) {
     const bool was_timing = p->timing;
     p->timing = false;
     for (int ln : todo) {
-        const size_t n = size_t(1) << ln;
+        const size_t n = len_of(ln);
         const int cnt = batch_count(ln);
         std::vector<ProdDesc> hd(cnt);
         for (int i = 0; i < cnt; ++i) {
@@ -822,13 +926,15 @@ ssmul_status autotune(ssmul_plan_t p) {
         if (cudaMemcpy(dd, hd.data(), cnt * sizeof(ProdDesc), cudaMemcpyHostToDevice) !=
             cudaSuccess)
             return done(SSMUL_CUDA_ERROR);
-        const int h = (ln + 1) / 2;
+        const bool three = ln >= LEN3;
+        const int k = three ? ln - LEN3 : ln;
+        const int h = (k + 1) / 2;
         float best = 1e30f;
         Geom best_g = p->geom[ln];
         for (int ln2 = h - 1; ln2 <= h + 1; ++ln2) {
-            if (!geom_valid(ln, ln2)) continue;
+            if (three ? !geom3_valid(k, ln2) : !geom_valid(ln, ln2)) continue;
             for (int cta = 9; cta <= 11; ++cta) {
-                const Geom g = make_geom(ln, ln2, cta);
+                const Geom g = three ? make_geom3(k, ln2, cta) : make_geom(ln, ln2, cta);
                 float t_min = 1e30f;
                 for (int rep = 0; rep < 4; ++rep) {
                     if (cudaMemsetAsync(ds, 0, cnt * sizeof(ProdState), p->stream) != cudaSuccess)
@@ -891,6 +997,14 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->s32);
     cudaFree(p->sd);
     cudaFree(p->sdd);
+    cudaFree(p->t64_3);
+    cudaFree(p->t32_3);
+    cudaFree(p->td_3);
+    cudaFree(p->tdd_3);
+    cudaFree(p->s64_3);
+    cudaFree(p->s32_3);
+    cudaFree(p->sd_3);
+    cudaFree(p->sdd_3);
     cudaFree(p->Z);
     cudaFree(p->W);
     cudaFree(p->coeff);
@@ -944,7 +1058,9 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     p->max_products = max_products;
     p->log_n_max = log_n;
     p->log_tab = log_n < 4 ? 4 : log_n;
-    for (int ln = 0; ln <= LOG_N_MAX; ++ln) p->geom[ln] = default_geom(ln);
+    for (int c = 0; c < GEOM_CODES; ++c) p->geom[c] = default_geom_code(c);
+    // lengths 3 2^j the plan's products can take: j <= log_n - 2
+    p->log_tab3 = log_n - 2 >= LOG3_MIN ? (log_n - 2 > LOG3_MAX ? LOG3_MAX : log_n - 2) : 0;
 
     const size_t n = size_t(1) << log_n;
     const size_t slots = max_products ? max_products : 1;
@@ -955,11 +1071,22 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (e == cudaSuccess) e = cudaMalloc(&p->t32, tab * sizeof(TwEntry<float>));
     if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscTw));
     if (e == cudaSuccess) e = cudaMalloc(&p->tdd, tab * sizeof(DDiscC));
-    if (e == cudaSuccess) e = cudaMalloc(&p->rho, 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&p->rho, 4 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&p->s64, 3 * STEP_TAB * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->s32, 3 * STEP_TAB * sizeof(CI<float>));
     if (e == cudaSuccess) e = cudaMalloc(&p->sd, 3 * STEP_TAB * sizeof(DiscTw));
     if (e == cudaSuccess) e = cudaMalloc(&p->sdd, 3 * STEP_TAB * sizeof(DDiscC));
+    const size_t tab3 = p->log_tab3 ? (size_t(3) << p->log_tab3) / 8 + 1 : 0;
+    if (tab3) {
+        if (e == cudaSuccess) e = cudaMalloc(&p->t64_3, tab3 * sizeof(TwEntry<double>));
+        if (e == cudaSuccess) e = cudaMalloc(&p->t32_3, tab3 * sizeof(TwEntry<float>));
+        if (e == cudaSuccess) e = cudaMalloc(&p->td_3, tab3 * sizeof(DiscTw));
+        if (e == cudaSuccess) e = cudaMalloc(&p->tdd_3, tab3 * sizeof(DDiscC));
+        if (e == cudaSuccess) e = cudaMalloc(&p->s64_3, 3 * STEP_TAB * sizeof(CI<double>));
+        if (e == cudaSuccess) e = cudaMalloc(&p->s32_3, 3 * STEP_TAB * sizeof(CI<float>));
+        if (e == cudaSuccess) e = cudaMalloc(&p->sd_3, 3 * STEP_TAB * sizeof(DiscTw));
+        if (e == cudaSuccess) e = cudaMalloc(&p->sdd_3, 3 * STEP_TAB * sizeof(DDiscC));
+    }
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->coeff, n * sizeof(int64_t));
@@ -997,26 +1124,37 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
 
     const int threads = 256;
     const int blocks = int((tab + threads - 1) / threads);
-    if ((e = cudaMemsetAsync(p->rho, 0, 2 * sizeof(float), p->stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(p->rho, 0, 4 * sizeof(float), p->stream)) != cudaSuccess)
         return fail(cuda_status(e));
-    k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->t32, p->log_tab);
-    k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->rho, p->log_tab);
-    k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->td, p->rho, p->tdd, p->log_tab);
+    k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->t32, p->log_tab, 1);
+    k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->rho, int64_t(tab));
+    k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->td, p->rho, p->tdd, int64_t(tab));
+    if (tab3) {
+        const int blocks3 = int((tab3 + threads - 1) / threads);
+        k_twiddle_gen<<<blocks3, threads, 0, p->stream>>>(p->t64_3, p->t32_3, p->log_tab3, 3);
+        k_disc_tw_gen<<<blocks3, threads, 0, p->stream>>>(p->t64_3, p->td_3, p->rho + 2, int64_t(tab3));
+        k_ddisc_tw_gen<<<blocks3, threads, 0, p->stream>>>(p->td_3, p->rho + 2, p->tdd_3, int64_t(tab3));
+    }
     {
         p->octant_only = true;
         const TwTable octant = p->tw();
+        const TwTable octant3 = p->tw3();
         p->octant_only = false;
-        k_step_tw_gen<<<(3 * STEP_TAB + threads - 1) / threads, threads, 0, p->stream>>>(
+        k_step_tw_gen<1><<<(3 * STEP_TAB + threads - 1) / threads, threads, 0, p->stream>>>(
             octant, p->s64, p->s32, p->sd, p->sdd);
+        if (tab3)
+            k_step_tw_gen<3><<<(3 * STEP_TAB + threads - 1) / threads, threads, 0, p->stream>>>(
+                octant3, p->s64_3, p->s32_3, p->sd_3, p->sdd_3);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_status(e));
-    float h_rho[2] = {0.f, 0.f};
+    float h_rho[4] = {0.f, 0.f, 0.f, 0.f};
     if ((e = cudaMemcpyAsync(h_rho, p->rho, sizeof(h_rho), cudaMemcpyDeviceToHost, p->stream)) !=
         cudaSuccess)
         return fail(cuda_status(e));
     if ((e = cudaEventRecord(p->desc_free, p->stream)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
     p->rho_dd = h_rho[1];
+    p->rho_dd3 = h_rho[3];
     *out = p;
     return SSMUL_OK;
 }
@@ -1035,7 +1173,7 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
             SS_TRY(cudaStreamSynchronize(p->stream));
             graph_drop(p->cached);
             if (value == 0) {
-                for (int ln = 0; ln <= LOG_N_MAX; ++ln) p->geom[ln] = default_geom(ln);
+                for (int c = 0; c < GEOM_CODES; ++c) p->geom[c] = default_geom_code(c);
                 return SSMUL_OK;
             }
             return autotune(p);
@@ -1048,6 +1186,11 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
             SS_TRY(cudaStreamSynchronize(p->stream));
             graph_drop(p->cached);
             p->balanced = value != 0;
+            return SSMUL_OK;
+        case SSMUL_OPT_RADIX3:
+            SS_TRY(cudaStreamSynchronize(p->stream));
+            graph_drop(p->cached);
+            p->radix3 = value != 0;
             return SSMUL_OK;
         case SSMUL_OPT_SPLIT_DIGITS: {
             if (value < 0 || (value > 0 && value < 1024)) return SSMUL_INVALID_ARG;
@@ -1172,7 +1315,9 @@ ssmul_status ssmul_debug_set_fault(ssmul_plan_t p, int kind, long long value) {
 
 ssmul_status ssmul_debug_geometry(ssmul_plan_t p, int log_n, int* log_n1, int* log_n2,
                                   int* log_cta) {
-    if (!p || log_n < 2 || log_n > LOG_N_MAX || !log_n1 || !log_n2 || !log_cta)
+    if (!p || !log_n1 || !log_n2 || !log_cta) return SSMUL_INVALID_ARG;
+    if (!((log_n >= 2 && log_n <= LOG_N_MAX) ||
+          (log_n >= LEN3 + LOG3_MIN && log_n <= LEN3 + LOG3_MAX)))
         return SSMUL_INVALID_ARG;
     const Geom& g = p->geom[log_n];
     *log_n1 = g.small ? 0 : g.log_n1;
@@ -1183,17 +1328,21 @@ ssmul_status ssmul_debug_geometry(ssmul_plan_t p, int log_n, int* log_n1, int* l
 
 ssmul_status ssmul_debug_twiddles(ssmul_plan_t p, int f32, double* h_out, size_t cap,
                                   int* log_ntab) {
-    if (!p || !h_out || !log_ntab) return SSMUL_INVALID_ARG;
-    const size_t tab = (size_t(1) << p->log_tab) / 8 + 1;
+    if (!p || !h_out || !log_ntab || f32 < 0 || f32 > 3) return SSMUL_INVALID_ARG;
+    const bool three = (f32 & 2) != 0;
+    if (three && !p->log_tab3) return SSMUL_INVALID_ARG;
+    const size_t tab = three ? (size_t(3) << p->log_tab3) / 8 + 1 : (size_t(1) << p->log_tab) / 8 + 1;
     if (cap < 4 * tab) return SSMUL_INVALID_ARG;
     ssmul_status s = check_device(p);
     if (s != SSMUL_OK) return s;
-    *log_ntab = p->log_tab;
-    if (!f32) {
-        SS_TRY(cudaMemcpy(h_out, p->t64, tab * sizeof(TwEntry<double>), cudaMemcpyDeviceToHost));
+    *log_ntab = three ? p->log_tab3 : p->log_tab;
+    if (!(f32 & 1)) {
+        SS_TRY(cudaMemcpy(h_out, three ? p->t64_3 : p->t64, tab * sizeof(TwEntry<double>),
+                          cudaMemcpyDeviceToHost));
     } else {
         std::vector<TwEntry<float>> t(tab);
-        SS_TRY(cudaMemcpy(t.data(), p->t32, tab * sizeof(TwEntry<float>), cudaMemcpyDeviceToHost));
+        SS_TRY(cudaMemcpy(t.data(), three ? p->t32_3 : p->t32, tab * sizeof(TwEntry<float>),
+                          cudaMemcpyDeviceToHost));
         for (size_t j = 0; j < tab; ++j) {
             h_out[4 * j] = t[j].cl;
             h_out[4 * j + 1] = t[j].ch;
@@ -1442,7 +1591,7 @@ unsigned char* noalloc_setup(int dev, cudaStream_t stream, ssmul_status* err) {
     if (e == cudaSuccess) {
         k_twiddle_gen<<<int((NOALLOC_TAB + 255) / 256), 256, 0, stream>>>(
             reinterpret_cast<TwEntry<double>*>(base + NA_OFF_T64),
-            reinterpret_cast<TwEntry<float>*>(base + NA_OFF_T32), NOALLOC_LOG_N);
+            reinterpret_cast<TwEntry<float>*>(base + NA_OFF_T32), NOALLOC_LOG_N, 1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

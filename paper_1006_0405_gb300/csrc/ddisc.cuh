@@ -235,8 +235,7 @@ __device__ __forceinline__ DDisc scale_pow2(const DDisc& a, int k) {
 // ch = RN32(c), cl = RN32(c - ch) (c - ch exact in binary64), so
 // |c - ch - cl| <= u |cl| <= 2^-48 for |c| <= 1; the radius grows by the
 // two components' errors: rho[1] = rho[0] + 2u^2 + ETA, rounded up
-__global__ void k_ddisc_tw_gen(const DiscTw* td, float* rho, DDiscC* tdd, int log_n) {
-    const int64_t count = (int64_t(1) << log_n) / 8 + 1;
+__global__ void k_ddisc_tw_gen(const DiscTw* td, float* rho, DDiscC* tdd, int64_t count) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
         const DiscTw e = td[j];

@@ -44,6 +44,12 @@ constexpr int CARRY_TILE = 4096;       // digits per carry CTA
 constexpr int CARRY_THREADS = 256;
 constexpr int CARRY_PER_THREAD = CARRY_TILE / CARRY_THREADS;
 constexpr uint32_t SPIN_LIMIT = 1u << 20;   // bounded look-back polls (about a second)
+// Transform length codes: c < LEN3 means N = 2^c; c >= LEN3 means
+// N = 3 2^(c - LEN3) (four-step only, LOG3_MIN <= c - LEN3 <= LOG3_MAX:
+// column length 3 2^a with a even and a <= 10, rows 2^b with 2 <= b <= 11).
+constexpr int LEN3 = 32;
+constexpr int LOG3_MIN = 11;           // 6144 = 3 2^11 > 4096, the single-CTA limit
+constexpr int LOG3_MAX = 21;           // 3 2^10 columns x 2^11 rows
 
 // Per-product accumulators of one call, zeroed before the call; one entry
 // per rung (value.cuh: 0 binary32 rectangles, 1 binary64 rectangles,
@@ -64,7 +70,7 @@ struct ProdDesc {
     const uint8_t* b;
     uint8_t* z;
     uint32_t na, nb;
-    int32_t log_n;                     // transform length N = 2^log_n
+    int32_t log_n;                     // length code: N = 2^log_n, or 3 2^(log_n - LEN3)
     int32_t balanced;                  // digits enter the transform as x_j - 128
     void* Z;                           // four-step workspace, N intervals
     void* W;                           // four-step workspace, N/2 intervals
@@ -213,18 +219,20 @@ __device__ void pair_products(SBuf<V> sm, int nl, int row0, int logN2) {
     }
 }
 
-// D_k for k2 < N2/2 of each line, written over the first half of the line.
-template <typename V>
+// D_k for k2 < N2/2 of each line, written over the first half of the line
+// (N1 = R 2^logN1, N = N1 N2; the twiddle table is of family R).
+template <typename V, int R = 1>
 __device__ void pack_half(SBuf<V> sm, int nl, int row0, int row1, int logN1, int logN2,
                           const TwTable& tw) {
     const int N2 = 1 << logN2, M2 = N2 >> 1;
+    const uint32_t N1 = uint32_t(R) << logN1;
     const int logN = logN1 + logN2;
     for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
         const int l = t >> (logN2 - 1), k2 = t & (M2 - 1);
         const int x = l * N2 + k2;
         const V c0 = sm[x], c1 = sm[x + M2];
-        const uint32_t k = uint32_t(l ? row1 : row0) + (uint32_t(k2) << logN1);
-        const auto w = get_twiddle<V, -1>(tw, k << (tw.log_n - logN));
+        const uint32_t k = uint32_t(l ? row1 : row0) + uint32_t(k2) * N1;
+        const auto w = get_twiddle<V, -1, R>(tw, k << (tw.log_n - logN));
         sm[x] = (c0 + c1) + mul_i(mul_tw(c0 - c1, w));
     }
 }
@@ -237,7 +245,10 @@ struct IsoAcc {
     unsigned int maxw_f32 = 0;          // the same for widths held in binary32
 };
 
-// Decide coefficient `idx` from its enclosure [lo, hi]; L = na + nb - 1.
+// Integer division by 3 rounded up / down (exact, no overflow).
+__device__ __forceinline__ long long ceil_div3(long long x) { return x / 3 + (x % 3 > 0 ? 1 : 0); }
+__device__ __forceinline__ long long floor_div3(long long x) { return x / 3 - (x % 3 < 0 ? 1 : 0); }
+
 // Decide coefficient idx from the enclosure [lo, hi] of c_idx (of c'_idx
 // with balanced digits, corrected here to c_idx); L = na + nb - 1.  The
 // decision is integer arithmetic on kl = ceil(lo) and kh = floor(hi),
@@ -246,7 +257,12 @@ struct IsoAcc {
 // negative value, and |k| >= 2^53 (an overflowed or infinite bound) is
 // never accepted.  The exact coefficient is a nonnegative integer: an
 // isolated negative value is a containment failure like an empty set.
-template <typename T>
+//
+// R = 3 (transform length 3 2^k): [lo, hi] encloses 3 c_idx (the 1/N
+// scaling applied only its power of two).  The integers of [lo/3, hi/3] are
+// those of [ceil(kl'/3), floor(kh'/3)] with kl' = ceil(lo), kh' = floor(hi),
+// so the same decision takes two exact integer divisions and no rounding.
+template <int R = 1, typename T>
 __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdDesc& d,
                                             IsoAcc& acc, int rung) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
@@ -257,14 +273,18 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
     }
     const unsigned long long wb = (unsigned long long)__double_as_longlong(__dsub_ru(dh, dl));
     acc.maxw_bits = wb > acc.maxw_bits ? wb : acc.maxw_bits;   // widths are >= 0 (or NaN)
-    const long long kl = __double2ll_ru(dl);
-    const long long kh = __double2ll_rd(dh);
+    long long kl = __double2ll_ru(dl);
+    long long kh = __double2ll_rd(dh);
+    if (R == 3) {
+        kl = ceil_div3(kl);
+        kh = floor_div3(kh);
+    }
     constexpr long long KMAX = 1ll << 53;
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
         if (d.iv != nullptr) {
-            d.iv[2 * idx] = __dadd_rd(dl, double(corr));
-            d.iv[2 * idx + 1] = __dadd_ru(dh, double(corr));
+            d.iv[2 * idx] = __dadd_rd(R == 3 ? __ddiv_rd(dl, 3.0) : dl, double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(R == 3 ? __ddiv_ru(dh, 3.0) : dh, double(corr));
         }
         int64_t v = 0;
         if (kl == kh && kl > -KMAX && kl < KMAX && kl + corr >= 0) {
@@ -280,6 +300,8 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
     }
 }
 
+// R = 3: the widths were those of 3 c; the largest is scaled by 1/3 rounded up
+template <int R = 1>
 __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
     if (acc.maxw_f32) {
         // binary32 -> binary64 is exact and keeps the order (NaN stays the largest)
@@ -287,6 +309,9 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
             (unsigned long long)__double_as_longlong(double(__uint_as_float(acc.maxw_f32)));
         acc.maxw_bits = w > acc.maxw_bits ? w : acc.maxw_bits;
     }
+    if (R == 3 && acc.maxw_bits)     // 0x3FD5555555555556 = RU(1/3)
+        acc.maxw_bits = (unsigned long long)__double_as_longlong(
+            __dmul_ru(__longlong_as_double((long long)acc.maxw_bits), __longlong_as_double(0x3FD5555555555556ll)));
     for (int o = 16; o > 0; o >>= 1) {
         acc.unisolated += __shfl_xor_sync(0xffffffffu, acc.unisolated, o);
         acc.empty += __shfl_xor_sync(0xffffffffu, acc.empty, o);
@@ -302,19 +327,20 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
 
 // Both coefficients carried by one complex value: c_{2j} (real part) and
 // c_{2j+1} (imaginary part).
-template <typename T>
+template <int R = 1, typename T>
 __device__ __forceinline__ void isolate_value(const CI<T>& v, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
-    constexpr int R = VTraits<CI<T>>::rung;
-    isolate_one(v.rl, v.rh, 2 * j, d, acc, R);
-    isolate_one(v.il, v.ih, 2 * j + 1, d, acc, R);
+    constexpr int RUNG = VTraits<CI<T>>::rung;
+    isolate_one<R>(v.rl, v.rh, 2 * j, d, acc, RUNG);
+    isolate_one<R>(v.il, v.ih, 2 * j + 1, d, acc, RUNG);
 }
 
+template <int R = 1>
 __device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
     const double r = double(v.r);
-    isolate_one(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, d, acc, 2);
-    isolate_one(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc, 2);
+    isolate_one<R>(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, d, acc, 2);
+    isolate_one<R>(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc, 2);
 }
 
 // rint(x) for |x| < 2^23 (x + 2^23 sign(x) has ulp 1), x itself otherwise
@@ -346,6 +372,9 @@ __device__ __forceinline__ long long int_of_f32(float x) {
 // Beyond that r > 2^21 (the set holds many integers) unless a part is NaN
 // or infinite (no integer: empty); a centre with |h| >= 2^53 cannot hold a
 // coefficient (they are below 2^53) and is empty unless it is wide.
+// R = 3: the set encloses 3 c (see isolate_one); the integer bounds are
+// divided by 3 exactly.
+template <int R = 1>
 __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t idx,
                                              const ProdDesc& d, IsoAcc& acc, int rung) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
@@ -364,6 +393,11 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
     const int cl = __float_as_int(__fadd_ru(lo, M)) - __float_as_int(M);
     const int fh = __float_as_int(__fadd_rd(hi, M)) - __float_as_int(M);
     const long long K = big ? 0ll : int_of_f32(k0) + int_of_f32(k1);
+    long long kl = K + cl, kh = K + fh;
+    if (R == 3) {
+        kl = ceil_div3(kl);
+        kh = floor_div3(kh);
+    }
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
         if (d.iv != nullptr) {
@@ -371,17 +405,17 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
             const double dr = double(r);
             const double dl = __dsub_rd(__dadd_rd(double(h), double(l)), dr);
             const double dh = __dadd_ru(__dadd_ru(double(h), double(l)), dr);
-            d.iv[2 * idx] = __dadd_rd(dl, double(corr));
-            d.iv[2 * idx + 1] = __dadd_ru(dh, double(corr));
+            d.iv[2 * idx] = __dadd_rd(R == 3 ? __ddiv_rd(dl, 3.0) : dl, double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(R == 3 ? __ddiv_ru(dh, 3.0) : dh, double(corr));
         }
         int64_t v = 0;
         if (bad) {
             acc.empty++;
         } else if (!fits) {
             acc.unisolated++;
-        } else if (cl == fh && !big && K + cl + corr >= 0) {
-            v = K + cl + corr;
-        } else if (cl < fh) {
+        } else if (kl == kh && !big && kl + corr >= 0) {
+            v = kl + corr;
+        } else if (kl < kh) {
             acc.unisolated++;
         } else {
             acc.empty++;           // no integer, a negative one or overflow
@@ -390,42 +424,47 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
     } else {
         // the exact value is 0; for a wide or far centre, 0 is outside when
         // |h| - |l| > r (a lower bound on |h + l| exceeds the radius)
-        const bool excl = (fits && !big) ? !(K + cl <= 0 && K + fh >= 0)
+        const bool excl = (fits && !big) ? !(kl <= 0 && kh >= 0)
                                          : __fsub_rd(__fsub_rd(fabsf(h), fabsf(l)), r) > 0.f;
         if (bad || excl) acc.empty++;
     }
 }
 
+template <int R = 1>
 __device__ __forceinline__ void isolate_value(const DDisc& v, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
-    isolate_pair(v.xh, v.xl, v.r, 2 * j, d, acc, 4);
-    isolate_pair(v.yh, v.yl, v.r, 2 * j + 1, d, acc, 4);
+    isolate_pair<R>(v.xh, v.xl, v.r, 2 * j, d, acc, 4);
+    isolate_pair<R>(v.yh, v.yl, v.r, 2 * j + 1, d, acc, 4);
 }
 
 // the naive transform rounds to the nearest integer without any proof; its
-// "width" statistic is the largest distance to that integer
+// "width" statistic is the largest distance to that integer (R = 3: v
+// approximates 3 c; the distance is kept for 3 c like the enclosures' widths)
+template <int R = 1>
 __device__ __forceinline__ void naive_one(double v, int64_t idx, const ProdDesc& d,
                                           IsoAcc& acc) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
-    const double k = rint(v);
-    const double dist = fabs(v - k);
+    const double vv = R == 3 ? v * (1.0 / 3.0) : v;
+    const double k = rint(vv);
+    const double dist = fabs(v - (R == 3 ? 3.0 * k : k));
     const unsigned long long db = (unsigned long long)__double_as_longlong(dist);
     acc.maxw_bits = db > acc.maxw_bits ? db : acc.maxw_bits;
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
         if (d.iv != nullptr) {
-            d.iv[2 * idx] = v + double(corr);
-            d.iv[2 * idx + 1] = v + double(corr);
+            d.iv[2 * idx] = vv + double(corr);
+            d.iv[2 * idx + 1] = vv + double(corr);
         }
         if (fabs(k) < 4.0e15 && int64_t(k) + corr >= 0) d.coeff[idx] = int64_t(k) + corr;
         else { d.coeff[idx] = 0; acc.empty++; }
     }
 }
 
+template <int R = 1>
 __device__ __forceinline__ void isolate_value(const Pt& v, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
-    naive_one(v.x, 2 * j, d, acc);
-    naive_one(v.y, 2 * j + 1, d, acc);
+    naive_one<R>(v.x, 2 * j, d, acc);
+    naive_one<R>(v.y, 2 * j + 1, d, acc);
 }
 
 // Global -> shared staging of `total` elements: a thread issues all of its
@@ -484,7 +523,9 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
 
 // ---- four-step kernels --------------------------------------------------------
 
-template <typename Tag, int BPT = 2>
+// R: 1 for N = 2^k, 3 for N = 3 2^k; N1 = R 2^logN1 (logN1 even when R = 3),
+// N2 = 2^logN2, and tw is the twiddle table of family R.
+template <typename Tag, int BPT = 2, int R = 1>
 __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
     using V = typename ValOf<Tag>::type;
@@ -492,42 +533,43 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
     const ProdDesc d = descs[blockIdx.y];
     if (gate && decided_by(d.st, gate)) return;
-    const int N1 = 1 << logN1, C = 1 << logC;
+    const int N1 = R << logN1, C = 1 << logC;
     const uint32_t j2_0 = blockIdx.x << logC;
     V* Z = reinterpret_cast<V*>(d.Z);
     const int bias = d.balanced ? 128 : 0;
     stage<4 * BPT, int2>(
-        C << logN1,
+        C * N1,
         [&](int idx) {
             const uint32_t j = (uint32_t(idx >> logC) << logN2) + j2_0 + (idx & (C - 1));
             return make_int2(j < d.na ? int(d.a[j]) - bias : 0, j < d.nb ? int(d.b[j]) - bias : 0);
         },
         [&](int idx, int2 v) {
-            sm[((idx & (C - 1)) << logN1) + (idx >> logC)] = make_point<V>(v.x, v.y);
+            sm[(idx & (C - 1)) * N1 + (idx >> logC)] = make_point<V>(v.x, v.y);
         });
     __syncthreads();
-    block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
+    if (R == 1) block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
+    else block_fft3<V, +1, BPT>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
-    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < C * N1; idx += blockDim.x) {
         const int c = idx & (C - 1), k1 = idx >> logC;
         const uint32_t j2 = j2_0 + c;
-        V v = sm[(c << logN1) + k1];
+        V v = sm[c * N1 + k1];
         const uint32_t e = j2 * uint32_t(k1);             // < N
-        if (e) v = mul_tw(v, get_twiddle<V, +1>(tw, e << (tw.log_n - logN)));
+        if (e) v = mul_tw(v, get_twiddle<V, +1, R>(tw, e << (tw.log_n - logN)));
         Z[(size_t(k1) << logN2) + j2] = v;
     }
 }
 
-template <typename Tag, int BPT = 2>
+template <typename Tag, int BPT = 2, int R = 1>
 __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_rows) k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
     const ProdDesc d = descs[blockIdx.y];
     if (gate && decided_by(d.st, gate)) return;
-    const int N1 = 1 << logN1, N2 = 1 << logN2, M2 = N2 >> 1;
+    const int N1 = R << logN1, N2 = 1 << logN2, M2 = N2 >> 1;
     const int k1 = blockIdx.x;                              // 0 .. N1/2
-    const int k1b = (N1 - k1) & (N1 - 1);
+    const int k1b = k1 ? N1 - k1 : 0;
     const int nl = (k1 == k1b) ? 1 : 2;
     const V* Z = reinterpret_cast<const V*>(d.Z);
     V* W = reinterpret_cast<V*>(d.W);
@@ -536,24 +578,24 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_rows) k_rows
         [&](int t) { return Z[(size_t((t >> logN2) ? k1b : k1) << logN2) + (t & (N2 - 1))]; },
         [&](int t, const V& v) { sm[t] = v; });
     __syncthreads();
-    block_fft<V, +1, BPT>(sm, logN2, nl, N2, tw);
+    block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw);
     pair_products(sm, nl, k1, logN2);
     __syncthreads();
-    pack_half(sm, nl, k1, k1b, logN1, logN2, tw);
+    pack_half<V, R>(sm, nl, k1, k1b, logN1, logN2, tw);
     __syncthreads();
-    block_fft<V, -1, BPT>(sm, logN2 - 1, nl, N2, tw);
+    block_fft<V, -1, BPT, R>(sm, logN2 - 1, nl, N2, tw);
     const int logM = logN1 + logN2 - 1;
     for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
         const int l = t >> (logN2 - 1), j2 = t & (M2 - 1);
         V v = sm[l * N2 + j2];
         const int row = l ? k1b : k1;
         const uint32_t e = uint32_t(row) * uint32_t(j2);        // < N/2
-        if (e) v = mul_tw(v, get_twiddle<V, -1>(tw, e << (tw.log_n - logM)));
+        if (e) v = mul_tw(v, get_twiddle<V, -1, R>(tw, e << (tw.log_n - logM)));
         W[(size_t(row) << (logN2 - 1)) + j2] = v;
     }
 }
 
-template <typename Tag, int BPT = 2>
+template <typename Tag, int BPT = 2, int R = 1>
 __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
                            int gate) {
     using V = typename ValOf<Tag>::type;
@@ -562,24 +604,26 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
     const ProdDesc d = descs[blockIdx.y];
     if (gate && decided_by(d.st, gate)) return;
-    const int N1 = 1 << logN1, C = 1 << logC;
+    const int N1 = R << logN1, C = 1 << logC;
     const int logM2 = logN2 - 1;
     const uint32_t j2_0 = blockIdx.x << logC;
     const V* W = reinterpret_cast<const V*>(d.W);
     stage<4 * BPT, V>(
-        C << logN1,
+        C * N1,
         [&](int idx) { return W[(size_t(idx >> logC) << logM2) + j2_0 + (idx & (C - 1))]; },
-        [&](int idx, const V& v) { sm[((idx & (C - 1)) << logN1) + (idx >> logC)] = v; });
+        [&](int idx, const V& v) { sm[(idx & (C - 1)) * N1 + (idx >> logC)] = v; });
     __syncthreads();
-    block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
+    if (R == 1) block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
+    else block_fft3<V, -1, BPT>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
     IsoAcc acc;
-    for (int idx = threadIdx.x; idx < (C << logN1); idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < C * N1; idx += blockDim.x) {
         const int c = idx & (C - 1), j1 = idx >> logC;
         const int64_t j = (int64_t(j1) << logM2) + j2_0 + c;
-        isolate_value(scale_pow2(sm[(c << logN1) + j1], logN + 2), j, d, acc);
+        // 1 / (4 N) up to the factor 1/3 of R = 3, which the isolation applies exactly
+        isolate_value<R>(scale_pow2(sm[c * N1 + j1], logN + 2), j, d, acc);
     }
-    flush_acc(acc, d.st, RUNG);
+    flush_acc<R>(acc, d.st, RUNG);
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
 }
 
@@ -848,10 +892,10 @@ __global__ void k_finalize(const ProdDesc* descs) {
         ssmul_result r;
         r.status = status;
         r.precision_used = rung_precision(rung);
-        r.fft_log2 = uint32_t(d.log_n);
+        r.fft_log2 = uint32_t(d.log_n >= LEN3 ? d.log_n - LEN3 : d.log_n);
         r.n_unisolated = d.st->unisolated[rung];
         r.n_empty = d.st->empty[rung];
-        r.reserved = 0;
+        r.fft_times3 = d.log_n >= LEN3 ? 1u : 0u;
         r.max_width = __longlong_as_double((long long)d.st->maxw[rung]);
         *d.res = r;
         s_status = status;

@@ -1,21 +1,35 @@
 // twiddle.cuh -- rigorous enclosures of the roots of unity omega_N^j.
 //
 // The DFT of Section 2.2 uses omega = e^{2 pi i / N}; its inverse uses
-// omega^-1.  The plan builds, once, a table of enclosures of
+// omega^-1.  The plan builds, once, tables of enclosures of
 // cos(2 pi j / Ntab) and sin(2 pi j / Ntab) for the first octant
-// j = 0 .. Ntab/8; every other power of every root omega_N (N <= Ntab, both
-// powers of two) is read from it through exact symmetries of the circle
+// j = 0 .. Ntab/8, for two families of lengths: Ntab = 2^K (R = 1) and
+// Ntab = 3 2^K (R = 3).  Every power of a root omega_N with N dividing
+// Ntab is read from the table through exact symmetries of the circle
 // (reflection about pi/4 swaps cos and sin; a quarter turn maps (c, s) to
-// (-s, c); the inverse root conjugates).
+// (-s, c); the inverse root conjugates).  These hold for every Ntab that
+// is a multiple of 8.
 //
-// Each table entry comes from the device's sincospi(2 j / Ntab), whose
-// argument is exact because Ntab is a power of two.  The CUDA Math API
-// documents a maximum error of 2 ulp for the binary64 sincospi; each value
-// is widened outward by TW_WIDEN_ULPS = 4 steps of nextafter (the bound
-// plus margin for the change of ulp size at a power of two), then clamped
-// to what is known exactly on the first octant (cos in [0, 1], sin in
-// [0, 1]).  j = 0 is the exact point (1, 0).  The binary32 table is the
-// binary64 one rounded outward.
+// Each table entry comes from the device's sincospi(x), x = 2 j / Ntab.
+// The CUDA Math API documents a maximum error of 2 ulp for the binary64
+// sincospi.
+//   R = 1: x is exact (Ntab is a power of two); each value is widened
+//          outward by TW_WIDEN_ULPS = 4 steps of nextafter (the bound plus
+//          margin for the change of ulp size at a power of two).
+//   R = 3: when 3 divides j the argument (2 j / 3) 2^-K is exact and the
+//          widening is TW_WIDEN_ULPS.  Otherwise x = q 2^-K with
+//          q = RN(2 j / 3); the remainder 2 j - 3 q is exact (one fma), so
+//          the true argument is x + d with d = ((2 j - 3 q) / 3) 2^-K,
+//          |d| <= 2^-53 x.  The values at x + d are those at x corrected to
+//          first order, s + pi d c and c - pi d s, each with one rounding
+//          (1/2 ulp); the second-order term (pi d)^2 / 2 < 2^-104 and the
+//          inputs' own errors times pi d are far below an ulp.  With
+//          sincospi's 2 ulp each value is within 2.5 ulp; counted in steps
+//          of a lower binade when the value sits just above a power of two,
+//          5 steps.  The widening is TW3_WIDEN_ULPS = 6.
+// The values are then clamped to what is known exactly on the first octant
+// (cos in [0, 1], sin in [0, 1]); j = 0 is the exact point (1, 0).  The
+// binary32 table is the binary64 one rounded outward.
 #pragma once
 #include "interval.cuh"
 #include "disc.cuh"
@@ -23,6 +37,7 @@
 namespace ssm {
 
 constexpr int TW_WIDEN_ULPS = 4;
+constexpr int TW3_WIDEN_ULPS = 6;
 constexpr int TW_DOC_ULPS = 2;
 
 template <typename T>
@@ -32,32 +47,39 @@ struct TwEntry {
 
 struct DDiscC;
 
-// Step-ordered twiddles.  The radix-4 step of sub-length n = 2^logn
-// (3 <= logn <= LOG_STEP_MAX) multiplies by omega_n^{u p} for p < n/4 and
-// u = 1, 2, 3; a step table holds that value of the forward transform at
-// [(u - 1) STEP_TAB + n/4 + p], so the lanes of a warp, which work on
-// consecutive p, read consecutive entries.  The entries are copies of the
-// octant table's values (moved by the same exact symmetries).
+// Step-ordered twiddles.  The radix-4 step of sub-length n multiplies by
+// omega_n^{u p} for p < n/4 and u = 1, 2, 3; a step table holds that value
+// of the forward transform at [(u - 1) STEP_TAB + n/4 + p], so the lanes
+// of a warp, which work on consecutive p, read consecutive entries.  One
+// set of tables serves n = 2^j (8 <= n <= 2^LOG_STEP_MAX), another
+// n = 3 2^j (12 <= n <= 3 2^10); in both the ranges [n/4, n/2) of
+// successive n are disjoint.  The entries are copies of the octant tables'
+// values (moved by the same exact symmetries).
 constexpr int LOG_STEP_MAX = 12;
 constexpr int STEP_TAB = 1 << (LOG_STEP_MAX - 1);
 
 struct TwTable {
     const TwEntry<double>* t64;   // Ntab/8 + 1 entries
     const TwEntry<float>* t32;    // same, binary32
-    int log_n;                    // log2 Ntab
+    int log_n;                    // Ntab = R 2^log_n (R: the kernel's family)
     const DiscTw* td;             // same, as discs (centre, radius)
     const DDiscC* tdd;            // same, as double-binary32 disc centres
     float rho_dd;                 // the radius of every entry of tdd
-    // step-ordered copies (3 STEP_TAB entries each), or all null: then the
-    // transforms read the octant tables
+    // step-ordered copies (3 STEP_TAB entries each) for n = 2^j, or all
+    // null: then the transforms read the octant tables
     const CI<double>* s64;
     const CI<float>* s32;
     const DiscTw* sd;
     const DDiscC* sdd;
+    // the same for n = 3 2^j (set in a table of the R = 3 family)
+    const CI<double>* s64_3;
+    const CI<float>* s32_3;
+    const DiscTw* sd_3;
+    const DDiscC* sdd_3;
 };
 
-__global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n) {
-    const int64_t ntab = int64_t(1) << log_n;
+__global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n, int R) {
+    const int64_t ntab = int64_t(R) << log_n;
     const int64_t count = ntab / 8 + 1;
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
@@ -65,12 +87,22 @@ __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log
         if (j == 0) {
             e = {1.0, 1.0, 0.0, 0.0};
         } else {
-            // 2 j / ntab is exact: a small integer times a power of two
-            const double x = ldexp(double(2 * j), -log_n);
+            // 2 j / ntab: exact for R = 1 and for j divisible by 3
+            const bool exact = R == 1 || j % 3 == 0;
+            const double q = R == 1 ? double(2 * j) : __ddiv_rn(double(2 * j), 3.0);
+            const double x = ldexp(q, -log_n);
             double s, c;
             sincospi(x, &s, &c);
+            if (!exact) {
+                const double rem = __fma_rn(-3.0, q, double(2 * j));          // exact
+                const double pd = __dmul_rn(3.141592653589793, ldexp(__ddiv_rn(rem, 3.0), -log_n));
+                const double s0 = s;
+                s = __fma_rn(pd, c, s);
+                c = __fma_rn(-pd, s0, c);
+            }
+            const int widen = exact ? TW_WIDEN_ULPS : TW3_WIDEN_ULPS;
             double cl = c, ch = c, sl = s, sh = s;
-            for (int k = 0; k < TW_WIDEN_ULPS; ++k) {
+            for (int k = 0; k < widen; ++k) {
                 cl = nextafter(cl, -1.0e300);
                 ch = nextafter(ch, 1.0e300);
                 sl = nextafter(sl, -1.0e300);
@@ -91,8 +123,7 @@ __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log
 // distance to any point of the rectangle.  *rho (zero on entry) becomes the
 // largest of these radii (nonnegative binary32 values order like their bit
 // patterns), the radius the double-binary32 table shares.
-__global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscTw* td, float* rho, int log_n) {
-    const int64_t count = (int64_t(1) << log_n) / 8 + 1;
+__global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscTw* td, float* rho, int64_t count) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
         const TwEntry<double> e = t64[j];
@@ -106,22 +137,41 @@ __global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscTw* td, float* rho
     }
 }
 
+// Position of omega_Ntab^j (any j >= 0; Ntab = R 2^ln, ln >= 3) relative
+// to the first octant: the quadrant (mod 4), and the octant entry jj, with
+// refl set when the angle inside the quadrant is past pi/4 (then jj is
+// measured back from the quadrant's end and cos and sin swap).
+struct TwPos {
+    uint32_t quad, jj;
+    bool refl;
+};
+
+template <int R>
+__device__ __forceinline__ TwPos tw_pos(int ln, uint32_t j) {
+    const uint32_t q = uint32_t(R) << (ln - 2);       // a quarter turn
+    uint32_t quad;
+    if (R == 1) {
+        j &= (1u << ln) - 1u;
+        quad = j >> (ln - 2);
+    } else {
+        quad = (j >> (ln - 2)) / 3u;                  // floor(j / q)
+    }
+    const uint32_t r = j - quad * q;
+    const bool refl = r > (q >> 1);
+    return {quad & 3u, refl ? q - r : r, refl};
+}
+
 // Disc enclosure of omega_Ntab^(sign * j): the same symmetries as twiddle();
 // they move the centre exactly and keep the radius.
-template <int SIGN>
+template <int SIGN, int R = 1>
 __device__ __forceinline__ DiscTw twiddle_disc(const TwTable& tw, uint32_t j) {
-    const int ln = tw.log_n;
-    j &= (1u << ln) - 1u;
-    const uint32_t q = 1u << (ln - 2);
-    const uint32_t quad = j >> (ln - 2);
-    const uint32_t r = j & (q - 1u);
-    const bool refl = r > (q >> 1);
-    const DiscTw e = tw.td[refl ? q - r : r];
-    const double c = refl ? e.s : e.c, s = refl ? e.c : e.s;
-    const bool swap = quad & 1u;
+    const TwPos ps = tw_pos<R>(tw.log_n, j);
+    const DiscTw e = tw.td[ps.jj];
+    const double c = ps.refl ? e.s : e.c, s = ps.refl ? e.c : e.s;
+    const bool swap = ps.quad & 1u;
     const double wc = swap ? s : c, ws = swap ? c : s;
-    const bool negr = quad == 1u || quad == 2u;
-    const bool negi = (quad >= 2u) != (SIGN < 0);
+    const bool negr = ps.quad == 1u || ps.quad == 2u;
+    const bool negi = (ps.quad >= 2u) != (SIGN < 0);
     return {negr ? flip(wc) : wc, negi ? flip(ws) : ws, e.rho, 0.f};
 }
 
@@ -133,30 +183,23 @@ template <>
 __device__ __forceinline__ const TwEntry<float>* tw_ptr<float>(const TwTable& tw) { return tw.t32; }
 
 // Enclosure of omega_Ntab^(sign * j) for any integer j (taken mod Ntab).
-template <typename T, int SIGN>
+template <typename T, int SIGN, int R = 1>
 __device__ __forceinline__ CI<T> twiddle(const TwTable& tw, uint32_t j) {
-    const int ln = tw.log_n;
-    const uint32_t mask = (1u << ln) - 1u;
-    j &= mask;
-    const uint32_t q = 1u << (ln - 2);               // a quarter turn
-    const uint32_t quad = j >> (ln - 2);
-    const uint32_t r = j & (q - 1u);
-    const bool refl = r > (q >> 1);                  // past pi/4 inside the quadrant
-    const uint32_t jj = refl ? q - r : r;
-    const TwEntry<T> e = tw_ptr<T>(tw)[jj];
-    const T cl = refl ? e.sl : e.cl, ch = refl ? e.sh : e.ch;
-    const T sl = refl ? e.cl : e.sl, sh = refl ? e.ch : e.sh;
+    const TwPos ps = tw_pos<R>(tw.log_n, j);
+    const TwEntry<T> e = tw_ptr<T>(tw)[ps.jj];
+    const T cl = ps.refl ? e.sl : e.cl, ch = ps.refl ? e.sh : e.ch;
+    const T sl = ps.refl ? e.cl : e.sl, sh = ps.refl ? e.ch : e.sh;
     // a quarter turn maps (c, s) to (-s, c); the negations are sign-bit
     // flips on the integer pipe (the interval -[l, h] is [-h, -l])
-    const bool swap = quad & 1u;                       // quadrants 1 and 3
-    const bool negr = quad == 1u || quad == 2u;        // real part negated
-    const bool negi = quad >= 2u;                      // imaginary part negated
-    T rl = swap ? sl : cl, rh = swap ? sh : ch;        // real part before sign
-    T il = swap ? cl : sl, ih = swap ? ch : sh;        // imaginary part before sign
+    const bool swap = ps.quad & 1u;                     // quadrants 1 and 3
+    const bool negr = ps.quad == 1u || ps.quad == 2u;   // real part negated
+    const bool negi = ps.quad >= 2u;                    // imaginary part negated
+    T rl = swap ? sl : cl, rh = swap ? sh : ch;         // real part before sign
+    T il = swap ? cl : sl, ih = swap ? ch : sh;         // imaginary part before sign
     CI<T> w;
     w.rl = negr ? flip(rh) : rl;
     w.rh = negr ? flip(rl) : rh;
-    const bool ni = negi != (SIGN < 0);                // the inverse conjugates
+    const bool ni = negi != (SIGN < 0);                 // the inverse conjugates
     w.il = ni ? flip(ih) : il;
     w.ih = ni ? flip(il) : ih;
     return w;

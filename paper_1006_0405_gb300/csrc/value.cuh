@@ -69,76 +69,58 @@ struct SBuf {
     }
 };
 
-template <typename V, int SIGN>
-__device__ __forceinline__ typename VTraits<V>::Tw get_twiddle(const TwTable& tw, uint32_t j);
-template <>
-__device__ __forceinline__ CI<float> get_twiddle<CI<float>, 1>(const TwTable& tw, uint32_t j) {
-    return twiddle<float, 1>(tw, j);
-}
-template <>
-__device__ __forceinline__ CI<float> get_twiddle<CI<float>, -1>(const TwTable& tw, uint32_t j) {
-    return twiddle<float, -1>(tw, j);
-}
-template <>
-__device__ __forceinline__ CI<double> get_twiddle<CI<double>, 1>(const TwTable& tw, uint32_t j) {
-    return twiddle<double, 1>(tw, j);
-}
-template <>
-__device__ __forceinline__ CI<double> get_twiddle<CI<double>, -1>(const TwTable& tw, uint32_t j) {
-    return twiddle<double, -1>(tw, j);
-}
-template <>
-__device__ __forceinline__ DiscTw get_twiddle<Disc, 1>(const TwTable& tw, uint32_t j) {
-    return twiddle_disc<1>(tw, j);
-}
-template <>
-__device__ __forceinline__ DiscTw get_twiddle<Disc, -1>(const TwTable& tw, uint32_t j) {
-    return twiddle_disc<-1>(tw, j);
-}
-template <>
-__device__ __forceinline__ DiscTw get_twiddle<Pt, 1>(const TwTable& tw, uint32_t j) {
-    return twiddle_disc<1>(tw, j);
-}
-template <>
-__device__ __forceinline__ DiscTw get_twiddle<Pt, -1>(const TwTable& tw, uint32_t j) {
-    return twiddle_disc<-1>(tw, j);
-}
+// Enclosure of omega_Ntab^(SIGN j) in the twiddle type of V, from a table
+// of family R (Ntab = R 2^tw.log_n).
+template <typename V, int SIGN, int R> struct TwOf;
+template <int SIGN, int R> struct TwOf<CI<float>, SIGN, R> {
+    static __device__ __forceinline__ CI<float> get(const TwTable& tw, uint32_t j) {
+        return twiddle<float, SIGN, R>(tw, j);
+    }
+};
+template <int SIGN, int R> struct TwOf<CI<double>, SIGN, R> {
+    static __device__ __forceinline__ CI<double> get(const TwTable& tw, uint32_t j) {
+        return twiddle<double, SIGN, R>(tw, j);
+    }
+};
+template <int SIGN, int R> struct TwOf<Disc, SIGN, R> {
+    static __device__ __forceinline__ DiscTw get(const TwTable& tw, uint32_t j) {
+        return twiddle_disc<SIGN, R>(tw, j);
+    }
+};
+template <int SIGN, int R> struct TwOf<Pt, SIGN, R> : TwOf<Disc, SIGN, R> {};
 
 // disc twiddle with double-binary32 centre: the symmetries of twiddle_disc
-template <int SIGN>
+template <int SIGN, int R = 1>
 __device__ __forceinline__ DDiscTw twiddle_ddisc(const TwTable& tw, uint32_t j) {
-    const int ln = tw.log_n;
-    j &= (1u << ln) - 1u;
-    const uint32_t q = 1u << (ln - 2);
-    const uint32_t quad = j >> (ln - 2);
-    const uint32_t r = j & (q - 1u);
-    const bool refl = r > (q >> 1);
-    const DDiscC e = tw.tdd[refl ? q - r : r];
-    const float ch = refl ? e.sh : e.ch, cl = refl ? e.sl : e.cl;
-    const float sh = refl ? e.ch : e.sh, sl = refl ? e.cl : e.sl;
-    const bool swap = quad & 1u;
+    const TwPos ps = tw_pos<R>(tw.log_n, j);
+    const DDiscC e = tw.tdd[ps.jj];
+    const float ch = ps.refl ? e.sh : e.ch, cl = ps.refl ? e.sl : e.cl;
+    const float sh = ps.refl ? e.ch : e.sh, sl = ps.refl ? e.cl : e.sl;
+    const bool swap = ps.quad & 1u;
     const float wch = swap ? sh : ch, wcl = swap ? sl : cl;
     const float wsh = swap ? ch : sh, wsl = swap ? cl : sl;
-    const bool negr = quad == 1u || quad == 2u;
-    const bool negi = (quad >= 2u) != (SIGN < 0);
+    const bool negr = ps.quad == 1u || ps.quad == 2u;
+    const bool negi = (ps.quad >= 2u) != (SIGN < 0);
     return {negr ? flip(wch) : wch, negr ? flip(wcl) : wcl, negi ? flip(wsh) : wsh,
             negi ? flip(wsl) : wsl, tw.rho_dd, 0.f};
 }
-template <>
-__device__ __forceinline__ DDiscTw get_twiddle<DDisc, 1>(const TwTable& tw, uint32_t j) {
-    return twiddle_ddisc<1>(tw, j);
-}
-template <>
-__device__ __forceinline__ DDiscTw get_twiddle<DDisc, -1>(const TwTable& tw, uint32_t j) {
-    return twiddle_ddisc<-1>(tw, j);
+template <int SIGN, int R> struct TwOf<DDisc, SIGN, R> {
+    static __device__ __forceinline__ DDiscTw get(const TwTable& tw, uint32_t j) {
+        return twiddle_ddisc<SIGN, R>(tw, j);
+    }
+};
+
+template <typename V, int SIGN, int R = 1>
+__device__ __forceinline__ typename VTraits<V>::Tw get_twiddle(const TwTable& tw, uint32_t j) {
+    return TwOf<V, SIGN, R>::get(tw, j);
 }
 
 // ---- step-ordered twiddles -------------------------------------------------------
 //
-// omega_n^(SIGN u p) for the radix-4 step of sub-length n = 2^logn: the
-// step table's entry (a forward twiddle; the inverse root is its conjugate,
-// a sign-bit flip), or the octant table's when the plan has no step tables.
-// Both give the same bits.
+// omega_n^(SIGN u p) for the radix-4 step of sub-length n: the step table's
+// entry (a forward twiddle; the inverse root is its conjugate, a sign-bit
+// flip), or the octant table's when the plan has no step tables.  Both give
+// the same bits.
 
 __device__ __forceinline__ CI<double> tw_conj(const CI<double>& w) { return conj_flip(w); }
 __device__ __forceinline__ CI<float> tw_conj(const CI<float>& w) { return conj_flip(w); }
@@ -147,64 +129,90 @@ __device__ __forceinline__ DDiscTw tw_conj(const DDiscTw& w) {
     return {w.ch, w.cl, flip(w.sh), flip(w.sl), w.rho, 0.f};
 }
 
+// table(tw, three): the step table of V for n = 2^j (three = false) or
+// n = 3 2^j (three = true)
 template <typename V> struct StepOf;
 template <> struct StepOf<CI<double>> {
-    static __device__ __forceinline__ const CI<double>* table(const TwTable& tw) { return tw.s64; }
+    static __device__ __forceinline__ const CI<double>* table(const TwTable& tw, bool three) {
+        return three ? tw.s64_3 : tw.s64;
+    }
     static __device__ __forceinline__ CI<double> load(const CI<double>* t, int i, const TwTable&) {
         return t[i];
     }
 };
 template <> struct StepOf<CI<float>> {
-    static __device__ __forceinline__ const CI<float>* table(const TwTable& tw) { return tw.s32; }
+    static __device__ __forceinline__ const CI<float>* table(const TwTable& tw, bool three) {
+        return three ? tw.s32_3 : tw.s32;
+    }
     static __device__ __forceinline__ CI<float> load(const CI<float>* t, int i, const TwTable&) {
         return t[i];
     }
 };
 template <> struct StepOf<Disc> {
-    static __device__ __forceinline__ const DiscTw* table(const TwTable& tw) { return tw.sd; }
+    static __device__ __forceinline__ const DiscTw* table(const TwTable& tw, bool three) {
+        return three ? tw.sd_3 : tw.sd;
+    }
     static __device__ __forceinline__ DiscTw load(const DiscTw* t, int i, const TwTable&) {
         return t[i];
     }
 };
 template <> struct StepOf<Pt> : StepOf<Disc> {};
 template <> struct StepOf<DDisc> {
-    static __device__ __forceinline__ const DDiscC* table(const TwTable& tw) { return tw.sdd; }
+    static __device__ __forceinline__ const DDiscC* table(const TwTable& tw, bool three) {
+        return three ? tw.sdd_3 : tw.sdd;
+    }
     static __device__ __forceinline__ DDiscTw load(const DDiscC* t, int i, const TwTable& tw) {
         const DDiscC e = t[i];
         return {e.ch, e.cl, e.sh, e.sl, tw.rho_dd, 0.f};
     }
 };
 
-template <typename V, int SIGN>
+// n = 2^logn, the table of family R
+template <typename V, int SIGN, int R = 1>
 __device__ __forceinline__ typename VTraits<V>::Tw step_twiddle(const TwTable& tw, int logn, int p,
                                                                 int u) {
-    const auto* t = StepOf<V>::table(tw);
-    if (t == nullptr) return get_twiddle<V, SIGN>(tw, uint32_t(u * p) << (tw.log_n - logn));
+    const auto* t = StepOf<V>::table(tw, false);
+    if (t == nullptr)        // Ntab / n = R 2^(log_n - logn)
+        return get_twiddle<V, SIGN, R>(tw, uint32_t(R * u * p) << (tw.log_n - logn));
     const auto w = StepOf<V>::load(t, (u - 1) * STEP_TAB + (1 << (logn - 2)) + p, tw);
     return SIGN > 0 ? w : tw_conj(w);
 }
 
-// Fills the step tables from the octant tables (the pair-disc step table
-// holds centres: its radius is the table's).
+// n = 3 2^logn2, the table of family 3
+template <typename V, int SIGN>
+__device__ __forceinline__ typename VTraits<V>::Tw step_twiddle3(const TwTable& tw, int logn2, int p,
+                                                                 int u) {
+    const auto* t = StepOf<V>::table(tw, true);
+    if (t == nullptr)        // Ntab / n = 2^(log_n - logn2)
+        return get_twiddle<V, SIGN, 3>(tw, uint32_t(u * p) << (tw.log_n - logn2));
+    const auto w = StepOf<V>::load(t, (u - 1) * STEP_TAB + (3 << (logn2 - 2)) + p, tw);
+    return SIGN > 0 ? w : tw_conj(w);
+}
+
+// Fills step tables from the octant tables of family R (the pair-disc step
+// table holds centres: its radius is the table's).  R = 1: the tables for
+// n = 2^j; R = 3: those for n = 3 2^j.
+template <int R>
 __global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscTw* sd,
                               DDiscC* sdd) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * STEP_TAB;
          i += gridDim.x * blockDim.x) {
         const int u = i / STEP_TAB + 1, pos = i % STEP_TAB;
-        const int lq = pos < 2 ? -1 : 31 - __clz(pos);        // log2(n/4)
-        const int logn = lq + 2;
-        if (lq < 1 || logn > tw.log_n) {
+        // n/4 = R 2^lq <= pos < R 2^(lq+1)
+        const int lq = pos < R ? -1 : 31 - __clz(pos / R);
+        const int logn = lq + 2;                                // n = R 2^logn
+        if (lq < (R == 1 ? 1 : 0) || logn > tw.log_n || (R == 3 && logn > 10)) {
             s64[i] = {};
             s32[i] = {};
             sd[i] = {};
             sdd[i] = {};
             continue;
         }
-        const uint32_t j = uint32_t(u * (pos - (1 << lq))) << (tw.log_n - logn);
-        s64[i] = twiddle<double, 1>(tw, j);
-        s32[i] = twiddle<float, 1>(tw, j);
-        sd[i] = twiddle_disc<1>(tw, j);
-        const DDiscTw dd = twiddle_ddisc<1>(tw, j);
+        const uint32_t j = uint32_t(u * (pos - (R << lq))) << (tw.log_n - logn);
+        s64[i] = twiddle<double, 1, R>(tw, j);
+        s32[i] = twiddle<float, 1, R>(tw, j);
+        sd[i] = twiddle_disc<1, R>(tw, j);
+        const DDiscTw dd = twiddle_ddisc<1, R>(tw, j);
         sdd[i] = {dd.ch, dd.cl, dd.sh, dd.sl};
     }
 }

@@ -46,12 +46,13 @@ class Plan:
         iv = div.cpu().numpy().reshape(L, 2)
         return s, r, dz.cpu().numpy(), iv[:, 0], iv[:, 1]
 
-    def twiddles(self, f32=False, log_max=24):
+    def twiddles(self, f32=False, log_max=24, three=False):
+        """(K, cos_lo, cos_hi, sin_lo, sin_hi) of the table Ntab = 2^K (or 3 2^K)."""
         cap = 4 * ((1 << log_max) // 8 + 1)
         buf = np.zeros(cap, np.float64)
-        s, ln = abi.ssmul_debug_twiddles(self.h, f32, buf.ctypes.data, cap)
+        s, ln = abi.ssmul_debug_twiddles(self.h, int(f32) | (2 if three else 0), buf.ctypes.data, cap)
         assert s == abi.SSMUL_OK
-        m = (1 << ln) // 8 + 1
+        m = ((3 if three else 1) << ln) // 8 + 1
         t = buf[:4 * m].reshape(m, 4)
         return ln, t[:, 0], t[:, 1], t[:, 2], t[:, 3]
 
