@@ -199,7 +199,12 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # L2): dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  Only
 # valid for the 75k workload and the kernels as captured; empty when the
 # kernels changed since.
-NCU_TRAFFIC_PER_PRODUCT: dict = {}
+NCU_TRAFFIC_PER_PRODUCT = {
+    # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
+    "k_rows<double>": (101.537280e6 + 19.416064e6) / 16,
+    "k_rows<disc>": (76.186880e6 + 6.035968e6) / 16,
+    "k_rows<disc32x2>": (75.972096e6 + 5.102336e6) / 16,
+}
 
 
 def algorithmic_bytes(n: int) -> float:
