@@ -166,7 +166,7 @@ def geometry(R: int, k: int):
             a, b = a + 2, b - 2
         while a > 10:
             a, b = a - 2, b + 2
-        c = max(0, 11 - a - 1)
+        c = max(0, 10 - a - 1)
     return a, b, min(c, b), min(c, b - 1)
 
 
