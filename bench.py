@@ -1,7 +1,7 @@
 """Benchmark: verified interval-FFT multiplications on one GB300 (or N replicas).
 
 Workload (default): the paper-scale binary64 interval method, products of
-two 75,000-digit base-256 operands (FFT length 3 2^16).  One step is one
+two 75,000-digit base-256 operands (FFT length 5 2^15).  One step is one
 ssmul_mul_batched call over a batch of B such products (B - 1 with uniform
 random digits, one with every digit 0xFF, the worst case of coefficient
 size), i.e. one pass of the whole path: interval transforms, pointwise
@@ -127,10 +127,12 @@ def _fft_ops(logL: int, nl: int, c: dict) -> int:
     return ops
 
 
-def _fft3_ops(loga: int, nl: int, c: dict) -> int:
-    """lines of length 3 2^loga (loga even): radix-4 steps, then one radix-3
-    step of 6 adds, a scaling by 1/2 and one twiddle product per butterfly"""
-    L = 3 << loga
+def _fft_odd_ops(R: int, loga: int, nl: int, c: dict) -> int:
+    """lines of length R 2^loga (R = 3 or 5, loga even): radix-4 steps, then
+    one radix-R step: radix 3 = 6 adds, a scaling by 1/2 and one twiddle
+    product per butterfly; radix 5 = 14 adds and 8 products by a real or
+    pure imaginary twiddle"""
+    L = R << loga
     ops = 0
     logn2, logs = loga, 0
     while logn2 >= 2:
@@ -138,42 +140,45 @@ def _fft3_ops(loga: int, nl: int, c: dict) -> int:
         ops += nl * (L // 4) * c["bfly"] + nl * (L // 4 - s) * 3 * c["tw"]
         logn2 -= 2
         logs += 2
-    return ops + nl * (L // 3) * (6 * c["add"] + c["scale"] + c["tw"])
+    last = (6 * c["add"] + c["scale"] + c["tw"]) if R == 3 else (14 * c["add"] + 8 * c["tw"])
+    return ops + nl * (L // R) * last
 
 
 def length_code(na: int, nb: int) -> tuple[int, int]:
-    """(R, k): the transform length R 2^k the library picks (SSMUL_OPT_RADIX3 on)."""
+    """(R, k): the transform length R 2^k the library picks (default lengths)."""
     L = na + nb - 1
     k = max(2, (L - 1).bit_length())
-    j = k - 2
-    if 11 <= j <= 21 and (3 << j) >= L:
-        return 3, j
+    if 10 <= k - 3 <= 19 and (5 << (k - 3)) >= L:
+        return 5, k - 3
+    if 11 <= k - 2 <= 21 and (3 << (k - 2)) >= L:
+        return 3, k - 2
     return 1, k
 
 
 def geometry(R: int, k: int):
-    """(R, log2 N1 / R, log2 N2, log2 C1, log2 C3) of the default four-step split"""
+    """(log2 N1 / R, log2 N2, log2 C1, log2 C3) of the default four-step split"""
     if R == 1:
         b = min((k + 1) // 2, 11)
         a = k - b
         c = max(0, 11 - a)
     else:
+        amax = 10 if R == 3 else 8
         b = (k + 1) // 2
         a = k - b
         if a & 1:
             a, b = a - 1, b + 1
         while b > 11:
             a, b = a + 2, b - 2
-        while a > 10:
+        while a > amax:
             a, b = a - 2, b + 2
-        c = max(0, 10 - a - 1)
+        c = max(0, 10 - a - (1 if R == 3 else 2))
     return a, b, min(c, b), min(c, b - 1)
 
 
 def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
     """arithmetic operations per product of each four-step kernel (N > 4096):
     radix-4 butterfly (8 adds) + 3 twiddle products unless p = 0; radix-2 =
-    2 adds; radix-3 = 6 adds + 1 scaling + 1 twiddle product; pair product =
+    2 adds; radix-3 and radix-5 as in _fft_odd_ops; pair product =
     2 adds + 1 general product; packing = 3 adds + 1 twiddle product;
     four-step twiddles; scaling and isolation."""
     c = COSTS[precision]
@@ -182,7 +187,7 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
     n1l, n2l, c1l, c3l = geometry(R, k)
     N1, N2 = R << n1l, 1 << n2l
     M2 = N2 // 2
-    col = (lambda nl: _fft_ops(n1l, nl, c)) if R == 1 else (lambda nl: _fft3_ops(n1l, nl, c))
+    col = (lambda nl: _fft_ops(n1l, nl, c)) if R == 1 else (lambda nl: _fft_odd_ops(R, n1l, nl, c))
     fwd = (N2 >> c1l) * col(1 << c1l) + (N1 - 1) * (N2 - 1) * c["tw"]
     rows = 0
     for k1 in range(N1 // 2 + 1):
@@ -199,17 +204,12 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # L2): dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  Only
 # valid for the 75k workload and the kernels as captured; empty when the
 # kernels changed since.
-NCU_TRAFFIC_PER_PRODUCT = {
-    # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
-    "k_rows<double>": (101.537280e6 + 19.416064e6) / 16,
-    "k_rows<disc>": (76.186880e6 + 6.035968e6) / 16,
-    "k_rows<disc32x2>": (75.972096e6 + 5.102336e6) / 16,
-}
+NCU_TRAFFIC_PER_PRODUCT: dict = {}
 
 
 def algorithmic_bytes(n: int) -> float:
     """HBM bytes one product's passes must move at minimum (binary64
-    rectangles, N = 3 2^16 for 75k digits): digits in, Z written and read,
+    rectangles, N = 5 2^15 for 75k digits): digits in, Z written and read,
     W written and read, coefficients written and read, digits out."""
     R, k = length_code(n, n)
     N = R << k
@@ -218,7 +218,7 @@ def algorithmic_bytes(n: int) -> float:
 
 def fft_len_str(n: int) -> str:
     R, k = length_code(n, n)
-    return f"2^{k}" if R == 1 else f"3*2^{k}"
+    return f"2^{k}" if R == 1 else f"{R}*2^{k}"
 
 
 def fp64_peak_gops(sm_mhz: float) -> float:

@@ -85,10 +85,10 @@ typedef struct {
                                  * SSMUL_PREC_FP32, _FP64, _DISC64,
                                  * _DISC32X2 or _NAIVE64 */
     uint32_t fft_log2;          /* the transform length is
-                                 * N = (fft_times3 ? 3 : 1) << fft_log2 */
+                                 * N = fft_odd << fft_log2 */
     uint32_t n_unisolated;      /* coefficients whose set holds >= 2 integers */
     uint32_t n_empty;           /* coefficients whose set holds no integer */
-    uint32_t fft_times3;        /* 1: N = 3 * 2^fft_log2 (SSMUL_OPT_RADIX3) */
+    uint32_t fft_odd;           /* 1, 3 or 5 (SSMUL_OPT_LENGTHS) */
     double   max_width;         /* largest coefficient interval width
                                  * (rounded up), in units of 1; for
                                  * SSMUL_PREC_NAIVE64 the largest distance
@@ -152,15 +152,17 @@ typedef enum {
      * Section 1 names ("use a different algorithm").  The status is the
      * worst of the parts'.  0 (default): off.  Batched calls do not split. */
     SSMUL_OPT_SPLIT_DIGITS = 4,
-    /* value != 0 (default): a product whose na + nb - 1 coefficients fit in
-     * 3 * 2^k < 2^ceil(log2(na + nb - 1)) points (and 3 * 2^k > 4096) uses
-     * the transform length N = 3 * 2^k: the zero padding of Section 2.3 to
-     * the next length of either family, a quarter less work than the next
-     * power of two.  The column transforms then take one radix-3 step, the
-     * roots of unity come from a second table (Ntab = 3 * 2^K), and the
-     * 1/N scaling leaves a factor 1/3 that the isolation applies exactly to
-     * the integer bounds.  0: powers of two only (the paper's 2^k). */
-    SSMUL_OPT_RADIX3 = 5
+    /* bit mask of the transform length families besides 2^k: bit 0 the
+     * lengths 3 * 2^k, bit 1 the lengths 5 * 2^k (default 3: both).  A
+     * product takes the shortest allowed length N >= na + nb - 1 (the zero
+     * padding of Section 2.3; odd lengths only above 4096): 5 * 2^(k-3) =
+     * 0.625 * 2^k or 3 * 2^(k-2) = 0.75 * 2^k instead of the next power of
+     * two 2^k.  The column transforms then end with one radix-5 or radix-3
+     * step, the roots of unity come from a table of Ntab = 5 * 2^K or
+     * 3 * 2^K, and the 1/N scaling leaves a factor 1/5 or 1/3 that the
+     * isolation applies exactly to the integer bounds.  0: powers of two
+     * only (the paper's 2^k). */
+    SSMUL_OPT_LENGTHS = 5
 } ssmul_option;
 
 /*

@@ -20,9 +20,10 @@ extern "C" {
  * of unity of the DFT, Section 2.2), as 4 doubles per entry
  * (cos_lo, cos_hi, sin_lo, sin_hi).  f32 bit 0 selects the binary32 table
  * (values widened to double exactly); bit 1 the family Ntab = 3 * 2^K of
- * the lengths 3 * 2^k (SSMUL_OPT_RADIX3; SSMUL_INVALID_ARG when the plan
- * has none), else Ntab = 2^K.  *log_ntab receives K.  cap is the capacity
- * of h_out in doubles; SSMUL_INVALID_ARG when too small.
+ * the lengths 3 * 2^k, bit 2 the family Ntab = 5 * 2^K of the lengths
+ * 5 * 2^k (SSMUL_OPT_LENGTHS; SSMUL_INVALID_ARG when the plan has none or
+ * both bits are set), else Ntab = 2^K.  *log_ntab receives K.  cap is the
+ * capacity of h_out in doubles; SSMUL_INVALID_ARG when too small.
  */
 ssmul_status ssmul_debug_twiddles(ssmul_plan_t plan, int f32, double* h_out, size_t cap,
                                   int* log_ntab);
@@ -132,8 +133,9 @@ ssmul_status ssmul_debug_set_fault(ssmul_plan_t plan, int kind, long long value)
  * The launch geometry the plan uses for transform length 2^log_n: the
  * four-step split (log2 N1, log2 N2) and log2 of the elements a column CTA
  * holds; for single-CTA lengths (N <= 4096) *log_n1 = 0 and the others are
- * log_n.  log_n = 32 + k (11 <= k <= 21) asks for the length 3 * 2^k, split
- * as N1 = 3 * 2^(*log_n1), N2 = 2^(*log_n2).
+ * log_n.  log_n = 32 + k (11 <= k <= 21) asks for the length 3 * 2^k and
+ * log_n = 64 + k (10 <= k <= 19) for 5 * 2^k, split as N1 = R * 2^(*log_n1),
+ * N2 = 2^(*log_n2) (R = 3 or 5).
  */
 ssmul_status ssmul_debug_geometry(ssmul_plan_t plan, int log_n, int* log_n1, int* log_n2,
                                   int* log_cta);

@@ -47,7 +47,7 @@ SSMUL_OPT_AUTOTUNE = 1
 SSMUL_OPT_FP32_MAX_DIGITS = 2
 SSMUL_OPT_BALANCED = 3
 SSMUL_OPT_SPLIT_DIGITS = 4
-SSMUL_OPT_RADIX3 = 5
+SSMUL_OPT_LENGTHS = 5
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")
@@ -62,7 +62,7 @@ class ssmul_result(ctypes.Structure):
         ("fft_log2", ctypes.c_uint32),
         ("n_unisolated", ctypes.c_uint32),
         ("n_empty", ctypes.c_uint32),
-        ("fft_times3", ctypes.c_uint32),
+        ("fft_odd", ctypes.c_uint32),
         ("max_width", ctypes.c_double),
     ]
 
@@ -224,7 +224,7 @@ def ssmul_mul_batched(plan: int, descs, d_a_pool: int, d_b_pool: int, d_z_pool: 
 
 
 def ssmul_debug_twiddles(plan: int, f32: int, h_out: int, cap: int):
-    """f32: bit 0 binary32, bit 1 the table of the lengths 3 2^k."""
+    """f32: bit 0 binary32, bit 1 the table of the lengths 3 2^k, bit 2 of 5 2^k."""
     ln = ctypes.c_int()
     s = load().ssmul_debug_twiddles(ctypes.c_void_p(plan), int(f32), ctypes.c_void_p(h_out), cap,
                                     ctypes.byref(ln))

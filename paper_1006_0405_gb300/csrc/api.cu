@@ -31,20 +31,23 @@ constexpr size_t FP32_MAX_DIGITS = 32;
 constexpr size_t ARENA_CAP = size_t(4) << 30;
 
 struct Geom {
-    int log_n;       // transform length code (N = 2^log_n, or 3 2^(log_n - LEN3))
+    int log_n;       // transform length code (see LEN3)
     bool small;      // whole product in one CTA
-    int r;           // 1, or 3: columns of 3 2^log_n1 (four-step only)
+    int r;           // 1, or 3 or 5: columns of r 2^log_n1 (four-step only)
     int log_n1, log_n2;
     int log_c1, log_c3;
     int log_cta;     // log2 of the elements a column CTA holds (at least N1)
 };
 
-constexpr int GEOM_CODES = LEN3 + LOG3_MAX + 1;
+constexpr int GEOM_CODES = LEN5 + LOG5_MAX + 1;
+
+// the odd factor and the power of two of a length code
+int odd_of(int code) { return code >= LEN5 ? 5 : (code >= LEN3 ? 3 : 1); }
+int log2_of(int code) { return code % LEN3; }
+int family_of(int code) { return code >= LEN5 ? 2 : (code >= LEN3 ? 1 : 0); }
 
 // the transform length of a length code
-size_t len_of(int code) {
-    return code >= LEN3 ? size_t(3) << (code - LEN3) : size_t(1) << code;
-}
+size_t len_of(int code) { return size_t(odd_of(code)) << log2_of(code); }
 
 int log_n_for(size_t na, size_t nb) {
     const size_t L = na + nb - 1;
@@ -53,14 +56,18 @@ int log_n_for(size_t na, size_t nb) {
     return k;
 }
 
-// The length code of a product: the next power of two N >= na + nb - 1, or
-// 3 2^(k-2) = 3N/4 when that is long enough and allowed (the only length
-// of the other family between N/2 and N).
-int length_code(size_t na, size_t nb, bool radix3) {
+// The length code of a product: the shortest allowed length >= na + nb - 1
+// among the next power of two 2^k, 5 2^(k-3) = 0.625 2^k (lengths bit 1)
+// and 3 2^(k-2) = 0.75 2^k (lengths bit 0), the only lengths of those
+// families between 2^(k-1) and 2^k.
+int length_code(size_t na, size_t nb, int lengths) {
     const int k = log_n_for(na, nb);
-    const int j = k - 2;
-    if (radix3 && j >= LOG3_MIN && j <= LOG3_MAX && (size_t(3) << j) >= na + nb - 1)
-        return LEN3 + j;
+    const size_t L = na + nb - 1;
+    const int j5 = k - 3, j3 = k - 2;
+    if ((lengths & 2) && j5 >= LOG5_MIN && j5 <= LOG5_MAX && (size_t(5) << j5) >= L)
+        return LEN5 + j5;
+    if ((lengths & 1) && j3 >= LOG3_MIN && j3 <= LOG3_MAX && (size_t(3) << j3) >= L)
+        return LEN3 + j3;
     return k;
 }
 
@@ -94,41 +101,43 @@ Geom default_geom(int log_n) {
     return make_geom(log_n, log_n2, LOG_CTA_ELEMS);
 }
 
-// N = 3 2^j = N1 N2 with N1 = 3 2^a (a even: the radix-4 steps of a column
-// end at length 3), N2 = 2^log_n2
-bool geom3_valid(int j, int log_n2) {
+// N = R 2^j = N1 N2 (R = 3 or 5) with N1 = R 2^a (a even: the radix-4 steps
+// of a column end at length R; N1 <= 4096), N2 = 2^log_n2
+bool geom_odd_valid(int R, int j, int log_n2) {
     const int a = j - log_n2;
-    return j >= LOG3_MIN && j <= LOG3_MAX && log_n2 >= 2 && log_n2 <= LOG_N2_MAX && a >= 2 &&
-           a <= 10 && (a & 1) == 0;
+    const bool jok = R == 3 ? (j >= LOG3_MIN && j <= LOG3_MAX) : (j >= LOG5_MIN && j <= LOG5_MAX);
+    return jok && log_n2 >= 2 && log_n2 <= LOG_N2_MAX && a >= 2 && (R << a) <= 4096 &&
+           (a & 1) == 0;
 }
 
-// column CTAs hold C 3 2^a >= 1.5 2^log_cta elements
-Geom make_geom3(int j, int log_n2, int log_cta) {
+// column CTAs hold C R 2^a elements, between 2^(log_cta-1) and 1.5 2^(log_cta-1)
+Geom make_geom_odd(int R, int j, int log_n2, int log_cta) {
     Geom g{};
-    g.log_n = LEN3 + j;
-    g.r = 3;
+    g.log_n = (R == 3 ? LEN3 : LEN5) + j;
+    g.r = R;
     g.small = false;
     g.log_n2 = log_n2;
     g.log_n1 = j - log_n2;
     g.log_cta = log_cta;
-    const int c = log_cta - g.log_n1 - 1;
+    const int c = log_cta - g.log_n1 - (R == 3 ? 1 : 2);
     g.log_c1 = clampi(c, 0, g.log_n2);
     g.log_c3 = clampi(c, 0, g.log_n2 - 1);
     return g;
 }
 
-Geom default_geom3(int j) {
+Geom default_geom_odd(int R, int j) {
+    const int amax = R == 3 ? 10 : 8;           // R 2^a <= 4096, a even
     int b = (j + 1) / 2, a = j - b;
     if (a & 1) { --a; ++b; }
     while (b > LOG_N2_MAX) { b -= 2; a += 2; }
-    while (a > 10) { a -= 2; b += 2; }
-    // column CTAs of 1.5 2^10 elements: the autotuner's choice at 3 2^16
+    while (a > amax) { a -= 2; b += 2; }
+    // column CTAs of about 2^10 elements: the autotuner's choice at 3 2^16
     // (against 3 2^10: 2-3% faster for every rung)
-    return make_geom3(j, b, LOG_CTA_ELEMS - 1);
+    return make_geom_odd(R, j, b, LOG_CTA_ELEMS - 1);
 }
 
 Geom default_geom_code(int code) {
-    return code >= LEN3 ? default_geom3(code - LEN3) : default_geom(code);
+    return code >= LEN3 ? default_geom_odd(odd_of(code), log2_of(code)) : default_geom(code);
 }
 
 int threads_for(int elems) {          // block_fft with 2 butterflies per thread
@@ -194,36 +203,36 @@ struct GraphEntry {
 
 }  // namespace
 
+// One family of twiddle tables, Ntab = R 2^log_tab (log_tab 0: none).
+// The step tables hold n = R 2^j (for R = 1, n = 2^j).
+struct TwFamily {
+    int R = 1;
+    int log_tab = 0;
+    TwEntry<double>* t64 = nullptr;
+    TwEntry<float>* t32 = nullptr;
+    DiscTw* td = nullptr;
+    DDiscC* tdd = nullptr;
+    float rho_dd = 0.f;                 // the radius of every entry of tdd
+    CI<double>* s64 = nullptr;          // step-ordered twiddles (STEP_TAB x 3 each)
+    CI<float>* s32 = nullptr;
+    DiscTw* sd = nullptr;
+    DDiscC* sdd = nullptr;
+    size_t entries() const { return log_tab ? (size_t(R) << log_tab) / 8 + 1 : 0; }
+};
+
+constexpr int FAMILIES = 3;             // R = 1, 3, 5
+constexpr int FAMILY_R[FAMILIES] = {1, 3, 5};
+
 struct ssmul_plan_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     ssmul_precision prec = SSMUL_PREC_FP64;
     size_t max_na = 0, max_nb = 0, max_products = 0;
     int log_n_max = 0;
-    int log_tab = 0;
-    TwEntry<double>* t64 = nullptr;
-    TwEntry<float>* t32 = nullptr;
-    DiscTw* td = nullptr;
-    DDiscC* tdd = nullptr;
-    float* rho = nullptr;               // device: the largest radius of td; the radius of tdd
-    float rho_dd = 0.f;
-    CI<double>* s64 = nullptr;          // step-ordered twiddles (STEP_TAB x 3 each)
-    CI<float>* s32 = nullptr;
-    DiscTw* sd = nullptr;
-    DDiscC* sdd = nullptr;
-    // the family Ntab3 = 3 2^log_tab3 (lengths 3 2^j; 0 when the plan has none)
-    int log_tab3 = 0;
-    TwEntry<double>* t64_3 = nullptr;
-    TwEntry<float>* t32_3 = nullptr;
-    DiscTw* td_3 = nullptr;
-    DDiscC* tdd_3 = nullptr;
-    float rho_dd3 = 0.f;
-    CI<double>* s64_3 = nullptr;        // step-ordered twiddles for n = 3 2^j
-    CI<float>* s32_3 = nullptr;
-    DiscTw* sd_3 = nullptr;
-    DDiscC* sdd_3 = nullptr;
+    TwFamily fam[FAMILIES];             // R = 1 always; R = 3, 5 when the plan reaches them
+    float* rho = nullptr;               // device, 2 per family: largest td radius, tdd radius
     Geom geom[GEOM_CODES] = {};           // by length code
-    bool radix3 = true;                 // SSMUL_OPT_RADIX3
+    int lengths = 3;                    // SSMUL_OPT_LENGTHS
     size_t fp32_max_digits = FP32_MAX_DIGITS;
     bool balanced = false;
     uint32_t* pre = nullptr;            // balanced: digit prefix sums of one product
@@ -266,21 +275,17 @@ struct ssmul_plan_s {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     double kt_ms[SSMUL_KERNEL_KINDS] = {};
     unsigned long long kt_launches[SSMUL_KERNEL_KINDS] = {};
-    TwTable tw() const {
-        if (octant_only)
-            return TwTable{t64, t32, log_tab, td, tdd, rho_dd, nullptr, nullptr, nullptr, nullptr,
-                           nullptr, nullptr, nullptr, nullptr};
-        return TwTable{t64, t32, log_tab, td, tdd, rho_dd, s64, s32, sd, sdd,
-                       nullptr, nullptr, nullptr, nullptr};
-    }
-    // the table of the family 3 2^K (its power-of-two step tables are the
-    // first family's: the same enclosed values)
-    TwTable tw3() const {
-        if (octant_only)
-            return TwTable{t64_3, t32_3, log_tab3, td_3, tdd_3, rho_dd3, nullptr, nullptr, nullptr,
-                           nullptr, nullptr, nullptr, nullptr, nullptr};
-        return TwTable{t64_3, t32_3, log_tab3, td_3, tdd_3, rho_dd3, s64, s32, sd, sdd,
-                       s64_3, s32_3, sd_3, sdd_3};
+    // the twiddle table of family f (0: R = 1; 1: R = 3; 2: R = 5).  Its
+    // power-of-two step tables are family 0's (the same enclosed values).
+    TwTable tw(int f = 0) const {
+        const TwFamily& F = fam[f];
+        const TwFamily& P = fam[0];
+        const bool st = !octant_only;
+        return TwTable{F.t64, F.t32, F.log_tab, F.td, F.tdd, F.rho_dd,
+                       st ? P.s64 : nullptr, st ? P.s32 : nullptr, st ? P.sd : nullptr,
+                       st ? P.sdd : nullptr,
+                       st && f ? F.s64 : nullptr, st && f ? F.s32 : nullptr,
+                       st && f ? F.sd : nullptr, st && f ? F.sdd : nullptr};
     }
 };
 
@@ -337,6 +342,9 @@ ssmul_status set_smem_attrs() {
     SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return SSMUL_OK;
 }
 
@@ -382,7 +390,9 @@ ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, con
         LaunchScope ls(p, SSMUL_K_SMALL + ko);
         k_small<T, B><<<count, fft_threads<V>(n), n * sizeof(V), p->stream>>>(d_desc, tw, gate);
     } else if (g.r == 3) {
-        enqueue_four_step<T, 3>(p, d_desc, count, g, gate, p->tw3());
+        enqueue_four_step<T, 3>(p, d_desc, count, g, gate, p->tw(1));
+    } else if (g.r == 5) {
+        enqueue_four_step<T, 5>(p, d_desc, count, g, gate, p->tw(2));
     } else {
         enqueue_four_step<T, 1>(p, d_desc, count, g, gate, tw);
     }
@@ -461,7 +471,7 @@ ssmul_status enqueue_prefix(ssmul_plan_t p, const ProdDesc* d_desc, int count, s
 // Enqueue one complete product (rungs, carry, outcome) for d_desc[0].
 ssmul_status enqueue_product(ssmul_plan_t p, const ProdDesc* d_desc, size_t na, size_t nb,
                              ssmul_precision prec) {
-    const Geom& g = p->geom[length_code(na, nb, p->radix3)];
+    const Geom& g = p->geom[length_code(na, nb, p->lengths)];
     {
         ssmul_status s0 = enqueue_prefix(p, d_desc, 1, na > nb ? na : nb);
         if (s0 != SSMUL_OK) return s0;
@@ -497,7 +507,7 @@ ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t*
     d.z = z;
     d.na = uint32_t(na);
     d.nb = uint32_t(nb);
-    d.log_n = length_code(na, nb, p->radix3);
+    d.log_n = length_code(na, nb, p->lengths);
     d.Z = p->Z;
     d.W = p->W;
     d.coeff = p->coeff;
@@ -631,7 +641,7 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
     std::vector<char> elig(count);
     for (size_t i = 0; i < count; ++i) {
         order[i] = int(i);
-        logn[i] = length_code(h_desc[i].na, h_desc[i].nb, p->radix3);
+        logn[i] = length_code(h_desc[i].na, h_desc[i].nb, p->lengths);
         elig[i] = p->prec == SSMUL_PREC_FP32 ||
                   (uses_fp32(p->prec) && fp32_eligible(p, h_desc[i].na, h_desc[i].nb, logn[i]));
     }
@@ -838,8 +848,8 @@ void tune_cache_read(const std::string& dev, std::vector<Geom>& found) {
             cta >= 9 && cta <= 12) {
             if (ln > LOG_SMALL && ln <= LOG_N_MAX && geom_valid(ln, ln2))
                 found.push_back(make_geom(ln, ln2, cta));
-            else if (ln >= LEN3 && geom3_valid(ln - LEN3, ln2))
-                found.push_back(make_geom3(ln - LEN3, ln2, cta));
+            else if (ln >= LEN3 && ln < GEOM_CODES && geom_odd_valid(odd_of(ln), log2_of(ln), ln2))
+                found.push_back(make_geom_odd(odd_of(ln), log2_of(ln), ln2, cta));
         }
     }
     std::fclose(f);
@@ -861,7 +871,8 @@ ssmul_status autotune(ssmul_plan_t p) {
     // the length codes the plan can use
     std::vector<int> codes;
     for (int ln = LOG_SMALL + 1; ln <= p->log_n_max; ++ln) codes.push_back(ln);
-    for (int j = LOG3_MIN; p->log_tab3 && j <= p->log_tab3; ++j) codes.push_back(LEN3 + j);
+    for (int j = LOG3_MIN; p->fam[1].log_tab && j <= p->fam[1].log_tab; ++j) codes.push_back(LEN3 + j);
+    for (int j = LOG5_MIN; p->fam[2].log_tab && j <= p->fam[2].log_tab; ++j) codes.push_back(LEN5 + j);
     std::vector<int> todo;
     for (int ln : codes) {
         bool have = false;
@@ -928,16 +939,16 @@ ssmul_status autotune(ssmul_plan_t p) {
         if (cudaMemcpy(dd, hd.data(), cnt * sizeof(ProdDesc), cudaMemcpyHostToDevice) !=
             cudaSuccess)
             return done(SSMUL_CUDA_ERROR);
-        const bool three = ln >= LEN3;
-        const int k = three ? ln - LEN3 : ln;
+        const bool three = ln >= LEN3;                // an odd family (3 or 5)
+        const int k = log2_of(ln), R = odd_of(ln);
         const int h = (k + 1) / 2;
         float best = 1e30f;
         Geom best_g = p->geom[ln];
         // family 3: the column exponent must stay even, so try two steps either way
         for (int ln2 = h - (three ? 2 : 1); ln2 <= h + (three ? 2 : 1); ++ln2) {
-            if (three ? !geom3_valid(k, ln2) : !geom_valid(ln, ln2)) continue;
+            if (three ? !geom_odd_valid(R, k, ln2) : !geom_valid(ln, ln2)) continue;
             for (int cta = 9; cta <= 11; ++cta) {
-                const Geom g = three ? make_geom3(k, ln2, cta) : make_geom(ln, ln2, cta);
+                const Geom g = three ? make_geom_odd(R, k, ln2, cta) : make_geom(ln, ln2, cta);
                 float t_min = 1e30f;
                 for (int rep = 0; rep < 4; ++rep) {
                     if (cudaMemsetAsync(ds, 0, cnt * sizeof(ProdState), p->stream) != cudaSuccess)
@@ -991,23 +1002,17 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
     graph_drop(p->cached);
-    cudaFree(p->t64);
-    cudaFree(p->t32);
-    cudaFree(p->td);
-    cudaFree(p->tdd);
+    for (TwFamily& F : p->fam) {
+        cudaFree(F.t64);
+        cudaFree(F.t32);
+        cudaFree(F.td);
+        cudaFree(F.tdd);
+        cudaFree(F.s64);
+        cudaFree(F.s32);
+        cudaFree(F.sd);
+        cudaFree(F.sdd);
+    }
     cudaFree(p->rho);
-    cudaFree(p->s64);
-    cudaFree(p->s32);
-    cudaFree(p->sd);
-    cudaFree(p->sdd);
-    cudaFree(p->t64_3);
-    cudaFree(p->t32_3);
-    cudaFree(p->td_3);
-    cudaFree(p->tdd_3);
-    cudaFree(p->s64_3);
-    cudaFree(p->s32_3);
-    cudaFree(p->sd_3);
-    cudaFree(p->sdd_3);
     cudaFree(p->Z);
     cudaFree(p->W);
     cudaFree(p->coeff);
@@ -1060,35 +1065,31 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     p->max_nb = max_nb;
     p->max_products = max_products;
     p->log_n_max = log_n;
-    p->log_tab = log_n < 4 ? 4 : log_n;
+    // families: Ntab = 2^log_n; 3 2^(log_n - 2) and 5 2^(log_n - 3) hold every
+    // odd length R 2^j the plan's products can take (R 2^j < 2^log_n)
+    for (int f = 0; f < FAMILIES; ++f) p->fam[f].R = FAMILY_R[f];
+    p->fam[0].log_tab = log_n < 4 ? 4 : log_n;
+    p->fam[1].log_tab = log_n - 2 >= LOG3_MIN ? (log_n - 2 > LOG3_MAX ? LOG3_MAX : log_n - 2) : 0;
+    p->fam[2].log_tab = log_n - 3 >= LOG5_MIN ? (log_n - 3 > LOG5_MAX ? LOG5_MAX : log_n - 3) : 0;
     for (int c = 0; c < GEOM_CODES; ++c) p->geom[c] = default_geom_code(c);
-    // lengths 3 2^j the plan's products can take: j <= log_n - 2
-    p->log_tab3 = log_n - 2 >= LOG3_MIN ? (log_n - 2 > LOG3_MAX ? LOG3_MAX : log_n - 2) : 0;
 
     const size_t n = size_t(1) << log_n;
     const size_t slots = max_products ? max_products : 1;
-    const size_t tab = (size_t(1) << p->log_tab) / 8 + 1;
+    const size_t tab = p->fam[0].entries();
     p->flags_per_product = carry_tiles(max_na + max_nb);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&p->t64, tab * sizeof(TwEntry<double>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->t32, tab * sizeof(TwEntry<float>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->td, tab * sizeof(DiscTw));
-    if (e == cudaSuccess) e = cudaMalloc(&p->tdd, tab * sizeof(DDiscC));
-    if (e == cudaSuccess) e = cudaMalloc(&p->rho, 4 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&p->s64, 3 * STEP_TAB * sizeof(CI<double>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->s32, 3 * STEP_TAB * sizeof(CI<float>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->sd, 3 * STEP_TAB * sizeof(DiscTw));
-    if (e == cudaSuccess) e = cudaMalloc(&p->sdd, 3 * STEP_TAB * sizeof(DDiscC));
-    const size_t tab3 = p->log_tab3 ? (size_t(3) << p->log_tab3) / 8 + 1 : 0;
-    if (tab3) {
-        if (e == cudaSuccess) e = cudaMalloc(&p->t64_3, tab3 * sizeof(TwEntry<double>));
-        if (e == cudaSuccess) e = cudaMalloc(&p->t32_3, tab3 * sizeof(TwEntry<float>));
-        if (e == cudaSuccess) e = cudaMalloc(&p->td_3, tab3 * sizeof(DiscTw));
-        if (e == cudaSuccess) e = cudaMalloc(&p->tdd_3, tab3 * sizeof(DDiscC));
-        if (e == cudaSuccess) e = cudaMalloc(&p->s64_3, 3 * STEP_TAB * sizeof(CI<double>));
-        if (e == cudaSuccess) e = cudaMalloc(&p->s32_3, 3 * STEP_TAB * sizeof(CI<float>));
-        if (e == cudaSuccess) e = cudaMalloc(&p->sd_3, 3 * STEP_TAB * sizeof(DiscTw));
-        if (e == cudaSuccess) e = cudaMalloc(&p->sdd_3, 3 * STEP_TAB * sizeof(DDiscC));
+    if (e == cudaSuccess) e = cudaMalloc(&p->rho, 2 * FAMILIES * sizeof(float));
+    for (TwFamily& F : p->fam) {
+        const size_t t = F.entries();
+        if (!t) continue;
+        if (e == cudaSuccess) e = cudaMalloc(&F.t64, t * sizeof(TwEntry<double>));
+        if (e == cudaSuccess) e = cudaMalloc(&F.t32, t * sizeof(TwEntry<float>));
+        if (e == cudaSuccess) e = cudaMalloc(&F.td, t * sizeof(DiscTw));
+        if (e == cudaSuccess) e = cudaMalloc(&F.tdd, t * sizeof(DDiscC));
+        if (e == cudaSuccess) e = cudaMalloc(&F.s64, 3 * STEP_TAB * sizeof(CI<double>));
+        if (e == cudaSuccess) e = cudaMalloc(&F.s32, 3 * STEP_TAB * sizeof(CI<float>));
+        if (e == cudaSuccess) e = cudaMalloc(&F.sd, 3 * STEP_TAB * sizeof(DiscTw));
+        if (e == cudaSuccess) e = cudaMalloc(&F.sdd, 3 * STEP_TAB * sizeof(DDiscC));
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
@@ -1126,38 +1127,39 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if ((s = set_smem_attrs<DDisc>()) != SSMUL_OK) return fail(s);
 
     const int threads = 256;
-    const int blocks = int((tab + threads - 1) / threads);
-    if ((e = cudaMemsetAsync(p->rho, 0, 4 * sizeof(float), p->stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(p->rho, 0, 2 * FAMILIES * sizeof(float), p->stream)) != cudaSuccess)
         return fail(cuda_status(e));
-    k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->t32, p->log_tab, 1);
-    k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->t64, p->td, p->rho, int64_t(tab));
-    k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(p->td, p->rho, p->tdd, int64_t(tab));
-    if (tab3) {
-        const int blocks3 = int((tab3 + threads - 1) / threads);
-        k_twiddle_gen<<<blocks3, threads, 0, p->stream>>>(p->t64_3, p->t32_3, p->log_tab3, 3);
-        k_disc_tw_gen<<<blocks3, threads, 0, p->stream>>>(p->t64_3, p->td_3, p->rho + 2, int64_t(tab3));
-        k_ddisc_tw_gen<<<blocks3, threads, 0, p->stream>>>(p->td_3, p->rho + 2, p->tdd_3, int64_t(tab3));
+    for (int f = 0; f < FAMILIES; ++f) {
+        TwFamily& F = p->fam[f];
+        const size_t t = F.entries();
+        if (!t) continue;
+        const int blocks = int((t + threads - 1) / threads);
+        k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(F.t64, F.t32, F.log_tab, F.R);
+        k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(F.t64, F.td, p->rho + 2 * f, int64_t(t));
+        k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(F.td, p->rho + 2 * f, F.tdd, int64_t(t));
     }
     {
         p->octant_only = true;
-        const TwTable octant = p->tw();
-        const TwTable octant3 = p->tw3();
+        const TwTable oct[FAMILIES] = {p->tw(0), p->tw(1), p->tw(2)};
         p->octant_only = false;
-        k_step_tw_gen<1><<<(3 * STEP_TAB + threads - 1) / threads, threads, 0, p->stream>>>(
-            octant, p->s64, p->s32, p->sd, p->sdd);
-        if (tab3)
-            k_step_tw_gen<3><<<(3 * STEP_TAB + threads - 1) / threads, threads, 0, p->stream>>>(
-                octant3, p->s64_3, p->s32_3, p->sd_3, p->sdd_3);
+        const int sb = (3 * STEP_TAB + threads - 1) / threads;
+        k_step_tw_gen<1><<<sb, threads, 0, p->stream>>>(oct[0], p->fam[0].s64, p->fam[0].s32,
+                                                        p->fam[0].sd, p->fam[0].sdd);
+        if (p->fam[1].entries())
+            k_step_tw_gen<3><<<sb, threads, 0, p->stream>>>(oct[1], p->fam[1].s64, p->fam[1].s32,
+                                                            p->fam[1].sd, p->fam[1].sdd);
+        if (p->fam[2].entries())
+            k_step_tw_gen<5><<<sb, threads, 0, p->stream>>>(oct[2], p->fam[2].s64, p->fam[2].s32,
+                                                            p->fam[2].sd, p->fam[2].sdd);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_status(e));
-    float h_rho[4] = {0.f, 0.f, 0.f, 0.f};
+    float h_rho[2 * FAMILIES] = {};
     if ((e = cudaMemcpyAsync(h_rho, p->rho, sizeof(h_rho), cudaMemcpyDeviceToHost, p->stream)) !=
         cudaSuccess)
         return fail(cuda_status(e));
     if ((e = cudaEventRecord(p->desc_free, p->stream)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(cuda_status(e));
-    p->rho_dd = h_rho[1];
-    p->rho_dd3 = h_rho[3];
+    for (int f = 0; f < FAMILIES; ++f) p->fam[f].rho_dd = h_rho[2 * f + 1];
     *out = p;
     return SSMUL_OK;
 }
@@ -1190,10 +1192,11 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
             graph_drop(p->cached);
             p->balanced = value != 0;
             return SSMUL_OK;
-        case SSMUL_OPT_RADIX3:
+        case SSMUL_OPT_LENGTHS:
+            if (value < 0 || value > 3) return SSMUL_INVALID_ARG;
             SS_TRY(cudaStreamSynchronize(p->stream));
             graph_drop(p->cached);
-            p->radix3 = value != 0;
+            p->lengths = int(value);
             return SSMUL_OK;
         case SSMUL_OPT_SPLIT_DIGITS: {
             if (value < 0 || (value > 0 && value < 1024)) return SSMUL_INVALID_ARG;
@@ -1320,7 +1323,8 @@ ssmul_status ssmul_debug_geometry(ssmul_plan_t p, int log_n, int* log_n1, int* l
                                   int* log_cta) {
     if (!p || !log_n1 || !log_n2 || !log_cta) return SSMUL_INVALID_ARG;
     if (!((log_n >= 2 && log_n <= LOG_N_MAX) ||
-          (log_n >= LEN3 + LOG3_MIN && log_n <= LEN3 + LOG3_MAX)))
+          (log_n >= LEN3 + LOG3_MIN && log_n <= LEN3 + LOG3_MAX) ||
+          (log_n >= LEN5 + LOG5_MIN && log_n <= LEN5 + LOG5_MAX)))
         return SSMUL_INVALID_ARG;
     const Geom& g = p->geom[log_n];
     *log_n1 = g.small ? 0 : g.log_n1;
@@ -1331,21 +1335,18 @@ ssmul_status ssmul_debug_geometry(ssmul_plan_t p, int log_n, int* log_n1, int* l
 
 ssmul_status ssmul_debug_twiddles(ssmul_plan_t p, int f32, double* h_out, size_t cap,
                                   int* log_ntab) {
-    if (!p || !h_out || !log_ntab || f32 < 0 || f32 > 3) return SSMUL_INVALID_ARG;
-    const bool three = (f32 & 2) != 0;
-    if (three && !p->log_tab3) return SSMUL_INVALID_ARG;
-    const size_t tab = three ? (size_t(3) << p->log_tab3) / 8 + 1 : (size_t(1) << p->log_tab) / 8 + 1;
-    if (cap < 4 * tab) return SSMUL_INVALID_ARG;
+    if (!p || !h_out || !log_ntab || f32 < 0 || f32 > 5 || (f32 & 6) == 6) return SSMUL_INVALID_ARG;
+    const TwFamily& F = p->fam[(f32 & 2) ? 1 : ((f32 & 4) ? 2 : 0)];
+    const size_t tab = F.entries();
+    if (!tab || cap < 4 * tab) return SSMUL_INVALID_ARG;
     ssmul_status s = check_device(p);
     if (s != SSMUL_OK) return s;
-    *log_ntab = three ? p->log_tab3 : p->log_tab;
+    *log_ntab = F.log_tab;
     if (!(f32 & 1)) {
-        SS_TRY(cudaMemcpy(h_out, three ? p->t64_3 : p->t64, tab * sizeof(TwEntry<double>),
-                          cudaMemcpyDeviceToHost));
+        SS_TRY(cudaMemcpy(h_out, F.t64, tab * sizeof(TwEntry<double>), cudaMemcpyDeviceToHost));
     } else {
         std::vector<TwEntry<float>> t(tab);
-        SS_TRY(cudaMemcpy(t.data(), three ? p->t32_3 : p->t32, tab * sizeof(TwEntry<float>),
-                          cudaMemcpyDeviceToHost));
+        SS_TRY(cudaMemcpy(t.data(), F.t32, tab * sizeof(TwEntry<float>), cudaMemcpyDeviceToHost));
         for (size_t j = 0; j < tab; ++j) {
             h_out[4 * j] = t[j].cl;
             h_out[4 * j + 1] = t[j].ch;
@@ -1400,7 +1401,7 @@ __global__ void k_disc_op(int op, const double* x, const double* y, double* out,
         switch (op) {
             case 0: r = a + b; break;
             case 1: r = a - b; break;
-            case 2: r = mul_tw(a, DiscTw{b.x, b.y, b.r, 0.f}); break;
+            case 2: r = mul_tw(a, DiscTw{b.x, b.y, b.r, TW_MOD_UP}); break;
             case 3: r = mul_ci(a, b); break;
             default: r = scale_pow2(a, int(y[3 * i])); break;
         }
@@ -1440,7 +1441,7 @@ __global__ void k_ddisc_op(int op, const double* x, const double* y, double* out
         switch (op) {
             case 0: r = a + b; break;
             case 1: r = a - b; break;
-            case 2: r = mul_tw(a, DDiscTw{b.xh, b.xl, b.yh, b.yl, b.r, 0.f}); break;
+            case 2: r = mul_tw(a, DDiscTw{b.xh, b.xl, b.yh, b.yl, b.r, TW_MOD_UP}); break;
             case 3: r = mul_ci(a, b); break;
             default: r = scale_pow2(a, int(b5[0])); break;
         }

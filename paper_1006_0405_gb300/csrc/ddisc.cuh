@@ -43,7 +43,7 @@ struct alignas(8) DDisc {
 struct alignas(8) DDiscTw {
     float ch, cl, sh, sl;   // centre (ch + cl) + i (sh + sl)
     float rho;
-    float pad;
+    float mod;              // upper bound on |centre| (see DiscTw)
 };
 
 // twiddle table entry: the centre only.  Every entry of a table shares one
@@ -196,15 +196,16 @@ __device__ __forceinline__ void pair_cmul(float axh, float axl, float ayh, float
 
 // a * w for a twiddle disc: |a w - a_c w_c| <= r (|w_c| + rho) + |a_c| rho
 // with |a_c| <= ma (1 + 2u), plus the centre's rounding DD_MUL ma mb + 6 ETA,
-// gathered as r (TW_MOD_UP + rho) + ma (DD_MUL mb + (1 + 2u) rho) + 6 ETA
-// (the terms in rho alone are the same for every twiddle of a table)
+// gathered as r (mod + rho) + ma (DD_MUL mb + (1 + 2u) rho) + 6 ETA with
+// |w_c| <= w.mod (the terms in rho and mod alone are the same for every
+// twiddle of a table)
 __device__ __forceinline__ DDisc mul_tw(const DDisc& a, const DDiscTw& w) {
     DDisc z;
     pair_cmul(a.xh, a.xl, a.yh, a.yl, w.ch, w.cl, w.sh, w.sl, z);
     const float ma = __fadd_ru(fabsf(a.xh), fabsf(a.yh));
     const float mb = __fadd_ru(fabsf(w.ch), fabsf(w.sh));
     const float k = __fmaf_ru(DD_MUL, mb, __fmul_ru(DD_ONE_U, w.rho));
-    z.r = __fmaf_ru(a.r, __fadd_ru(TW_MOD_UP, w.rho), __fmaf_ru(ma, k, 6.f * DD_ETA));
+    z.r = __fmaf_ru(a.r, __fadd_ru(w.mod, w.rho), __fmaf_ru(ma, k, 6.f * DD_ETA));
     z.pad = 0.f;
     return z;
 }

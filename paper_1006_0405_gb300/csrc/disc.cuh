@@ -35,11 +35,14 @@ struct alignas(16) Pt {
     double x, y;
 };
 
-// disc twiddle: centre and radius of an enclosure of omega^j
+// disc twiddle: centre and radius of an enclosure of omega^j, and an
+// upper bound on the modulus of the centre (TW_MOD_UP for the roots of
+// unity; smaller for the real and imaginary scalars of the radix-3 and
+// radix-5 steps)
 struct DiscTw {
     double c, s;
     float rho;
-    float pad;
+    float mod;
 };
 
 // ---- bounds from the bit patterns (integer pipe) ----------------------------------
@@ -107,7 +110,7 @@ __device__ __forceinline__ Disc conj(const Disc& a) { return {a.x, -a.y, a.r, 0.
 __device__ __forceinline__ Disc conj_flip(const Disc& a) { return {a.x, flip(a.y), a.r, 0.f}; }
 __device__ __forceinline__ Disc mul_negi_flip(const Disc& a) { return {a.y, flip(a.x), a.r, 0.f}; }
 
-// a * w for a twiddle disc w = D(c + i s, rho):
+// a * w for a twiddle disc w = D(c + i s, rho) with |w_c| <= w.mod:
 // |a w - a_c w_c| <= r (|w_c| + rho) + |a_c| rho, plus the centre rounding:
 // x = RN(fma(ax, c, -RN(ay s))) errs by <= hu(t1) + hu(x), likewise y.
 __device__ __forceinline__ Disc mul_tw(const Disc& a, const DiscTw& w) {
@@ -117,7 +120,7 @@ __device__ __forceinline__ Disc mul_tw(const Disc& a, const DiscTw& w) {
     const double t2 = mul_rn(a.y, w.c);
     z.y = __fma_rn(a.x, w.s, t2);
     const float rnd = __fadd_ru(err2(t1, z.x), err2(t2, z.y));
-    const float prop = __fmaf_ru(a.r, __fadd_ru(TW_MOD_UP, w.rho), __fmul_ru(mod_up(a.x, a.y), w.rho));
+    const float prop = __fmaf_ru(a.r, __fadd_ru(w.mod, w.rho), __fmul_ru(mod_up(a.x, a.y), w.rho));
     z.r = __fadd_ru(prop, rnd);
     z.pad = 0.f;
     return z;

@@ -105,46 +105,80 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
     }
 }
 
-// ---- lines of length L = 3 2^a --------------------------------------------------
+// ---- lines of length L = R 2^a, R = 3 or 5 ---------------------------------------
 //
 // The same Stockham factorisation with the radix-4 steps first (sub-lengths
-// n = 3 2^a, 3 2^(a-2), ..., 12; a even, so s stays a power of two and the
-// twiddles omega_n^{p u} come from the family-3 tables) and one radix-3
-// step last (n = 3, s = L/3, no twiddle):
-//   y[q + s u] = sum_t x[q + s t] omega_3^{SIGN t u},   u = 0, 1, 2.
-// With S = x1 + x2, D = x1 - x2 and omega_3^{+-1} = -1/2 +- i sqrt(3)/2:
+// n = R 2^a, R 2^(a-2), ..., 4 R; a even, so s stays a power of two and the
+// twiddles omega_n^{p u} come from the family-R tables) and one radix-R
+// step last (n = R, s = L/R, no twiddle):
+//   y[q + s u] = sum_t x[q + s t] omega_R^{SIGN t u},   u = 0 .. R-1.
+// Radix 3, with S = x1 + x2, D = x1 - x2 and omega_3^{+-1} = -1/2 +- i sqrt(3)/2:
 //   y0 = x0 + S,   y1 = T + U,   y2 = T - U,
-//   T = x0 - S/2,  U = (SIGN i sqrt(3)/2) D,
-// where S/2 is an exact scaling (scale_pow2) and U a product with the
-// enclosure of SIGN i sqrt(3)/2: the imaginary part of the family-3 table's
-// enclosure of omega_3^SIGN, its real part replaced by the point 0 (the
-// rectangle or disc of that pure imaginary number lies inside).
+//   T = x0 - S/2,  U = (SIGN i sqrt(3)/2) D.
+// Radix 5, with S1 = x1 + x4, D1 = x1 - x4, S2 = x2 + x3, D2 = x2 - x3 and
+// omega_5^{SIGN k} = c_k + i s_k (k = 1, 2):
+//   y0 = x0 + S1 + S2,
+//   y1, y4 = A +- U,  A = x0 + c1 S1 + c2 S2,  U = i (s1 D1 + s2 D2),
+//   y2, y3 = B +- W,  B = x0 + c2 S1 + c1 S2,  W = i (s2 D1 - s1 D2).
+// S/2 is an exact scaling (scale_pow2); the products by the real numbers c_k
+// and the pure imaginary numbers i s_k use enclosures of those numbers alone
+// (ScalarTw), taken from the family-R table's enclosure of omega_R^{SIGN k}.
 // Requires nl * L / 4 <= BPT * blockDim.x, like block_fft.
 
-template <typename V> __device__ __forceinline__ typename VTraits<V>::Tw imag_only(const typename VTraits<V>::Tw& w);
-template <> __device__ __forceinline__ CI<double> imag_only<CI<double>>(const CI<double>& w) {
-    return {0.0, 0.0, w.il, w.ih};
+// The real number cos or the pure imaginary number i sin of the enclosure
+// omega_Ntab^(SIGN j) (family R) in the twiddle type of V, built from the
+// one component of the rectangle table that it needs: a rectangle with the
+// other part the point 0; a disc whose radius bounds that component's
+// error alone (a twiddle disc's radius covers both components).
+template <typename V, int SIGN, int R> struct ScalarTw;
+template <int SIGN, int R> struct ScalarTw<CI<double>, SIGN, R> {
+    static __device__ __forceinline__ CI<double> get(const TwTable& tw, uint32_t j, bool imag) {
+        const CI<double> w = twiddle<double, SIGN, R>(tw, j);
+        return imag ? CI<double>{0.0, 0.0, w.il, w.ih} : CI<double>{w.rl, w.rh, 0.0, 0.0};
+    }
+};
+template <int SIGN, int R> struct ScalarTw<CI<float>, SIGN, R> {
+    static __device__ __forceinline__ CI<float> get(const TwTable& tw, uint32_t j, bool imag) {
+        const CI<float> w = twiddle<float, SIGN, R>(tw, j);
+        return imag ? CI<float>{0.f, 0.f, w.il, w.ih} : CI<float>{w.rl, w.rh, 0.f, 0.f};
+    }
+};
+// centre = RN midpoint of [lo, hi], radius = RU of the larger distance to an end
+__device__ __forceinline__ void mid_rad(double lo, double hi, double& c, float& r) {
+    c = __dadd_rn(0.5 * lo, 0.5 * hi);
+    r = __double2float_ru(fmax(__dsub_ru(c, lo), __dsub_ru(hi, c)));
 }
-template <> __device__ __forceinline__ CI<float> imag_only<CI<float>>(const CI<float>& w) {
-    return {0.f, 0.f, w.il, w.ih};
-}
-template <> __device__ __forceinline__ DiscTw imag_only<Disc>(const DiscTw& w) {
-    return {0.0, w.s, w.rho, 0.f};
-}
-template <> __device__ __forceinline__ DiscTw imag_only<Pt>(const DiscTw& w) {
-    return {0.0, w.s, w.rho, 0.f};
-}
-template <> __device__ __forceinline__ DDiscTw imag_only<DDisc>(const DDiscTw& w) {
-    return {0.f, 0.f, w.sh, w.sl, w.rho, 0.f};
-}
+template <int SIGN, int R> struct ScalarTw<Disc, SIGN, R> {
+    static __device__ __forceinline__ DiscTw get(const TwTable& tw, uint32_t j, bool imag) {
+        const CI<double> w = twiddle<double, SIGN, R>(tw, j);
+        double c;
+        float r;
+        mid_rad(imag ? w.il : w.rl, imag ? w.ih : w.rh, c, r);
+        const float m = abs_up(c);                      // |centre| (a scalar's modulus)
+        return imag ? DiscTw{0.0, c, r, m} : DiscTw{c, 0.0, r, m};
+    }
+};
+template <int SIGN, int R> struct ScalarTw<Pt, SIGN, R> : ScalarTw<Disc, SIGN, R> {};
+// the binary64 centre split into a pair as in k_ddisc_tw_gen (|c| <= 1)
+template <int SIGN, int R> struct ScalarTw<DDisc, SIGN, R> {
+    static __device__ __forceinline__ DDiscTw get(const TwTable& tw, uint32_t j, bool imag) {
+        const DiscTw d = ScalarTw<Disc, SIGN, R>::get(tw, j, imag);
+        const double c = imag ? d.s : d.c;
+        const float h = __double2float_rn(c), l = __double2float_rn(c - double(h));
+        const float r = __fadd_ru(d.rho, 2.f * DD_U2 + DD_ETA);
+        const float m = dd_mod_up(h, 0.f);              // >= |h + l|
+        return imag ? DDiscTw{0.f, 0.f, h, l, r, m} : DDiscTw{h, l, 0.f, 0.f, r, m};
+    }
+};
 
-template <typename V, int SIGN, int BPT = 2>
-__device__ void block_fft3(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw) {
-    const int L = 3 << loga;
+template <typename V, int SIGN, int BPT = 2, int R = 3>
+__device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw) {
+    static_assert(R == 3 || R == 5, "odd factor 3 or 5");
+    const int L = R << loga;
     const int Lq = L >> 2;                      // butterflies per line in a radix-4 step
-    int logn2 = loga, logs = 0;                 // n = 3 2^logn2, s = 2^logs
+    int logn2 = loga, logs = 0;                 // n = R 2^logn2, s = 2^logs
     while (logn2 >= 2) {
-        const int m = 3 << (logn2 - 2);         // n / 4
+        const int m = R << (logn2 - 2);         // n / 4
         const int s = 1 << logs;
         const int nbf = nl * Lq;
         V v[BPT][4];
@@ -163,9 +197,9 @@ __device__ void block_fft3(SBuf<V> buf, int loga, int nl, int pitch, const TwTab
                 for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
                 bfly4<V, SIGN>(v[h][0], v[h][1], v[h][2], v[h][3]);
                 if (p != 0) {
-                    v[h][1] = mul_tw(v[h][1], step_twiddle3<V, SIGN>(tw, logn2, p, 1));
-                    v[h][2] = mul_tw(v[h][2], step_twiddle3<V, SIGN>(tw, logn2, p, 2));
-                    v[h][3] = mul_tw(v[h][3], step_twiddle3<V, SIGN>(tw, logn2, p, 3));
+                    v[h][1] = mul_tw(v[h][1], step_twiddle_r<V, SIGN, R>(tw, logn2, p, 1));
+                    v[h][2] = mul_tw(v[h][2], step_twiddle_r<V, SIGN, R>(tw, logn2, p, 2));
+                    v[h][3] = mul_tw(v[h][3], step_twiddle_r<V, SIGN, R>(tw, logn2, p, 3));
                 }
                 base[h] = line * pitch + q + s * 4 * p;
                 pp[h] = s;
@@ -183,19 +217,41 @@ __device__ void block_fft3(SBuf<V> buf, int loga, int nl, int pitch, const TwTab
         logn2 -= 2;
         logs += 2;
     }
-    // radix-3 step: n = 3, s = 2^loga; each thread owns its three elements
-    const auto w3 = imag_only<V>(get_twiddle<V, SIGN, 3>(tw, 1u << tw.log_n));   // omega_3^SIGN
-    const int third = 1 << loga;
-    for (int b = threadIdx.x; b < nl * third; b += blockDim.x) {
-        const int line = b >> loga, q = b & (third - 1);
-        const int x = line * pitch + q;
-        const V x0 = buf[x], x1 = buf[x + third], x2 = buf[x + 2 * third];
-        const V S = x1 + x2, D = x1 - x2;
-        const V T = x0 - scale_pow2(S, 1);
-        const V U = mul_tw(D, w3);
-        buf[x] = x0 + S;
-        buf[x + third] = T + U;
-        buf[x + 2 * third] = T - U;
+    // radix-R step: n = R, s = 2^loga; each thread owns its R elements
+    const int part = 1 << loga;
+    if (R == 3) {
+        const auto w3 = ScalarTw<V, SIGN, R>::get(tw, 1u << tw.log_n, true);   // i Im omega_3^SIGN
+        for (int b = threadIdx.x; b < nl * part; b += blockDim.x) {
+            const int x = (b >> loga) * pitch + (b & (part - 1));
+            const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];
+            const V S = x1 + x2, D = x1 - x2;
+            const V T = x0 - scale_pow2(S, 1);
+            const V U = mul_tw(D, w3);
+            buf[x] = x0 + S;
+            buf[x + part] = T + U;
+            buf[x + 2 * part] = T - U;
+        }
+    } else {
+        // omega_5^(SIGN k) = c_k + i s_k, k = 1, 2
+        const auto c1 = ScalarTw<V, SIGN, R>::get(tw, 1u << tw.log_n, false);
+        const auto c2 = ScalarTw<V, SIGN, R>::get(tw, 2u << tw.log_n, false);
+        const auto s1 = ScalarTw<V, SIGN, R>::get(tw, 1u << tw.log_n, true);
+        const auto s2 = ScalarTw<V, SIGN, R>::get(tw, 2u << tw.log_n, true);
+        for (int b = threadIdx.x; b < nl * part; b += blockDim.x) {
+            const int x = (b >> loga) * pitch + (b & (part - 1));
+            const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];
+            const V x3 = buf[x + 3 * part], x4 = buf[x + 4 * part];
+            const V S1 = x1 + x4, D1 = x1 - x4, S2 = x2 + x3, D2 = x2 - x3;
+            const V A = (x0 + mul_tw(S1, c1)) + mul_tw(S2, c2);
+            const V B = (x0 + mul_tw(S1, c2)) + mul_tw(S2, c1);
+            const V U = mul_tw(D1, s1) + mul_tw(D2, s2);
+            const V W = mul_tw(D1, s2) - mul_tw(D2, s1);
+            buf[x] = (x0 + S1) + S2;
+            buf[x + part] = A + U;
+            buf[x + 4 * part] = A - U;
+            buf[x + 2 * part] = B + W;
+            buf[x + 3 * part] = B - W;
+        }
     }
     __syncthreads();
 }

@@ -44,12 +44,16 @@ constexpr int CARRY_TILE = 4096;       // digits per carry CTA
 constexpr int CARRY_THREADS = 256;
 constexpr int CARRY_PER_THREAD = CARRY_TILE / CARRY_THREADS;
 constexpr uint32_t SPIN_LIMIT = 1u << 20;   // bounded look-back polls (about a second)
-// Transform length codes: c < LEN3 means N = 2^c; c >= LEN3 means
-// N = 3 2^(c - LEN3) (four-step only, LOG3_MIN <= c - LEN3 <= LOG3_MAX:
-// column length 3 2^a with a even and a <= 10, rows 2^b with 2 <= b <= 11).
+// Transform length codes: c < LEN3 means N = 2^c; LEN3 <= c < LEN5 means
+// N = 3 2^(c - LEN3); c >= LEN5 means N = 5 2^(c - LEN5).  The odd lengths
+// are four-step only: columns R 2^a with a even and R 2^a <= 4096, rows 2^b
+// with 2 <= b <= 11.
 constexpr int LEN3 = 32;
+constexpr int LEN5 = 64;
 constexpr int LOG3_MIN = 11;           // 6144 = 3 2^11 > 4096, the single-CTA limit
 constexpr int LOG3_MAX = 21;           // 3 2^10 columns x 2^11 rows
+constexpr int LOG5_MIN = 10;           // 5120 = 5 2^10
+constexpr int LOG5_MAX = 19;           // 5 2^8 columns x 2^11 rows
 
 // Per-product accumulators of one call, zeroed before the call; one entry
 // per rung (value.cuh: 0 binary32 rectangles, 1 binary64 rectangles,
@@ -70,7 +74,7 @@ struct ProdDesc {
     const uint8_t* b;
     uint8_t* z;
     uint32_t na, nb;
-    int32_t log_n;                     // length code: N = 2^log_n, or 3 2^(log_n - LEN3)
+    int32_t log_n;                     // length code (see LEN3)
     int32_t balanced;                  // digits enter the transform as x_j - 128
     void* Z;                           // four-step workspace, N intervals
     void* W;                           // four-step workspace, N/2 intervals
@@ -245,9 +249,17 @@ struct IsoAcc {
     unsigned int maxw_f32 = 0;          // the same for widths held in binary32
 };
 
-// Integer division by 3 rounded up / down (exact, no overflow).
-__device__ __forceinline__ long long ceil_div3(long long x) { return x / 3 + (x % 3 > 0 ? 1 : 0); }
-__device__ __forceinline__ long long floor_div3(long long x) { return x / 3 - (x % 3 < 0 ? 1 : 0); }
+// Integer division by R rounded up / down (exact, no overflow).
+template <int R>
+__device__ __forceinline__ long long ceil_div(long long x) { return x / R + (x % R > 0 ? 1 : 0); }
+template <int R>
+__device__ __forceinline__ long long floor_div(long long x) { return x / R - (x % R < 0 ? 1 : 0); }
+
+// RU(1/R) for R = 1, 3, 5 (bit patterns: 1, the successor of RN(1/3), RN(1/5) > 1/5)
+template <int R>
+__device__ __forceinline__ double inv_up() {
+    return R == 1 ? 1.0 : __longlong_as_double(R == 3 ? 0x3FD5555555555556ll : 0x3FC999999999999All);
+}
 
 // Decide coefficient idx from the enclosure [lo, hi] of c_idx (of c'_idx
 // with balanced digits, corrected here to c_idx); L = na + nb - 1.  The
@@ -258,9 +270,9 @@ __device__ __forceinline__ long long floor_div3(long long x) { return x / 3 - (x
 // never accepted.  The exact coefficient is a nonnegative integer: an
 // isolated negative value is a containment failure like an empty set.
 //
-// R = 3 (transform length 3 2^k): [lo, hi] encloses 3 c_idx (the 1/N
-// scaling applied only its power of two).  The integers of [lo/3, hi/3] are
-// those of [ceil(kl'/3), floor(kh'/3)] with kl' = ceil(lo), kh' = floor(hi),
+// R = 3 or 5 (transform length R 2^k): [lo, hi] encloses R c_idx (the 1/N
+// scaling applied only its power of two).  The integers of [lo/R, hi/R] are
+// those of [ceil(kl'/R), floor(kh'/R)] with kl' = ceil(lo), kh' = floor(hi),
 // so the same decision takes two exact integer divisions and no rounding.
 template <int R = 1, typename T>
 __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdDesc& d,
@@ -268,23 +280,23 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
     const int64_t L = int64_t(d.na) + d.nb - 1;
     double dl = double(lo), dh = double(hi);          // exact widening
     if (d.fault_widen == rung + 1) {                  // test fault: still an enclosure
-        dl = __dsub_rd(dl, 4.0);
-        dh = __dadd_ru(dh, 4.0);
+        dl = __dsub_rd(dl, 4.0 * R);                  // 4 in units of c (the set is of R c)
+        dh = __dadd_ru(dh, 4.0 * R);
     }
     const unsigned long long wb = (unsigned long long)__double_as_longlong(__dsub_ru(dh, dl));
     acc.maxw_bits = wb > acc.maxw_bits ? wb : acc.maxw_bits;   // widths are >= 0 (or NaN)
     long long kl = __double2ll_ru(dl);
     long long kh = __double2ll_rd(dh);
-    if (R == 3) {
-        kl = ceil_div3(kl);
-        kh = floor_div3(kh);
+    if (R != 1) {
+        kl = ceil_div<R>(kl);
+        kh = floor_div<R>(kh);
     }
     constexpr long long KMAX = 1ll << 53;
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
         if (d.iv != nullptr) {
-            d.iv[2 * idx] = __dadd_rd(R == 3 ? __ddiv_rd(dl, 3.0) : dl, double(corr));
-            d.iv[2 * idx + 1] = __dadd_ru(R == 3 ? __ddiv_ru(dh, 3.0) : dh, double(corr));
+            d.iv[2 * idx] = __dadd_rd(R != 1 ? __ddiv_rd(dl, double(R)) : dl, double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(R != 1 ? __ddiv_ru(dh, double(R)) : dh, double(corr));
         }
         int64_t v = 0;
         if (kl == kh && kl > -KMAX && kl < KMAX && kl + corr >= 0) {
@@ -300,7 +312,7 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
     }
 }
 
-// R = 3: the widths were those of 3 c; the largest is scaled by 1/3 rounded up
+// R = 3, 5: the widths were those of R c; the largest is scaled by RU(1/R)
 template <int R = 1>
 __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
     if (acc.maxw_f32) {
@@ -309,9 +321,9 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
             (unsigned long long)__double_as_longlong(double(__uint_as_float(acc.maxw_f32)));
         acc.maxw_bits = w > acc.maxw_bits ? w : acc.maxw_bits;
     }
-    if (R == 3 && acc.maxw_bits)     // 0x3FD5555555555556 = RU(1/3)
+    if (R != 1 && acc.maxw_bits)
         acc.maxw_bits = (unsigned long long)__double_as_longlong(
-            __dmul_ru(__longlong_as_double((long long)acc.maxw_bits), __longlong_as_double(0x3FD5555555555556ll)));
+            __dmul_ru(__longlong_as_double((long long)acc.maxw_bits), inv_up<R>()));
     for (int o = 16; o > 0; o >>= 1) {
         acc.unisolated += __shfl_xor_sync(0xffffffffu, acc.unisolated, o);
         acc.empty += __shfl_xor_sync(0xffffffffu, acc.empty, o);
@@ -372,13 +384,13 @@ __device__ __forceinline__ long long int_of_f32(float x) {
 // Beyond that r > 2^21 (the set holds many integers) unless a part is NaN
 // or infinite (no integer: empty); a centre with |h| >= 2^53 cannot hold a
 // coefficient (they are below 2^53) and is empty unless it is wide.
-// R = 3: the set encloses 3 c (see isolate_one); the integer bounds are
-// divided by 3 exactly.
+// R = 3, 5: the set encloses R c (see isolate_one); the integer bounds are
+// divided by R exactly.
 template <int R = 1>
 __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t idx,
                                              const ProdDesc& d, IsoAcc& acc, int rung) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
-    if (d.fault_widen == rung + 1) r = __fadd_ru(r, 4.f);     // test fault: still an enclosure
+    if (d.fault_widen == rung + 1) r = __fadd_ru(r, 4.f * R); // test fault: 4 in units of c
     const float k0 = rint_f32(h), k1 = rint_f32(l);
     const float t = __fsub_rn(h, k0), t2 = __fsub_rn(l, k1);
     const float lo = __fsub_rd(__fadd_rd(t, t2), r);
@@ -394,9 +406,9 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
     const int fh = __float_as_int(__fadd_rd(hi, M)) - __float_as_int(M);
     const long long K = big ? 0ll : int_of_f32(k0) + int_of_f32(k1);
     long long kl = K + cl, kh = K + fh;
-    if (R == 3) {
-        kl = ceil_div3(kl);
-        kh = floor_div3(kh);
+    if (R != 1) {
+        kl = ceil_div<R>(kl);
+        kh = floor_div<R>(kh);
     }
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
@@ -405,8 +417,8 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
             const double dr = double(r);
             const double dl = __dsub_rd(__dadd_rd(double(h), double(l)), dr);
             const double dh = __dadd_ru(__dadd_ru(double(h), double(l)), dr);
-            d.iv[2 * idx] = __dadd_rd(R == 3 ? __ddiv_rd(dl, 3.0) : dl, double(corr));
-            d.iv[2 * idx + 1] = __dadd_ru(R == 3 ? __ddiv_ru(dh, 3.0) : dh, double(corr));
+            d.iv[2 * idx] = __dadd_rd(R != 1 ? __ddiv_rd(dl, double(R)) : dl, double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(R != 1 ? __ddiv_ru(dh, double(R)) : dh, double(corr));
         }
         int64_t v = 0;
         if (bad) {
@@ -438,15 +450,15 @@ __device__ __forceinline__ void isolate_value(const DDisc& v, int64_t j, const P
 }
 
 // the naive transform rounds to the nearest integer without any proof; its
-// "width" statistic is the largest distance to that integer (R = 3: v
-// approximates 3 c; the distance is kept for 3 c like the enclosures' widths)
+// "width" statistic is the largest distance to that integer (R = 3, 5: v
+// approximates R c; the distance is kept for R c like the enclosures' widths)
 template <int R = 1>
 __device__ __forceinline__ void naive_one(double v, int64_t idx, const ProdDesc& d,
                                           IsoAcc& acc) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
-    const double vv = R == 3 ? v * (1.0 / 3.0) : v;
+    const double vv = R != 1 ? v * (1.0 / R) : v;
     const double k = rint(vv);
-    const double dist = fabs(v - (R == 3 ? 3.0 * k : k));
+    const double dist = fabs(v - double(R) * k);
     const unsigned long long db = (unsigned long long)__double_as_longlong(dist);
     acc.maxw_bits = db > acc.maxw_bits ? db : acc.maxw_bits;
     if (idx < L) {
@@ -523,7 +535,7 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
 
 // ---- four-step kernels --------------------------------------------------------
 
-// R: 1 for N = 2^k, 3 for N = 3 2^k; N1 = R 2^logN1 (logN1 even when R = 3),
+// R: 1, 3 or 5 for N = R 2^k; N1 = R 2^logN1 (logN1 even when R > 1),
 // N2 = 2^logN2, and tw is the twiddle table of family R.
 template <typename Tag, int BPT = 2, int R = 1>
 __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
@@ -547,8 +559,8 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_
             sm[(idx & (C - 1)) * N1 + (idx >> logC)] = make_point<V>(v.x, v.y);
         });
     __syncthreads();
-    if (R == 1) block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
-    else block_fft3<V, +1, BPT>(sm, logN1, C, N1, tw);
+    if constexpr (R == 1) block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
+    else block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
     for (int idx = threadIdx.x; idx < C * N1; idx += blockDim.x) {
         const int c = idx & (C - 1), k1 = idx >> logC;
@@ -613,14 +625,14 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_
         [&](int idx) { return W[(size_t(idx >> logC) << logM2) + j2_0 + (idx & (C - 1))]; },
         [&](int idx, const V& v) { sm[(idx & (C - 1)) * N1 + (idx >> logC)] = v; });
     __syncthreads();
-    if (R == 1) block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
-    else block_fft3<V, -1, BPT>(sm, logN1, C, N1, tw);
+    if constexpr (R == 1) block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
+    else block_fft_odd<V, -1, BPT, R>(sm, logN1, C, N1, tw);
     const int logN = logN1 + logN2;
     IsoAcc acc;
     for (int idx = threadIdx.x; idx < C * N1; idx += blockDim.x) {
         const int c = idx & (C - 1), j1 = idx >> logC;
         const int64_t j = (int64_t(j1) << logM2) + j2_0 + c;
-        // 1 / (4 N) up to the factor 1/3 of R = 3, which the isolation applies exactly
+        // 1 / (4 N) up to the factor 1/R, which the isolation applies exactly
         isolate_value<R>(scale_pow2(sm[c * N1 + j1], logN + 2), j, d, acc);
     }
     flush_acc<R>(acc, d.st, RUNG);
@@ -892,10 +904,10 @@ __global__ void k_finalize(const ProdDesc* descs) {
         ssmul_result r;
         r.status = status;
         r.precision_used = rung_precision(rung);
-        r.fft_log2 = uint32_t(d.log_n >= LEN3 ? d.log_n - LEN3 : d.log_n);
+        r.fft_log2 = uint32_t(d.log_n % LEN3);
         r.n_unisolated = d.st->unisolated[rung];
         r.n_empty = d.st->empty[rung];
-        r.fft_times3 = d.log_n >= LEN3 ? 1u : 0u;
+        r.fft_odd = d.log_n >= LEN5 ? 5u : (d.log_n >= LEN3 ? 3u : 1u);
         r.max_width = __longlong_as_double((long long)d.st->maxw[rung]);
         *d.res = r;
         s_status = status;

@@ -3,8 +3,8 @@
 // The DFT of Section 2.2 uses omega = e^{2 pi i / N}; its inverse uses
 // omega^-1.  The plan builds, once, tables of enclosures of
 // cos(2 pi j / Ntab) and sin(2 pi j / Ntab) for the first octant
-// j = 0 .. Ntab/8, for two families of lengths: Ntab = 2^K (R = 1) and
-// Ntab = 3 2^K (R = 3).  Every power of a root omega_N with N dividing
+// j = 0 .. Ntab/8, for up to three families of lengths Ntab = R 2^K with
+// R = 1, 3 or 5.  Every power of a root omega_N with N dividing
 // Ntab is read from the table through exact symmetries of the circle
 // (reflection about pi/4 swaps cos and sin; a quarter turn maps (c, s) to
 // (-s, c); the inverse root conjugates).  These hold for every Ntab that
@@ -16,10 +16,10 @@
 //   R = 1: x is exact (Ntab is a power of two); each value is widened
 //          outward by TW_WIDEN_ULPS = 4 steps of nextafter (the bound plus
 //          margin for the change of ulp size at a power of two).
-//   R = 3: when 3 divides j the argument (2 j / 3) 2^-K is exact and the
-//          widening is TW_WIDEN_ULPS.  Otherwise x = q 2^-K with
-//          q = RN(2 j / 3); the remainder 2 j - 3 q is exact (one fma), so
-//          the true argument is x + d with d = ((2 j - 3 q) / 3) 2^-K,
+//   R = 3, 5: when R divides j the argument (2 j / R) 2^-K is exact and
+//          the widening is TW_WIDEN_ULPS.  Otherwise x = q 2^-K with
+//          q = RN(2 j / R); the remainder 2 j - R q is exact (one fma), so
+//          the true argument is x + d with d = ((2 j - R q) / R) 2^-K,
 //          |d| <= 2^-53 x.  The values at x + d are those at x corrected to
 //          first order, s + pi d c and c - pi d s, each with one rounding
 //          (1/2 ulp); the second-order term (pi d)^2 / 2 < 2^-104 and the
@@ -51,10 +51,10 @@ struct DDiscC;
 // omega_n^{u p} for p < n/4 and u = 1, 2, 3; a step table holds that value
 // of the forward transform at [(u - 1) STEP_TAB + n/4 + p], so the lanes
 // of a warp, which work on consecutive p, read consecutive entries.  One
-// set of tables serves n = 2^j (8 <= n <= 2^LOG_STEP_MAX), another
-// n = 3 2^j (12 <= n <= 3 2^10); in both the ranges [n/4, n/2) of
-// successive n are disjoint.  The entries are copies of the octant tables'
-// values (moved by the same exact symmetries).
+// set of tables serves n = 2^j (8 <= n <= 2^LOG_STEP_MAX), another, in a
+// table of family R = 3 or 5, n = R 2^j (4 R <= n <= 4096); in both the
+// ranges [n/4, n/2) of successive n are disjoint.  The entries are copies
+// of the octant tables' values (moved by the same exact symmetries).
 constexpr int LOG_STEP_MAX = 12;
 constexpr int STEP_TAB = 1 << (LOG_STEP_MAX - 1);
 
@@ -71,11 +71,11 @@ struct TwTable {
     const CI<float>* s32;
     const DiscTw* sd;
     const DDiscC* sdd;
-    // the same for n = 3 2^j (set in a table of the R = 3 family)
-    const CI<double>* s64_3;
-    const CI<float>* s32_3;
-    const DiscTw* sd_3;
-    const DDiscC* sdd_3;
+    // the same for n = R 2^j (set in a table of family R = 3 or 5)
+    const CI<double>* s64_r;
+    const CI<float>* s32_r;
+    const DiscTw* sd_r;
+    const DDiscC* sdd_r;
 };
 
 __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n, int R) {
@@ -87,15 +87,15 @@ __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log
         if (j == 0) {
             e = {1.0, 1.0, 0.0, 0.0};
         } else {
-            // 2 j / ntab: exact for R = 1 and for j divisible by 3
-            const bool exact = R == 1 || j % 3 == 0;
-            const double q = R == 1 ? double(2 * j) : __ddiv_rn(double(2 * j), 3.0);
+            // 2 j / ntab: exact for R = 1 and for j divisible by R
+            const bool exact = R == 1 || j % R == 0;
+            const double q = R == 1 ? double(2 * j) : __ddiv_rn(double(2 * j), double(R));
             const double x = ldexp(q, -log_n);
             double s, c;
             sincospi(x, &s, &c);
             if (!exact) {
-                const double rem = __fma_rn(-3.0, q, double(2 * j));          // exact
-                const double pd = __dmul_rn(3.141592653589793, ldexp(__ddiv_rn(rem, 3.0), -log_n));
+                const double rem = __fma_rn(-double(R), q, double(2 * j));    // exact
+                const double pd = __dmul_rn(3.141592653589793, ldexp(__ddiv_rn(rem, double(R)), -log_n));
                 const double s0 = s;
                 s = __fma_rn(pd, c, s);
                 c = __fma_rn(-pd, s0, c);
@@ -132,7 +132,7 @@ __global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscTw* td, float* rho
         const double ec = fmax(__dsub_ru(c, e.cl), __dsub_ru(e.ch, c));
         const double es = fmax(__dsub_ru(s, e.sl), __dsub_ru(e.sh, s));
         const float r = __double2float_ru(__dadd_ru(ec, es));
-        td[j] = {c, s, r, 0.f};
+        td[j] = {c, s, r, TW_MOD_UP};
         atomicMax(reinterpret_cast<int*>(rho), __float_as_int(r));
     }
 }
@@ -154,7 +154,7 @@ __device__ __forceinline__ TwPos tw_pos(int ln, uint32_t j) {
         j &= (1u << ln) - 1u;
         quad = j >> (ln - 2);
     } else {
-        quad = (j >> (ln - 2)) / 3u;                  // floor(j / q)
+        quad = (j >> (ln - 2)) / uint32_t(R);          // floor(j / q)
     }
     const uint32_t r = j - quad * q;
     const bool refl = r > (q >> 1);
@@ -172,7 +172,7 @@ __device__ __forceinline__ DiscTw twiddle_disc(const TwTable& tw, uint32_t j) {
     const double wc = swap ? s : c, ws = swap ? c : s;
     const bool negr = ps.quad == 1u || ps.quad == 2u;
     const bool negi = (ps.quad >= 2u) != (SIGN < 0);
-    return {negr ? flip(wc) : wc, negi ? flip(ws) : ws, e.rho, 0.f};
+    return {negr ? flip(wc) : wc, negi ? flip(ws) : ws, e.rho, e.mod};
 }
 
 template <typename T>

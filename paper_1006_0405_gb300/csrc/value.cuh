@@ -102,7 +102,7 @@ __device__ __forceinline__ DDiscTw twiddle_ddisc(const TwTable& tw, uint32_t j) 
     const bool negr = ps.quad == 1u || ps.quad == 2u;
     const bool negi = (ps.quad >= 2u) != (SIGN < 0);
     return {negr ? flip(wch) : wch, negr ? flip(wcl) : wcl, negi ? flip(wsh) : wsh,
-            negi ? flip(wsl) : wsl, tw.rho_dd, 0.f};
+            negi ? flip(wsl) : wsl, tw.rho_dd, TW_MOD_UP};
 }
 template <int SIGN, int R> struct TwOf<DDisc, SIGN, R> {
     static __device__ __forceinline__ DDiscTw get(const TwTable& tw, uint32_t j) {
@@ -124,9 +124,9 @@ __device__ __forceinline__ typename VTraits<V>::Tw get_twiddle(const TwTable& tw
 
 __device__ __forceinline__ CI<double> tw_conj(const CI<double>& w) { return conj_flip(w); }
 __device__ __forceinline__ CI<float> tw_conj(const CI<float>& w) { return conj_flip(w); }
-__device__ __forceinline__ DiscTw tw_conj(const DiscTw& w) { return {w.c, flip(w.s), w.rho, 0.f}; }
+__device__ __forceinline__ DiscTw tw_conj(const DiscTw& w) { return {w.c, flip(w.s), w.rho, w.mod}; }
 __device__ __forceinline__ DDiscTw tw_conj(const DDiscTw& w) {
-    return {w.ch, w.cl, flip(w.sh), flip(w.sl), w.rho, 0.f};
+    return {w.ch, w.cl, flip(w.sh), flip(w.sl), w.rho, w.mod};
 }
 
 // table(tw, three): the step table of V for n = 2^j (three = false) or
@@ -134,7 +134,7 @@ __device__ __forceinline__ DDiscTw tw_conj(const DDiscTw& w) {
 template <typename V> struct StepOf;
 template <> struct StepOf<CI<double>> {
     static __device__ __forceinline__ const CI<double>* table(const TwTable& tw, bool three) {
-        return three ? tw.s64_3 : tw.s64;
+        return three ? tw.s64_r : tw.s64;
     }
     static __device__ __forceinline__ CI<double> load(const CI<double>* t, int i, const TwTable&) {
         return t[i];
@@ -142,7 +142,7 @@ template <> struct StepOf<CI<double>> {
 };
 template <> struct StepOf<CI<float>> {
     static __device__ __forceinline__ const CI<float>* table(const TwTable& tw, bool three) {
-        return three ? tw.s32_3 : tw.s32;
+        return three ? tw.s32_r : tw.s32;
     }
     static __device__ __forceinline__ CI<float> load(const CI<float>* t, int i, const TwTable&) {
         return t[i];
@@ -150,7 +150,7 @@ template <> struct StepOf<CI<float>> {
 };
 template <> struct StepOf<Disc> {
     static __device__ __forceinline__ const DiscTw* table(const TwTable& tw, bool three) {
-        return three ? tw.sd_3 : tw.sd;
+        return three ? tw.sd_r : tw.sd;
     }
     static __device__ __forceinline__ DiscTw load(const DiscTw* t, int i, const TwTable&) {
         return t[i];
@@ -159,11 +159,11 @@ template <> struct StepOf<Disc> {
 template <> struct StepOf<Pt> : StepOf<Disc> {};
 template <> struct StepOf<DDisc> {
     static __device__ __forceinline__ const DDiscC* table(const TwTable& tw, bool three) {
-        return three ? tw.sdd_3 : tw.sdd;
+        return three ? tw.sdd_r : tw.sdd;
     }
     static __device__ __forceinline__ DDiscTw load(const DDiscC* t, int i, const TwTable& tw) {
         const DDiscC e = t[i];
-        return {e.ch, e.cl, e.sh, e.sl, tw.rho_dd, 0.f};
+        return {e.ch, e.cl, e.sh, e.sl, tw.rho_dd, TW_MOD_UP};
     }
 };
 
@@ -178,20 +178,20 @@ __device__ __forceinline__ typename VTraits<V>::Tw step_twiddle(const TwTable& t
     return SIGN > 0 ? w : tw_conj(w);
 }
 
-// n = 3 2^logn2, the table of family 3
-template <typename V, int SIGN>
-__device__ __forceinline__ typename VTraits<V>::Tw step_twiddle3(const TwTable& tw, int logn2, int p,
-                                                                 int u) {
+// n = R 2^logn2 (R = 3 or 5), the table of family R
+template <typename V, int SIGN, int R>
+__device__ __forceinline__ typename VTraits<V>::Tw step_twiddle_r(const TwTable& tw, int logn2, int p,
+                                                                  int u) {
     const auto* t = StepOf<V>::table(tw, true);
     if (t == nullptr)        // Ntab / n = 2^(log_n - logn2)
-        return get_twiddle<V, SIGN, 3>(tw, uint32_t(u * p) << (tw.log_n - logn2));
-    const auto w = StepOf<V>::load(t, (u - 1) * STEP_TAB + (3 << (logn2 - 2)) + p, tw);
+        return get_twiddle<V, SIGN, R>(tw, uint32_t(u * p) << (tw.log_n - logn2));
+    const auto w = StepOf<V>::load(t, (u - 1) * STEP_TAB + (R << (logn2 - 2)) + p, tw);
     return SIGN > 0 ? w : tw_conj(w);
 }
 
 // Fills step tables from the octant tables of family R (the pair-disc step
 // table holds centres: its radius is the table's).  R = 1: the tables for
-// n = 2^j; R = 3: those for n = 3 2^j.
+// n = 2^j; R = 3, 5: those for n = R 2^j (n <= 4096).
 template <int R>
 __global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscTw* sd,
                               DDiscC* sdd) {
@@ -201,7 +201,7 @@ __global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscT
         // n/4 = R 2^lq <= pos < R 2^(lq+1)
         const int lq = pos < R ? -1 : 31 - __clz(pos / R);
         const int logn = lq + 2;                                // n = R 2^logn
-        if (lq < (R == 1 ? 1 : 0) || logn > tw.log_n || (R == 3 && logn > 10)) {
+        if (lq < (R == 1 ? 1 : 0) || logn > tw.log_n || (R > 1 && (R << logn) > 4096)) {
             s64[i] = {};
             s32[i] = {};
             sd[i] = {};

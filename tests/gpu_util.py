@@ -46,13 +46,14 @@ class Plan:
         iv = div.cpu().numpy().reshape(L, 2)
         return s, r, dz.cpu().numpy(), iv[:, 0], iv[:, 1]
 
-    def twiddles(self, f32=False, log_max=24, three=False):
-        """(K, cos_lo, cos_hi, sin_lo, sin_hi) of the table Ntab = 2^K (or 3 2^K)."""
+    def twiddles(self, f32=False, log_max=24, odd=1):
+        """(K, cos_lo, cos_hi, sin_lo, sin_hi) of the table Ntab = odd * 2^K (odd 1, 3 or 5)."""
         cap = 4 * ((1 << log_max) // 8 + 1)
         buf = np.zeros(cap, np.float64)
-        s, ln = abi.ssmul_debug_twiddles(self.h, int(f32) | (2 if three else 0), buf.ctypes.data, cap)
+        flags = int(f32) | {1: 0, 3: 2, 5: 4}[odd]
+        s, ln = abi.ssmul_debug_twiddles(self.h, flags, buf.ctypes.data, cap)
         assert s == abi.SSMUL_OK
-        m = ((3 if three else 1) << ln) // 8 + 1
+        m = (odd << ln) // 8 + 1
         t = buf[:4 * m].reshape(m, 4)
         return ln, t[:, 0], t[:, 1], t[:, 2], t[:, 3]
 

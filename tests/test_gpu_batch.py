@@ -96,13 +96,16 @@ def test_autotuned_geometry_is_exact(tmp_path):
                 s, r, z = p.mul(a, b)
                 assert s == OK and np.array_equal(z, E.product(a, b))
         lines = open(tmp_path / "tune.txt").read().splitlines()
-        assert len(lines) == 10                        # 2^13 .. 2^17 and 3 2^11 .. 3 2^15
+        assert len(lines) == 15                        # 2^13..2^17, 3 2^11..3 2^15, 5 2^10..5 2^14
         with Plan(n, n) as p:                          # read back from the cache
             assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_AUTOTUNE, 1) == OK
-            assert len(open(tmp_path / "tune.txt").read().splitlines()) == 10
+            assert len(open(tmp_path / "tune.txt").read().splitlines()) == 15
             for j in range(11, 16):
                 s, (l1, l2, lc) = abi.ssmul_debug_geometry(p.h, 32 + j)
                 assert s == OK and l1 + l2 == j and l1 % 2 == 0
+            for j in range(10, 15):
+                s, (l1, l2, lc) = abi.ssmul_debug_geometry(p.h, 64 + j)
+                assert s == OK and l1 + l2 == j and l1 % 2 == 0 and (5 << l1) <= 4096
     finally:
         del os.environ["SSMUL_TUNE_CACHE"]
 

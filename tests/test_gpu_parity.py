@@ -180,7 +180,7 @@ def test_paper_scale_75000(dist):
     a, b = _pair(2, 75000, 75000, dist)
     with Plan(75000, 75000) as p:
         s, r, z, lo, hi = p.mul_intervals(a, b, abi.SSMUL_PREC_FP64)
-    assert (r.fft_times3, r.fft_log2) == (1, 16)        # N = 3 2^16 >= 149,999
+    assert (r.fft_odd, r.fft_log2) == (5, 15)           # N = 5 2^15 >= 149,999
     assert s == OK, abi.status_string(s)
     assert np.array_equal(z, E.product(a, b))
     c = E.conv_ntt(a, b).astype(np.float64)

@@ -17,7 +17,7 @@ def test_pi_digits():
     assert abs(pi - PI_60) <= Fr(e + 1, 1 << tw.PREC) + Fr(1, 10 ** 60)
 
 
-@pytest.mark.parametrize("N", [1, 2, 4, 8, 16, 1024, 8192, 24, 96, 3072])
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 16, 1024, 8192, 24, 96, 3072, 40, 640])
 def test_exact_points_and_widths(N):
     c_lo, c_hi, s_lo, s_hi = tw.enclosures(N)
     pts = {0: (1, 0)}
@@ -39,7 +39,7 @@ def test_exact_points_and_widths(N):
             assert np.all(one)
 
 
-@pytest.mark.parametrize("N", [16, 256, 4096, 48, 1536])
+@pytest.mark.parametrize("N", [16, 256, 4096, 48, 1536, 80, 1280])
 def test_pythagoras_and_libm(N):
     c_lo, c_hi, s_lo, s_hi = tw.enclosures(N)
     for j in range(0, N, max(1, N // 512)):
@@ -98,7 +98,7 @@ def test_closed_forms_thirds():
     assert f(Fr(float(c_lo[1]))) <= Fr(3, 4) <= f(Fr(float(c_hi[1])))
 
 
-@pytest.mark.parametrize("N", [96, 3072])
+@pytest.mark.parametrize("N", [96, 3072, 160, 2560])
 def test_double_angle_thirds(N):
     # cos(2t) = 2 cos(t)^2 - 1 between entries j of N and j of N/2 (both 3 2^k)
     c_lo, c_hi, _, _ = tw.enclosures(N)
@@ -112,3 +112,14 @@ def test_double_angle_thirds(N):
 def test_rejects_lengths_without_octant_symmetry():
     with pytest.raises(ValueError):
         tw.octant_table(12)
+
+
+def test_closed_forms_fifths():
+    # lengths 5 2^k: cos(2 pi / 5) = (sqrt 5 - 1)/4 is the root of 4c^2 + 2c - 1
+    # (increasing for c > -1/4); cos(pi / 5) = (sqrt 5 + 1)/4 that of 4c^2 - 2c - 1
+    # (increasing for c > 1/4) (N = 40, j = 8 and j = 4)
+    c_lo, c_hi, _, _ = tw.enclosures(40)
+    f = lambda c: 4 * c * c + 2 * c - 1
+    assert f(Fr(float(c_lo[8]))) <= 0 <= f(Fr(float(c_hi[8])))
+    g = lambda c: 4 * c * c - 2 * c - 1
+    assert g(Fr(float(c_lo[4]))) <= 0 <= g(Fr(float(c_hi[4])))
