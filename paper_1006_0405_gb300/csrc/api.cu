@@ -217,6 +217,7 @@ struct TwFamily {
     CI<float>* s32 = nullptr;
     DiscTw* sd = nullptr;
     DDiscC* sdd = nullptr;
+    ScalarSet* scal = nullptr;          // radix-3 / radix-5 scalars (R > 1)
     size_t entries() const { return log_tab ? (size_t(R) << log_tab) / 8 + 1 : 0; }
 };
 
@@ -285,7 +286,8 @@ struct ssmul_plan_s {
                        st ? P.s64 : nullptr, st ? P.s32 : nullptr, st ? P.sd : nullptr,
                        st ? P.sdd : nullptr,
                        st && f ? F.s64 : nullptr, st && f ? F.s32 : nullptr,
-                       st && f ? F.sd : nullptr, st && f ? F.sdd : nullptr};
+                       st && f ? F.sd : nullptr, st && f ? F.sdd : nullptr,
+                       f ? F.scal : nullptr};
     }
 };
 
@@ -1011,6 +1013,7 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
         cudaFree(F.s32);
         cudaFree(F.sd);
         cudaFree(F.sdd);
+        cudaFree(F.scal);
     }
     cudaFree(p->rho);
     cudaFree(p->Z);
@@ -1090,6 +1093,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
         if (e == cudaSuccess) e = cudaMalloc(&F.s32, 3 * STEP_TAB * sizeof(CI<float>));
         if (e == cudaSuccess) e = cudaMalloc(&F.sd, 3 * STEP_TAB * sizeof(DiscTw));
         if (e == cudaSuccess) e = cudaMalloc(&F.sdd, 3 * STEP_TAB * sizeof(DDiscC));
+        if (F.R > 1 && e == cudaSuccess) e = cudaMalloc(&F.scal, sizeof(ScalarSet));
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
@@ -1151,6 +1155,8 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
         if (p->fam[2].entries())
             k_step_tw_gen<5><<<sb, threads, 0, p->stream>>>(oct[2], p->fam[2].s64, p->fam[2].s32,
                                                             p->fam[2].sd, p->fam[2].sdd);
+        if (p->fam[1].entries()) k_scalar_gen<3><<<1, 32, 0, p->stream>>>(oct[1], p->fam[1].scal);
+        if (p->fam[2].entries()) k_scalar_gen<5><<<1, 32, 0, p->stream>>>(oct[2], p->fam[2].scal);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_status(e));
     float h_rho[2 * FAMILIES] = {};

@@ -122,54 +122,78 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
 //   y2, y3 = B +- W,  B = x0 + c2 S1 + c1 S2,  W = i (s2 D1 - s1 D2).
 // S/2 is an exact scaling (scale_pow2); the products by the real numbers c_k
 // and the pure imaginary numbers i s_k use enclosures of those numbers alone
-// (ScalarTw), taken from the family-R table's enclosure of omega_R^{SIGN k}.
+// (ScalarSet, computed once per plan from the family-R table).
 // Requires nl * L / 4 <= BPT * blockDim.x, like block_fft.
 
 // The real number cos or the pure imaginary number i sin of the enclosure
-// omega_Ntab^(SIGN j) (family R) in the twiddle type of V, built from the
-// one component of the rectangle table that it needs: a rectangle with the
-// other part the point 0; a disc whose radius bounds that component's
-// error alone (a twiddle disc's radius covers both components).
-template <typename V, int SIGN, int R> struct ScalarTw;
-template <int SIGN, int R> struct ScalarTw<CI<double>, SIGN, R> {
-    static __device__ __forceinline__ CI<double> get(const TwTable& tw, uint32_t j, bool imag) {
-        const CI<double> w = twiddle<double, SIGN, R>(tw, j);
-        return imag ? CI<double>{0.0, 0.0, w.il, w.ih} : CI<double>{w.rl, w.rh, 0.0, 0.0};
-    }
-};
-template <int SIGN, int R> struct ScalarTw<CI<float>, SIGN, R> {
-    static __device__ __forceinline__ CI<float> get(const TwTable& tw, uint32_t j, bool imag) {
-        const CI<float> w = twiddle<float, SIGN, R>(tw, j);
-        return imag ? CI<float>{0.f, 0.f, w.il, w.ih} : CI<float>{w.rl, w.rh, 0.f, 0.f};
-    }
-};
-// centre = RN midpoint of [lo, hi], radius = RU of the larger distance to an end
+// omega_Ntab^j (family R, forward sign) in the twiddle type of V, built
+// from the one component of the rectangle table that it needs: a rectangle
+// with the other part the point 0; a disc whose radius bounds that
+// component's error alone (a twiddle disc's radius covers both components)
+// and whose modulus bound is |centre|.
 __device__ __forceinline__ void mid_rad(double lo, double hi, double& c, float& r) {
     c = __dadd_rn(0.5 * lo, 0.5 * hi);
     r = __double2float_ru(fmax(__dsub_ru(c, lo), __dsub_ru(hi, c)));
 }
-template <int SIGN, int R> struct ScalarTw<Disc, SIGN, R> {
-    static __device__ __forceinline__ DiscTw get(const TwTable& tw, uint32_t j, bool imag) {
-        const CI<double> w = twiddle<double, SIGN, R>(tw, j);
-        double c;
-        float r;
-        mid_rad(imag ? w.il : w.rl, imag ? w.ih : w.rh, c, r);
-        const float m = abs_up(c);                      // |centre| (a scalar's modulus)
-        return imag ? DiscTw{0.0, c, r, m} : DiscTw{c, 0.0, r, m};
+
+template <int R>
+__device__ void scalar_entry(const TwTable& tw, uint32_t j, bool imag, int k, ScalarSet& out) {
+    const CI<double> w = twiddle<double, 1, R>(tw, j);
+    const CI<float> f = twiddle<float, 1, R>(tw, j);
+    out.d[k] = imag ? CI<double>{0.0, 0.0, w.il, w.ih} : CI<double>{w.rl, w.rh, 0.0, 0.0};
+    out.f[k] = imag ? CI<float>{0.f, 0.f, f.il, f.ih} : CI<float>{f.rl, f.rh, 0.f, 0.f};
+    double c;
+    float r;
+    mid_rad(imag ? w.il : w.rl, imag ? w.ih : w.rh, c, r);
+    const float m = abs_up(c);
+    out.disc[k] = imag ? DiscTw{0.0, c, r, m} : DiscTw{c, 0.0, r, m};
+    // the binary64 centre split into a pair as in k_ddisc_tw_gen (|c| <= 1)
+    const float h = __double2float_rn(c), l = __double2float_rn(c - double(h));
+    const float rr = __fadd_ru(r, 2.f * DD_U2 + DD_ETA);
+    const float mm = dd_mod_up(h, 0.f);
+    out.dd[k] = imag ? DDiscTw{0.f, 0.f, h, l, rr, mm} : DDiscTw{h, l, 0.f, 0.f, rr, mm};
+}
+
+// R = 3: [0] = i sin(2 pi/3).  R = 5: [0] = cos(2 pi/5), [1] = cos(4 pi/5),
+// [2] = i sin(2 pi/5), [3] = i sin(4 pi/5).  Written by one thread.
+template <int R>
+__global__ void k_scalar_gen(TwTable tw, ScalarSet* out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    ScalarSet s{};
+    const uint32_t third = 1u << tw.log_n;                   // Ntab / R
+    if (R == 3) {
+        scalar_entry<R>(tw, third, true, 0, s);
+    } else {
+        scalar_entry<R>(tw, third, false, 0, s);
+        scalar_entry<R>(tw, 2u * third, false, 1, s);
+        scalar_entry<R>(tw, third, true, 2, s);
+        scalar_entry<R>(tw, 2u * third, true, 3, s);
     }
+    *out = s;
+}
+
+template <typename V> struct ScalarOf;
+template <> struct ScalarOf<CI<double>> {
+    static __device__ __forceinline__ CI<double> get(const ScalarSet* s, int k) { return s->d[k]; }
 };
-template <int SIGN, int R> struct ScalarTw<Pt, SIGN, R> : ScalarTw<Disc, SIGN, R> {};
-// the binary64 centre split into a pair as in k_ddisc_tw_gen (|c| <= 1)
-template <int SIGN, int R> struct ScalarTw<DDisc, SIGN, R> {
-    static __device__ __forceinline__ DDiscTw get(const TwTable& tw, uint32_t j, bool imag) {
-        const DiscTw d = ScalarTw<Disc, SIGN, R>::get(tw, j, imag);
-        const double c = imag ? d.s : d.c;
-        const float h = __double2float_rn(c), l = __double2float_rn(c - double(h));
-        const float r = __fadd_ru(d.rho, 2.f * DD_U2 + DD_ETA);
-        const float m = dd_mod_up(h, 0.f);              // >= |h + l|
-        return imag ? DDiscTw{0.f, 0.f, h, l, r, m} : DDiscTw{h, l, 0.f, 0.f, r, m};
-    }
+template <> struct ScalarOf<CI<float>> {
+    static __device__ __forceinline__ CI<float> get(const ScalarSet* s, int k) { return s->f[k]; }
 };
+template <> struct ScalarOf<Disc> {
+    static __device__ __forceinline__ DiscTw get(const ScalarSet* s, int k) { return s->disc[k]; }
+};
+template <> struct ScalarOf<Pt> : ScalarOf<Disc> {};
+template <> struct ScalarOf<DDisc> {
+    static __device__ __forceinline__ DDiscTw get(const ScalarSet* s, int k) { return s->dd[k]; }
+};
+
+// scalar k for the transform of sign SIGN: the inverse conjugates, which
+// negates the imaginary scalars (a sign-bit flip) and keeps the real ones
+template <typename V, int SIGN>
+__device__ __forceinline__ typename VTraits<V>::Tw scalar_tw(const TwTable& tw, int k) {
+    const auto w = ScalarOf<V>::get(tw.scal, k);
+    return SIGN > 0 ? w : tw_conj(w);
+}
 
 template <typename V, int SIGN, int BPT = 2, int R = 3>
 __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw) {
@@ -220,7 +244,7 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
     // radix-R step: n = R, s = 2^loga; each thread owns its R elements
     const int part = 1 << loga;
     if (R == 3) {
-        const auto w3 = ScalarTw<V, SIGN, R>::get(tw, 1u << tw.log_n, true);   // i Im omega_3^SIGN
+        const auto w3 = scalar_tw<V, SIGN>(tw, 0);        // i Im omega_3^SIGN
         for (int b = threadIdx.x; b < nl * part; b += blockDim.x) {
             const int x = (b >> loga) * pitch + (b & (part - 1));
             const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];
@@ -233,10 +257,8 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
         }
     } else {
         // omega_5^(SIGN k) = c_k + i s_k, k = 1, 2
-        const auto c1 = ScalarTw<V, SIGN, R>::get(tw, 1u << tw.log_n, false);
-        const auto c2 = ScalarTw<V, SIGN, R>::get(tw, 2u << tw.log_n, false);
-        const auto s1 = ScalarTw<V, SIGN, R>::get(tw, 1u << tw.log_n, true);
-        const auto s2 = ScalarTw<V, SIGN, R>::get(tw, 2u << tw.log_n, true);
+        const auto c1 = scalar_tw<V, SIGN>(tw, 0), c2 = scalar_tw<V, SIGN>(tw, 1);
+        const auto s1 = scalar_tw<V, SIGN>(tw, 2), s2 = scalar_tw<V, SIGN>(tw, 3);
         for (int b = threadIdx.x; b < nl * part; b += blockDim.x) {
             const int x = (b >> loga) * pitch + (b & (part - 1));
             const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];

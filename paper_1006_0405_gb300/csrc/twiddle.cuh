@@ -46,6 +46,7 @@ struct TwEntry {
 };
 
 struct DDiscC;
+struct ScalarSet;
 
 // Step-ordered twiddles.  The radix-4 step of sub-length n multiplies by
 // omega_n^{u p} for p < n/4 and u = 1, 2, 3; a step table holds that value
@@ -76,6 +77,8 @@ struct TwTable {
     const CI<float>* s32_r;
     const DiscTw* sd_r;
     const DDiscC* sdd_r;
+    // the real and imaginary scalars of the radix-R step (family R = 3, 5)
+    const ScalarSet* scal;
 };
 
 __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n, int R) {

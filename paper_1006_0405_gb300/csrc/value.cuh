@@ -217,6 +217,15 @@ __global__ void k_step_tw_gen(TwTable tw, CI<double>* s64, CI<float>* s32, DiscT
     }
 }
 
+// The scalars of a radix-3 or radix-5 step in every twiddle type (see
+// k_scalar_gen): R = 3 uses [0], R = 5 [0 .. 3].
+struct ScalarSet {
+    CI<double> d[4];
+    CI<float> f[4];
+    DiscTw disc[4];
+    DDiscTw dd[4];
+};
+
 // a digit pair as an exact point (small integers are exact in every type)
 template <typename V> __device__ __forceinline__ V make_point(int re, int im);
 template <> __device__ __forceinline__ CI<float> make_point<CI<float>>(int re, int im) {
