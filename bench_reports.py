@@ -169,7 +169,7 @@ def sweep(args):
             z = dz.cpu().numpy()
             exact = bool(s in (abi.SSMUL_OK, abi.SSMUL_UNVERIFIED) and
                          np.array_equal(z, E.carry(E.conv_ntt(a, b), na + nb)))
-            rows.append({"na": na, "nb": nb, "dist": dist, "log2_N": r.fft_log2, "N": (3 if r.fft_times3 else 1) << r.fft_log2,
+            rows.append({"na": na, "nb": nb, "dist": dist, "log2_N": r.fft_log2, "N": r.fft_odd << r.fft_log2,
                          "status": abi.status_string(s), "max_width": r.max_width,
                          "n_unisolated": r.n_unisolated, "verified": exact, "ms": 1e3 * el})
             if na == nb and dist == "uniform" and exact and (largest == na // 2 or largest is None):
