@@ -204,7 +204,12 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # L2): dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  Only
 # valid for the 75k workload and the kernels as captured; empty when the
 # kernels changed since.
-NCU_TRAFFIC_PER_PRODUCT: dict = {}
+NCU_TRAFFIC_PER_PRODUCT = {
+    # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
+    "k_rows<double>": (84.798976e6 + 10.976256e6) / 16,
+    "k_rows<disc>": (63.491328e6 + 4.022016e6) / 16,
+    "k_rows<disc32x2>": (63.340800e6 + 3.411968e6) / 16,
+}
 
 
 def algorithmic_bytes(n: int) -> float:
