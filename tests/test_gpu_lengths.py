@@ -145,3 +145,20 @@ def test_batched_mix_of_families():
         assert (r.fft_odd, r.fft_log2) == expect_len(len(a), len(b))
         seen.add(r.fft_odd)
     assert seen == {1, 3, 5}
+
+
+@pytest.mark.parametrize("odd,K", [(3, 21), (5, 19)])
+def test_largest_odd_families_contain_exact_sampled(odd, K):
+    """The largest odd-family tables (a plan of 2^22 x 2^22 digits), sampled:
+    the first and last octant entries and a stride through the rest."""
+    from fractions import Fraction as Fr
+    n = 1 << 22
+    with Plan(n, n) as p:
+        ln, cl, ch, sl, sh = p.twiddles(False, odd=odd)
+        assert ln == K
+        N = odd << ln
+        m = N // 8
+        for j in list(range(0, 30)) + list(range(m - 30, m + 1)) + list(range(1, m, 7919)):
+            (c, ec), (s, es) = tw.exact_fraction(N, j)
+            assert Fr(float(cl[j])) <= c - ec and c + ec <= Fr(float(ch[j])), j
+            assert Fr(float(sl[j])) <= s - es and s + es <= Fr(float(sh[j])), j
