@@ -44,7 +44,6 @@ constexpr int GEOM_CODES = LEN5 + LOG5_MAX + 1;
 // the odd factor and the power of two of a length code
 int odd_of(int code) { return code >= LEN5 ? 5 : (code >= LEN3 ? 3 : 1); }
 int log2_of(int code) { return code % LEN3; }
-int family_of(int code) { return code >= LEN5 ? 2 : (code >= LEN3 ? 1 : 0); }
 
 // the transform length of a length code
 size_t len_of(int code) { return size_t(odd_of(code)) << log2_of(code); }

@@ -38,7 +38,6 @@ namespace ssm {
 
 constexpr int TW_WIDEN_ULPS = 4;
 constexpr int TW3_WIDEN_ULPS = 6;
-constexpr int TW_DOC_ULPS = 2;
 
 template <typename T>
 struct TwEntry {
