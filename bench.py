@@ -69,9 +69,10 @@ def parse():
                     help="skip the extra lines for the other rungs (disc64, naive64)")
     ap.add_argument("--balanced", action="store_true",
                     help="balanced digits (the transforms carry digit - 128)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "sweep", "ladder", "uneven"],
-                    help="paper: the headline line; sweep / ladder / uneven: report lines of "
-                         "the size sweep, the precision ladder and the uneven batch")
+    ap.add_argument("--workload", default="paper", choices=["paper", "sweep", "ladder", "uneven", "split"],
+                    help="paper: the headline line; sweep / ladder / uneven / split: report "
+                         "lines of the size sweep, the precision ladder, the uneven batch and "
+                         "the products past the isolation limit")
     return ap.parse_args()
 
 

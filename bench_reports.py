@@ -12,6 +12,11 @@ ladder  4,096 square products, n ~ U{512..32768}, 10% all-0xFF: the ladder
 uneven  20,000 products with na, nb independent and log-uniform in
         [64, 131072]: the ladder in one graph-captured batched call against
         the same set one product at a time in binary64.
+split   square products of 2^19 .. 2^22 uniform digits, past the binary64
+        rectangles' isolation limit: rectangles on the whole product, the
+        same cut into parts of 2^18 digits (SSMUL_OPT_SPLIT_DIGITS, Section
+        1's "different algorithm"), and binary64 discs on the whole product;
+        status, time per product and residue verification of each.
 
 Verification is against the CPU oracle: every product's digits against the
 exact product for sweep and ladder; for the uneven batch every product's
@@ -301,5 +306,42 @@ def _uneven_batched(torch, abi, batch, max_n, prec, stream, seed):
         "kernel_s_per_batch": kernel_s, "kernel_time_fraction": kernel_s / t}
 
 
+def split(args):
+    torch = _torch()
+    from oracle import exact as E
+    from paper_1006_0405_gb300 import abi
+    abi.load()
+    part = 1 << 18
+    rows = []
+    for k in (19, 20, 21, 22):
+        n = 1 << k
+        a, b = synth.operand_pair(synth.SEED_BASE + 6, n, n)
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        dz = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
+        want = [E.residue(a, q) * E.residue(b, q) % q for q in PRIMES]
+        for name, prec, split_m in (("fp64", abi.SSMUL_PREC_FP64, 0),
+                                    ("fp64_split_2^18", abi.SSMUL_PREC_FP64, part),
+                                    ("disc64", abi.SSMUL_PREC_DISC64, 0)):
+            plan = abi.ssmul_plan(n, n, 0, prec, 0)
+            if split_m:
+                assert abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_SPLIT_DIGITS, split_m) == 0
+            s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
+            reps = 3
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
+            el = (time.perf_counter() - t0) / reps
+            abi.ssmul_plan_destroy(plan)
+            z = dz.cpu().numpy()
+            ok = bool(s == abi.SSMUL_OK and
+                      all(E.residue(z, q) == w for q, w in zip(PRIMES, want)))
+            rows.append({"digits": n, "method": name, "status": abi.status_string(s),
+                         "max_width": r.max_width, "N": r.fft_odd << r.fft_log2,
+                         "residue_verified": ok, "ms": 1e3 * el,
+                         "verified_digits_per_s": (2 * n / el) if ok else 0.0})
+    print(json.dumps({"report": "split", "part_digits": part, "rows": rows}), flush=True)
+
+
 def run(args):
-    {"sweep": sweep, "ladder": ladder, "uneven": uneven}[args.workload](args)
+    {"sweep": sweep, "ladder": ladder, "uneven": uneven, "split": split}[args.workload](args)
