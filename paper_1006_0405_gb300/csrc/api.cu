@@ -145,10 +145,11 @@ int threads_for(int elems) {          // block_fft with 2 butterflies per thread
     return t;
 }
 
-// radix-4 butterflies per thread the plan's launches use: two (one
-// butterfly per thread halves the registers but measured slower on GB300,
-// and leaves too few registers at 1024 threads)
-template <typename V> constexpr int plan_bpt() { return 2; }
+// radix-4 butterflies per thread the plan's launches use: two for the
+// binary64 types (one halves the registers but measured 6% slower on GB300),
+// one for the double-binary32 discs (twice the warps for the issue-bound
+// binary32 kernels: 5% faster at 75k digits)
+template <typename V> constexpr int plan_bpt() { return std::is_same<V, DDisc>::value ? 1 : 2; }
 
 template <typename V>
 int fft_threads(int elems) {          // block_fft: nl * L / (4 BPT) threads
