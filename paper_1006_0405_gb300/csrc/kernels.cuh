@@ -646,21 +646,24 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_
 // points): the first that isolated
 // every coefficient, or found an empty set, decides; otherwise the last one
 // that ran reports its isolation failure.
-__device__ __forceinline__ int decide(const ProdState* st, int* rung) {
+__device__ __forceinline__ int decide(const ProdState* stp, int* rung) {
+    // one copy of the state: its loads are independent and go out together
+    // (a walk over the rungs through the pointer would chain them)
+    const ProdState st = *stp;
     const int order[RUNGS] = {0, 4, 2, 1, 3};
     int last = -1;
     int status = SSMUL_ISOLATION_FAILED;
     for (int k = 0; k < RUNGS; ++k) {
         const int r = order[k];
-        if (!st->ran[r]) continue;
+        if (!st.ran[r]) continue;
         last = r;
         if (r == 3) { status = SSMUL_UNVERIFIED; break; }
-        if (st->empty[r]) { status = SSMUL_CONTAINMENT_FAILED; break; }
-        if (st->unisolated[r] == 0) { status = SSMUL_OK; break; }
+        if (st.empty[r]) { status = SSMUL_CONTAINMENT_FAILED; break; }
+        if (st.unisolated[r] == 0) { status = SSMUL_OK; break; }
     }
     *rung = last < 0 ? 1 : last;
-    if (st->forced) status = int(st->forced);
-    return st->timeout ? SSMUL_TIMEOUT : status;
+    if (st.forced) status = int(st.forced);
+    return st.timeout ? SSMUL_TIMEOUT : status;
 }
 
 __device__ __forceinline__ int rung_precision(int rung) {
@@ -740,12 +743,16 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) 
         return;
     }
     const bool publish = d.fault_stall != int32_t(tile) + 1;   // test fault
-    // stage c[tile start - CARRY_HALO .. tile end) with coalesced loads
+    // stage c[tile start - CARRY_HALO .. tile end) with coalesced loads, all
+    // of a thread's loads issued before its first shared store
     const int64_t kt = int64_t(tile) * CARRY_TILE;
-    for (int i = threadIdx.x; i < CARRY_TILE + CARRY_HALO; i += CARRY_THREADS) {
-        const int64_t idx = kt - CARRY_HALO + i;
-        s_c[i] = (idx >= 0 && idx < L) ? d.coeff[idx] : 0;
-    }
+    stage<(CARRY_TILE + CARRY_HALO + CARRY_THREADS - 1) / CARRY_THREADS, int64_t>(
+        CARRY_TILE + CARRY_HALO,
+        [&](int i) {
+            const int64_t idx = kt - CARRY_HALO + i;
+            return (idx >= 0 && idx < L) ? d.coeff[idx] : int64_t(0);
+        },
+        [&](int i, int64_t c) { s_c[i] = c; });
     __syncthreads();
     // byte sums u_k, one position per thread at a time (consecutive lanes,
     // consecutive coefficients)
