@@ -207,9 +207,9 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # kernels changed since.
 NCU_TRAFFIC_PER_PRODUCT = {
     # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
-    "k_rows<double>": (84.798976e6 + 10.976256e6) / 16,
-    "k_rows<disc>": (63.491328e6 + 4.022016e6) / 16,
-    "k_rows<disc32x2>": (63.340800e6 + 3.411968e6) / 16,
+    "k_rows<double>": (84.642560e6 + 10.915072e6) / 16,
+    "k_rows<disc>": (63.490560e6 + 3.824128e6) / 16,
+    "k_rows<disc32x2>": (63.305984e6 + 5.205760e6) / 16,
 }
 
 
