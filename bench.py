@@ -102,14 +102,15 @@ COSTS = {
     "fp64": dict(add=4, bfly=32, tw=8, mul=12, scale=4, iso=1),
     "disc64": dict(add=2, bfly=16, tw=4, mul=4, scale=2, iso=3),
     "naive64": dict(add=2, bfly=16, tw=4, mul=4, scale=2, iso=0),
-    # double-binary32 discs count binary32 operations: a complex add is two
-    # pair sums (2 x 14) and its radius (6); the radix-4 butterfly's eight
-    # sums share one radius (8 x 28 + 13); a twiddle product is four pair
-    # products (4 x 7), two pair sums and 5 radius operations (the terms in
-    # the table's radius alone are loop invariants); a general product 56 + 10;
-    # the binary32 isolation of a component 12 (two roundings to integers,
-    # the remainders' sum and its bounds, the width, two magic-number roundings)
-    "disc32x2": dict(add=34, bfly=237, tw=61, mul=66, scale=6, iso=12),
+    # double-binary32 discs count binary32 operations: a pair sum is TwoSum,
+    # two adds and FastTwoSum (11); a complex add is two pair sums and its
+    # radius (2 x 11 + 6); the radix-4 butterfly's eight sums share one
+    # radius (8 x 22 + 13); a twiddle product is four pair products (4 x 7),
+    # two pair sums and 5 radius operations (the terms in the table's radius
+    # alone are loop invariants); a general product 28 + 22 + 10; the binary32
+    # isolation of a component 12 (two roundings to integers, the
+    # remainders' sum and its bounds, the width, two magic-number roundings)
+    "disc32x2": dict(add=28, bfly=189, tw=55, mul=60, scale=6, iso=12),
 }
 TAGS = {"fp64": "double", "disc64": "disc", "naive64": "naive", "disc32x2": "disc32x2"}
 
@@ -209,7 +210,6 @@ NCU_TRAFFIC_PER_PRODUCT = {
     # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
     "k_rows<double>": (84.642560e6 + 10.915072e6) / 16,
     "k_rows<disc>": (63.490560e6 + 3.824128e6) / 16,
-    "k_rows<disc32x2>": (63.305984e6 + 5.205760e6) / 16,
 }
 
 

@@ -12,9 +12,18 @@
 // of its own rounding error (derivations beside each rule):
 //
 //   pair sum     (s, e) = TwoSum(xh, yh); v = RN(e + RN(xl + yl));
-//                z = TwoSum(s, v).  |z - (x + y)| <= u |RN(xl + yl)| + u |v|
+//                z = FastTwoSum(s, v).  |z - (x + y)| <= u |RN(xl + yl)| + u |v|
 //                <= u^2 (|xh| + |yh|) (2 + u) + u^2 (1 + u) (|xh| + |yh|)
-//                <= 3.0001 u^2 (|xh| + |yh|).
+//                <= 3.0001 u^2 (|xh| + |yh|).  FastTwoSum is exact here
+//                (Dekker: when s = 0 or exp(s) >= exp(v)) for normalised
+//                operands, h = RN(h + l), so |l| <= ulp(h) / 2 <= u |h|:
+//                without cancellation (|xh + yh| >= (|xh| + |yh|) / 3)
+//                |v| <= 4.01 u |s|; with it (yh within a factor 2 of -xh)
+//                Sterbenz makes s = xh + yh exact and e = 0, s is a nonzero
+//                multiple of U = min(ulp(xh), ulp(yh)) or zero, and
+//                |v| = |RN(xl + yl)| <= (ulp(xh) + ulp(yh)) / 2 <= 1.5 U, so
+//                exp(v) <= exp(U) <= exp(s).  Every result is again
+//                normalised (zh = RN(zh + zl)).
 //   pair product p = RN(xh wh); pe = fma(xh, wh, -p) (exact);
 //                r = RN(xl wh + RN(xh wl + pe)); z = FastTwoSum(p, r) (exact,
 //                |r| <= 3u|p|).  The dropped xl wl and the two roundings give
@@ -76,7 +85,7 @@ __device__ __forceinline__ void pair_add(float xh, float xl, float yh, float yl,
     float s, e;
     two_sum(xh, yh, s, e);
     const float v = __fadd_rn(e, __fadd_rn(xl, yl));
-    two_sum(s, v, zh, zl);
+    fast_two_sum(s, v, zh, zl);
 }
 
 __device__ __forceinline__ void pair_mul(float xh, float xl, float wh, float wl, float& zh,

@@ -179,3 +179,59 @@ def test_pair_disc_butterfly_contains(op):
             for u in range(4):
                 ox, oy, orr = outs[u]
                 assert (ex[u][0] - ox) ** 2 + (ex[u][1] - oy) ** 2 <= orr * orr, (op, i, u)
+
+
+def _f32(x):
+    return np.float32(x)
+
+
+def _normalised_low(rng, h, n):
+    """low parts of magnitude up to half an ulp of h, each pair normalised
+    (RN32(h + l) == h)"""
+    ulp = np.spacing(np.abs(h).astype(np.float32)).astype(np.float64)
+    lo = (rng.uniform(-0.5, 0.5, n) * ulp).astype(np.float32)
+    edge = rng.random(n) < 0.5                    # the extremes, just inside the tie
+    lo[edge] = (np.sign(rng.uniform(-1, 1, edge.sum())) * ulp[edge] * (0.5 - 2.0 ** -20)).astype(np.float32)
+    keep = (h.astype(np.float32) + lo).astype(np.float32) == h.astype(np.float32)
+    return lo.astype(np.float64), keep
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_pair_sum_exact_renormalisation_under_cancellation(op):
+    """A pair sum ends with FastTwoSum(s, v), exact only when exp(s) >= exp(v).
+    Operands whose high parts cancel (within a factor 2, across binade
+    boundaries) with low parts at half an ulp are the case where |v| comes
+    closest to |s|: the result must be exactly s + v (s, v as the rule
+    computes them, emulated here in binary32), normalised, and contain the
+    exact sum."""
+    rng = np.random.default_rng(90 + op)
+    n = 4000
+    xh = rng.uniform(0.5, 4.0, n).astype(np.float32)
+    f = np.where(rng.random(n) < 0.5, rng.uniform(0.5, 2.0, n),
+                 1.0 + rng.integers(-4, 5, n) * 2.0 ** -23)            # near-total cancellation
+    yh = (-(xh.astype(np.float64) * f)).astype(np.float32)
+    if op == 1:
+        yh = -yh                                                          # x - y cancels
+    xh, yh = xh.astype(np.float64), yh.astype(np.float64)
+    xl, k1 = _normalised_low(rng, xh, n)
+    yl, k2 = _normalised_low(rng, yh, n)
+    keep = k1 & k2
+    xh, xl, yh, yl = xh[keep], xl[keep], yh[keep], yl[keep]
+    m = len(xh)
+    z = np.zeros(m)
+    a = np.stack([xh, xl, z, z, z], 1)
+    b = np.stack([yh, yl, z, z, z], 1)
+    out = _op(op, a, b)
+    sgn = 1.0 if op == 0 else -1.0
+    for i in range(m):
+        ah, al = _f32(xh[i]), _f32(xl[i])
+        bh, bl = _f32(sgn * yh[i]), _f32(sgn * yl[i])
+        s = _f32(ah + bh)
+        bb = _f32(s - ah)
+        e = _f32(_f32(ah - _f32(s - bb)) + _f32(bh - bb))
+        v = _f32(e + _f32(al + bl))
+        zh, zl = out[i, 0], out[i, 1]
+        assert Fr(float(zh)) + Fr(float(zl)) == Fr(float(s)) + Fr(float(v)), i
+        assert _f32(_f32(zh) + _f32(zl)) == _f32(zh)
+        exact = Fr(float(xh[i])) + Fr(float(xl[i])) + Fr(sgn) * (Fr(float(yh[i])) + Fr(float(yl[i])))
+        assert abs(exact - Fr(float(zh)) - Fr(float(zl))) <= Fr(float(out[i, 4])), i
