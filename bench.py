@@ -99,9 +99,10 @@ def make_batch(rank: int, batch: int, n: int):
 # 1 per coefficient width) and discs / points (2, 4, 4, 2; isolation of a
 # disc: 2 bounds + 1 width per coefficient)
 COSTS = {
-    "fp64": dict(add=4, bfly=32, tw=8, mul=12, scale=4, iso=1),
-    "disc64": dict(add=2, bfly=16, tw=4, mul=4, scale=2, iso=3),
-    "naive64": dict(add=2, bfly=16, tw=4, mul=4, scale=2, iso=0),
+    # stw: a product by a real or pure imaginary scalar (radix-3, radix-5)
+    "fp64": dict(add=4, bfly=32, tw=8, stw=4, mul=12, scale=4, iso=1),
+    "disc64": dict(add=2, bfly=16, tw=4, stw=2, mul=4, scale=2, iso=3),
+    "naive64": dict(add=2, bfly=16, tw=4, stw=2, mul=4, scale=2, iso=0),
     # double-binary32 discs count binary32 operations: a pair sum is TwoSum,
     # two adds and FastTwoSum (11); a complex add is two pair sums and its
     # radius (2 x 11 + 6); the radix-4 butterfly's eight sums share one
@@ -109,19 +110,24 @@ COSTS = {
     # two pair sums and 5 radius operations (the terms in the table's radius
     # alone are loop invariants); a general product 28 + 22 + 10; the binary32
     # isolation of a component 12 (two roundings to integers, the
-    # remainders' sum and its bounds, the width, two magic-number roundings)
-    "disc32x2": dict(add=28, bfly=189, tw=55, mul=60, scale=6, iso=12),
+    # remainders' sum and its bounds, the width, two magic-number roundings);
+    # a product by a real or imaginary scalar is two pair products and 5
+    # radius operations
+    "disc32x2": dict(add=28, bfly=189, tw=55, stw=19, mul=60, scale=6, iso=12),
 }
 TAGS = {"fp64": "double", "disc64": "disc", "naive64": "naive", "disc32x2": "disc32x2"}
 
 
-def _fft_ops(logL: int, nl: int, c: dict) -> int:
+def _fft_ops(logL: int, nl: int, c: dict, exact_first: bool = False) -> int:
+    """exact_first: the first step's 4-point sums are integer arithmetic on
+    the digits (forward column transforms), only its twiddle products count"""
     L = 1 << logL
     ops = 0
     logn, logs = logL, 0
     while logn >= 2:
         s = 1 << logs
-        ops += nl * (L // 4) * c["bfly"] + nl * (L // 4 - s) * 3 * c["tw"]
+        sums = 0 if (exact_first and logs == 0) else nl * (L // 4) * c["bfly"]
+        ops += sums + nl * (L // 4 - s) * 3 * c["tw"]
         logn -= 2
         logs += 2
     if logn == 1:
@@ -129,20 +135,21 @@ def _fft_ops(logL: int, nl: int, c: dict) -> int:
     return ops
 
 
-def _fft_odd_ops(R: int, loga: int, nl: int, c: dict) -> int:
+def _fft_odd_ops(R: int, loga: int, nl: int, c: dict, exact_first: bool = False) -> int:
     """lines of length R 2^loga (R = 3 or 5, loga even): radix-4 steps, then
-    one radix-R step: radix 3 = 6 adds, a scaling by 1/2 and one twiddle
-    product per butterfly; radix 5 = 14 adds and 8 products by a real or
-    pure imaginary twiddle"""
+    one radix-R step: radix 3 = 6 adds, a scaling by 1/2 and one product by
+    a pure imaginary scalar per butterfly; radix 5 = 14 adds and 8 products
+    by a real or pure imaginary scalar"""
     L = R << loga
     ops = 0
     logn2, logs = loga, 0
     while logn2 >= 2:
         s = 1 << logs
-        ops += nl * (L // 4) * c["bfly"] + nl * (L // 4 - s) * 3 * c["tw"]
+        sums = 0 if (exact_first and logs == 0) else nl * (L // 4) * c["bfly"]
+        ops += sums + nl * (L // 4 - s) * 3 * c["tw"]
         logn2 -= 2
         logs += 2
-    last = (6 * c["add"] + c["scale"] + c["tw"]) if R == 3 else (14 * c["add"] + 8 * c["tw"])
+    last = (6 * c["add"] + c["scale"] + c["stw"]) if R == 3 else (14 * c["add"] + 8 * c["stw"])
     return ops + nl * (L // R) * last
 
 
@@ -189,8 +196,11 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
     n1l, n2l, c1l, c3l = geometry(R, k)
     N1, N2 = R << n1l, 1 << n2l
     M2 = N2 // 2
-    col = (lambda nl: _fft_ops(n1l, nl, c)) if R == 1 else (lambda nl: _fft_odd_ops(R, n1l, nl, c))
-    fwd = (N2 >> c1l) * col(1 << c1l) + (N1 - 1) * (N2 - 1) * c["tw"]
+    def col(nl, exact_first=False):
+        if R == 1:
+            return _fft_ops(n1l, nl, c, exact_first and n1l >= 2)
+        return _fft_odd_ops(R, n1l, nl, c, exact_first)
+    fwd = (N2 >> c1l) * col(1 << c1l, True) + (N1 - 1) * (N2 - 1) * c["tw"]
     rows = 0
     for k1 in range(N1 // 2 + 1):
         nl = 1 if k1 == (N1 - k1) % N1 else 2

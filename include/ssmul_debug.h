@@ -46,8 +46,11 @@ ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t plan, const uint8_t* d_a, si
  * unit tests of the device arithmetic.  d_x, d_y, d_out: device arrays of
  * 4 doubles per operand (re_lo, re_hi, im_lo, im_hi).  op: 0 add, 1
  * subtract, 2 product by a twiddle enclosure d_y (components that do not
- * contain 0 unless they are the point 0), 3 general product.  f32 != 0
- * runs the binary32 arithmetic on operands that must be binary32 values.
+ * contain 0 unless they are the point 0), 3 general product, 4 product by
+ * the real enclosure d_y (its real part, not containing 0; the imaginary
+ * part is not read), 5 product by the pure imaginary enclosure d_y (its
+ * imaginary part, not containing 0).  f32 != 0 runs the binary32
+ * arithmetic on operands that must be binary32 values.
  */
 ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double* d_y,
                                double* d_out, size_t n);
@@ -58,7 +61,8 @@ ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double*
  * d_y, d_out: device arrays of 3 doubles per operand (centre re, centre im,
  * radius; the radius is used as a binary32 value).  op: 0 add, 1 subtract,
  * 2 product by a twiddle disc d_y (|centre| <= 1), 3 general product,
- * 4 scaling by 2^-k with k = (int) d_y[3 i].
+ * 4 scaling by 2^-k with k = (int) d_y[3 i], 5 (6) product by the real
+ * (pure imaginary) disc d_y: the disc's centre im (re) is taken as 0.
  */
 ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y, double* d_out,
                                  size_t n);
@@ -71,7 +75,8 @@ ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y, d
  * with k = (int) d_y[5 i].  op 5 (6): the radix-4 butterfly of the
  * transform (the inverse's) on the four discs d_x[20 i .. 20 i + 20), its
  * four outputs at d_out[20 i ..] sharing one radius; d_y is not read and
- * may be NULL.
+ * may be NULL.  op 7 (8): product by the real (pure imaginary) disc d_y,
+ * whose centre im (re) is taken as 0.
  */
 ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y, double* d_out,
                                   size_t n);

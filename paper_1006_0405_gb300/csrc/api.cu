@@ -1389,7 +1389,9 @@ __global__ void k_ci_op(int op, const double* x, const double* y, double* out, s
             case 0: r = a + b; break;
             case 1: r = a - b; break;
             case 2: r = mul_tw(a, b); break;
-            default: r = mul_ci(a, b); break;
+            case 3: r = mul_ci(a, b); break;
+            case 4: r = mul_real(a, b); break;
+            default: r = mul_imag(a, b); break;
         }
         out[4 * i] = r.rl;
         out[4 * i + 1] = r.rh;
@@ -1409,7 +1411,9 @@ __global__ void k_disc_op(int op, const double* x, const double* y, double* out,
             case 1: r = a - b; break;
             case 2: r = mul_tw(a, DiscTw{b.x, b.y, b.r, TW_MOD_UP}); break;
             case 3: r = mul_ci(a, b); break;
-            default: r = scale_pow2(a, int(y[3 * i])); break;
+            case 4: r = scale_pow2(a, int(y[3 * i])); break;
+            case 5: r = mul_real(a, DiscTw{b.x, 0.0, b.r, abs_up(b.x)}); break;
+            default: r = mul_imag(a, DiscTw{0.0, b.y, b.r, abs_up(b.y)}); break;
         }
         out[3 * i] = r.x;
         out[3 * i + 1] = r.y;
@@ -1420,7 +1424,7 @@ __global__ void k_disc_op(int op, const double* x, const double* y, double* out,
 __global__ void k_ddisc_op(int op, const double* x, const double* y, double* out, size_t n) {
     for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
          i += size_t(gridDim.x) * blockDim.x) {
-        if (op >= 5) {
+        if (op == 5 || op == 6) {
             // radix-4 butterfly of the four discs x[20 i ..] (SIGN +1 for op 5, -1 for op 6)
             DDisc v[4];
             for (int t = 0; t < 4; ++t) {
@@ -1449,7 +1453,9 @@ __global__ void k_ddisc_op(int op, const double* x, const double* y, double* out
             case 1: r = a - b; break;
             case 2: r = mul_tw(a, DDiscTw{b.xh, b.xl, b.yh, b.yl, b.r, TW_MOD_UP}); break;
             case 3: r = mul_ci(a, b); break;
-            default: r = scale_pow2(a, int(b5[0])); break;
+            case 4: r = scale_pow2(a, int(b5[0])); break;
+            case 7: r = mul_real(a, DDiscTw{b.xh, b.xl, 0.f, 0.f, b.r, dd_mod_up(b.xh, 0.f)}); break;
+            default: r = mul_imag(a, DDiscTw{0.f, 0.f, b.yh, b.yl, b.r, dd_mod_up(0.f, b.yh)}); break;
         }
         double* o = out + 5 * i;
         o[0] = r.xh;
@@ -1501,7 +1507,7 @@ extern "C" ssmul_status ssmul_debug_isolate(int path, const double* d_x, int64_t
 
 extern "C" ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y,
                                              double* d_out, size_t n) {
-    if (op < 0 || op > 6 || (n && (!d_x || !d_out || (op < 5 && !d_y)))) return SSMUL_INVALID_ARG;
+    if (op < 0 || op > 8 || (n && (!d_x || !d_out || ((op < 5 || op > 6) && !d_y)))) return SSMUL_INVALID_ARG;
     if (n == 0) return SSMUL_OK;
     const int threads = 256;
     const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);
@@ -1513,7 +1519,7 @@ extern "C" ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const do
 
 extern "C" ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const double* d_y,
                                             double* d_out, size_t n) {
-    if (op < 0 || op > 4 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
+    if (op < 0 || op > 6 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
     if (n == 0) return SSMUL_OK;
     const int threads = 256;
     const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);
@@ -1525,7 +1531,7 @@ extern "C" ssmul_status ssmul_debug_disc_op(int op, const double* d_x, const dou
 
 extern "C" ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, const double* d_y,
                                           double* d_out, size_t n) {
-    if (op < 0 || op > 3 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
+    if (op < 0 || op > 5 || (n && (!d_x || !d_y || !d_out))) return SSMUL_INVALID_ARG;
     if (n == 0) return SSMUL_OK;
     const int threads = 256;
     const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);

@@ -219,6 +219,38 @@ __device__ __forceinline__ DDisc mul_tw(const DDisc& a, const DDiscTw& w) {
     return z;
 }
 
+// a * w for a real twiddle w = D(ch + cl, rho) (sh = sl = 0, |centre| <=
+// w.mod): two pair products, whose rounding errs by at most
+// DD_PMUL (|axh| + |ayh|) |ch| + 2 ETA; the propagation is mul_tw's
+constexpr float DD_PMUL = 6.001f * DD_U2;
+
+__device__ __forceinline__ DDisc mul_real(const DDisc& a, const DDiscTw& w) {
+    DDisc z;
+    pair_mul(a.xh, a.xl, w.ch, w.cl, z.xh, z.xl);
+    pair_mul(a.yh, a.yl, w.ch, w.cl, z.yh, z.yl);
+    const float ma = __fadd_ru(fabsf(a.xh), fabsf(a.yh));
+    const float k = __fmaf_ru(DD_PMUL, fabsf(w.ch), __fmul_ru(DD_ONE_U, w.rho));
+    z.r = __fmaf_ru(a.r, __fadd_ru(w.mod, w.rho), __fmaf_ru(ma, k, 4.f * DD_ETA));
+    z.pad = 0.f;
+    return z;
+}
+
+// a * w for a pure imaginary twiddle w = D(i (sh + sl), rho) (ch = cl = 0):
+// (-ay s, ax s), the same bounds with |sh|
+__device__ __forceinline__ DDisc mul_imag(const DDisc& a, const DDiscTw& w) {
+    DDisc z;
+    float th, tl;
+    pair_mul(a.yh, a.yl, w.sh, w.sl, th, tl);
+    z.xh = flip(th);
+    z.xl = flip(tl);
+    pair_mul(a.xh, a.xl, w.sh, w.sl, z.yh, z.yl);
+    const float ma = __fadd_ru(fabsf(a.xh), fabsf(a.yh));
+    const float k = __fmaf_ru(DD_PMUL, fabsf(w.sh), __fmul_ru(DD_ONE_U, w.rho));
+    z.r = __fmaf_ru(a.r, __fadd_ru(w.mod, w.rho), __fmaf_ru(ma, k, 4.f * DD_ETA));
+    z.pad = 0.f;
+    return z;
+}
+
 // general product (pointwise step): |a b - a_c b_c| <= |a_c| rb + |b_c| ra + ra rb
 __device__ __forceinline__ DDisc mul_ci(const DDisc& a, const DDisc& b) {
     DDisc z;

@@ -126,6 +126,31 @@ __device__ __forceinline__ Disc mul_tw(const Disc& a, const DiscTw& w) {
     return z;
 }
 
+// a * w for a real twiddle disc w = D(c, rho) (w.s = 0, |c| <= w.mod): the
+// centre (RN(ax c), RN(ay c)) errs by hu(x) + hu(y); the propagation is
+// mul_tw's
+__device__ __forceinline__ Disc mul_real(const Disc& a, const DiscTw& w) {
+    Disc z;
+    z.x = mul_rn(a.x, w.c);
+    z.y = mul_rn(a.y, w.c);
+    const float prop = __fmaf_ru(a.r, __fadd_ru(w.mod, w.rho), __fmul_ru(mod_up(a.x, a.y), w.rho));
+    z.r = __fadd_ru(prop, err2(z.x, z.y));
+    z.pad = 0.f;
+    return z;
+}
+
+// a * w for a pure imaginary twiddle disc w = D(i s, rho) (w.c = 0):
+// (-RN(ay s), RN(ax s)), the same bounds
+__device__ __forceinline__ Disc mul_imag(const Disc& a, const DiscTw& w) {
+    Disc z;
+    z.x = flip(mul_rn(a.y, w.s));
+    z.y = mul_rn(a.x, w.s);
+    const float prop = __fmaf_ru(a.r, __fadd_ru(w.mod, w.rho), __fmul_ru(mod_up(a.x, a.y), w.rho));
+    z.r = __fadd_ru(prop, err2(z.x, z.y));
+    z.pad = 0.f;
+    return z;
+}
+
 // general product (pointwise step): |a b - a_c b_c| <= |a_c| rb + |b_c| ra + ra rb
 __device__ __forceinline__ Disc mul_ci(const Disc& a, const Disc& b) {
     Disc z;
@@ -168,6 +193,12 @@ __device__ __forceinline__ Pt conj_flip(const Pt& a) { return {a.x, flip(a.y)}; 
 __device__ __forceinline__ Pt mul_negi_flip(const Pt& a) { return {a.y, flip(a.x)}; }
 __device__ __forceinline__ Pt mul_tw(const Pt& a, const DiscTw& w) {
     return {__fma_rn(a.x, w.c, -mul_rn(a.y, w.s)), __fma_rn(a.x, w.s, mul_rn(a.y, w.c))};
+}
+__device__ __forceinline__ Pt mul_real(const Pt& a, const DiscTw& w) {
+    return {mul_rn(a.x, w.c), mul_rn(a.y, w.c)};
+}
+__device__ __forceinline__ Pt mul_imag(const Pt& a, const DiscTw& w) {
+    return {flip(mul_rn(a.y, w.s)), mul_rn(a.x, w.s)};
 }
 __device__ __forceinline__ Pt mul_ci(const Pt& a, const Pt& b) {
     return {__fma_rn(a.x, b.x, -mul_rn(a.y, b.y)), __fma_rn(a.x, b.y, mul_rn(a.y, b.x))};

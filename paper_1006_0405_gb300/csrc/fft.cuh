@@ -43,12 +43,15 @@ __device__ __forceinline__ void bfly4(V& a, V& b, V& c, V& d) {
     }
 }
 
-// R: the family of the twiddle table tw (the line length is 2^logL either way)
+// R: the family of the twiddle table tw (the line length is 2^logL either way).
+// skip_first: the first radix-4 step (n = L) is done already
+// (first_step_exact), so the steps start at n = L / 4, s = 4.
 template <typename V, int SIGN, int BPT = 2, int R = 1>
-__device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTable& tw) {
+__device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTable& tw,
+                          bool skip_first = false) {
     const int L = 1 << logL;
     const int quarter_log = logL - 2;
-    int logn = logL, logs = 0;
+    int logn = skip_first ? logL - 2 : logL, logs = skip_first ? 2 : 0;
     while (logn >= 2) {
         const int m = 1 << (logn - 2);          // n / 4
         const int s = 1 << logs;
@@ -122,7 +125,8 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
 //   y2, y3 = B +- W,  B = x0 + c2 S1 + c1 S2,  W = i (s2 D1 - s1 D2).
 // S/2 is an exact scaling (scale_pow2); the products by the real numbers c_k
 // and the pure imaginary numbers i s_k use enclosures of those numbers alone
-// (ScalarSet, computed once per plan from the family-R table).
+// (ScalarSet, computed once per plan from the family-R table), in half the
+// operations of a general twiddle product (mul_real, mul_imag).
 // Requires nl * L / 4 <= BPT * blockDim.x, like block_fft.
 
 // The real number cos or the pure imaginary number i sin of the enclosure
@@ -196,11 +200,13 @@ __device__ __forceinline__ typename VTraits<V>::Tw scalar_tw(const TwTable& tw, 
 }
 
 template <typename V, int SIGN, int BPT = 2, int R = 3>
-__device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw) {
+__device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw,
+                              bool skip_first = false) {
     static_assert(R == 3 || R == 5, "odd factor 3 or 5");
     const int L = R << loga;
     const int Lq = L >> 2;                      // butterflies per line in a radix-4 step
-    int logn2 = loga, logs = 0;                 // n = R 2^logn2, s = 2^logs
+    int logn2 = skip_first ? loga - 2 : loga;   // n = R 2^logn2, s = 2^logs
+    int logs = skip_first ? 2 : 0;
     while (logn2 >= 2) {
         const int m = R << (logn2 - 2);         // n / 4
         const int s = 1 << logs;
@@ -250,7 +256,7 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
             const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];
             const V S = x1 + x2, D = x1 - x2;
             const V T = x0 - scale_pow2(S, 1);
-            const V U = mul_tw(D, w3);
+            const V U = mul_imag(D, w3);
             buf[x] = x0 + S;
             buf[x + part] = T + U;
             buf[x + 2 * part] = T - U;
@@ -264,15 +270,71 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
             const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];
             const V x3 = buf[x + 3 * part], x4 = buf[x + 4 * part];
             const V S1 = x1 + x4, D1 = x1 - x4, S2 = x2 + x3, D2 = x2 - x3;
-            const V A = (x0 + mul_tw(S1, c1)) + mul_tw(S2, c2);
-            const V B = (x0 + mul_tw(S1, c2)) + mul_tw(S2, c1);
-            const V U = mul_tw(D1, s1) + mul_tw(D2, s2);
-            const V W = mul_tw(D1, s2) - mul_tw(D2, s1);
+            const V A = (x0 + mul_real(S1, c1)) + mul_real(S2, c2);
+            const V B = (x0 + mul_real(S1, c2)) + mul_real(S2, c1);
+            const V U = mul_imag(D1, s1) + mul_imag(D2, s2);
+            const V W = mul_imag(D1, s2) - mul_imag(D2, s1);
             buf[x] = (x0 + S1) + S2;
             buf[x + part] = A + U;
             buf[x + 4 * part] = A - U;
             buf[x + 2 * part] = B + W;
             buf[x + 3 * part] = B - W;
+        }
+    }
+    __syncthreads();
+}
+
+// ---- the first step of a forward transform of digits ---------------------------------
+//
+// The forward transform's inputs are the Gaussian integers a_j + i b_j of
+// the digits (Section 2.3), so the first radix-4 step's 4-point sums (n = L,
+// s = 1, p < L/4) are exact in integer arithmetic: only its twiddle
+// products omega_L^{p u} round.  in[line * ipitch + j] holds the inputs;
+// the step's outputs go to buf at block_fft's positions (line * pitch +
+// 4 p + u), after every input has been read, so in may share memory with
+// buf.  ODD: L = R 2^lg with the family-R step twiddles (block_fft_odd);
+// otherwise L = 2^lg >= 4.  The remaining steps are block_fft(...,
+// skip_first = true) or block_fft_odd(..., true).  Requires
+// nl * L / 4 <= BPT * blockDim.x.
+template <typename V, int BPT, int R, bool ODD>
+__device__ void first_step_exact(const int2* in, int ipitch, SBuf<V> buf, int lg, int nl, int pitch,
+                                 const TwTable& tw) {
+    const int m = ODD ? (R << (lg - 2)) : (1 << (lg - 2));      // L / 4
+    const int nbf = nl * m;
+    V v[BPT][4];
+    int base[BPT];
+    bool act[BPT];
+#pragma unroll
+    for (int h = 0; h < BPT; ++h) {
+        const int b = threadIdx.x + h * blockDim.x;
+        act[h] = b < nbf;
+        if (act[h]) {
+            const int line = ODD ? b / m : b >> (lg - 2);
+            const int p = b - line * m;
+            const int2* x = in + line * ipitch + p;
+            const int2 x0 = x[0], x1 = x[m], x2 = x[2 * m], x3 = x[3 * m];
+            const int apr = x0.x + x2.x, api = x0.y + x2.y, amr = x0.x - x2.x, ami = x0.y - x2.y;
+            const int bpr = x1.x + x3.x, bpi = x1.y + x3.y, bmr = x1.x - x3.x, bmi = x1.y - x3.y;
+            v[h][0] = make_point<V>(apr + bpr, api + bpi);      // u = 0
+            v[h][2] = make_point<V>(apr - bpr, api - bpi);      // u = 2
+            v[h][1] = make_point<V>(amr - bmi, ami + bmr);      // u = 1: + i (x1 - x3)
+            v[h][3] = make_point<V>(amr + bmi, ami - bmr);      // u = 3: - i (x1 - x3)
+            if (p != 0) {
+#pragma unroll
+                for (int u = 1; u < 4; ++u) {
+                    if constexpr (ODD) v[h][u] = mul_tw(v[h][u], step_twiddle_r<V, 1, R>(tw, lg, p, u));
+                    else v[h][u] = mul_tw(v[h][u], step_twiddle<V, 1, R>(tw, lg, p, u));
+                }
+            }
+            base[h] = line * pitch + 4 * p;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < BPT; ++h) {
+        if (act[h]) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) buf[base[h] + u] = v[h][u];
         }
     }
     __syncthreads();

@@ -148,6 +148,29 @@ __device__ __forceinline__ CI<T> mul_tw(const CI<T>& x, const CI<T>& w) {
     return r;
 }
 
+// x * w for a real twiddle w = [w.rl, w.rh] (w.il = w.ih = 0, the radix-3
+// and radix-5 scalars cos(2 pi k / R)): 4 directed products.  The same
+// bounds as mul_tw's, without its products by the zero imaginary part.
+template <typename T>
+__device__ __forceinline__ CI<T> mul_real(const CI<T>& x, const CI<T>& w) {
+    Pair<T> r_lo, r_hi, i_lo, i_hi;
+    pick_tw(x.rl, x.rh, w.rl, w.rh, r_lo, r_hi);     // xr * wr
+    pick_tw(x.il, x.ih, w.rl, w.rh, i_lo, i_hi);     // xi * wr
+    return {mul_dn(r_lo.a, r_lo.b), mul_up(r_hi.a, r_hi.b), mul_dn(i_lo.a, i_lo.b),
+            mul_up(i_hi.a, i_hi.b)};
+}
+
+// x * w for a pure imaginary twiddle w = i [w.il, w.ih] (the scalars
+// i sin(2 pi k / R)): x w = -xi wi + i xr wi, 4 directed products
+template <typename T>
+__device__ __forceinline__ CI<T> mul_imag(const CI<T>& x, const CI<T>& w) {
+    Pair<T> a_lo, a_hi, b_lo, b_hi;
+    pick_tw(x.il, x.ih, w.il, w.ih, a_lo, a_hi);     // xi * wi
+    pick_tw(x.rl, x.rh, w.il, w.ih, b_lo, b_hi);     // xr * wi
+    return {flip(mul_up(a_hi.a, a_hi.b)), flip(mul_dn(a_lo.a, a_lo.b)), mul_dn(b_lo.a, b_lo.b),
+            mul_up(b_hi.a, b_hi.b)};
+}
+
 // ---- general real interval product (Section 2.5) -------------------------------
 //
 // [a][b] = [min, max] of the four endpoint products.  The sign classes of

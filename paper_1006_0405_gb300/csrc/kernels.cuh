@@ -512,15 +512,19 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     if (gate && decided_by(d.st, gate)) return;
     const int logN = d.log_n, N = 1 << logN;
     const int bias = d.balanced ? 128 : 0;
+    // the digit pairs as integers (8 bytes each, inside the buffer), then the
+    // forward transform's exact first step (logN >= 2 for every plan length)
+    int2* const si = reinterpret_cast<int2*>(smem_raw);
     stage<4 * BPT, int2>(
         N,
         [&](int j) {
             return make_int2(j < int(d.na) ? int(d.a[j]) - bias : 0,
                              j < int(d.nb) ? int(d.b[j]) - bias : 0);
         },
-        [&](int j, int2 v) { sm[j] = make_point<V>(v.x, v.y); });
+        [&](int j, int2 v) { si[j] = v; });
     __syncthreads();
-    block_fft<V, +1, BPT>(sm, logN, 1, N, tw);
+    first_step_exact<V, BPT, 1, false>(si, N, sm, logN, 1, N, tw);
+    block_fft<V, +1, BPT>(sm, logN, 1, N, tw, true);
     pair_products(sm, 1, 0, logN);
     __syncthreads();
     pack_half(sm, 1, 0, 0, 0, logN, tw);
@@ -549,18 +553,29 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_
     const uint32_t j2_0 = blockIdx.x << logC;
     V* Z = reinterpret_cast<V*>(d.Z);
     const int bias = d.balanced ? 128 : 0;
-    stage<4 * BPT, int2>(
-        C * N1,
-        [&](int idx) {
-            const uint32_t j = (uint32_t(idx >> logC) << logN2) + j2_0 + (idx & (C - 1));
-            return make_int2(j < d.na ? int(d.a[j]) - bias : 0, j < d.nb ? int(d.b[j]) - bias : 0);
-        },
-        [&](int idx, int2 v) {
+    const auto digits = [&](int idx) {
+        const uint32_t j = (uint32_t(idx >> logC) << logN2) + j2_0 + (idx & (C - 1));
+        return make_int2(j < d.na ? int(d.a[j]) - bias : 0, j < d.nb ? int(d.b[j]) - bias : 0);
+    };
+    if (R > 1 || logN1 >= 2) {
+        // the digit pairs as integers, column c at c (N1 + 1) (the odd pitch
+        // spreads the staging stores over the banks; C (N1 + 1) 8 bytes fit
+        // in the buffer), then the exact first radix-4 step
+        int2* const si = reinterpret_cast<int2*>(smem_raw);
+        const int ip = N1 + 1;
+        stage<4 * BPT, int2>(C * N1, digits,
+                             [&](int idx, int2 v) { si[(idx & (C - 1)) * ip + (idx >> logC)] = v; });
+        __syncthreads();
+        first_step_exact<V, BPT, R, (R > 1)>(si, ip, sm, logN1, C, N1, tw);
+        if constexpr (R == 1) block_fft<V, +1, BPT>(sm, logN1, C, N1, tw, true);
+        else block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true);
+    } else {
+        stage<4 * BPT, int2>(C * N1, digits, [&](int idx, int2 v) {
             sm[(idx & (C - 1)) * N1 + (idx >> logC)] = make_point<V>(v.x, v.y);
         });
-    __syncthreads();
-    if constexpr (R == 1) block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
-    else block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw);
+        __syncthreads();
+        block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
+    }
     const int logN = logN1 + logN2;
     for (int idx = threadIdx.x; idx < C * N1; idx += blockDim.x) {
         const int c = idx & (C - 1), k1 = idx >> logC;

@@ -59,11 +59,15 @@ def _centre(row):
             Fr(float(row[4])))
 
 
-@pytest.mark.parametrize("op", [0, 1, 2, 3])
+@pytest.mark.parametrize("op", [0, 1, 2, 3, 7, 8])
 def test_pair_disc_ops_contain_exact_results(op):
+    """ops 7, 8: products by the real and pure imaginary scalar discs of the
+    radix-3 and radix-5 steps (the other centre pair is 0)"""
     rng = np.random.default_rng(70 + op)
     a = _rand(rng, 300)
-    b = _rand(rng, 300, tw=(op == 2))
+    b = _rand(rng, 300, tw=(op in (2, 7, 8)))
+    if op in (7, 8):
+        b[:, [2, 3] if op == 7 else [0, 1]] = 0.0
     out = _op(op, a, b)
     for i in range(0, 300, 3):
         ax, ay, ar = _centre(a[i])

@@ -56,11 +56,16 @@ def _contains(o, re, im):
     return (re - cx) ** 2 + (im - cy) ** 2 <= r * r
 
 
-@pytest.mark.parametrize("op", [0, 1, 2, 3])
+@pytest.mark.parametrize("op", [0, 1, 2, 3, 5, 6])
 def test_disc_ops_contain_exact_results(op):
+    """ops 5, 6: products by the real and pure imaginary scalar discs of the
+    radix-3 and radix-5 steps (the other centre component is 0)"""
     rng = np.random.default_rng(40 + op)
     a = _rand_discs(rng, 400)
-    b = _rand_discs(rng, 400, tw=(op == 2))
+    b = _rand_discs(rng, 400, tw=(op in (2, 5, 6)))
+    if op in (5, 6):
+        b[:, 1 if op == 5 else 0] = 0.0
+        b[:, 2] = (np.abs(b[:, 0 if op == 5 else 1]) * 2.0 ** -50).astype(np.float32)
     out = _disc_op(op, a, b)
     for i in range(0, 400, 3):
         ax, ay, ar = (Fr(float(v)) for v in a[i])

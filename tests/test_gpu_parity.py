@@ -136,6 +136,30 @@ def test_ci_twiddle_product_between_hull_and_paper_formula(f32):
         assert Fr(float(got[i, 2])) <= min(im) and max(im) <= Fr(float(got[i, 3]))
 
 
+@pytest.mark.parametrize("f32", [False, True])
+def test_ci_real_and_imaginary_scalar_products_equal_paper_formula(f32):
+    """The radix-3 and radix-5 steps multiply by real enclosures (cos) and
+    pure imaginary ones (i sin) in 4 directed products: the result must be
+    the paper's interval product (Section 2.5) with the zero part taken as
+    the point 0, bit for bit."""
+    rng = np.random.default_rng(12 + f32)
+    x = _rand_ci(rng, 3000, f32)
+    x[:200, 0] = -np.abs(x[:200, 1]); x[:200, 1] = np.abs(x[:200, 1])       # straddling 0
+    w = _rand_ci(rng, 3000, f32, sign_definite=True)
+    prec = iv.F32 if f32 else iv.F64
+    X = tuple(x[:, k] for k in range(4))
+    for op, keep in ((4, (0, 1)), (5, (2, 3))):
+        wz = w.copy()
+        zero = (2, 3) if op == 4 else (0, 1)
+        wz[:, zero[0]] = 0.0
+        wz[:, zero[1]] = 0.0
+        ok = (wz[:, keep[0]] > 0) | (wz[:, keep[1]] < 0)                   # sign-definite part
+        got = _run_op(op, f32, x, wz)[ok]
+        want = np.stack(iv.ic_mul(X, tuple(wz[:, k] for k in range(4)), prec), axis=1)[ok]
+        assert ok.sum() > 2500
+        assert np.array_equal(got, want), f"op {op}"
+
+
 # ---- end-to-end parity ---------------------------------------------------------
 
 SMALL_SIZES = [(1, 1), (1, 2), (2, 1), (2, 2), (3, 1), (1, 7), (5, 5), (8, 9), (17, 16), (31, 33),
