@@ -69,6 +69,9 @@ def parse():
                     help="skip the extra lines for the other rungs (disc64, naive64)")
     ap.add_argument("--balanced", action="store_true",
                     help="balanced digits (the transforms carry digit - 128)")
+    ap.add_argument("--lengths", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="transform length families besides 2^k (SSMUL_OPT_LENGTHS bit mask: "
+                         "1 = 3 2^k, 2 = 5 2^k)")
     ap.add_argument("--workload", default="paper", choices=["paper", "sweep", "ladder", "uneven", "split"],
                     help="paper: the headline line; sweep / ladder / uneven / split: report "
                          "lines of the size sweep, the precision ladder, the uneven batch and "
@@ -153,13 +156,18 @@ def _fft_odd_ops(R: int, loga: int, nl: int, c: dict, exact_first: bool = False)
     return ops + nl * (L // R) * last
 
 
-def length_code(na: int, nb: int) -> tuple[int, int]:
-    """(R, k): the transform length R 2^k the library picks (default lengths)."""
+LENGTHS = 3          # SSMUL_OPT_LENGTHS of the plans this run makes
+
+
+def length_code(na: int, nb: int, mask: int | None = None) -> tuple[int, int]:
+    """(R, k): the transform length R 2^k the library picks under the
+    length mask (default: this run's)."""
+    mask = LENGTHS if mask is None else mask
     L = na + nb - 1
     k = max(2, (L - 1).bit_length())
-    if 10 <= k - 3 <= 19 and (5 << (k - 3)) >= L:
+    if mask & 2 and 10 <= k - 3 <= 19 and (5 << (k - 3)) >= L:
         return 5, k - 3
-    if 11 <= k - 2 <= 21 and (3 << (k - 2)) >= L:
+    if mask & 1 and 11 <= k - 2 <= 21 and (3 << (k - 2)) >= L:
         return 3, k - 2
     return 1, k
 
@@ -218,8 +226,9 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # kernels changed since.
 NCU_TRAFFIC_PER_PRODUCT = {
     # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
-    "k_rows<double>": (84.642560e6 + 10.915072e6) / 16,
-    "k_rows<disc>": (63.490560e6 + 3.824128e6) / 16,
+    "k_rows<double>": (84.642304e6 + 10.949888e6) / 16,
+    "k_rows<disc>": (63.490304e6 + 3.872256e6) / 16,
+    "k_rows<disc32x2>": (63.301120e6 + 4.766208e6) / 16,
 }
 
 
@@ -410,6 +419,8 @@ def run_ours(args):
     plan = abi.ssmul_plan(n, n, B, prec, stream.cuda_stream)
     if args.balanced:
         abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
+    if args.lengths != 3:
+        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_LENGTHS, args.lengths)
     descs = (abi.ssmul_desc * B)()
     for i in range(B):
         descs[i] = abi.ssmul_desc(int(a_off[i]), int(b_off[i]), int(z_off[i]), n, n)
@@ -511,6 +522,8 @@ def run_ours(args):
             aplan = abi.ssmul_plan(n, n, B, PRECS[alt], stream.cuda_stream)
             if args.balanced:
                 abi.ssmul_plan_set_option(aplan, abi.SSMUL_OPT_BALANCED, 1)
+            if args.lengths != 3:
+                abi.ssmul_plan_set_option(aplan, abi.SSMUL_OPT_LENGTHS, args.lengths)
             with torch.cuda.stream(stream):
                 for _ in range(args.warmup):
                     s_ = abi.ssmul_mul_batched(aplan, descs, da.data_ptr(), db.data_ptr(),
@@ -639,7 +652,9 @@ def run_ours(args):
 
 
 def main():
+    global LENGTHS
     args = parse()
+    LENGTHS = args.lengths
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "paper":

@@ -89,7 +89,9 @@ ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y, 
  * enclosure [h + l - r, h + l + r]; pad != 0 makes it a value past the
  * product's last coefficient, which must contain 0.  path 0: the rung's
  * decision on the binary32 and integer pipes; path 1: the same set bounded
- * in binary64 and decided there.  Outputs (device): d_class[i] = 0
+ * in binary64 and decided there.  paths 2, 3 (4, 5): the same two for a
+ * transform of length 3 2^k (5 2^k), where the set encloses 3 c (5 c) and
+ * the decision is on the set divided by 3 (5).  Outputs (device): d_class[i] = 0
  * isolated (d_value[i] = the integer), 1 not isolated, 2 empty (no
  * integer, a negative one, NaN, a centre beyond 2^53, or for pad rows a
  * set that excludes 0); d_value[i] = 0 otherwise.

@@ -1480,12 +1480,16 @@ __global__ void k_iso_op(int path, const double* x, int64_t* value, int* cls, si
         const int64_t idx = r4[3] != 0.0 ? 1 : 0;
         value[i] = 0;
         IsoAcc acc;
-        if (path == 0) {
-            isolate_pair(h, l, r, idx, d, acc, 4);
-        } else {
-            const double dr = double(r);
-            isolate_one(__dsub_rd(__dadd_rd(double(h), double(l)), dr),
-                        __dadd_ru(__dadd_ru(double(h), double(l)), dr), idx, d, acc, 4);
+        const double dr = double(r);
+        const double lo = __dsub_rd(__dadd_rd(double(h), double(l)), dr);
+        const double hi = __dadd_ru(__dadd_ru(double(h), double(l)), dr);
+        switch (path) {
+            case 0: isolate_pair<1>(h, l, r, idx, d, acc, 4); break;
+            case 1: isolate_one<1>(lo, hi, idx, d, acc, 4); break;
+            case 2: isolate_pair<3>(h, l, r, idx, d, acc, 4); break;
+            case 3: isolate_one<3>(lo, hi, idx, d, acc, 4); break;
+            case 4: isolate_pair<5>(h, l, r, idx, d, acc, 4); break;
+            default: isolate_one<5>(lo, hi, idx, d, acc, 4); break;
         }
         cls[i] = acc.empty ? 2 : (acc.unisolated ? 1 : 0);
     }
@@ -1495,7 +1499,7 @@ __global__ void k_iso_op(int path, const double* x, int64_t* value, int* cls, si
 
 extern "C" ssmul_status ssmul_debug_isolate(int path, const double* d_x, int64_t* d_value,
                                             int* d_class, size_t n) {
-    if (path < 0 || path > 1 || (n && (!d_x || !d_value || !d_class))) return SSMUL_INVALID_ARG;
+    if (path < 0 || path > 5 || (n && (!d_x || !d_value || !d_class))) return SSMUL_INVALID_ARG;
     if (n == 0) return SSMUL_OK;
     const int threads = 256;
     const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);

@@ -254,6 +254,8 @@ template <int R>
 __device__ __forceinline__ long long ceil_div(long long x) { return x / R + (x % R > 0 ? 1 : 0); }
 template <int R>
 __device__ __forceinline__ long long floor_div(long long x) { return x / R - (x % R < 0 ? 1 : 0); }
+template <int R>
+__device__ __forceinline__ int floor_div32(int x) { return x / R - (x % R < 0 ? 1 : 0); }
 
 // RU(1/R) for R = 1, 3, 5 (bit patterns: 1, the successor of RN(1/3), RN(1/5) > 1/5)
 template <int R>
@@ -407,8 +409,13 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
     const long long K = big ? 0ll : int_of_f32(k0) + int_of_f32(k1);
     long long kl = K + cl, kh = K + fh;
     if (R != 1) {
-        kl = ceil_div<R>(kl);
-        kh = floor_div<R>(kh);
+        // [ceil(kl / R), floor(kh / R)] with one 64-bit division: kl = q R + rm
+        // (0 <= rm < R) and kh = kl + (fh - cl), a difference below 2^23 + 2
+        // whenever the set fits (kl and kh decide nothing otherwise)
+        const long long q = floor_div<R>(kl);
+        const int rm = int(kl - q * R);
+        kl = q + (rm > 0 ? 1 : 0);
+        kh = q + floor_div32<R>(rm + (fits ? fh - cl : 0));
     }
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;

@@ -66,8 +66,9 @@ def _pair(c: Fr):
     return h, _f32(float(c - Fr(h)))
 
 
-def _cases(seed: int):
-    """(h, l, r, pad) rows: crafted edges first, then seeded random sets."""
+def _cases(seed: int, R: int = 1):
+    """(h, l, r, pad) rows: crafted edges first, then seeded random sets
+    (R = 3, 5: mostly around R times an integer, radii times R)."""
     rows = [
         (0.0, 0.0, 0.0, 0), (5.0, 0.0, 0.0, 0), (-5.0, 0.0, 0.0, 0), (-5.0, 0.0, 0.1, 0),
         (0.25, 0.0, 0.25, 0), (0.5, 0.0, 0.5, 0), (7.5, 0.0, 0.5, 0), (7.5, 0.0, 0.49, 0),
@@ -84,9 +85,10 @@ def _cases(seed: int):
     for _ in range(4000):
         mag = int(rng.choice([0, 4, 10, 20, 30, 40, 45, 50]))
         k = int(rng.integers(0, 2 ** mag + 1)) * (1 if rng.random() < 0.9 else -1)
-        off = Fr(int(rng.integers(-7000, 7001)), 10000)
+        k *= R if rng.random() < 0.85 else 1
+        off = Fr(int(rng.integers(-7000, 7001)) * R, 10000)
         h, l = _pair(Fr(k) + off)
-        r = _f32(rng.choice(radii) * (1.0 if rng.random() < 0.7 else rng.random()))
+        r = _f32(R * rng.choice(radii) * (1.0 if rng.random() < 0.7 else rng.random()))
         rows.append((h, l, r, int(rng.random() < 0.1)))
     return rows
 
@@ -108,7 +110,8 @@ def _floor(q: Fr) -> int:
     return q.numerator // q.denominator
 
 
-def _check(row, value, cls, slack):
+def _check(row, value, cls, slack, R=1):
+    """R = 3, 5: the set encloses R c, and the decision is on it divided by R"""
     h, l, r, pad = row
     if math.isnan(h) or math.isnan(l) or math.isnan(r) or math.isinf(h) or math.isinf(l):
         assert cls == 2, row
@@ -117,9 +120,9 @@ def _check(row, value, cls, slack):
         assert cls == (0 if pad else 1), row
         return
     c = Fr(h) + Fr(l)
-    lo, hi = c - Fr(r), c + Fr(r)
+    lo, hi = (c - Fr(r)) / R, (c + Fr(r)) / R
     d = Fr(slack(c, r))
-    wlo, whi = lo - d, hi + d                       # the decision's set lies inside this one
+    wlo, whi = lo - d / R, hi + d / R               # the decision's set lies inside this one
     if pad:
         if lo <= 0 <= hi:
             assert cls == 0, row                    # contains 0: never reported empty
@@ -151,13 +154,17 @@ def _slack64(c, r):
     return 2.0 ** -50 * (abs(float(c)) + r + 1.0)
 
 
-def test_pair_disc_isolation_is_sound():
-    rows = _cases(1234)
-    v32, c32 = _run(0, rows)
-    v64, c64 = _run(1, rows)
+@pytest.mark.parametrize("R", [1, 3, 5])
+def test_pair_disc_isolation_is_sound(R):
+    """R = 3, 5: the decisions of the transform lengths 3 2^k and 5 2^k,
+    on sets around R times an integer (and plain ones, mostly empty)"""
+    rows = _cases(1234 + R, R)
+    path = {1: 0, 3: 2, 5: 4}[R]
+    v32, c32 = _run(path, rows)
+    v64, c64 = _run(path + 1, rows)
     for i, row in enumerate(rows):
-        _check(row, int(v32[i]), int(c32[i]), _slack32)
-        _check(row, int(v64[i]), int(c64[i]), _slack64)
+        _check(row, int(v32[i]), int(c32[i]), _slack32, R)
+        _check(row, int(v64[i]), int(c64[i]), _slack64, R)
         if c32[i] == 0 and c64[i] == 0:
             assert v32[i] == v64[i], row
     # the binary32 decision loses only borderline sets to "not isolated"
