@@ -102,9 +102,11 @@ def make_batch(rank: int, batch: int, n: int):
 # 1 per coefficient width) and discs / points (2, 4, 4, 2; isolation of a
 # disc: 2 bounds + 1 width per coefficient)
 COSTS = {
-    # stw: a product by a real or pure imaginary scalar (radix-3, radix-5)
-    "fp64": dict(add=4, bfly=32, tw=8, stw=4, mul=12, scale=4, iso=1),
-    "disc64": dict(add=2, bfly=16, tw=4, stw=2, mul=4, scale=2, iso=3),
+    # stw: a product by a real or pure imaginary scalar (radix-3, radix-5);
+    # scale 0: the rectangles and binary64 discs fold the 1/N scaling into
+    # the isolation's integer conversion
+    "fp64": dict(add=4, bfly=32, tw=8, stw=4, mul=12, scale=0, iso=1),
+    "disc64": dict(add=2, bfly=16, tw=4, stw=2, mul=4, scale=0, iso=3),
     "naive64": dict(add=2, bfly=16, tw=4, stw=2, mul=4, scale=2, iso=0),
     # double-binary32 discs count binary32 operations: a pair sum is TwoSum,
     # two adds and FastTwoSum (11); a complex add is two pair sums and its

@@ -99,6 +99,14 @@ ssmul_status ssmul_debug_ddisc_op(int op, const double* d_x, const double* d_y, 
 ssmul_status ssmul_debug_isolate(int path, const double* d_x, int64_t* d_value, int* d_class,
                                  size_t n);
 
+/*
+ * The exact scaled conversion the isolation uses: d_out[2 i] =
+ * floor(d_x[i] 2^-d_k[i]), d_out[2 i + 1] = ceil(d_x[i] 2^-d_k[i]) for
+ * 0 <= d_k[i] <= 1023 (device arrays, n entries); magnitudes of 2^62 or
+ * more are capped at +-2^62, a NaN gives INT64_MIN for both.
+ */
+ssmul_status ssmul_debug_floor_ceil(const double* d_x, const int* d_k, int64_t* d_out, size_t n);
+
 /* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays):
  * kernel * 5 + rung for the four transform kernels (rungs: 0 F32 and 1 F64
  * rectangles, 2 DISC binary64 discs, 3 NAIVE points, 4 DISC32X2 discs),

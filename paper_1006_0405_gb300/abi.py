@@ -37,7 +37,7 @@ EXPORTS = (
     "ssmul_plan", "ssmul_plan_set_option", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
     "ssmul_plan_destroy", "ssmul_status_string",
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op", "ssmul_debug_disc_op",
-    "ssmul_debug_ddisc_op", "ssmul_debug_isolate",
+    "ssmul_debug_ddisc_op", "ssmul_debug_isolate", "ssmul_debug_floor_ceil",
     "ssmul_debug_kernel_stats", "ssmul_debug_geometry", "ssmul_debug_set_fault",
 )
 
@@ -137,6 +137,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_debug_ddisc_op.restype = st
     L.ssmul_debug_isolate.argtypes = [ctypes.c_int, vp, vp, vp, sz]
     L.ssmul_debug_isolate.restype = st
+    L.ssmul_debug_floor_ceil.argtypes = [vp, vp, vp, sz]
+    L.ssmul_debug_floor_ceil.restype = st
     L.ssmul_debug_kernel_stats.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.ssmul_debug_kernel_stats.restype = st
     _lib = L
@@ -248,6 +250,11 @@ def ssmul_debug_disc_op(op: int, d_x: int, d_y: int, d_out: int, n: int) -> int:
 def ssmul_debug_isolate(path: int, d_x: int, d_value: int, d_class: int, n: int) -> int:
     return load().ssmul_debug_isolate(path, ctypes.c_void_p(d_x), ctypes.c_void_p(d_value),
                                       ctypes.c_void_p(d_class), n)
+
+
+def ssmul_debug_floor_ceil(d_x: int, d_k: int, d_out: int, n: int) -> int:
+    return load().ssmul_debug_floor_ceil(ctypes.c_void_p(d_x), ctypes.c_void_p(d_k),
+                                         ctypes.c_void_p(d_out), n)
 
 
 def ssmul_debug_ddisc_op(op: int, d_x: int, d_y: int, d_out: int, n: int) -> int:

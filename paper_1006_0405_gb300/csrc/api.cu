@@ -1485,17 +1485,37 @@ __global__ void k_iso_op(int path, const double* x, int64_t* value, int* cls, si
         const double hi = __dadd_ru(__dadd_ru(double(h), double(l)), dr);
         switch (path) {
             case 0: isolate_pair<1>(h, l, r, idx, d, acc, 4); break;
-            case 1: isolate_one<1>(lo, hi, idx, d, acc, 4); break;
+            case 1: isolate_one<1>(lo, hi, 0, idx, d, acc, 4); break;
             case 2: isolate_pair<3>(h, l, r, idx, d, acc, 4); break;
-            case 3: isolate_one<3>(lo, hi, idx, d, acc, 4); break;
+            case 3: isolate_one<3>(lo, hi, 0, idx, d, acc, 4); break;
             case 4: isolate_pair<5>(h, l, r, idx, d, acc, 4); break;
-            default: isolate_one<5>(lo, hi, idx, d, acc, 4); break;
+            default: isolate_one<5>(lo, hi, 0, idx, d, acc, 4); break;
         }
         cls[i] = acc.empty ? 2 : (acc.unisolated ? 1 : 0);
     }
 }
 
 }  // namespace
+
+namespace {
+__global__ void k_floor_ceil(const double* x, const int* k, long long* out, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x)
+        floor_ceil_scaled(x[i], k[i], out[2 * i], out[2 * i + 1]);
+}
+}  // namespace
+
+extern "C" ssmul_status ssmul_debug_floor_ceil(const double* d_x, const int* d_k, int64_t* d_out,
+                                               size_t n) {
+    if (n && (!d_x || !d_k || !d_out)) return SSMUL_INVALID_ARG;
+    if (n == 0) return SSMUL_OK;
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024);
+    k_floor_ceil<<<blocks, threads>>>(d_x, d_k, reinterpret_cast<long long*>(d_out), n);
+    SS_TRY(cudaGetLastError());
+    SS_TRY(cudaDeviceSynchronize());
+    return SSMUL_OK;
+}
 
 extern "C" ssmul_status ssmul_debug_isolate(int path, const double* d_x, int64_t* d_value,
                                             int* d_class, size_t n) {

@@ -29,6 +29,8 @@
 //   k_inv_cols  inverse column DFTs of length N1, scaling and isolation
 #pragma once
 #include <cuda_runtime.h>
+#include <climits>
+#include <type_traits>
 #include "../../include/ssmul.h"
 #include "value.cuh"
 #include "fft.cuh"
@@ -247,7 +249,44 @@ struct IsoAcc {
     unsigned int unisolated = 0, empty = 0;
     unsigned long long maxw_bits = 0;   // bit pattern of the largest width (>= 0)
     unsigned int maxw_f32 = 0;          // the same for widths held in binary32
+    int wscale = 0;                     // maxw_bits is of sets 2^wscale times the coefficients'
 };
+
+// floor(x 2^-k) and ceil(x 2^-k) for a binary64 x and 0 <= k <= 1023, exact,
+// on the integer pipe (the scaling by the transform length folded into the
+// conversion, so neither takes a binary64 operation).  Results of magnitude
+// 2^62 or more are capped at +-2^62 (past every value the isolation
+// accepts); a NaN gives INT64_MIN for both.
+__device__ __forceinline__ void floor_ceil_scaled(double x, int k, long long& fl, long long& ce) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (b >> 63) != 0;
+    const int e = int((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) {
+        fl = ce = m ? LLONG_MIN : (neg ? -(1ll << 62) : (1ll << 62));
+        return;
+    }
+    if (e) m |= 1ull << 52;
+    const int sh = (e ? e : 1) - 1075 - k;       // |x| 2^-k = m 2^sh
+    unsigned long long q;
+    bool frac;
+    if (sh >= 0) {
+        q = sh > 9 ? (1ull << 62) : (m << sh);     // m < 2^53
+        frac = false;
+    } else if (sh > -64) {
+        q = m >> -sh;
+        frac = (m & ((1ull << -sh) - 1ull)) != 0ull;
+    } else {
+        q = 0;
+        frac = m != 0ull;
+    }
+    const long long qi = (long long)q, f = frac ? 1 : 0;
+    fl = neg ? -qi - f : qi;
+    ce = neg ? -qi : qi + f;
+}
+
+// 2^k for 0 <= k <= 1023
+__device__ __forceinline__ double pow2_pos(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
 
 // Integer division by R rounded up / down (exact, no overflow).
 template <int R>
@@ -276,19 +315,25 @@ __device__ __forceinline__ double inv_up() {
 // scaling applied only its power of two).  The integers of [lo/R, hi/R] are
 // those of [ceil(kl'/R), floor(kh'/R)] with kl' = ceil(lo), kh' = floor(hi),
 // so the same decision takes two exact integer divisions and no rounding.
+//
+// [lo, hi] 2^-k is the set (k: the power of two of the 1/N scaling, applied
+// here exactly by floor_ceil_scaled; the widths are scaled at flush_acc).
 template <int R = 1, typename T>
-__device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdDesc& d,
+__device__ __forceinline__ void isolate_one(T lo, T hi, int k, int64_t idx, const ProdDesc& d,
                                             IsoAcc& acc, int rung) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
     double dl = double(lo), dh = double(hi);          // exact widening
     if (d.fault_widen == rung + 1) {                  // test fault: still an enclosure
-        dl = __dsub_rd(dl, 4.0 * R);                  // 4 in units of c (the set is of R c)
-        dh = __dadd_ru(dh, 4.0 * R);
+        const double f = 4.0 * R * pow2_pos(k);       // 4 in units of c (the set is of R c)
+        dl = __dsub_rd(dl, f);
+        dh = __dadd_ru(dh, f);
     }
     const unsigned long long wb = (unsigned long long)__double_as_longlong(__dsub_ru(dh, dl));
     acc.maxw_bits = wb > acc.maxw_bits ? wb : acc.maxw_bits;   // widths are >= 0 (or NaN)
-    long long kl = __double2ll_ru(dl);
-    long long kh = __double2ll_rd(dh);
+    acc.wscale = k;
+    long long kl, kh, unused;
+    floor_ceil_scaled(dl, k, unused, kl);
+    floor_ceil_scaled(dh, k, kh, unused);
     if (R != 1) {
         kl = ceil_div<R>(kl);
         kh = floor_div<R>(kh);
@@ -297,8 +342,9 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
     if (idx < L) {
         const int64_t corr = d.balanced ? balance_corr(d, idx) : 0;
         if (d.iv != nullptr) {
-            d.iv[2 * idx] = __dadd_rd(R != 1 ? __ddiv_rd(dl, double(R)) : dl, double(corr));
-            d.iv[2 * idx + 1] = __dadd_ru(R != 1 ? __ddiv_ru(dh, double(R)) : dh, double(corr));
+            const double sl = __dmul_rd(dl, pow2_neg(k)), sh = __dmul_ru(dh, pow2_neg(k));
+            d.iv[2 * idx] = __dadd_rd(R != 1 ? __ddiv_rd(sl, double(R)) : sl, double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(R != 1 ? __ddiv_ru(sh, double(R)) : sh, double(corr));
         }
         int64_t v = 0;
         if (kl == kh && kl > -KMAX && kl < KMAX && kl + corr >= 0) {
@@ -317,6 +363,9 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int64_t idx, const ProdD
 // R = 3, 5: the widths were those of R c; the largest is scaled by RU(1/R)
 template <int R = 1>
 __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
+    if (acc.wscale && acc.maxw_bits)
+        acc.maxw_bits = (unsigned long long)__double_as_longlong(
+            __dmul_ru(__longlong_as_double((long long)acc.maxw_bits), pow2_neg(acc.wscale)));
     if (acc.maxw_f32) {
         // binary32 -> binary64 is exact and keeps the order (NaN stays the largest)
         const unsigned long long w =
@@ -341,20 +390,23 @@ __device__ __forceinline__ void flush_acc(IsoAcc acc, ProdState* st, int rung) {
 
 // Both coefficients carried by one complex value: c_{2j} (real part) and
 // c_{2j+1} (imaginary part).
+// v 2^-k (k: the 1/N scaling's power of two) for the binary64 and binary32
+// rectangles and the binary64 discs, whose bounds are scaled exactly inside
+// the integer conversion
 template <int R = 1, typename T>
-__device__ __forceinline__ void isolate_value(const CI<T>& v, int64_t j, const ProdDesc& d,
+__device__ __forceinline__ void isolate_value(const CI<T>& v, int k, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
     constexpr int RUNG = VTraits<CI<T>>::rung;
-    isolate_one<R>(v.rl, v.rh, 2 * j, d, acc, RUNG);
-    isolate_one<R>(v.il, v.ih, 2 * j + 1, d, acc, RUNG);
+    isolate_one<R>(v.rl, v.rh, k, 2 * j, d, acc, RUNG);
+    isolate_one<R>(v.il, v.ih, k, 2 * j + 1, d, acc, RUNG);
 }
 
 template <int R = 1>
-__device__ __forceinline__ void isolate_value(const Disc& v, int64_t j, const ProdDesc& d,
+__device__ __forceinline__ void isolate_value(const Disc& v, int k, int64_t j, const ProdDesc& d,
                                               IsoAcc& acc) {
     const double r = double(v.r);
-    isolate_one<R>(__dsub_rd(v.x, r), __dadd_ru(v.x, r), 2 * j, d, acc, 2);
-    isolate_one<R>(__dsub_rd(v.y, r), __dadd_ru(v.y, r), 2 * j + 1, d, acc, 2);
+    isolate_one<R>(__dsub_rd(v.x, r), __dadd_ru(v.x, r), k, 2 * j, d, acc, 2);
+    isolate_one<R>(__dsub_rd(v.y, r), __dadd_ru(v.y, r), k, 2 * j + 1, d, acc, 2);
 }
 
 // rint(x) for |x| < 2^23 (x + 2^23 sign(x) has ulp 1), x itself otherwise
@@ -486,6 +538,18 @@ __device__ __forceinline__ void isolate_value(const Pt& v, int64_t j, const Prod
     naive_one<R>(v.y, 2 * j + 1, d, acc);
 }
 
+// v 2^-k isolated: the rectangles and binary64 discs scale inside the
+// integer conversion, the other types by scale_pow2 first
+template <int R, typename V>
+__device__ __forceinline__ void isolate_scaled(const V& v, int k, int64_t j, const ProdDesc& d,
+                                               IsoAcc& acc) {
+    if constexpr (std::is_same<V, CI<double>>::value || std::is_same<V, CI<float>>::value ||
+                  std::is_same<V, Disc>::value)
+        isolate_value<R>(v, k, j, d, acc);
+    else
+        isolate_value<R>(scale_pow2(v, k), j, d, acc);
+}
+
 // Global -> shared staging of `total` elements: a thread issues all of its
 // (up to EPT) loads before its first store, so their latencies overlap.
 template <int EPT, typename T, typename Load, typename Store>
@@ -539,7 +603,7 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     block_fft<V, -1, BPT>(sm, logN - 1, 1, N, tw);
     IsoAcc acc;
     for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x)
-        isolate_value(scale_pow2(sm[j], logN + 2), j, d, acc);
+        isolate_scaled<1>(sm[j], logN + 2, j, d, acc);
     flush_acc(acc, d.st, RUNG);
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
 }
@@ -655,7 +719,7 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_
         const int c = idx & (C - 1), j1 = idx >> logC;
         const int64_t j = (int64_t(j1) << logM2) + j2_0 + c;
         // 1 / (4 N) up to the factor 1/R, which the isolation applies exactly
-        isolate_value<R>(scale_pow2(sm[c * N1 + j1], logN + 2), j, d, acc);
+        isolate_scaled<R>(sm[c * N1 + j1], logN + 2, j, d, acc);
     }
     flush_acc<R>(acc, d.st, RUNG);
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);

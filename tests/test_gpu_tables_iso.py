@@ -146,6 +146,17 @@ def _check(row, value, cls, slack, R=1):
         assert cls == 1, row
 
 
+def _exact_isolated(row, R):
+    """the exact set [c - r, c + r] / R holds exactly one integer, >= 0, and
+    its centre is below 2^52"""
+    h, l, r, pad = row
+    if pad or any(math.isnan(v) or math.isinf(v) for v in (h, l, r)):
+        return False
+    c = Fr(h) + Fr(l)
+    lo, hi = (c - Fr(r)) / R, (c + Fr(r)) / R
+    return _floor(hi) == _ceil(lo) and _ceil(lo) >= 0 and abs(c) < 2 ** 52
+
+
 def _slack32(c, r):
     return 2.0 ** -22 * (1.0 + r)
 
@@ -167,6 +178,48 @@ def test_pair_disc_isolation_is_sound(R):
         _check(row, int(v64[i]), int(c64[i]), _slack64, R)
         if c32[i] == 0 and c64[i] == 0:
             assert v32[i] == v64[i], row
-    # the binary32 decision loses only borderline sets to "not isolated"
-    both = np.sum((c64 == 0) & (c32 == 0))
-    assert both >= 0.99 * np.sum(c64 == 0)
+    # both decide nearly every set that holds exactly one integer (one
+    # multiple of R): the binary32 path works relative to the integer part,
+    # the binary64 bounds of a centre near 2^52 round to the nearest half
+    exact = np.array([_exact_isolated(row, R) for row in rows])
+    assert np.sum(exact & (c32 == 0)) >= 0.99 * np.sum(exact)
+    assert np.sum(exact & (c64 == 0)) >= 0.98 * np.sum(exact)
+
+
+def test_scaled_floor_ceil_exact():
+    """floor and ceil of x 2^-k, the 1/N scaling folded into the isolation's
+    integer conversion: exact for every binary64 class (normal, subnormal,
+    zero of either sign, huge, inf, NaN)"""
+    rng = np.random.default_rng(99)
+    n = 6000
+    mant = rng.uniform(1.0, 2.0, n) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    ex = rng.integers(-80, 80, n)
+    x = np.ldexp(mant, ex)
+    k = rng.integers(0, 64, n).astype(np.int32)
+    # integers and half-integers after scaling, ties, and the special classes
+    x[:400] = np.ldexp(np.round(x[:400]), k[:400].astype(int))
+    x[400:800] = np.ldexp(np.floor(x[400:800]) + 0.5, k[400:800].astype(int))
+    special = [0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, -1e-310, 1.0, -1.0,
+               2.0 ** 52, 2.0 ** 53 + 2, -(2.0 ** 61), 2.0 ** 62, 2.0 ** 70, -(2.0 ** 80),
+               1.7976931348623157e308, math.inf, -math.inf, math.nan]
+    x[800:800 + len(special)] = special
+    k[800:800 + len(special)] = [0, 0, 0, 3, 1, 5, 0, 0, 0, 0, 0, 0, 0, 0, 1023, 0, 0, 0]
+    x[900:910] = [3.0] * 10
+    k[900:910] = [0, 1, 2, 60, 61, 62, 63, 64, 100, 1023]
+    dx = dev(x)
+    dk = torch.from_numpy(k).cuda()
+    out = torch.zeros(2 * n, dtype=torch.int64, device="cuda")
+    assert abi.ssmul_debug_floor_ceil(dx.data_ptr(), dk.data_ptr(), out.data_ptr(), n) == OK
+    o = out.cpu().numpy().reshape(n, 2)
+    cap = 2 ** 62
+    for i in range(n):
+        if math.isnan(x[i]):
+            assert o[i, 0] == o[i, 1] == -(2 ** 63)
+            continue
+        if math.isinf(x[i]):
+            assert o[i, 0] == o[i, 1] == (cap if x[i] > 0 else -cap)
+            continue
+        q = Fr(float(x[i])) / 2 ** int(k[i])
+        fl, ce = _floor(q), _ceil(q)
+        want = (max(-cap, min(cap, fl)), max(-cap, min(cap, ce)))
+        assert (int(o[i, 0]), int(o[i, 1])) == want, (i, x[i], k[i])
