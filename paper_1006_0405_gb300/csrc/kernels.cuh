@@ -189,10 +189,22 @@ __global__ void k_prefix_tiles(const ProdDesc* descs) {
 // true when a rung in `mask` (bit r: rung r) already decided this product:
 // it ran and either isolated every coefficient or found an empty set
 __device__ __forceinline__ bool decided_by(const ProdState* st, int mask) {
+    // every field read up front and combined without branches, so the loads
+    // go out together (short-circuit tests through the pointer would chain
+    // them, and a launch whose products are all decided pays that chain in
+    // every one of its CTAs)
+    unsigned int ran[RUNGS], uni[RUNGS], emp[RUNGS];
+#pragma unroll
+    for (int r = 0; r < RUNGS; ++r) {
+        ran[r] = st->ran[r];
+        uni[r] = st->unisolated[r];
+        emp[r] = st->empty[r];
+    }
+    bool dec = false;
+#pragma unroll
     for (int r = 0; r < RUNGS; ++r)
-        if (((mask >> r) & 1) && st->ran[r] && (st->unisolated[r] == 0 || st->empty[r] != 0))
-            return true;
-    return false;
+        dec |= (((mask >> r) & 1) != 0) & (ran[r] != 0u) & ((uni[r] == 0u) | (emp[r] != 0u));
+    return dec;
 }
 
 // kernel template argument -> value type: float and double name the inf-sup
