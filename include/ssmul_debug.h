@@ -110,11 +110,12 @@ ssmul_status ssmul_debug_floor_ceil(const double* d_x, const int* d_k, int64_t* 
 /* Kernel kinds counted by ssmul_debug_kernel_stats (index into its arrays):
  * kernel * 5 + rung for the four transform kernels (rungs: 0 F32 and 1 F64
  * rectangles, 2 DISC binary64 discs, 3 NAIVE points, 4 DISC32X2 discs),
- * then the carry, the finalisation and the balanced-digit prefix sums. */
+ * then the carry, the finalisation, the balanced-digit prefix sums and the
+ * ladder's lists of the products a later rung still runs. */
 enum {
     SSMUL_K_SMALL = 0, SSMUL_K_FWD_COLS = 5, SSMUL_K_ROWS = 10, SSMUL_K_INV_COLS = 15,
-    SSMUL_K_CARRY = 20, SSMUL_K_FINALIZE = 21, SSMUL_K_PREFIX = 22,
-    SSMUL_KERNEL_KINDS = 23
+    SSMUL_K_CARRY = 20, SSMUL_K_FINALIZE = 21, SSMUL_K_PREFIX = 22, SSMUL_K_GATE = 23,
+    SSMUL_KERNEL_KINDS = 24
 };
 
 /*

@@ -52,7 +52,7 @@ SSMUL_OPT_LENGTHS = 5
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")
                      for r in ("float", "double", "disc", "naive", "disc32x2")) + (
-    "k_carry", "k_finalize", "k_prefix")
+    "k_carry", "k_finalize", "k_prefix", "k_gate_list")
 
 
 class ssmul_result(ctypes.Structure):

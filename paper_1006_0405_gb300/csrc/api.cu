@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -254,6 +255,8 @@ struct ssmul_plan_s {
     size_t flags_per_product = 0;
     ProdState* st = nullptr;            // max(1, max_products) entries
     ProdDesc* d_desc = nullptr;         // max(1, max_products) entries
+    int* gate_list = nullptr;           // 1 + max(1, max_products) entries (k_gate_list)
+    int sms = 1;                        // streaming multiprocessors of the device
     ssmul_result* d_res = nullptr;
     ProdDesc* h_desc = nullptr;         // pinned
     ssmul_result* h_res = nullptr;      // pinned
@@ -333,72 +336,110 @@ struct LaunchScope {
 
 template <typename W> constexpr int kind_off() { return VTraits<typename ValOf<W>::type>::rung; }
 
+// the rungs a ladder can run after another one (binary32 rectangles and
+// the naive points are only ever first), which also get the LIST kernels
 template <typename T>
-ssmul_status set_smem_attrs() {
+constexpr bool gateable() {
+    return !std::is_same<T, float>::value && !std::is_same<T, Pt>::value;
+}
+
+template <typename T, bool LIST>
+ssmul_status set_smem_attrs_as() {
     constexpr int B = plan_bpt<typename ValOf<T>::type>();
     const int big = 160 * 1024;
-    SS_TRY(cudaFuncSetAttribute(k_small<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_rows<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    SS_TRY(cudaFuncSetAttribute(k_small<T, B, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 1, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 1, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 1, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 3, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 3, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 3, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_fwd_cols<T, B, 5, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_rows<T, B, 5, LIST>, a, big));
+    SS_TRY(cudaFuncSetAttribute(k_inv_cols<T, B, 5, LIST>, a, big));
     return SSMUL_OK;
 }
 
-// The three four-step launches of one transform length of family R.
-template <typename T, int R>
-void enqueue_four_step(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g, int gate,
-                       const TwTable& tw) {
+template <typename T>
+ssmul_status set_smem_attrs() {
+    ssmul_status s = set_smem_attrs_as<T, false>();
+    if constexpr (gateable<T>()) {
+        if (s == SSMUL_OK) s = set_smem_attrs_as<T, true>();
+    }
+    return s;
+}
+
+
+// The three four-step launches of one transform length of family R, one CTA
+// row per product (LIST: per entry of list, a gated rung's products).
+template <typename T, int R, bool LIST>
+void enqueue_four_step(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
+                       const int* list, const TwTable& tw) {
     using V = typename ValOf<T>::type;
     constexpr int B = plan_bpt<V>();
     const int ko = kind_off<T>();
     const int n1 = R << g.log_n1, n2 = 1 << g.log_n2;
     const int e1 = n1 << g.log_c1, e3 = n1 << g.log_c3;
+    const int t1 = n2 >> g.log_c1, t2 = n1 / 2 + 1, t3 = (n2 / 2) >> g.log_c3;
     {
         LaunchScope ls(p, SSMUL_K_FWD_COLS + ko);
-        k_fwd_cols<T, B, R><<<dim3(n2 >> g.log_c1, count), fft_threads<V>(e1), e1 * sizeof(V),
-                              p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, g.log_c1, gate);
+        k_fwd_cols<T, B, R, LIST><<<dim3(t1, count),
+                                    fft_threads<V>(e1), e1 * sizeof(V), p->stream>>>(
+            d_desc, tw, g.log_n1, g.log_n2, g.log_c1, list);
     }
     {
         LaunchScope ls(p, SSMUL_K_ROWS + ko);
-        k_rows<T, B, R><<<dim3(n1 / 2 + 1, count), fft_threads<V>(2 * n2), 2 * n2 * sizeof(V),
-                          p->stream>>>(d_desc, tw, g.log_n1, g.log_n2, gate);
+        k_rows<T, B, R, LIST><<<dim3(t2, count),
+                                fft_threads<V>(2 * n2), 2 * n2 * sizeof(V), p->stream>>>(
+            d_desc, tw, g.log_n1, g.log_n2, list);
     }
     {
         LaunchScope ls(p, SSMUL_K_INV_COLS + ko);
-        k_inv_cols<T, B, R><<<dim3((n2 / 2) >> g.log_c3, count), fft_threads<V>(e3),
-                              e3 * sizeof(V), p->stream>>>(d_desc, tw, g.log_n1, g.log_n2,
-                                                           g.log_c3, gate);
+        k_inv_cols<T, B, R, LIST><<<dim3(t3, count),
+                                    fft_threads<V>(e3), e3 * sizeof(V), p->stream>>>(
+            d_desc, tw, g.log_n1, g.log_n2, g.log_c3, list);
     }
 }
 
-// Enqueue the interval convolution of `count` products that share one
-// transform length, described by d_desc[0 .. count).  gate: skip products
-// the binary32 rung already decided.
-template <typename T>
-ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
-                          int gate) {
+template <typename T, bool LIST>
+ssmul_status enqueue_rung_as(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
+                             const int* list) {
     using V = typename ValOf<T>::type;
     constexpr int B = plan_bpt<V>();
-    const TwTable tw = p->tw();
     const int ko = kind_off<T>();
     if (g.small) {
         const int n = 1 << g.log_n;
         LaunchScope ls(p, SSMUL_K_SMALL + ko);
-        k_small<T, B><<<count, fft_threads<V>(n), n * sizeof(V), p->stream>>>(d_desc, tw, gate);
+        k_small<T, B, LIST><<<count, fft_threads<V>(n), n * sizeof(V),
+                              p->stream>>>(d_desc, p->tw(), list);
     } else if (g.r == 3) {
-        enqueue_four_step<T, 3>(p, d_desc, count, g, gate, p->tw(1));
+        enqueue_four_step<T, 3, LIST>(p, d_desc, count, g, list, p->tw(1));
     } else if (g.r == 5) {
-        enqueue_four_step<T, 5>(p, d_desc, count, g, gate, p->tw(2));
+        enqueue_four_step<T, 5, LIST>(p, d_desc, count, g, list, p->tw(2));
     } else {
-        enqueue_four_step<T, 1>(p, d_desc, count, g, gate, tw);
+        enqueue_four_step<T, 1, LIST>(p, d_desc, count, g, list, p->tw());
     }
     return cuda_status(cudaGetLastError());
+}
+
+// Enqueue the interval convolution of `count` products that share one
+// transform length, described by d_desc[0 .. count).  gate: skip products
+// an earlier rung in this bit mask already decided (k_gate_list lists the
+// others, and the rung's kernels run over that list).
+template <typename T>
+ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, const Geom& g,
+                          int gate) {
+    if (!gate) return enqueue_rung_as<T, false>(p, d_desc, count, g, nullptr);
+    if constexpr (gateable<T>()) {
+        {
+            LaunchScope ls(p, SSMUL_K_GATE);
+            k_gate_list<<<1, 256, 0, p->stream>>>(d_desc, count, gate, p->gate_list);
+        }
+        return enqueue_rung_as<T, true>(p, d_desc, count, g, p->gate_list);
+    } else {
+        return SSMUL_INVALID_ARG;          // never gated (see gateable)
+    }
 }
 
 bool fp32_eligible(ssmul_plan_t p, size_t na, size_t nb, int log_n) {
@@ -1022,6 +1063,7 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->flags);
     cudaFree(p->st);
     cudaFree(p->d_desc);
+    cudaFree(p->gate_list);
     cudaFree(p->d_res);
     cudaFree(p->stage);
     cudaFree(p->pre);
@@ -1062,6 +1104,8 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
         return e;
     };
     if (cudaGetDevice(&p->device) != cudaSuccess) return fail(SSMUL_CUDA_ERROR);
+    if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+        return fail(SSMUL_CUDA_ERROR);
     p->stream = static_cast<cudaStream_t>(cuda_stream);
     p->prec = prec;
     p->max_na = max_na;
@@ -1101,6 +1145,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (e == cudaSuccess) e = cudaMalloc(&p->flags, slots * p->flags_per_product * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->st, slots * sizeof(ProdState));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, slots * sizeof(ProdDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&p->gate_list, (slots + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_res, slots * sizeof(ssmul_result));
     if (e == cudaSuccess) e = cudaMalloc(&p->stage, 2 * (max_na + max_nb));
     if (e == cudaSuccess) e = cudaMalloc(&p->pre, pre_bytes(max_na, max_nb));
@@ -1675,7 +1720,7 @@ extern "C" ssmul_status ssmul_mul_noalloc(const uint8_t* d_a, size_t na, const u
     const int n = 1 << d.log_n;
 
     k_noalloc_init<<<1, 64, 0, stream>>>(d, base);
-    k_small<double><<<1, threads_for(n), n * sizeof(CI<double>), stream>>>(slot, tw, 0);
+    k_small<double><<<1, threads_for(n), n * sizeof(CI<double>), stream>>>(slot, tw, nullptr);
     k_carry<<<unsigned(carry_tiles(na + nb)), CARRY_THREADS, 0, stream>>>(slot);
     k_finalize<<<1, 256, 0, stream>>>(slot);
     SS_TRY(cudaGetLastError());

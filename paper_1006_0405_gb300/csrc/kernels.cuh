@@ -207,6 +207,21 @@ __device__ __forceinline__ bool decided_by(const ProdState* st, int mask) {
     return dec;
 }
 
+// The products of a batch that a later rung of the ladder still has to run:
+// list[0] = n, list[1 .. n] their indices into descs (any order).  CTA row
+// y of the rung's kernels runs product list[1 + y]; rows y >= n end after
+// reading list[0], one load that every CTA shares, where a test of the
+// product's own state would take two dependent loads.  One CTA.
+__global__ void k_gate_list(const ProdDesc* descs, int count, int mask, int* list) {
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x)
+        if (!decided_by(descs[i].st, mask)) list[1 + atomicAdd(&s_n, 1)] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) list[0] = s_n;
+}
+
 // kernel template argument -> value type: float and double name the inf-sup
 // rectangles, Disc and Pt themselves
 template <typename W> struct ValOf { using type = W; };
@@ -582,17 +597,16 @@ __device__ __forceinline__ void stage(int total, Load load, Store store) {
 
 // ---- k_small: the whole interval convolution of one product in one CTA -----
 
-// gate: bit mask of rungs whose decision makes this rung skip the product;
-// BPT: radix-4 butterflies per thread in block_fft (the launch gives
+// One product per CTA (descs[blockIdx.x]), or with LIST the CTA's entry of
+// the products a later rung of the ladder still runs (k_gate_list).  BPT:
+// radix-4 butterflies per thread in block_fft (the launch gives
 // nl * L / (4 BPT) threads)
-template <typename Tag, int BPT = 2>
-__global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
+template <typename Tag, int BPT>
+__device__ __forceinline__ void small_one(const ProdDesc d, const TwTable& tw) {
     using V = typename ValOf<Tag>::type;
     constexpr int RUNG = VTraits<V>::rung;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
-    const ProdDesc d = descs[blockIdx.x];
-    if (gate && decided_by(d.st, gate)) return;
     const int logN = d.log_n, N = 1 << logN;
     const int bias = d.balanced ? 128 : 0;
     // the digit pairs as integers (8 bytes each, inside the buffer), then the
@@ -620,18 +634,26 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, int gate) {
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
 }
 
+template <typename Tag, int BPT = 2, bool LIST = false>
+__global__ void k_small(const ProdDesc* descs, TwTable tw, const int* list) {
+    if constexpr (LIST) {
+        // rows past the list's length have nothing to do: they end after one load
+        if (int(blockIdx.x) < list[0]) small_one<Tag, BPT>(descs[list[1 + blockIdx.x]], tw);
+    } else {
+        small_one<Tag, BPT>(descs[blockIdx.x], tw);
+    }
+}
+
 // ---- four-step kernels --------------------------------------------------------
 
 // R: 1, 3 or 5 for N = R 2^k; N1 = R 2^logN1 (logN1 even when R > 1),
 // N2 = 2^logN2, and tw is the twiddle table of family R.
-template <typename Tag, int BPT = 2, int R = 1>
-__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
-                           int gate) {
+template <typename Tag, int BPT, int R>
+__device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw, int logN1,
+                                             int logN2, int logC) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
-    const ProdDesc d = descs[blockIdx.y];
-    if (gate && decided_by(d.st, gate)) return;
     const int N1 = R << logN1, C = 1 << logC;
     const uint32_t j2_0 = blockIdx.x << logC;
     V* Z = reinterpret_cast<V*>(d.Z);
@@ -670,13 +692,23 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_fwd_
     }
 }
 
-template <typename Tag, int BPT = 2, int R = 1>
-__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_rows) k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int gate) {
+template <typename Tag, int BPT = 2, int R = 1, bool LIST = false>
+__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols)
+k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC, const int* list) {
+    if constexpr (LIST) {
+        // rows past the list's length have nothing to do: they end after one load
+        if (int(blockIdx.y) < list[0]) fwd_cols_one<Tag, BPT, R>(descs[list[1 + blockIdx.y]], tw, logN1, logN2, logC);
+    } else {
+        fwd_cols_one<Tag, BPT, R>(descs[blockIdx.y], tw, logN1, logN2, logC);
+    }
+}
+
+template <typename Tag, int BPT, int R>
+__device__ __forceinline__ void rows_one(const ProdDesc d, const TwTable& tw, int logN1,
+                                         int logN2) {
     using V = typename ValOf<Tag>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
-    const ProdDesc d = descs[blockIdx.y];
-    if (gate && decided_by(d.st, gate)) return;
     const int N1 = R << logN1, N2 = 1 << logN2, M2 = N2 >> 1;
     const int k1 = blockIdx.x;                              // 0 .. N1/2
     const int k1b = k1 ? N1 - k1 : 0;
@@ -705,15 +737,24 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_rows) k_rows
     }
 }
 
-template <typename Tag, int BPT = 2, int R = 1>
-__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC,
-                           int gate) {
+template <typename Tag, int BPT = 2, int R = 1, bool LIST = false>
+__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_rows)
+k_rows(const ProdDesc* descs, TwTable tw, int logN1, int logN2, const int* list) {
+    if constexpr (LIST) {
+        // rows past the list's length have nothing to do: they end after one load
+        if (int(blockIdx.y) < list[0]) rows_one<Tag, BPT, R>(descs[list[1 + blockIdx.y]], tw, logN1, logN2);
+    } else {
+        rows_one<Tag, BPT, R>(descs[blockIdx.y], tw, logN1, logN2);
+    }
+}
+
+template <typename Tag, int BPT, int R>
+__device__ __forceinline__ void inv_cols_one(const ProdDesc d, const TwTable& tw, int logN1,
+                                             int logN2, int logC) {
     using V = typename ValOf<Tag>::type;
     constexpr int RUNG = VTraits<V>::rung;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
-    const ProdDesc d = descs[blockIdx.y];
-    if (gate && decided_by(d.st, gate)) return;
     const int N1 = R << logN1, C = 1 << logC;
     const int logM2 = logN2 - 1;
     const uint32_t j2_0 = blockIdx.x << logC;
@@ -735,6 +776,17 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols) k_inv_
     }
     flush_acc<R>(acc, d.st, RUNG);
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
+}
+
+template <typename Tag, int BPT = 2, int R = 1, bool LIST = false>
+__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols)
+k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC, const int* list) {
+    if constexpr (LIST) {
+        // rows past the list's length have nothing to do: they end after one load
+        if (int(blockIdx.y) < list[0]) inv_cols_one<Tag, BPT, R>(descs[list[1 + blockIdx.y]], tw, logN1, logN2, logC);
+    } else {
+        inv_cols_one<Tag, BPT, R>(descs[blockIdx.y], tw, logN1, logN2, logC);
+    }
 }
 
 // ---- the decision of a product ---------------------------------------------
