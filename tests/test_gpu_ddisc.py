@@ -239,3 +239,22 @@ def test_pair_sum_exact_renormalisation_under_cancellation(op):
         assert _f32(_f32(zh) + _f32(zl)) == _f32(zh)
         exact = Fr(float(xh[i])) + Fr(float(xl[i])) + Fr(sgn) * (Fr(float(yh[i])) + Fr(float(yl[i])))
         assert abs(exact - Fr(float(zh)) - Fr(float(zl))) <= Fr(float(out[i, 4])), i
+
+
+def test_fast_ladder_escalates_part_of_one_length_group():
+    """One transform length, some products escalating and some not: at 2^19
+    digits the pair discs fail uniform operands and isolate all-0xFF ones,
+    so the binary64 disc rung runs a list holding only the uniform products
+    (the list's order is free; each product must come out exact under its
+    own rung)."""
+    n = 1 << 19
+    dists = ["uniform", "ff", "uniform", "ff", "ff", "uniform"]
+    pairs = [synth.operand_pair(synth.SEED_BASE + 950 + i, n, n, d) for i, d in enumerate(dists)]
+    with Plan(n, n, len(pairs), abi.SSMUL_PREC_LADDER_FAST) as p:
+        s, res, digits = batched(p, pairs)
+    assert s == OK
+    for (a, b), r, z, d in zip(pairs, res, digits, dists):
+        assert r.status == OK, abi.status_string(r.status)
+        want = abi.SSMUL_PREC_DISC32X2 if d == "ff" else abi.SSMUL_PREC_DISC64
+        assert r.precision_used == want, (d, r.precision_used)
+        assert np.array_equal(z, E.product(a, b))
