@@ -864,7 +864,7 @@ __device__ __forceinline__ uint32_t digit_byte_sum_s(const int64_t* sc, int rel)
     return u;
 }
 
-__global__ void __launch_bounds__(CARRY_THREADS) k_carry(const ProdDesc* descs) {
+__global__ void __launch_bounds__(CARRY_THREADS, 4) k_carry(const ProdDesc* descs) {
     // coefficients of the tile (later reused for its output digits) and the
     // byte sums u_k, padded by one entry per 16 so that a thread's 16
     // consecutive entries fall into distinct banks
