@@ -121,6 +121,9 @@ COSTS = {
     "disc32x2": dict(add=28, bfly=189, tw=55, stw=19, mul=60, scale=6, iso=12),
 }
 TAGS = {"fp64": "double", "disc64": "disc", "naive64": "naive", "disc32x2": "disc32x2"}
+SETS = {"fp64": "binary64 inf-sup intervals", "disc64": "binary64 midpoint-radius discs",
+        "naive64": "unverified binary64 points", "disc32x2": "double-binary32 midpoint-radius discs",
+        "ladder_fast": "ladder of double-binary32 then binary64 discs"}
 
 
 def _fft_ops(logL: int, nl: int, c: dict, exact_first: bool = False) -> int:
@@ -633,8 +636,7 @@ def run_ours(args):
             "precision": args.precision,
             "balanced_digits": bool(args.balanced),
             "data": "synthetic",
-            "config": {"workload": f"{n}x{n} base-256 digits, "
-                                   f"{ {'fp64': 'binary64 inf-sup intervals', 'disc64': 'binary64 midpoint-radius discs', 'naive64': 'unverified binary64 points', 'disc32x2': 'double-binary32 midpoint-radius discs', 'ladder_fast': 'ladder of double-binary32 then binary64 discs'}[args.precision]}, "
+            "config": {"workload": f"{n}x{n} base-256 digits, {SETS[args.precision]}, "
                                    f"FFT length {fft_len_str(n)}; batch of {B} per step ({B - 1} uniform "
                                    f"random, 1 all-0xFF) per GPU",
                        "batch_per_gpu": B, "digits": n, "precision": args.precision,

@@ -161,8 +161,9 @@ __device__ __forceinline__ DDisc centre_sub(const DDisc& a, const DDisc& b) {
 
 template <int SIGN>
 __device__ __forceinline__ void bfly4_dd(DDisc& a, DDisc& b, DDisc& c, DDisc& d) {
-    const float m = __fadd_ru(__fadd_ru(__fadd_ru(fabsf(a.xh), fabsf(a.yh)), __fadd_ru(fabsf(b.xh), fabsf(b.yh))),
-                              __fadd_ru(__fadd_ru(fabsf(c.xh), fabsf(c.yh)), __fadd_ru(fabsf(d.xh), fabsf(d.yh))));
+    const float mab = __fadd_ru(__fadd_ru(fabsf(a.xh), fabsf(a.yh)), __fadd_ru(fabsf(b.xh), fabsf(b.yh)));
+    const float mcd = __fadd_ru(__fadd_ru(fabsf(c.xh), fabsf(c.yh)), __fadd_ru(fabsf(d.xh), fabsf(d.yh)));
+    const float m = __fadd_ru(mab, mcd);
     const float rs = __fadd_ru(__fadd_ru(a.r, b.r), __fadd_ru(c.r, d.r));
     const float r = __fmaf_ru(DD_BFLY, m, __fadd_ru(rs, 6.f * DD_ETA));
     const DDisc apc = centre_add(a, c), amc = centre_sub(a, c);

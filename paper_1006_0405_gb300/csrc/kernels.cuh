@@ -313,7 +313,9 @@ __device__ __forceinline__ void floor_ceil_scaled(double x, int k, long long& fl
 }
 
 // 2^k for 0 <= k <= 1023
-__device__ __forceinline__ double pow2_pos(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+__device__ __forceinline__ double pow2_pos(int k) {
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
 
 // Integer division by R rounded up / down (exact, no overflow).
 template <int R>
@@ -697,7 +699,8 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols)
 k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC, const int* list) {
     if constexpr (LIST) {
         // rows past the list's length have nothing to do: they end after one load
-        if (int(blockIdx.y) < list[0]) fwd_cols_one<Tag, BPT, R>(descs[list[1 + blockIdx.y]], tw, logN1, logN2, logC);
+        if (int(blockIdx.y) < list[0])
+            fwd_cols_one<Tag, BPT, R>(descs[list[1 + blockIdx.y]], tw, logN1, logN2, logC);
     } else {
         fwd_cols_one<Tag, BPT, R>(descs[blockIdx.y], tw, logN1, logN2, logC);
     }
@@ -783,7 +786,8 @@ __global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols)
 k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC, const int* list) {
     if constexpr (LIST) {
         // rows past the list's length have nothing to do: they end after one load
-        if (int(blockIdx.y) < list[0]) inv_cols_one<Tag, BPT, R>(descs[list[1 + blockIdx.y]], tw, logN1, logN2, logC);
+        if (int(blockIdx.y) < list[0])
+            inv_cols_one<Tag, BPT, R>(descs[list[1 + blockIdx.y]], tw, logN1, logN2, logC);
     } else {
         inv_cols_one<Tag, BPT, R>(descs[blockIdx.y], tw, logN1, logN2, logC);
     }
