@@ -315,3 +315,17 @@ def test_large_products_residues(na, nb):
     assert np.array_equal(z, E.carry(E.conv_ntt(a, b), na + nb))
     for q in (2**61 - 1, 1_000_000_007):
         assert E.residue(z, q) == E.residue(a, q) * E.residue(b, q) % q
+
+
+def test_largest_plan_size_discs_and_empty_batch():
+    """The largest transform the plans support (2^22 x 2^22 digits, N = 2^23)
+    under the binary64 discs, which isolate it: bit-exact; and a batched call
+    with no products is a no-op that succeeds."""
+    n = 1 << 22
+    a, b = _pair(4242, n, n)
+    with Plan(n, n, 4, abi.SSMUL_PREC_DISC64) as p:
+        s, r, z = p.mul(a, b)
+        assert s == OK, abi.status_string(s)
+        assert (r.fft_odd, r.fft_log2) == (1, 23)
+        assert np.array_equal(z, E.carry(E.conv_ntt(a, b), 2 * n))
+        assert abi.ssmul_mul_batched(p.h, [], 0, 0, 0, 0) == OK
