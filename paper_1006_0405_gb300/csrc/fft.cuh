@@ -43,16 +43,64 @@ __device__ __forceinline__ void bfly4(V& a, V& b, V& c, V& d) {
     }
 }
 
+// The last step of a line of odd log2 length L >= 8 in radix 8 (n = 8,
+// s = L/8, p = 0, so no step twiddles): y[q + s u] = sum_t x[q + s t]
+// omega_8^{SIGN t u}, evaluated as the 4-point DFTs of a_t = x_t + x_{t+4}
+// (outputs u = 0, 2, 4, 6) and of b_t = (x_t - x_{t+4}) omega_8^{SIGN t}
+// (outputs u = 1, 3, 5, 7), omega_8^{2 SIGN} = SIGN i being exact.  It
+// replaces the radix-4 step at n = 8 and the radix-2 step after it: one
+// pass over shared memory instead of two.  Each thread owns the eight
+// slots it reads and writes.
+template <typename V, int SIGN, int R>
+__device__ void radix8_last(SBuf<V> buf, int logL, int nl, int pitch, const TwTable& tw) {
+    const int logs = logL - 3, s = 1 << logs;
+    const int nbf = nl << logs;
+    const uint32_t j8 = uint32_t(R) << (tw.log_n - 3);       // omega_Ntab^j8 = omega_8
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+        const int x = (b >> logs) * pitch + (b & (s - 1));
+        V a0 = buf[x], a1 = buf[x + s], a2 = buf[x + 2 * s], a3 = buf[x + 3 * s];
+        V c0 = buf[x + 4 * s], c1 = buf[x + 5 * s], c2 = buf[x + 6 * s], c3 = buf[x + 7 * s];
+        const V d0 = a0 - c0, d1 = a1 - c1, d2 = a2 - c2, d3 = a3 - c3;
+        a0 = a0 + c0;
+        a1 = a1 + c1;
+        a2 = a2 + c2;
+        a3 = a3 + c3;
+        bfly4<V, SIGN>(a0, a1, a2, a3);
+        buf[x] = a0;
+        buf[x + 2 * s] = a1;
+        buf[x + 4 * s] = a2;
+        buf[x + 6 * s] = a3;
+        c0 = d0;
+        c1 = mul_tw(d1, get_twiddle<V, SIGN, R>(tw, j8));
+        c2 = SIGN > 0 ? mul_i(d2) : mul_negi(d2);
+        c3 = mul_tw(d3, get_twiddle<V, SIGN, R>(tw, 3u * j8));
+        bfly4<V, SIGN>(c0, c1, c2, c3);
+        buf[x + s] = c0;
+        buf[x + 3 * s] = c1;
+        buf[x + 5 * s] = c2;
+        buf[x + 7 * s] = c3;
+    }
+    __syncthreads();
+}
+
+// the value types whose odd-length lines end with radix8_last (the pair
+// discs, whose kernels are issue-bound: one pass less pays; the binary64
+// types would spill the eight values under their register caps)
+template <typename V>
+__host__ __device__ constexpr bool last_radix8() { return std::is_same<V, DDisc>::value; }
+
 // R: the family of the twiddle table tw (the line length is 2^logL either way).
 // skip_first: the first radix-4 step (n = L) is done already
-// (first_step_exact), so the steps start at n = L / 4, s = 4.
-template <typename V, int SIGN, int BPT = 2, int R = 1>
+// (first_step_exact), so the steps start at n = L / 4, s = 4.  LAST8: an
+// odd-length line of a last_radix8 type ends with radix8_last.
+template <typename V, int SIGN, int BPT = 2, int R = 1, bool LAST8 = true>
 __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTable& tw,
                           bool skip_first = false) {
     const int L = 1 << logL;
     const int quarter_log = logL - 2;
     int logn = skip_first ? logL - 2 : logL, logs = skip_first ? 2 : 0;
-    while (logn >= 2) {
+    const int stop = (LAST8 && last_radix8<V>() && (logL & 1) && logL >= 3) ? 3 : 1;
+    while (logn > stop) {
         const int m = 1 << (logn - 2);          // n / 4
         const int s = 1 << logs;
         const int nbf = nl << (logL - 2);       // butterflies in this step
@@ -93,7 +141,9 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
         logn -= 2;
         logs += 2;
     }
-    if (logn == 1) {
+    if (logn == 3 && stop == 3) {
+        radix8_last<V, SIGN, R>(buf, logL, nl, pitch, tw);
+    } else if (logn == 1) {
         // final radix-2 step: n = 2, s = L/2, no twiddle
         const int half = L >> 1;
         const int nbf = nl * half;

@@ -623,12 +623,14 @@ __device__ __forceinline__ void small_one(const ProdDesc d, const TwTable& tw) {
         [&](int j, int2 v) { si[j] = v; });
     __syncthreads();
     first_step_exact<V, BPT, 1, false>(si, N, sm, logN, 1, N, tw);
-    block_fft<V, +1, BPT>(sm, logN, 1, N, tw, true);
+    // no radix-8 last step here: with one butterfly per thread a block
+    // reaches 1024 threads at N = 4096, and its registers must stay <= 64
+    block_fft<V, +1, BPT, 1, false>(sm, logN, 1, N, tw, true);
     pair_products(sm, 1, 0, logN);
     __syncthreads();
     pack_half(sm, 1, 0, 0, 0, logN, tw);
     __syncthreads();
-    block_fft<V, -1, BPT>(sm, logN - 1, 1, N, tw);
+    block_fft<V, -1, BPT, 1, false>(sm, logN - 1, 1, N, tw);
     IsoAcc acc;
     for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x)
         isolate_scaled<1>(sm[j], logN + 2, j, d, acc);
