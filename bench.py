@@ -233,7 +233,7 @@ NCU_TRAFFIC_PER_PRODUCT = {
     # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
     "k_rows<double>": (84.639488e6 + 10.984192e6) / 16,
     "k_rows<disc>": (63.496448e6 + 3.831040e6) / 16,
-    "k_rows<disc32x2>": (63.304704e6 + 5.040128e6) / 16,
+    "k_rows<disc32x2>": (63.328000e6 + 5.305856e6) / 16,
 }
 
 
