@@ -438,28 +438,11 @@ __device__ __forceinline__ void isolate_value(const Disc& v, int k, int64_t j, c
     isolate_one<R>(__dsub_rd(v.y, r), __dadd_ru(v.y, r), k, 2 * j + 1, d, acc, 2);
 }
 
-// rint(x) for |x| < 2^23 (x + 2^23 sign(x) has ulp 1), x itself otherwise
-// (then x is an integer, inf or NaN)
-__device__ __forceinline__ float rint_f32(float x) {
-    const float S = __int_as_float(0x4B000000 | (__float_as_int(x) & int(0x80000000)));
-    return fabsf(x) < 8388608.f ? __fsub_rn(__fadd_rn(x, S), S) : x;
-}
-
-// the integer value of an integer-valued binary32 x with |x| < 2^53, on the
-// integer pipe
-__device__ __forceinline__ long long int_of_f32(float x) {
-    const int b = __float_as_int(x);
-    const int ef = (b >> 23) & 0xFF;
-    const long long m = (b & 0x7FFFFF) | 0x800000;
-    const int e = ef - 150;                                    // x = m 2^e
-    long long v = e >= 0 ? (m << (e > 40 ? 40 : e)) : (m >> (-e > 31 ? 31 : -e));
-    v = ef == 0 ? 0ll : v;
-    return b < 0 ? -v : v;
-}
-
 // The decision of isolate_one for a component held as a double-binary32
-// centre h + l and a binary32 radius r, on the binary32 and integer pipes
-// only.  With k0 = rint(h), k1 = rint(l) (exact) the remainders t = h - k0
+// centre h + l and a binary32 radius r, without binary64 arithmetic (k0
+// and k1 become integers by the conversion instructions, which take fewer
+// issue slots than the same conversions done with integer operations).
+// With k0 = rint(h), k1 = rint(l) (exact) the remainders t = h - k0
 // and t' = l - k1 are exact and |t + t'| <= 1, so the component lies in
 // [k0 + k1 + lo, k0 + k1 + hi] with lo = RD(RD(t + t') - r) and
 // hi = RU(RU(t + t') + r).  While |lo|, |hi| < 2^22, ceil(lo) and floor(hi)
@@ -474,7 +457,7 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
                                              const ProdDesc& d, IsoAcc& acc, int rung) {
     const int64_t L = int64_t(d.na) + d.nb - 1;
     if (d.fault_widen == rung + 1) r = __fadd_ru(r, 4.f * R); // test fault: 4 in units of c
-    const float k0 = rint_f32(h), k1 = rint_f32(l);
+    const float k0 = rintf(h), k1 = rintf(l);
     const float t = __fsub_rn(h, k0), t2 = __fsub_rn(l, k1);
     const float lo = __fsub_rd(__fadd_rd(t, t2), r);
     const float hi = __fadd_ru(__fadd_ru(t, t2), r);
@@ -487,7 +470,8 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
     const bool big = fabsf(h) >= 9007199254740992.f;            // 2^53
     const int cl = __float_as_int(__fadd_ru(lo, M)) - __float_as_int(M);
     const int fh = __float_as_int(__fadd_rd(hi, M)) - __float_as_int(M);
-    const long long K = big ? 0ll : int_of_f32(k0) + int_of_f32(k1);
+    // k0 and k1 are integers (|k0| < 2^53, |k1| < 2^30): hardware conversions
+    const long long K = big ? 0ll : __float2ll_rz(k0) + (long long)__float2int_rz(k1);
     long long kl = K + cl, kh = K + fh;
     if (R != 1) {
         // [ceil(kl / R), floor(kh / R)] with one 64-bit division: kl = q R + rm
