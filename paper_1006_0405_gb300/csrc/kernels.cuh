@@ -364,8 +364,21 @@ __device__ __forceinline__ void isolate_one(T lo, T hi, int k, int64_t idx, cons
     floor_ceil_scaled(dl, k, unused, kl);
     floor_ceil_scaled(dh, k, kh, unused);
     if (R != 1) {
-        kl = ceil_div<R>(kl);
-        kh = floor_div<R>(kh);
+        // [ceil(kl / R), floor(kh / R)]; a narrow set of moderate bounds (the
+        // usual case) takes one 64-bit division: kl = q R + rm (0 <= rm < R),
+        // kh = kl + span.  Capped, NaN or wide bounds take two.
+        const bool narrow = kl > -(1ll << 61) && kl < (1ll << 61) && kh >= kl &&
+                            kh - kl < (1ll << 30);
+        const long long span = narrow ? kh - kl : 0;
+        if (narrow) {
+            const long long q = floor_div<R>(kl);
+            const int rm = int(kl - q * R);
+            kh = q + floor_div32<R>(rm + int(span));
+            kl = q + (rm > 0 ? 1 : 0);
+        } else {
+            kl = ceil_div<R>(kl);
+            kh = floor_div<R>(kh);
+        }
     }
     constexpr long long KMAX = 1ll << 53;
     if (idx < L) {
@@ -470,8 +483,9 @@ __device__ __forceinline__ void isolate_pair(float h, float l, float r, int64_t 
     const bool big = fabsf(h) >= 9007199254740992.f;            // 2^53
     const int cl = __float_as_int(__fadd_ru(lo, M)) - __float_as_int(M);
     const int fh = __float_as_int(__fadd_rd(hi, M)) - __float_as_int(M);
-    // k0 and k1 are integers (|k0| < 2^53, |k1| < 2^30): hardware conversions
-    const long long K = big ? 0ll : __float2ll_rz(k0) + (long long)__float2int_rz(k1);
+    // k0 and k1 are integers (|k0| < 2^53, |k1| < 2^30) unless a part is
+    // large, infinite or NaN, when K plays no part in the decision
+    const long long K = (big || bad) ? 0ll : __float2ll_rz(k0) + (long long)__float2int_rz(k1);
     long long kl = K + cl, kh = K + fh;
     if (R != 1) {
         // [ceil(kl / R), floor(kh / R)] with one 64-bit division: kl = q R + rm
