@@ -231,9 +231,9 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # kernels changed since.
 NCU_TRAFFIC_PER_PRODUCT = {
     # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
-    "k_rows<double>": (84.639488e6 + 10.984192e6) / 16,
-    "k_rows<disc>": (63.496448e6 + 3.831040e6) / 16,
-    "k_rows<disc32x2>": (63.328000e6 + 5.305856e6) / 16,
+    "k_rows<double>": (84.672768e6 + 11.277568e6) / 16,
+    "k_rows<disc>": (63.490304e6 + 2.964992e6) / 16,
+    "k_rows<disc32x2>": (63.329280e6 + 5.290752e6) / 16,
 }
 
 
