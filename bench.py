@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=256,
+                    help="products per step (every 64th all-0xFF, the rest uniform)")
     ap.add_argument("--digits", type=int, default=75000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="time budget of the CPU oracle sample")
@@ -90,7 +91,8 @@ def dist_env():
 
 def make_batch(rank: int, batch: int, n: int):
     seed = synth.SEED_BASE + 1 + 1000 * rank
-    dists = ["ff" if i == batch - 1 else "uniform" for i in range(batch)]
+    # one product in 64 (and the last of a smaller batch) has all digits 0xFF
+    dists = ["ff" if i % 64 == 63 or i == batch - 1 else "uniform" for i in range(batch)]
     na = [n] * batch
     return synth.batch_operands(seed, na, na, dists), dists
 
@@ -637,8 +639,9 @@ def run_ours(args):
             "balanced_digits": bool(args.balanced),
             "data": "synthetic",
             "config": {"workload": f"{n}x{n} base-256 digits, {SETS[args.precision]}, "
-                                   f"FFT length {fft_len_str(n)}; batch of {B} per step ({B - 1} uniform "
-                                   f"random, 1 all-0xFF) per GPU",
+                                   f"FFT length {fft_len_str(n)}; batch of {B} per step "
+                                   f"({dists.count('uniform')} uniform random, {dists.count('ff')} "
+                                   f"all-0xFF) per GPU",
                        "batch_per_gpu": B, "digits": n, "precision": args.precision,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
