@@ -66,6 +66,8 @@ def parse():
                     help="rung of the paper workload: binary64 rectangles (default), binary64 "
                          "discs, the unverified naive transform, double-binary32 discs, or the "
                          "fast ladder (double-binary32 discs, escalating to binary64)")
+    ap.add_argument("--host-pieces", type=int, default=2,
+                    help="pieces of the end-to-end host-buffer call (SSMUL_OPT_HOST_PIECES)")
     ap.add_argument("--no-alternates", action="store_true",
                     help="skip the extra lines for the other rungs (disc64, naive64)")
     ap.add_argument("--balanced", action="store_true",
@@ -228,15 +230,44 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 
 # DRAM bytes per product of one launch of the dominant kernels, from ncu
 # captures (16 products of 75k x 75k digits per launch, spectra larger than
-# L2): dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  Only
-# valid for the 75k workload and the kernels as captured; empty when the
-# kernels changed since.
-NCU_TRAFFIC_PER_PRODUCT = {
-    # profiles/fp64_kernels_75k_full.md, disc_kernels_75k_full.md, ddisc_kernels_75k_full.md
-    "k_rows<double>": (84.672768e6 + 11.277568e6) / 16,
-    "k_rows<disc>": (63.490304e6 + 2.964992e6) / 16,
-    "k_rows<disc32x2>": (63.329280e6 + 5.290752e6) / 16,
+# L2): dram__bytes_read.sum + dram__bytes_write.sum divided by 16.  They hold
+# only for the kernel sources they were captured with (the hash of the
+# device headers csrc/*.cuh) and the four-step geometry of the 75k length
+# (log2(N1 / 5), log2 N2, log2 column CTA elements); the bench checks both
+# at run time and reports null traffic when either differs.
+NCU_TRAFFIC = {
+    "cuh_sha256_16": "22a8c64ea07fc82c",
+    "geometry_75k": (6, 9, 10),
+    "per_product": {
+        "k_rows<double>": (84.672768e6 + 11.277568e6) / 16,
+        "k_rows<disc>": (63.490304e6 + 2.964992e6) / 16,
+        "k_rows<disc32x2>": (63.329280e6 + 5.290752e6) / 16,
+    },
 }
+
+
+def kernel_source_hash() -> str:
+    """sha256 (first 16 hex digits) of the device headers the kernels are built from."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1006_0405_gb300", "csrc", "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel: str, n: int, geometry) -> tuple:
+    """(bytes per product, why) of the ncu capture, or (None, reason) when the
+    workload, the kernel sources or the geometry differ from the captured ones."""
+    if n != 75000 or kernel not in NCU_TRAFFIC["per_product"]:
+        return None, "no ncu capture of this kernel at this size"
+    if kernel_source_hash() != NCU_TRAFFIC["cuh_sha256_16"]:
+        return None, "kernel sources changed since the ncu capture"
+    if tuple(geometry) != NCU_TRAFFIC["geometry_75k"]:
+        return None, "four-step geometry differs from the ncu capture"
+    return NCU_TRAFFIC["per_product"][kernel], "ncu capture of the same kernel sources and geometry"
 
 
 def algorithmic_bytes(n: int) -> float:
@@ -253,15 +284,15 @@ def fft_len_str(n: int) -> str:
     return f"2^{k}" if R == 1 else f"{R}*2^{k}"
 
 
-def fp64_peak_gops(sm_mhz: float) -> float:
-    """152 SMs x 2 binary64 operations per clock (the nominal 1.25 TFLOP/s
-    counts an fma as 2 flops: 152 * 2 * 2 * 2.07 GHz)."""
-    return 152 * 2 * sm_mhz * 1e6 / 1e9
+def fp64_peak_gops(sm_mhz: float, sms: int) -> float:
+    """sms SMs x 2 binary64 operations per clock (GB300's nominal 1.25 TFLOP/s
+    counts an fma as 2 flops: 152 SMs * 2 * 2 * 2.07 GHz)."""
+    return sms * 2 * sm_mhz * 1e6 / 1e9
 
 
-def fp32_peak_gops(sm_mhz: float) -> float:
-    """152 SMs x 128 binary32 lanes per clock."""
-    return 152 * 128 * sm_mhz * 1e6 / 1e9
+def fp32_peak_gops(sm_mhz: float, sms: int) -> float:
+    """sms SMs x 128 binary32 lanes per clock."""
+    return sms * 128 * sm_mhz * 1e6 / 1e9
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -416,6 +447,7 @@ def run_ours(args):
     from paper_1006_0405_gb300 import abi
     abi.load()
     n, B = args.digits, args.batch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     (a_pool, b_pool, a_off, b_off, z_off), dists = make_batch(rank, B, n)
     nz = 2 * n
     stream = torch.cuda.Stream(device=dev)
@@ -424,6 +456,7 @@ def run_ours(args):
              "ladder_fast": abi.SSMUL_PREC_LADDER_FAST}
     prec = PRECS[args.precision]
     plan = abi.ssmul_plan(n, n, B, prec, stream.cuda_stream)
+    abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_HOST_PIECES, args.host_pieces)
     if args.balanced:
         abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
     if args.lengths != 3:
@@ -475,59 +508,54 @@ def run_ours(args):
         _, kstats = abi.ssmul_debug_kernel_stats(plan, False)
         step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
 
-        # end to end through host buffers, run like a serving loop: every
-        # step copies its operands from pinned host memory to the device and
-        # reads its digits and per-product outcomes back; with two device
-        # buffer sets, an upload stream moves step k+1's operands and a
-        # download stream step k-1's results while step k computes
-        ha = torch.from_numpy(a_pool).pin_memory()
-        hb = torch.from_numpy(b_pool).pin_memory()
-        hz = [torch.empty(B * nz, dtype=torch.uint8).pin_memory() for _ in range(2)]
-        hres = [torch.empty(res_bytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
-        bufs = [(da, db, dz, dres),
-                (torch.empty_like(da), torch.empty_like(db), torch.empty_like(dz),
-                 torch.empty_like(dres))]
-        up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        loaded = [torch.cuda.Event() for _ in range(2)]
-        computed = [torch.cuda.Event() for _ in range(2)]
-        read = [torch.cuda.Event() for _ in range(2)]
-        e2e_steps = max(4, min(args.steps, 12))
-        torch.cuda.synchronize()
-        te0 = time.perf_counter()
-        for k in range(e2e_steps):
-            j = k & 1
-            xa, xb, xz, xr = bufs[j]
-            with torch.cuda.stream(up):
-                if k >= 2:
-                    up.wait_event(computed[j])            # step k-2 is done with these operands
-                xa.copy_(ha, non_blocking=True)
-                xb.copy_(hb, non_blocking=True)
-                loaded[j].record(up)
-            stream.wait_event(loaded[j])
-            if k >= 2:
-                stream.wait_event(read[j])                # step k-2's results are on the host
-            s_ = abi.ssmul_mul_batched(plan, descs, xa.data_ptr(), xb.data_ptr(), xz.data_ptr(),
-                                       xr.data_ptr())
-            if s_ != abi.SSMUL_OK:
-                raise RuntimeError(abi.status_string(s_))
-            computed[j].record(stream)
-            with torch.cuda.stream(down):
-                down.wait_event(computed[j])
-                hz[j].copy_(xz, non_blocking=True)
-                hres[j].copy_(xr, non_blocking=True)
-                read[j].record(down)
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - te0) / e2e_steps
     torch.cuda.synchronize()
 
-    # verification of every timed step against the CPU oracle
+    # the exact products, from the CPU oracle (NTT convolution and carry)
     from oracle import exact as E
     expect = []
     for i in range(B):
         a = a_pool[a_off[i]:a_off[i] + n]
         b = b_pool[b_off[i]:b_off[i] + n]
         expect.append(E.carry(E.conv_ntt(a, b), nz))
-    verified = 0
+
+    # end to end through the library's host-buffer call: every step hands
+    # the operands in page-locked host memory to ssmul_mul_batched_host,
+    # which uploads them, runs the batch in pieces whose copies overlap the
+    # computation, and returns once the digits and outcomes are back in host
+    # memory; each step is timed on the host around that call (it waits)
+    ha = torch.from_numpy(a_pool).pin_memory()
+    hb = torch.from_numpy(b_pool).pin_memory()
+    hz = torch.empty(B * nz, dtype=torch.uint8).pin_memory()
+    hres = torch.empty(res_bytes, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(4, min(args.steps, 12))
+    e2e_times, e2e_ok = [], True
+
+    def host_step():
+        s_ = abi.ssmul_mul_batched_host(plan, descs, ha.data_ptr(), hb.data_ptr(), hz.data_ptr(),
+                                        hres.data_ptr())
+        if s_ != abi.SSMUL_OK:
+            raise RuntimeError(abi.status_string(s_))
+
+    with torch.cuda.stream(stream):
+        host_step()                                   # warm-up: the plan's device copies grow
+        for k in range(e2e_steps):
+            hz.zero_()
+            flush.zero_()                             # L2 flushed between steps
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            host_step()
+            e2e_times.append(time.perf_counter() - t0)
+            rr = (abi.ssmul_result * B)()
+            ctypes.memmove(rr, hres.numpy().ctypes.data, res_bytes)
+            zh = hz.numpy()
+            e2e_ok &= all(rr[i].status == abi.SSMUL_OK and
+                          np.array_equal(zh[z_off[i]:z_off[i] + nz], expect[i]) for i in range(B))
+    e2e_s = sum(e2e_times) / len(e2e_times)
+
+    # verification of every timed step against the CPU oracle: a product is
+    # verified when its status is SSMUL_OK and its digits are the oracle's
+    # (the naive transform's digits can match without being verified)
+    verified, matched = 0, 0
     widths = []
     statuses = {}
     for k in range(args.steps):
@@ -538,13 +566,11 @@ def run_ours(args):
         for i in range(B):
             st = rr[i].status
             statuses[abi.status_string(st)] = statuses.get(abi.status_string(st), 0) + 1
-            ok = st in (abi.SSMUL_OK, abi.SSMUL_UNVERIFIED) and \
-                np.array_equal(z[z_off[i]:z_off[i] + nz], expect[i])
-            verified += int(ok)
+            same = bool(np.array_equal(z[z_off[i]:z_off[i] + nz], expect[i]))
+            verified += int(st == abi.SSMUL_OK and same)
+            matched += int(same)
             if k == 0:
                 widths.append((dists[i], rr[i].max_width))
-    e2e_ok = all(np.array_equal(h.numpy()[z_off[i]:z_off[i] + nz], expect[i])
-                 for h in hz for i in range(B))
 
     # the other rungs on the same batch (context for the headline rung)
     alternatives = {}
@@ -575,16 +601,16 @@ def run_ours(args):
                 stream.synchronize()
                 _, akst = abi.ssmul_debug_kernel_stats(aplan, False)
             abi.ssmul_plan_destroy(aplan)
-            a_ok, a_w = 0, 0.0
+            a_ok, a_match, a_w = 0, 0, 0.0
             for k in range(args.steps):
                 z = zs[k].cpu().numpy()
                 rr = (abi.ssmul_result * B)()
                 host = rs[k].cpu().numpy()
                 ctypes.memmove(rr, host.ctypes.data, res_bytes)
                 for i in range(B):
-                    if rr[i].status in (abi.SSMUL_OK, abi.SSMUL_UNVERIFIED) and \
-                            np.array_equal(z[z_off[i]:z_off[i] + nz], expect[i]):
-                        a_ok += 1
+                    same = bool(np.array_equal(z[z_off[i]:z_off[i] + nz], expect[i]))
+                    a_ok += int(rr[i].status == abi.SSMUL_OK and same)
+                    a_match += int(same)
                     a_w = max(a_w, rr[i].max_width)
             a_t = sum(e0.elapsed_time(e1) for e0, e1 in aev) / 1e3
             amodel = "disc32x2" if alt == "ladder_fast" else alt
@@ -593,11 +619,16 @@ def run_ours(args):
             ala, ams = akst[adom]
             aach = aops[adom] * B / (ams / ala * 1e-3) / 1e9 if ala else 0.0
             alternatives[alt] = {
-                "value": a_ok / a_t, "unit": "multiplies/s", "ms_per_step": 1e3 * a_t / args.steps,
+                "value": a_ok / a_t, "unit": "verified multiplies/s",
+                "ms_per_step": 1e3 * a_t / args.steps,
                 "verified": f"{a_ok}/{args.steps * B}", "max_width": a_w,
-                "status": "unverified digits (naive transform)" if alt == "naive64" else "verified",
                 "dominant_kernel": adom,
                 ("fp32_gops" if amodel == "disc32x2" else "fp64_gops"): aach}
+            if alt == "naive64":
+                # never verified (status SSMUL_UNVERIFIED): its speed is that of
+                # the products whose digits happened to equal the oracle's
+                alternatives[alt]["unverified_digits_matched"] = f"{a_match}/{args.steps * B}"
+                alternatives[alt]["unverified_multiplies_per_s"] = a_match / a_t
 
     t_steps = sum(step_ms) / 1e3
     value, e2e_value = aggregate_ranks(t_steps, verified, e2e_s, B, world, dev)
@@ -613,7 +644,11 @@ def run_ours(args):
         # one launch covers all B products of the batch
         achieved = ops[dom] * B / (ms / launches * 1e-3) / 1e9 if launches else 0.0
         sm_mhz = clk.get("sm_mhz") or 2070.0
-        peak = fp32_peak_gops(sm_mhz) if model == "disc32x2" else fp64_peak_gops(sm_mhz)
+        peak = (fp32_peak_gops(sm_mhz, sms) if model == "disc32x2"
+                else fp64_peak_gops(sm_mhz, sms))
+        R_, k_ = length_code(n, n)
+        geo = abi.ssmul_debug_geometry(plan, (64 if R_ == 5 else 32 if R_ == 3 else 0) + k_)[1]
+        traffic_pp, traffic_why = captured_traffic(dom, n, geo)
         total_ms = sum(v[1] for v in kstats.values())
         shares = {k: round(v[1] / total_ms, 4) for k, v in kstats.items() if v[0]}
         cpu = None
@@ -646,25 +681,28 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "verified": f"{verified}/{args.steps * B} per rank 0",
+            "digits_matched": f"{matched}/{args.steps * B} per rank 0",
             "statuses": statuses,
             "max_width": {"uniform": max(w for d, w in widths if d == "uniform"),
                           "all_ff": max((w for d, w in widths if d == "ff"), default=None)},
             "e2e": {"value": e2e_value, "unit": "multiplies/s",
                     "h2d_bytes_per_step": int(a_pool.nbytes + b_pool.nbytes + ctypes.sizeof(descs)),
-                    "d2h_bytes_per_step": int(B * nz + res_bytes)},
+                    "d2h_bytes_per_step": int(B * nz + res_bytes),
+                    "call": "ssmul_mul_batched_host (page-locked host pools in, host digits out)",
+                    "host_pieces": int(args.host_pieces), "steps": e2e_steps,
+                    "verified": "all" if e2e_ok else "not all products SSMUL_OK and exact"},
             "gpu_launches": int(gpu_launches),
             "alternatives": alternatives,
             "kernel_ms_share": shares,
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "fp32 Gop/s" if model == "disc32x2" else "fp64 Gop/s",
                          "frac": achieved / peak,
-                         "traffic": (NCU_TRAFFIC_PER_PRODUCT[dom] * B
-                                     if n == 75000 and dom in NCU_TRAFFIC_PER_PRODUCT else None),
+                         "traffic": traffic_pp * B if traffic_pp is not None else None,
                          "traffic_note": "bytes per launch: ncu DRAM bytes of a 16-product launch "
-                                         "scaled to the B products of this launch",
-                         "peak_note": ("binary32 pipe: 152 SMs x 128 lanes/clk"
+                                         "scaled to the B products of this launch; " + traffic_why,
+                         "peak_note": (f"binary32 pipe: {sms} SMs x 128 lanes/clk"
                                        if model == "disc32x2" else
-                                       "binary64 pipe: 152 SMs x 2 ops/clk")
+                                       f"binary64 pipe: {sms} SMs x 2 ops/clk")
                                       + " at the median sampled SM clock (recipe unit counts "
                                         "and clocks)"},
             "hbm_roofline": {"achieved_gbs": value * algorithmic_bytes(n) / 1e9,

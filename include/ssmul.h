@@ -123,20 +123,25 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb,
                         size_t max_products, ssmul_precision prec,
                         void* cuda_stream);
 
-/* Plan options (ssmul_plan_set_option). */
+/* Plan options (ssmul_plan_set_option).  None of them changes a product's
+ * digits; they change how the work of Sections 2.3-2.5 is scheduled or
+ * represented. */
 typedef enum {
     /* value != 0: ssmul_mul_batched captures its launches in a CUDA graph and
      * replays the graph when the next call describes the same batch (same
      * descriptors, pools and result array); needs a plan stream other than
-     * the legacy default stream, and is ignored on that stream */
+     * the legacy default stream, and is ignored on that stream.  A schedule
+     * of the batch's transforms (Section 2.3); the paper has none. */
     SSMUL_OPT_GRAPH = 0,
     /* value != 0: time every candidate four-step geometry (split N = N1 N2,
      * column tile size) for each transform length of the plan now, and
      * keep the fastest; results are cached in the file named by the
-     * environment variable SSMUL_TUNE_CACHE when it is set.  0: defaults */
+     * environment variable SSMUL_TUNE_CACHE when it is set.  0: defaults.
+     * The factorisation of the DFT of Section 2.2 changes, not its value. */
     SSMUL_OPT_AUTOTUNE = 1,
     /* under the ladders, try binary32 only for products with
-     * na + nb <= value digits (and N <= 4096); default 32 */
+     * na + nb <= value digits (and N <= 4096); default 32.  The first rung
+     * of Section 1's "more precision on failure". */
     SSMUL_OPT_FP32_MAX_DIGITS = 2,
     /* value != 0: balanced digits.  The transforms carry a_j - 128 and
      * b_j - 128 instead of the digits, so their values (and the widths of
@@ -162,11 +167,20 @@ typedef enum {
      * 3 * 2^K, and the 1/N scaling leaves a factor 1/5 or 1/3 that the
      * isolation applies exactly to the integer bounds.  0: powers of two
      * only (the paper's 2^k). */
-    SSMUL_OPT_LENGTHS = 5
+    SSMUL_OPT_LENGTHS = 5,
+    /* value 1 .. 64: ssmul_mul_batched_host runs its batch in this many
+     * pieces (consecutive runs of the descriptors), so that the operands of
+     * piece k + 1 upload and the digits of piece k - 1 download while piece
+     * k computes.  1: one upload, the whole batch, one download.  Default 2.
+     * Data movement only: the paper's method starts from digit vectors
+     * (Section 2) and ends with the digits of the carry (Section 2.4). */
+    SSMUL_OPT_HOST_PIECES = 6
 } ssmul_option;
 
 /*
- * Set a plan option.  Waits for the plan's queued work first.
+ * Set a plan option (ssmul_option: how the work of Sections 2.3-2.5 is
+ * scheduled and represented; the products are the same).  Waits for the
+ * plan's queued work first.
  * Errors: SSMUL_INVALID_ARG (null plan, unknown option, negative value),
  * SSMUL_OUT_OF_MEMORY / SSMUL_CUDA_ERROR from the autotuner.
  */
@@ -188,26 +202,63 @@ ssmul_status ssmul_mul(ssmul_plan_t plan, const uint8_t* d_a, size_t na,
                        ssmul_result* h_res);
 
 /*
- * Same as ssmul_mul, with a, b and z in host memory.  The host-device copies
- * go through the plan's device buffers on the plan's stream.
+ * Same as ssmul_mul (Sections 2.3-2.5 and the carry of Section 2.4), with
+ * a, b and z in host memory.  The host-device copies go through the plan's
+ * device buffers on the plan's stream.  Errors: as ssmul_mul.
  */
 ssmul_status ssmul_mul_host(ssmul_plan_t plan, const uint8_t* h_a, size_t na,
                             const uint8_t* h_b, size_t nb, uint8_t* h_z,
                             ssmul_result* h_res);
 
 /*
- * count independent products described by h_desc (host memory, count
- * entries) over device digit pools.  Every product obeys the plan's size
- * maxima and count <= max_products.  The work is only enqueued on the
+ * count independent products z = a * b, each computed as ssmul_mul computes
+ * one (the fast convolution of Section 2.3 in the interval arithmetic of
+ * Section 2.5, the isolation of Section 1 and the carry of Section 2.4),
+ * described by h_desc (host memory, count entries) over device digit
+ * pools: a_pool[a_off .. a_off + na), b_pool[b_off .. b_off + nb) and
+ * z_pool[z_off .. z_off + na + nb), little-endian base 256.  Every product
+ * obeys the plan's size maxima and count <= max_products; the z ranges of
+ * different products must not overlap.  The work is only enqueued on the
  * plan's stream: the return value covers argument and launch errors, and
  * the per-product outcomes land in d_res (device memory, count entries),
  * valid after the stream is synchronised.  Products whose status is not
- * SSMUL_OK have their digits zero-filled.
+ * SSMUL_OK have their digits zero-filled.  h_desc may be reused as soon as
+ * the call returns.
+ * Errors: SSMUL_INVALID_ARG (null plan or pointers with count > 0, na or nb
+ * zero), SSMUL_TOO_LARGE (count > max_products, a size above the plan's
+ * maxima), SSMUL_OUT_OF_MEMORY, SSMUL_CUDA_ERROR.
  */
 ssmul_status ssmul_mul_batched(ssmul_plan_t plan, size_t count,
                                const ssmul_desc* h_desc,
                                const uint8_t* d_a_pool, const uint8_t* d_b_pool,
                                uint8_t* d_z_pool, ssmul_result* d_res);
+
+/*
+ * ssmul_mul_batched from host memory to host memory: the digit vectors in
+ * (Section 2's digit convention), the digits of Section 2.4's carry out.
+ * h_desc offsets index the host pools h_a_pool, h_b_pool and h_z_pool;
+ * h_res (host memory, count entries) receives the per-product outcomes.
+ * The plan copies the bytes its products read to device buffers of its
+ * own, runs the batch and copies the products' digits (exactly the bytes
+ * [z_off, z_off + na + nb) of each product; nothing else of h_z_pool is
+ * written) and outcomes back.  The batch runs in SSMUL_OPT_HOST_PIECES
+ * pieces so that copies overlap the computation.  The call waits: on return
+ * h_z_pool and h_res hold the results, and the return value covers argument,
+ * memory and launch errors (each product's status is in h_res; digits of a
+ * product whose status is not SSMUL_OK are zero-filled).
+ * Page-locked host memory (cudaMallocHost, cudaHostAlloc, cudaHostRegister)
+ * lets every copy run asynchronously; pageable memory works too, but its
+ * copies go through driver staging and hold the calling thread.
+ * Device memory: the plan's copies of the pools grow, on the first call that
+ * needs more, to the span of the bytes a call touches in each pool (a
+ * cudaMalloc after waiting for the plan's queued work).  SSMUL_OPT_GRAPH
+ * does not apply to this call.
+ * Errors: as ssmul_mul_batched, and SSMUL_INVALID_ARG for a null h_res.
+ */
+ssmul_status ssmul_mul_batched_host(ssmul_plan_t plan, size_t count,
+                                    const ssmul_desc* h_desc,
+                                    const uint8_t* h_a_pool, const uint8_t* h_b_pool,
+                                    uint8_t* h_z_pool, ssmul_result* h_res);
 
 /*
  * z = a * b without any device allocation, for callers that cannot call
@@ -223,10 +274,13 @@ ssmul_status ssmul_mul_batched(ssmul_plan_t plan, size_t count,
  * coefficients, carry words, outcome: about 60 KB) is one static device
  * array of the library, held on every device that loads it until the
  * process exits.  The first call on a device sets that array up (finds its
- * address, builds the twiddle table and waits for it); make that first
- * call before any stream capture.  Every call on a device shares the one
- * array, so calls that may overlap on the GPU race and must be serialised
- * by the caller (for example: one stream).  d_a, d_b, d_z: device memory
+ * address, builds the twiddle table, marks it built and waits for it); make
+ * that first call before any stream capture.  Every call looks the array's
+ * address up again and its first kernel checks the mark, so after a device
+ * reset (which re-creates the array, zero-filled) the next call sets it up
+ * again instead of transforming with a missing table.  Every call on a
+ * device shares the one array, so calls that may overlap on the GPU race
+ * and must be serialised by the caller (for example: one stream).  d_a, d_b, d_z: device memory
  * of the current device; h_res: host memory, may be NULL; cuda_stream: a
  * cudaStream_t (NULL: legacy default stream).  The call waits for the
  * product and returns its status; d_z is zero-filled unless SSMUL_OK.

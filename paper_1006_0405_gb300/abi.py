@@ -34,7 +34,8 @@ SSMUL_PREC_LADDER_FAST = 7
 
 #: every symbol the headers declare
 EXPORTS = (
-    "ssmul_plan", "ssmul_plan_set_option", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched", "ssmul_mul_noalloc",
+    "ssmul_plan", "ssmul_plan_set_option", "ssmul_mul", "ssmul_mul_host", "ssmul_mul_batched",
+    "ssmul_mul_batched_host", "ssmul_mul_noalloc",
     "ssmul_plan_destroy", "ssmul_status_string",
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op", "ssmul_debug_disc_op",
     "ssmul_debug_ddisc_op", "ssmul_debug_isolate", "ssmul_debug_floor_ceil",
@@ -48,6 +49,7 @@ SSMUL_OPT_FP32_MAX_DIGITS = 2
 SSMUL_OPT_BALANCED = 3
 SSMUL_OPT_SPLIT_DIGITS = 4
 SSMUL_OPT_LENGTHS = 5
+SSMUL_OPT_HOST_PIECES = 6
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")
@@ -120,6 +122,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_mul_noalloc.restype = st
     L.ssmul_mul_batched.argtypes = [vp, sz, ctypes.POINTER(ssmul_desc), vp, vp, vp, vp]
     L.ssmul_mul_batched.restype = st
+    L.ssmul_mul_batched_host.argtypes = [vp, sz, ctypes.POINTER(ssmul_desc), vp, vp, vp, vp]
+    L.ssmul_mul_batched_host.restype = st
     L.ssmul_plan_destroy.argtypes = [vp]
     L.ssmul_plan_destroy.restype = None
     L.ssmul_status_string.argtypes = [ctypes.c_int]
@@ -223,6 +227,23 @@ def ssmul_mul_batched(plan: int, descs, d_a_pool: int, d_b_pool: int, d_z_pool: 
     return load().ssmul_mul_batched(ctypes.c_void_p(plan), len(descs), descs,
                                     ctypes.c_void_p(d_a_pool), ctypes.c_void_p(d_b_pool),
                                     ctypes.c_void_p(d_z_pool), ctypes.c_void_p(d_res))
+
+
+def ssmul_mul_batched_host(plan: int, descs, h_a_pool: int, h_b_pool: int, h_z_pool: int,
+                           h_res) -> int:
+    """Host pools in, host digits out.  descs: a ctypes array of ssmul_desc (or
+    a sequence of 5-tuples); h_res: a ctypes array of len(descs) ssmul_result,
+    or the address of host memory holding that many."""
+    if not isinstance(descs, ctypes.Array):
+        arr = (ssmul_desc * len(descs))()
+        for i, (ao, bo, zo, na, nb) in enumerate(descs):
+            arr[i] = ssmul_desc(ao, bo, zo, na, nb)
+        descs = arr
+    return load().ssmul_mul_batched_host(ctypes.c_void_p(plan), len(descs), descs,
+                                         ctypes.c_void_p(h_a_pool), ctypes.c_void_p(h_b_pool),
+                                         ctypes.c_void_p(h_z_pool),
+                                         ctypes.c_void_p(h_res if isinstance(h_res, int)
+                                                         else ctypes.addressof(h_res)))
 
 
 def ssmul_debug_twiddles(plan: int, f32: int, h_out: int, cap: int):

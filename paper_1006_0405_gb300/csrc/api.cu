@@ -31,6 +31,10 @@ constexpr size_t FP32_MAX_DIGITS = 32;
 // largest batch arena a plan allocates (the batch runs in chunks beyond it)
 constexpr size_t ARENA_CAP = size_t(4) << 30;
 
+// pieces of a host-buffer batch (ssmul_mul_batched_host): piece k + 1's
+// operands upload and piece k - 1's digits download while piece k computes
+constexpr int HOST_PIECES = 2;
+
 struct Geom {
     int log_n;       // transform length code (see LEN3)
     bool small;      // whole product in one CTA
@@ -268,6 +272,17 @@ struct ssmul_plan_s {
     size_t arena_bytes = 0;
     std::vector<int> order;             // host scratch of a batched call
     std::vector<BatchChunk> chunks;
+    // host-buffer batches (ssmul_mul_batched_host): device copies of the
+    // pools and outcomes (grown on demand), two copy streams and the events
+    // that order the pieces of a call
+    uint8_t* hb_a = nullptr;
+    uint8_t* hb_b = nullptr;
+    uint8_t* hb_z = nullptr;
+    size_t hb_a_cap = 0, hb_b_cap = 0, hb_z_cap = 0;
+    ssmul_result* hb_res = nullptr;     // max(1, max_products) entries
+    cudaStream_t up = nullptr, down = nullptr;
+    std::vector<cudaEvent_t> hb_ev;     // two per piece
+    int host_pieces = HOST_PIECES;      // SSMUL_OPT_HOST_PIECES
     // CUDA graph of the last batched call (SSMUL_OPT_GRAPH)
     bool graph = false;
     bool capturing = false;
@@ -675,7 +690,11 @@ size_t arena_need(int log_n) {
 // every launch covers a contiguous run of descriptors; descriptors written
 // to the pinned array; products packed into the arena in that order, each
 // full arena one chunk of launches.
-ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
+// The batch occupies slots [base, base + count) of the plan's per-product
+// arrays (descriptors, states, look-back words), so that the pieces of one
+// host-buffer call can be prepared while earlier pieces still wait for
+// their descriptor uploads.
+ssmul_status prepare_batch(ssmul_plan_t p, size_t base, size_t count, const ssmul_desc* h_desc,
                            const uint8_t* d_a_pool, const uint8_t* d_b_pool, uint8_t* d_z_pool,
                            ssmul_result* d_res) {
     std::vector<int>& order = p->order;
@@ -697,9 +716,9 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
         const int i = order[k];
         const ssmul_desc& h = h_desc[i];
         ProdDesc d = single_desc(p, d_a_pool + h.a_off, h.na, d_b_pool + h.b_off, h.nb,
-                                 d_z_pool + h.z_off, k);
+                                 d_z_pool + h.z_off, base + k);
         d.res = d_res + i;
-        p->h_desc[k] = d;
+        p->h_desc[base + k] = d;
     }
     p->chunks.clear();
     size_t k0 = 0;
@@ -713,7 +732,7 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
             const size_t pb = p->balanced ? pre_bytes(hd.na, hd.nb) : 0;
             const size_t need = arena_need(ln) + pb;
             if (used + need > p->arena_bytes) break;
-            ProdDesc& d = p->h_desc[k1];
+            ProdDesc& d = p->h_desc[base + k1];
             unsigned char* base = p->arena + used;
             if (pb) {
                 d.pre_a = reinterpret_cast<uint32_t*>(base + arena_need(ln));
@@ -757,34 +776,35 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
     return SSMUL_OK;
 }
 
-// Device half of a batch: every stream operation of the prepared batch.
-ssmul_status issue_batch(ssmul_plan_t p, size_t count) {
+// Device half of a batch: every stream operation of the batch prepared in
+// slots [base, base + count).
+ssmul_status issue_batch(ssmul_plan_t p, size_t base, size_t count) {
     ssmul_status s = SSMUL_OK;
-    SS_TRY(cudaMemsetAsync(p->st, 0, count * sizeof(ProdState), p->stream));
-    SS_TRY(cudaMemsetAsync(p->flags, 0, count * p->flags_per_product * sizeof(uint32_t),
-                           p->stream));
+    ProdDesc* const dd = p->d_desc + base;
+    SS_TRY(cudaMemsetAsync(p->st + base, 0, count * sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->flags + base * p->flags_per_product, 0,
+                           count * p->flags_per_product * sizeof(uint32_t), p->stream));
     for (const BatchChunk& c : p->chunks) {
-        SS_TRY(cudaMemcpyAsync(p->d_desc + c.k0, p->h_desc + c.k0,
+        SS_TRY(cudaMemcpyAsync(dd + c.k0, p->h_desc + base + c.k0,
                                (c.k1 - c.k0) * sizeof(ProdDesc), cudaMemcpyHostToDevice,
                                p->stream));
-        s = enqueue_prefix(p, p->d_desc + c.k0, int(c.k1 - c.k0),
+        s = enqueue_prefix(p, dd + c.k0, int(c.k1 - c.k0),
                            p->max_na > p->max_nb ? p->max_na : p->max_nb);
         if (s != SSMUL_OK) return s;
         for (const BatchGroup& g : c.groups) {
             const Geom& geo = p->geom[g.log_n];
-            s = enqueue_rungs(p, p->prec, p->d_desc + g.g0, int(g.g1 - g.g0),
-                              int(g.e1 - g.g0), geo);
+            s = enqueue_rungs(p, p->prec, dd + g.g0, int(g.g1 - g.g0), int(g.e1 - g.g0), geo);
             if (s != SSMUL_OK) return s;
             {
                 LaunchScope ls(p, SSMUL_K_CARRY);
                 k_carry<<<dim3(unsigned(carry_tiles(g.max_nz)), unsigned(g.g1 - g.g0)),
-                          CARRY_THREADS, 0, p->stream>>>(p->d_desc + g.g0);
+                          CARRY_THREADS, 0, p->stream>>>(dd + g.g0);
             }
             SS_TRY(cudaGetLastError());
         }
         {
             LaunchScope ls(p, SSMUL_K_FINALIZE);
-            k_finalize<<<unsigned(c.k1 - c.k0), 256, 0, p->stream>>>(p->d_desc + c.k0);
+            k_finalize<<<unsigned(c.k1 - c.k0), 256, 0, p->stream>>>(dd + c.k0);
         }
         SS_TRY(cudaGetLastError());
     }
@@ -816,10 +836,10 @@ ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
         SS_TRY(cudaEventRecord(p->desc_free, p->stream));
         return SSMUL_OK;
     }
-    ssmul_status s = prepare_batch(p, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res);
+    ssmul_status s = prepare_batch(p, 0, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res);
     if (s != SSMUL_OK) return s;
     if (!use_graph) {
-        s = issue_batch(p, count);
+        s = issue_batch(p, 0, count);
         if (s != SSMUL_OK) return s;
         SS_TRY(cudaEventRecord(p->desc_free, p->stream));
         return SSMUL_OK;
@@ -828,7 +848,7 @@ ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
     std::memset(p->cap_launches, 0, sizeof(p->cap_launches));
     SS_TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
     p->capturing = true;
-    s = issue_batch(p, count);
+    s = issue_batch(p, 0, count);
     p->capturing = false;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(p->stream, &graph);
@@ -1018,6 +1038,162 @@ ssmul_status autotune(ssmul_plan_t p) {
     return done(SSMUL_OK);
 }
 
+// ---- host-buffer batches --------------------------------------------------------
+
+// Grows a device buffer to hold at least `need` bytes (waits for the plan's
+// queued work before the old buffer is released).
+template <typename T>
+ssmul_status grow_device(ssmul_plan_t p, T*& buf, size_t& cap, size_t need) {
+    if (need <= cap && buf) return SSMUL_OK;
+    SS_TRY(cudaStreamSynchronize(p->stream));
+    cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    const size_t bytes = (need + (size_t(1) << 20) - 1) & ~((size_t(1) << 20) - 1);
+    SS_TRY(cudaMalloc(reinterpret_cast<void**>(&buf), bytes));
+    cap = bytes;
+    return SSMUL_OK;
+}
+
+// Byte ranges [lo, hi) merged where they overlap or touch, in ascending order.
+void merge_ranges(std::vector<std::pair<uint64_t, uint64_t>>& r) {
+    std::sort(r.begin(), r.end());
+    size_t w = 0;
+    for (size_t i = 0; i < r.size(); ++i) {
+        if (w && r[i].first <= r[w - 1].second) {
+            if (r[i].second > r[w - 1].second) r[w - 1].second = r[i].second;
+        } else {
+            r[w++] = r[i];
+        }
+    }
+    r.resize(w);
+}
+
+// Uploads of one operand pool in ascending offset order: upload(end) copies
+// every byte of the pool's merged ranges below `end` not copied yet.
+struct PoolUpload {
+    std::vector<std::pair<uint64_t, uint64_t>> ranges;
+    size_t next = 0;
+    uint64_t pos = 0;
+    ssmul_status upload(uint64_t end, uint8_t* dev, uint64_t lo, const uint8_t* host,
+                        cudaStream_t st) {
+        while (next < ranges.size() && ranges[next].first < end) {
+            const uint64_t a = ranges[next].first > pos ? ranges[next].first : pos;
+            const uint64_t b = ranges[next].second < end ? ranges[next].second : end;
+            if (b > a) SS_TRY(cudaMemcpyAsync(dev + (a - lo), host + a, b - a,
+                                              cudaMemcpyHostToDevice, st));
+            if (ranges[next].second <= end) {
+                pos = ranges[next].second;
+                ++next;
+            } else {
+                pos = end;
+                break;
+            }
+        }
+        return SSMUL_OK;
+    }
+};
+
+// The pieces of a host-buffer batch, in the caller's descriptor order:
+// piece k waits for the uploads that reach its operands' last byte, runs
+// as a batch in slots [i0, i1) of the plan's arrays, and its digits and
+// outcomes are copied back once it is done.  Every compute piece is
+// enqueued before the first download, so pageable destination memory
+// (whose copies hold the calling thread) leaves no gap on the GPU.
+ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
+                              const uint8_t* h_a, const uint8_t* h_b, uint8_t* h_z,
+                              ssmul_result* h_res) {
+    uint64_t a_lo = UINT64_MAX, a_hi = 0, b_lo = UINT64_MAX, b_hi = 0, z_lo = UINT64_MAX, z_hi = 0;
+    for (size_t i = 0; i < count; ++i) {
+        const ssmul_desc& d = h_desc[i];
+        a_lo = std::min(a_lo, d.a_off);
+        a_hi = std::max(a_hi, d.a_off + d.na);
+        b_lo = std::min(b_lo, d.b_off);
+        b_hi = std::max(b_hi, d.b_off + d.nb);
+        z_lo = std::min(z_lo, d.z_off);
+        z_hi = std::max(z_hi, d.z_off + d.na + d.nb);
+    }
+    ssmul_status s = SSMUL_OK;
+    if ((s = grow_device(p, p->hb_a, p->hb_a_cap, a_hi - a_lo)) != SSMUL_OK) return s;
+    if ((s = grow_device(p, p->hb_b, p->hb_b_cap, b_hi - b_lo)) != SSMUL_OK) return s;
+    if ((s = grow_device(p, p->hb_z, p->hb_z_cap, z_hi - z_lo)) != SSMUL_OK) return s;
+    if (!p->hb_res) {
+        SS_TRY(cudaMalloc(&p->hb_res, (p->max_products ? p->max_products : 1) * sizeof(ssmul_result)));
+    }
+    if (!p->up) SS_TRY(cudaStreamCreateWithFlags(&p->up, cudaStreamNonBlocking));
+    if (!p->down) SS_TRY(cudaStreamCreateWithFlags(&p->down, cudaStreamNonBlocking));
+    const size_t pieces = std::min(count, size_t(p->host_pieces));
+    while (p->hb_ev.size() < 2 * pieces) {
+        cudaEvent_t e = nullptr;
+        SS_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->hb_ev.push_back(e);
+    }
+    // descriptors rebased onto the device copies of the pools
+    std::vector<ssmul_desc> rd(h_desc, h_desc + count);
+    PoolUpload ua, ub;
+    ua.ranges.resize(count);
+    ub.ranges.resize(count);
+    for (size_t i = 0; i < count; ++i) {
+        ua.ranges[i] = {h_desc[i].a_off, h_desc[i].a_off + h_desc[i].na};
+        ub.ranges[i] = {h_desc[i].b_off, h_desc[i].b_off + h_desc[i].nb};
+        rd[i].a_off -= a_lo;
+        rd[i].b_off -= b_lo;
+        rd[i].z_off -= z_lo;
+    }
+    merge_ranges(ua.ranges);
+    merge_ranges(ub.ranges);
+    SS_TRY(cudaEventSynchronize(p->desc_free));
+    // on an error after the first copy, wait for everything queued before
+    // returning, so no copy into the caller's memory outlives the call
+    auto drain = [&](ssmul_status e) {
+        cudaStreamSynchronize(p->up);
+        cudaStreamSynchronize(p->stream);
+        cudaStreamSynchronize(p->down);
+        return e;
+    };
+    for (size_t k = 0; k < pieces; ++k) {
+        const size_t i0 = count * k / pieces, i1 = count * (k + 1) / pieces;
+        uint64_t ea = 0, eb = 0;
+        for (size_t i = i0; i < i1; ++i) {
+            ea = std::max(ea, h_desc[i].a_off + h_desc[i].na);
+            eb = std::max(eb, h_desc[i].b_off + h_desc[i].nb);
+        }
+        if ((s = ua.upload(ea, p->hb_a, a_lo, h_a, p->up)) != SSMUL_OK) return drain(s);
+        if ((s = ub.upload(eb, p->hb_b, b_lo, h_b, p->up)) != SSMUL_OK) return drain(s);
+        cudaEvent_t in = p->hb_ev[2 * k], done = p->hb_ev[2 * k + 1];
+        if (cudaEventRecord(in, p->up) != cudaSuccess ||
+            cudaStreamWaitEvent(p->stream, in, 0) != cudaSuccess)
+            return drain(SSMUL_CUDA_ERROR);
+        s = prepare_batch(p, i0, i1 - i0, rd.data() + i0, p->hb_a, p->hb_b, p->hb_z,
+                          p->hb_res + i0);
+        if (s == SSMUL_OK) s = issue_batch(p, i0, i1 - i0);
+        if (s != SSMUL_OK) return drain(s);
+        if (cudaEventRecord(done, p->stream) != cudaSuccess) return drain(SSMUL_CUDA_ERROR);
+    }
+    if (cudaEventRecord(p->desc_free, p->stream) != cudaSuccess) return drain(SSMUL_CUDA_ERROR);
+    std::vector<std::pair<uint64_t, uint64_t>> zr;
+    for (size_t k = 0; k < pieces; ++k) {
+        const size_t i0 = count * k / pieces, i1 = count * (k + 1) / pieces;
+        if (cudaStreamWaitEvent(p->down, p->hb_ev[2 * k + 1], 0) != cudaSuccess)
+            return drain(SSMUL_CUDA_ERROR);
+        zr.clear();
+        for (size_t i = i0; i < i1; ++i)
+            zr.push_back({h_desc[i].z_off, h_desc[i].z_off + h_desc[i].na + h_desc[i].nb});
+        merge_ranges(zr);
+        for (const auto& r : zr) {
+            if (cudaMemcpyAsync(h_z + r.first, p->hb_z + (r.first - z_lo), r.second - r.first,
+                                cudaMemcpyDeviceToHost, p->down) != cudaSuccess)
+                return drain(SSMUL_CUDA_ERROR);
+        }
+        if (cudaMemcpyAsync(h_res + i0, p->hb_res + i0, (i1 - i0) * sizeof(ssmul_result),
+                            cudaMemcpyDeviceToHost, p->down) != cudaSuccess)
+            return drain(SSMUL_CUDA_ERROR);
+    }
+    const cudaError_t e = cudaStreamSynchronize(p->down);
+    if (e != cudaSuccess) return drain(cuda_status(e));
+    return drain(SSMUL_OK);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1068,6 +1244,13 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->stage);
     cudaFree(p->pre);
     cudaFree(p->arena);
+    cudaFree(p->hb_a);
+    cudaFree(p->hb_b);
+    cudaFree(p->hb_z);
+    cudaFree(p->hb_res);
+    if (p->up) cudaStreamDestroy(p->up);
+    if (p->down) cudaStreamDestroy(p->down);
+    for (cudaEvent_t e : p->hb_ev) cudaEventDestroy(e);
     cudaFree(p->coeff_total);
     cudaFree(p->split_st);
     cudaFree(p->d_split);
@@ -1243,6 +1426,10 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
             graph_drop(p->cached);
             p->balanced = value != 0;
             return SSMUL_OK;
+        case SSMUL_OPT_HOST_PIECES:
+            if (value < 1 || value > 64) return SSMUL_INVALID_ARG;
+            p->host_pieces = int(value);
+            return SSMUL_OK;
         case SSMUL_OPT_LENGTHS:
             if (value < 0 || value > 3) return SSMUL_INVALID_ARG;
             SS_TRY(cudaStreamSynchronize(p->stream));
@@ -1318,6 +1505,26 @@ ssmul_status ssmul_mul_batched(ssmul_plan_t p, size_t count, const ssmul_desc* h
     ssmul_status s = check_device(p);
     if (s != SSMUL_OK) return s;
     return enqueue_batch(p, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res);
+}
+
+ssmul_status ssmul_mul_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
+                                    const uint8_t* h_a_pool, const uint8_t* h_b_pool,
+                                    uint8_t* h_z_pool, ssmul_result* h_res) {
+    if (!p || (count && (!h_desc || !h_a_pool || !h_b_pool || !h_z_pool || !h_res)))
+        return SSMUL_INVALID_ARG;
+    if (count > p->max_products) return SSMUL_TOO_LARGE;
+    for (size_t i = 0; i < count; ++i) {
+        const ssmul_desc& d = h_desc[i];
+        if (d.na == 0 || d.nb == 0) return SSMUL_INVALID_ARG;
+        if (d.na > p->max_na || d.nb > p->max_nb) return SSMUL_TOO_LARGE;
+        if (d.a_off > UINT64_MAX - d.na || d.b_off > UINT64_MAX - d.nb ||
+            d.z_off > UINT64_MAX - d.na - d.nb)
+            return SSMUL_INVALID_ARG;
+    }
+    if (count == 0) return SSMUL_OK;
+    ssmul_status s = check_device(p);
+    if (s != SSMUL_OK) return s;
+    return run_batched_host(p, count, h_desc, h_a_pool, h_b_pool, h_z_pool, h_res);
 }
 
 // ---- inspection entry points (include/ssmul_debug.h) ----------------------------
@@ -1618,9 +1825,10 @@ extern "C" ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, co
 // Everything the one-CTA binary64 path needs beyond the caller's inputs and
 // outputs lives in one file-scope device array: the twiddle table for
 // N <= 4096, the product descriptor, the per-call accumulators, the integer
-// coefficients, the carry look-back words and the outcome.  Host code must
-// not use the array's name as an address; each device's address comes from
-// cudaGetSymbolAddress in noalloc_setup.
+// coefficients, the carry look-back words, the outcome and a word that
+// marks the table as built.  Host code must not use the array's name as an
+// address; each device's address comes from cudaGetSymbolAddress in
+// noalloc_setup.
 
 namespace {
 
@@ -1637,7 +1845,11 @@ constexpr size_t NA_OFF_ST = na_align(NA_OFF_DESC + sizeof(ProdDesc));
 constexpr size_t NA_OFF_RES = na_align(NA_OFF_ST + sizeof(ProdState));
 constexpr size_t NA_OFF_FLAGS = na_align(NA_OFF_RES + sizeof(ssmul_result));
 constexpr size_t NA_OFF_COEFF = na_align(NA_OFF_FLAGS + NOALLOC_TILES * sizeof(uint32_t));
-constexpr size_t NOALLOC_BYTES = na_align(NA_OFF_COEFF + NOALLOC_N * sizeof(int64_t));
+constexpr size_t NA_OFF_MAGIC = na_align(NA_OFF_COEFF + NOALLOC_N * sizeof(int64_t));
+constexpr size_t NOALLOC_BYTES = na_align(NA_OFF_MAGIC + sizeof(unsigned long long));
+// written after the twiddle table is built; a device reset re-creates the
+// array zero-filled, and a call that finds the word missing builds again
+constexpr unsigned long long NOALLOC_MAGIC = 0x5353'4D55'4C54'5742ull;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
@@ -1646,7 +1858,10 @@ std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_dev_ptr[NOALLOC_MAX_DEVICES] = {};
 
 // Writes the descriptor and clears what must start at zero: the
-// accumulators, the look-back words and the outcome.
+// accumulators, the look-back words and the outcome.  Without the magic
+// word the twiddle table is not there (the array was re-created by a device
+// reset): the product is forced to SSMUL_CUDA_ERROR, so its digits are
+// zero-filled and the host builds the table again.
 __global__ void k_noalloc_init(ProdDesc d, unsigned char* base) {
     if (threadIdx.x == 0) *reinterpret_cast<ProdDesc*>(base + NA_OFF_DESC) = d;
     unsigned int* st = reinterpret_cast<unsigned int*>(base + NA_OFF_ST);
@@ -1656,20 +1871,31 @@ __global__ void k_noalloc_init(ProdDesc d, unsigned char* base) {
     for (size_t i = threadIdx.x; i < NOALLOC_TILES; i += blockDim.x) fl[i] = 0u;
     unsigned char* res = base + NA_OFF_RES;
     for (size_t i = threadIdx.x; i < sizeof(ssmul_result); i += blockDim.x) res[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0 &&
+        *reinterpret_cast<const unsigned long long*>(base + NA_OFF_MAGIC) != NOALLOC_MAGIC)
+        reinterpret_cast<ProdState*>(base + NA_OFF_ST)->forced = SSMUL_CUDA_ERROR;
 }
 
-// Once per device, with that device current: find the array's device
-// address, build the twiddle table in it and allow the kernel's shared
-// memory size.  Returns the address, or nullptr with *err set.
-unsigned char* noalloc_setup(int dev, cudaStream_t stream, ssmul_status* err) {
+__global__ void k_noalloc_mark(unsigned char* base) {
+    *reinterpret_cast<unsigned long long*>(base + NA_OFF_MAGIC) = NOALLOC_MAGIC;
+}
+
+// Once per device, with that device current (and again after a device
+// reset, which may move the array): find the array's device address, build
+// the twiddle table in it, mark it built and allow the kernel's shared
+// memory size.  Returns the address, or nullptr with *err set.  rebuild:
+// the last call found the table missing.
+unsigned char* noalloc_setup(int dev, cudaStream_t stream, bool rebuild, ssmul_status* err) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_dev_ptr[dev]) return g_noalloc_dev_ptr[dev];
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || ptr == nullptr) {
         *err = cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
         return nullptr;
     }
+    if (!rebuild && g_noalloc_dev_ptr[dev] == ptr) return g_noalloc_dev_ptr[dev];
+    g_noalloc_dev_ptr[dev] = nullptr;
     unsigned char* base = static_cast<unsigned char*>(ptr);
     e = cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(NOALLOC_N * sizeof(CI<double>)));
@@ -1677,6 +1903,7 @@ unsigned char* noalloc_setup(int dev, cudaStream_t stream, ssmul_status* err) {
         k_twiddle_gen<<<int((NOALLOC_TAB + 255) / 256), 256, 0, stream>>>(
             reinterpret_cast<TwEntry<double>*>(base + NA_OFF_T64),
             reinterpret_cast<TwEntry<float>*>(base + NA_OFF_T32), NOALLOC_LOG_N, 1);
+        k_noalloc_mark<<<1, 1, 0, stream>>>(base);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -1688,21 +1915,9 @@ unsigned char* noalloc_setup(int dev, cudaStream_t stream, ssmul_status* err) {
     return base;
 }
 
-}  // namespace
-
-extern "C" ssmul_status ssmul_mul_noalloc(const uint8_t* d_a, size_t na, const uint8_t* d_b,
-                                          size_t nb, uint8_t* d_z, ssmul_result* h_res,
-                                          void* cuda_stream) {
-    if (!d_a || !d_b || !d_z || na == 0 || nb == 0) return SSMUL_INVALID_ARG;
-    if (na + nb > SSMUL_NOALLOC_MAX_DIGITS) return SSMUL_TOO_LARGE;
-    int dev = -1;
-    SS_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SSMUL_CUDA_ERROR;
-    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    ssmul_status err = SSMUL_OK;
-    unsigned char* base = noalloc_setup(dev, stream, &err);
-    if (!base) return err;
-
+// One product on the array at `base`; waits for it and reads its outcome.
+ssmul_status noalloc_run(unsigned char* base, const uint8_t* d_a, size_t na, const uint8_t* d_b,
+                         size_t nb, uint8_t* d_z, cudaStream_t stream, ssmul_result* out) {
     ProdDesc d{};
     d.a = d_a;
     d.b = d_b;
@@ -1724,9 +1939,32 @@ extern "C" ssmul_status ssmul_mul_noalloc(const uint8_t* d_a, size_t na, const u
     k_carry<<<unsigned(carry_tiles(na + nb)), CARRY_THREADS, 0, stream>>>(slot);
     k_finalize<<<1, 256, 0, stream>>>(slot);
     SS_TRY(cudaGetLastError());
-    ssmul_result r{};
-    SS_TRY(cudaMemcpyAsync(&r, base + NA_OFF_RES, sizeof(r), cudaMemcpyDeviceToHost, stream));
+    SS_TRY(cudaMemcpyAsync(out, base + NA_OFF_RES, sizeof(*out), cudaMemcpyDeviceToHost, stream));
     SS_TRY(cudaStreamSynchronize(stream));
-    if (h_res) *h_res = r;
-    return ssmul_status(r.status);
+    return SSMUL_OK;
+}
+
+}  // namespace
+
+extern "C" ssmul_status ssmul_mul_noalloc(const uint8_t* d_a, size_t na, const uint8_t* d_b,
+                                          size_t nb, uint8_t* d_z, ssmul_result* h_res,
+                                          void* cuda_stream) {
+    if (!d_a || !d_b || !d_z || na == 0 || nb == 0) return SSMUL_INVALID_ARG;
+    if (na + nb > SSMUL_NOALLOC_MAX_DIGITS) return SSMUL_TOO_LARGE;
+    int dev = -1;
+    SS_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SSMUL_CUDA_ERROR;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int attempt = 0;; ++attempt) {
+        ssmul_status err = SSMUL_OK;
+        unsigned char* base = noalloc_setup(dev, stream, attempt > 0, &err);
+        if (!base) return err;
+        ssmul_result r{};
+        err = noalloc_run(base, d_a, na, d_b, nb, d_z, stream, &r);
+        if (err != SSMUL_OK) return err;
+        // the table was missing (see k_noalloc_init): build it, run once more
+        if (r.status == SSMUL_CUDA_ERROR && attempt == 0) continue;
+        if (h_res) *h_res = r;
+        return ssmul_status(r.status);
+    }
 }

@@ -50,6 +50,8 @@ def test_plan_argument_checks_without_device():
     assert L.ssmul_plan(ctypes.byref(h), 1, 1, 0, 99, None) == abi.SSMUL_INVALID_ARG
     assert L.ssmul_plan(ctypes.byref(h), 1 << 24, 1 << 24, 0, 0, None) == abi.SSMUL_TOO_LARGE
     assert L.ssmul_mul(None, None, 1, None, 1, None, None) == abi.SSMUL_INVALID_ARG
+    assert L.ssmul_mul_batched_host(None, 0, None, None, None, None, None) == abi.SSMUL_INVALID_ARG
+    assert L.ssmul_mul_noalloc(None, 1, None, 1, None, None, None) == abi.SSMUL_INVALID_ARG
 
 
 def test_cpu_has_no_compute_path():
