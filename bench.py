@@ -66,7 +66,10 @@ def parse():
                     help="rung of the paper workload: binary64 rectangles (default), binary64 "
                          "discs, the unverified naive transform, double-binary32 discs, or the "
                          "fast ladder (double-binary32 discs, escalating to binary64)")
-    ap.add_argument("--host-pieces", type=int, default=2,
+    ap.add_argument("--lanes", type=int, default=4,
+                    help="streams over which batched calls spread their length groups "
+                         "(SSMUL_OPT_LANES)")
+    ap.add_argument("--host-pieces", type=int, default=4,
                     help="pieces of the end-to-end host-buffer call (SSMUL_OPT_HOST_PIECES)")
     ap.add_argument("--no-alternates", action="store_true",
                     help="skip the extra lines for the other rungs (disc64, naive64)")

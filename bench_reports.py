@@ -221,6 +221,7 @@ def ladder(args):
                        ("ladder_fast_batched", abi.SSMUL_PREC_LADDER_FAST)):
         plan = abi.ssmul_plan(max_n, max_n, batch.count, prec, stream.cuda_stream)
         abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 1)
+        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_LANES, args.lanes)
         t = _time_batch(torch, plan, batch, 3, stream)
         rs, zs = batch.results(), batch.digits()
         ok = _verify_full(rs, zs, expect)
@@ -251,10 +252,11 @@ def uneven(args):
     batch = Batch(torch, seed, na, nb, dists)
     max_n = int(max(na.max(), nb.max()))
     stream = torch.cuda.Stream()
-    out = {"report": "uneven", "count": batch.count, "digits_total": int(batch.nz.sum())}
+    out = {"report": "uneven", "count": batch.count, "digits_total": int(batch.nz.sum()),
+           "lanes": args.lanes}
     for name, prec in (("ladder_graph_batched", abi.SSMUL_PREC_LADDER),
                        ("ladder_fast_graph_batched", abi.SSMUL_PREC_LADDER_FAST)):
-        out[name] = _uneven_batched(torch, abi, batch, max_n, prec, stream, seed)
+        out[name] = _uneven_batched(torch, abi, batch, max_n, prec, stream, seed, args.lanes)
     el, outs = _one_at_a_time(torch, abi, batch, max_n, abi.SSMUL_PREC_FP64)
     zs = batch.digits()
     rs1 = [type("R", (), {"status": s})() for s, _ in outs]
@@ -268,9 +270,10 @@ def uneven(args):
     print(json.dumps(out), flush=True)
 
 
-def _uneven_batched(torch, abi, batch, max_n, prec, stream, seed):
+def _uneven_batched(torch, abi, batch, max_n, prec, stream, seed, lanes=1):
     plan = abi.ssmul_plan(max_n, max_n, batch.count, prec, stream.cuda_stream)
     abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 1)
+    abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_LANES, lanes)
     abi.ssmul_debug_kernel_stats(plan, False)
     t = _time_batch(torch, plan, batch, 3, stream)
     _, kst = abi.ssmul_debug_kernel_stats(plan, False)

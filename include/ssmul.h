@@ -169,12 +169,21 @@ typedef enum {
      * only (the paper's 2^k). */
     SSMUL_OPT_LENGTHS = 5,
     /* value 1 .. 64: ssmul_mul_batched_host runs its batch in this many
-     * pieces (consecutive runs of the descriptors), so that the operands of
-     * piece k + 1 upload and the digits of piece k - 1 download while piece
-     * k computes.  1: one upload, the whole batch, one download.  Default 2.
+     * pieces (consecutive runs of the descriptors) on internal streams of
+     * decreasing priority, so that later pieces' operands upload and
+     * earlier pieces' digits download while a piece computes, and a later
+     * piece's thread blocks fill an earlier one's last waves.  1: one
+     * upload, the whole batch, one download.  Default 4.
      * Data movement only: the paper's method starts from digit vectors
      * (Section 2) and ends with the digits of the carry (Section 2.4). */
-    SSMUL_OPT_HOST_PIECES = 6
+    SSMUL_OPT_HOST_PIECES = 6,
+    /* value 1 .. 4: ssmul_mul_batched spreads the transform-length groups of
+     * a batch (each a set of independent products, Section 2.3) over this
+     * many streams, the plan's own and internal ones, so that one group's
+     * partly filled last wave of thread blocks overlaps another group's
+     * work; they join the plan's stream before the outcomes are written.
+     * Default 4; 1 puts every launch on the plan's stream. */
+    SSMUL_OPT_LANES = 7
 } ssmul_option;
 
 /*

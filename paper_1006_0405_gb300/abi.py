@@ -50,6 +50,7 @@ SSMUL_OPT_BALANCED = 3
 SSMUL_OPT_SPLIT_DIGITS = 4
 SSMUL_OPT_LENGTHS = 5
 SSMUL_OPT_HOST_PIECES = 6
+SSMUL_OPT_LANES = 7
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")

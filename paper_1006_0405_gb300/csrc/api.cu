@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -31,9 +32,20 @@ constexpr size_t FP32_MAX_DIGITS = 32;
 // largest batch arena a plan allocates (the batch runs in chunks beyond it)
 constexpr size_t ARENA_CAP = size_t(4) << 30;
 
-// pieces of a host-buffer batch (ssmul_mul_batched_host): piece k + 1's
-// operands upload and piece k - 1's digits download while piece k computes
-constexpr int HOST_PIECES = 2;
+// pieces of a host-buffer batch (ssmul_mul_batched_host): later pieces'
+// operands upload and earlier pieces' digits download while a piece
+// computes.  256 products of 75,000 x 75,000 digits took 16.72 / 16.60 /
+// 16.55 / 16.60 ms in 1 / 2 / 4 / 8 pieces (16.31 ms on device buffers)
+constexpr int HOST_PIECES = 4;
+
+// compute lanes of a plan (streams that run independent work concurrently)
+constexpr int LANES = 4;
+// streams of the pieces of a host-buffer call
+constexpr int PIECE_LANES = 4;
+// lanes over which a batched call spreads the transform-length groups of a
+// chunk (SSMUL_OPT_LANES): on 20,000 products of log-uniform sizes (64 to
+// 131,072 digits, about 30 groups) four lanes took 0.8-1.1% less time than one
+constexpr int GROUP_LANES = 4;
 
 struct Geom {
     int log_n;       // transform length code (see LEN3)
@@ -260,6 +272,24 @@ struct ssmul_plan_s {
     ProdState* st = nullptr;            // max(1, max_products) entries
     ProdDesc* d_desc = nullptr;         // max(1, max_products) entries
     int* gate_list = nullptr;           // 1 + max(1, max_products) entries (k_gate_list)
+    // compute lanes: lane 0 is the plan's stream, lanes 1 .. LANES-1 are
+    // internal streams (created on first use) on which independent parts of
+    // a batch run concurrently, each with a gate list of its own.  cur and
+    // cur_gate are what the enqueue functions launch on: lane 0's, except
+    // while a batch issues work on another lane.
+    cudaStream_t lane_stream[LANES] = {};
+    int* lane_gate[LANES] = {};
+    cudaEvent_t lane_ev[LANES] = {};    // fork / join marks
+    cudaStream_t cur = nullptr;
+    int* cur_gate = nullptr;
+    // host-buffer pieces (ssmul_mul_batched_host): internal streams of
+    // decreasing priority, piece k on stream k mod PIECE_LANES, each with a
+    // gate list of its own; piece_ev[0] marks the call's start on the plan's
+    // stream, piece_ev[1 + l] the end of stream l's pieces
+    cudaStream_t piece_stream[PIECE_LANES] = {};
+    int* piece_gate[PIECE_LANES] = {};
+    cudaEvent_t piece_ev[PIECE_LANES + 1] = {};
+    int piece_lanes = 0;                // streams created (limited by the priority levels)
     int sms = 1;                        // streaming multiprocessors of the device
     ssmul_result* d_res = nullptr;
     ProdDesc* h_desc = nullptr;         // pinned
@@ -283,6 +313,7 @@ struct ssmul_plan_s {
     cudaStream_t up = nullptr, down = nullptr;
     std::vector<cudaEvent_t> hb_ev;     // two per piece
     int host_pieces = HOST_PIECES;      // SSMUL_OPT_HOST_PIECES
+    int group_lanes = GROUP_LANES;      // SSMUL_OPT_LANES
     // CUDA graph of the last batched call (SSMUL_OPT_GRAPH)
     bool graph = false;
     bool capturing = false;
@@ -337,15 +368,76 @@ struct LaunchScope {
         p->kt_launches[kind]++;
         if (p->timing) {
             e0 = take_event(p);
-            cudaEventRecord(e0, p->stream);
+            cudaEventRecord(e0, p->cur);
         }
     }
     ~LaunchScope() {
         if (e0) {
             cudaEvent_t e1 = take_event(p);
-            cudaEventRecord(e1, p->stream);
+            cudaEventRecord(e1, p->cur);
             p->pending.push_back({kind, {e0, e1}});
         }
+    }
+};
+
+// Lanes 1 .. n-1 (streams, gate lists) and the fork / join events of
+// lanes 0 .. n-1, created on first use.
+ssmul_status ensure_lanes(ssmul_plan_t p, int n) {
+    const size_t slots = p->max_products ? p->max_products : 1;
+    for (int l = 1; l < n; ++l) {
+        if (!p->lane_stream[l])
+            SS_TRY(cudaStreamCreateWithFlags(&p->lane_stream[l], cudaStreamNonBlocking));
+        if (!p->lane_gate[l]) SS_TRY(cudaMalloc(&p->lane_gate[l], (slots + 1) * sizeof(int)));
+    }
+    for (int l = 0; l < n; ++l)
+        if (!p->lane_ev[l]) SS_TRY(cudaEventCreateWithFlags(&p->lane_ev[l], cudaEventDisableTiming));
+    return SSMUL_OK;
+}
+
+// Streams for the pieces of host-buffer calls, of decreasing priority
+// (piece stream l at the device's greatest priority + l, while there are
+// that many levels), created on first use; returns how many exist.
+int ensure_piece_lanes(ssmul_plan_t p, int n, ssmul_status* err) {
+    *err = SSMUL_OK;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+    const int levels = least - greatest + 1;
+    n = std::min(n, std::min(PIECE_LANES, levels < 1 ? 1 : levels));
+    const size_t slots = p->max_products ? p->max_products : 1;
+    for (int l = p->piece_lanes; l < n; ++l) {
+        cudaError_t e = cudaStreamCreateWithPriority(&p->piece_stream[l], cudaStreamNonBlocking,
+                                                     greatest + l);
+        if (e == cudaSuccess) e = cudaMalloc(&p->piece_gate[l], (slots + 1) * sizeof(int));
+        if (e != cudaSuccess) {
+            *err = cuda_status(e);
+            return 0;
+        }
+        p->piece_lanes = l + 1;
+    }
+    for (int l = 0; l <= n; ++l) {
+        if (!p->piece_ev[l] &&
+            cudaEventCreateWithFlags(&p->piece_ev[l], cudaEventDisableTiming) != cudaSuccess) {
+            *err = SSMUL_CUDA_ERROR;
+            return 0;
+        }
+    }
+    return n;
+}
+
+// The enqueue functions launch on `stream` with gate list `gate` while this
+// lives; the lane that was current before is restored after.
+struct OnLane {
+    ssmul_plan_t p;
+    cudaStream_t prev;
+    int* prev_gate;
+    OnLane(ssmul_plan_t p_, cudaStream_t stream, int* gate)
+        : p(p_), prev(p_->cur), prev_gate(p_->cur_gate) {
+        p->cur = stream;
+        p->cur_gate = gate;
+    }
+    ~OnLane() {
+        p->cur = prev;
+        p->cur_gate = prev_gate;
     }
 };
 
@@ -400,19 +492,19 @@ void enqueue_four_step(ssmul_plan_t p, const ProdDesc* d_desc, int count, const 
     {
         LaunchScope ls(p, SSMUL_K_FWD_COLS + ko);
         k_fwd_cols<T, B, R, LIST><<<dim3(t1, count),
-                                    fft_threads<V>(e1), e1 * sizeof(V), p->stream>>>(
+                                    fft_threads<V>(e1), e1 * sizeof(V), p->cur>>>(
             d_desc, tw, g.log_n1, g.log_n2, g.log_c1, list);
     }
     {
         LaunchScope ls(p, SSMUL_K_ROWS + ko);
         k_rows<T, B, R, LIST><<<dim3(t2, count),
-                                fft_threads<V>(2 * n2), 2 * n2 * sizeof(V), p->stream>>>(
+                                fft_threads<V>(2 * n2), 2 * n2 * sizeof(V), p->cur>>>(
             d_desc, tw, g.log_n1, g.log_n2, list);
     }
     {
         LaunchScope ls(p, SSMUL_K_INV_COLS + ko);
         k_inv_cols<T, B, R, LIST><<<dim3(t3, count),
-                                    fft_threads<V>(e3), e3 * sizeof(V), p->stream>>>(
+                                    fft_threads<V>(e3), e3 * sizeof(V), p->cur>>>(
             d_desc, tw, g.log_n1, g.log_n2, g.log_c3, list);
     }
 }
@@ -427,7 +519,7 @@ ssmul_status enqueue_rung_as(ssmul_plan_t p, const ProdDesc* d_desc, int count, 
         const int n = 1 << g.log_n;
         LaunchScope ls(p, SSMUL_K_SMALL + ko);
         k_small<T, B, LIST><<<count, fft_threads<V>(n), n * sizeof(V),
-                              p->stream>>>(d_desc, p->tw(), list);
+                              p->cur>>>(d_desc, p->tw(), list);
     } else if (g.r == 3) {
         enqueue_four_step<T, 3, LIST>(p, d_desc, count, g, list, p->tw(1));
     } else if (g.r == 5) {
@@ -449,9 +541,9 @@ ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, con
     if constexpr (gateable<T>()) {
         {
             LaunchScope ls(p, SSMUL_K_GATE);
-            k_gate_list<<<1, 256, 0, p->stream>>>(d_desc, count, gate, p->gate_list);
+            k_gate_list<<<1, 256, 0, p->cur>>>(d_desc, count, gate, p->cur_gate);
         }
-        return enqueue_rung_as<T, true>(p, d_desc, count, g, p->gate_list);
+        return enqueue_rung_as<T, true>(p, d_desc, count, g, p->cur_gate);
     } else {
         return SSMUL_INVALID_ARG;          // never gated (see gateable)
     }
@@ -517,11 +609,11 @@ ssmul_status enqueue_prefix(ssmul_plan_t p, const ProdDesc* d_desc, int count, s
     {
         LaunchScope ls(p, SSMUL_K_PREFIX);
         k_prefix<<<dim3(unsigned((max_n + PRE_TILE - 1) / PRE_TILE), unsigned(count), 2),
-                   PRE_THREADS, 0, p->stream>>>(d_desc);
+                   PRE_THREADS, 0, p->cur>>>(d_desc);
     }
     {
         LaunchScope ls(p, SSMUL_K_PREFIX);
-        k_prefix_tiles<<<dim3(unsigned(count), 2), 32, 0, p->stream>>>(d_desc);
+        k_prefix_tiles<<<dim3(unsigned(count), 2), 32, 0, p->cur>>>(d_desc);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -693,10 +785,11 @@ size_t arena_need(int log_n) {
 // The batch occupies slots [base, base + count) of the plan's per-product
 // arrays (descriptors, states, look-back words), so that the pieces of one
 // host-buffer call can be prepared while earlier pieces still wait for
-// their descriptor uploads.
+// their descriptor uploads, and bytes [arena_off, arena_off + arena_len) of
+// the arena (pieces that run concurrently take disjoint windows).
 ssmul_status prepare_batch(ssmul_plan_t p, size_t base, size_t count, const ssmul_desc* h_desc,
                            const uint8_t* d_a_pool, const uint8_t* d_b_pool, uint8_t* d_z_pool,
-                           ssmul_result* d_res) {
+                           ssmul_result* d_res, size_t arena_off, size_t arena_len) {
     std::vector<int>& order = p->order;
     order.resize(count);
     std::vector<int> logn(count);
@@ -731,11 +824,11 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t base, size_t count, const ssmu
             const ssmul_desc& hd = h_desc[order[k1]];
             const size_t pb = p->balanced ? pre_bytes(hd.na, hd.nb) : 0;
             const size_t need = arena_need(ln) + pb;
-            if (used + need > p->arena_bytes) break;
+            if (used + need > arena_len) break;
             ProdDesc& d = p->h_desc[base + k1];
-            unsigned char* base = p->arena + used;
+            unsigned char* const ws = p->arena + arena_off + used;   // this product's workspace
             if (pb) {
-                d.pre_a = reinterpret_cast<uint32_t*>(base + arena_need(ln));
+                d.pre_a = reinterpret_cast<uint32_t*>(ws + arena_need(ln));
                 d.pre_b = d.pre_a + pre_words(hd.na);
             }
             if (ln <= LOG_SMALL) {
@@ -743,10 +836,10 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t base, size_t count, const ssmu
                 d.W = nullptr;
             } else {
                 const size_t zb = (len_of(ln) * sizeof(CI<double>) + 255) & ~size_t(255);
-                d.Z = base;
-                d.W = base + zb;
+                d.Z = ws;
+                d.W = ws + zb;
             }
-            d.coeff = reinterpret_cast<int64_t*>(base);
+            d.coeff = reinterpret_cast<int64_t*>(ws);
             used += need;
             ++k1;
         }
@@ -777,34 +870,60 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t base, size_t count, const ssmu
 }
 
 // Device half of a batch: every stream operation of the batch prepared in
-// slots [base, base + count).
-ssmul_status issue_batch(ssmul_plan_t p, size_t base, size_t count) {
+// slots [base, base + count).  With fork_groups and more than one group
+// lane, the length groups of a chunk (independent until the chunk's
+// outcomes) run on up to group_lanes lanes: each group goes to the lane
+// with the least work so far (the groups come longest first), the lanes
+// fork from the plan's stream after the chunk's descriptor upload and join
+// it before the chunk's outcomes are written.
+ssmul_status issue_batch(ssmul_plan_t p, size_t base, size_t count, bool fork_groups = false) {
     ssmul_status s = SSMUL_OK;
     ProdDesc* const dd = p->d_desc + base;
-    SS_TRY(cudaMemsetAsync(p->st + base, 0, count * sizeof(ProdState), p->stream));
+    // the stream and gate list the batch was issued on (a host-buffer
+    // piece's own); group lane 0 is that stream
+    cudaStream_t const origin = p->cur;
+    int* const origin_gate = p->cur_gate;
+    const int lanes = fork_groups && origin == p->stream ? p->group_lanes : 1;
+    SS_TRY(cudaMemsetAsync(p->st + base, 0, count * sizeof(ProdState), p->cur));
     SS_TRY(cudaMemsetAsync(p->flags + base * p->flags_per_product, 0,
-                           count * p->flags_per_product * sizeof(uint32_t), p->stream));
+                           count * p->flags_per_product * sizeof(uint32_t), p->cur));
     for (const BatchChunk& c : p->chunks) {
         SS_TRY(cudaMemcpyAsync(dd + c.k0, p->h_desc + base + c.k0,
                                (c.k1 - c.k0) * sizeof(ProdDesc), cudaMemcpyHostToDevice,
-                               p->stream));
+                               p->cur));
         s = enqueue_prefix(p, dd + c.k0, int(c.k1 - c.k0),
                            p->max_na > p->max_nb ? p->max_na : p->max_nb);
         if (s != SSMUL_OK) return s;
+        const int nl = std::min<int>(lanes, int(c.groups.size()));
+        if (nl > 1) {
+            SS_TRY(cudaEventRecord(p->lane_ev[0], origin));
+            for (int l = 1; l < nl; ++l) SS_TRY(cudaStreamWaitEvent(p->lane_stream[l], p->lane_ev[0], 0));
+        }
+        double load[LANES] = {};
         for (const BatchGroup& g : c.groups) {
+            int lane = 0;
+            for (int l = 1; l < nl; ++l)
+                if (load[l] < load[lane]) lane = l;
+            const double n = double(len_of(g.log_n));
+            load[lane] += double(g.g1 - g.g0) * n * std::log2(n);
+            OnLane on(p, lane ? p->lane_stream[lane] : origin, lane ? p->lane_gate[lane] : origin_gate);
             const Geom& geo = p->geom[g.log_n];
             s = enqueue_rungs(p, p->prec, dd + g.g0, int(g.g1 - g.g0), int(g.e1 - g.g0), geo);
             if (s != SSMUL_OK) return s;
             {
                 LaunchScope ls(p, SSMUL_K_CARRY);
                 k_carry<<<dim3(unsigned(carry_tiles(g.max_nz)), unsigned(g.g1 - g.g0)),
-                          CARRY_THREADS, 0, p->stream>>>(dd + g.g0);
+                          CARRY_THREADS, 0, p->cur>>>(dd + g.g0);
             }
             SS_TRY(cudaGetLastError());
         }
+        for (int l = 1; l < nl; ++l) {
+            SS_TRY(cudaEventRecord(p->lane_ev[l], p->lane_stream[l]));
+            SS_TRY(cudaStreamWaitEvent(origin, p->lane_ev[l], 0));
+        }
         {
             LaunchScope ls(p, SSMUL_K_FINALIZE);
-            k_finalize<<<unsigned(c.k1 - c.k0), 256, 0, p->stream>>>(dd + c.k0);
+            k_finalize<<<unsigned(c.k1 - c.k0), 256, 0, p->cur>>>(dd + c.k0);
         }
         SS_TRY(cudaGetLastError());
     }
@@ -836,10 +955,12 @@ ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
         SS_TRY(cudaEventRecord(p->desc_free, p->stream));
         return SSMUL_OK;
     }
-    ssmul_status s = prepare_batch(p, 0, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res);
+    ssmul_status s = prepare_batch(p, 0, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res, 0,
+                                   p->arena_bytes);
     if (s != SSMUL_OK) return s;
+    if ((s = ensure_lanes(p, p->group_lanes)) != SSMUL_OK) return s;
     if (!use_graph) {
-        s = issue_batch(p, 0, count);
+        s = issue_batch(p, 0, count, true);
         if (s != SSMUL_OK) return s;
         SS_TRY(cudaEventRecord(p->desc_free, p->stream));
         return SSMUL_OK;
@@ -848,7 +969,7 @@ ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_des
     std::memset(p->cap_launches, 0, sizeof(p->cap_launches));
     SS_TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
     p->capturing = true;
-    s = issue_batch(p, 0, count);
+    s = issue_batch(p, 0, count, true);
     p->capturing = false;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(p->stream, &graph);
@@ -1123,6 +1244,18 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
     if (!p->up) SS_TRY(cudaStreamCreateWithFlags(&p->up, cudaStreamNonBlocking));
     if (!p->down) SS_TRY(cudaStreamCreateWithFlags(&p->down, cudaStreamNonBlocking));
     const size_t pieces = std::min(count, size_t(p->host_pieces));
+    // The pieces run on internal streams of decreasing priority with
+    // disjoint windows of the arena: the block scheduler starts a later
+    // piece's thread blocks only where an earlier piece leaves SMs idle (its
+    // last waves), so the pieces finish in order, each download overlaps the
+    // next pieces' work, and no piece waits for another's tail.  Fewer
+    // streams when a window could not hold a product of the plan's largest
+    // size (a piece reuses a stream, and its window, after the piece before).
+    const size_t one = arena_need(p->log_n_max) + pre_bytes(p->max_na, p->max_nb);
+    int lanes = ensure_piece_lanes(p, int(pieces), &s);
+    if (s != SSMUL_OK) return s;
+    while (lanes > 1 && ((p->arena_bytes / lanes) & ~size_t(255)) < one) --lanes;
+    const size_t window = lanes > 1 ? (p->arena_bytes / lanes) & ~size_t(255) : p->arena_bytes;
     while (p->hb_ev.size() < 2 * pieces) {
         cudaEvent_t e = nullptr;
         SS_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1148,9 +1281,15 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
     auto drain = [&](ssmul_status e) {
         cudaStreamSynchronize(p->up);
         cudaStreamSynchronize(p->stream);
+        for (int l = 0; l < lanes; ++l) cudaStreamSynchronize(p->piece_stream[l]);
         cudaStreamSynchronize(p->down);
         return e;
     };
+    // the pieces follow the work already queued on the plan's stream
+    SS_TRY(cudaEventRecord(p->piece_ev[0], p->stream));
+    for (int l = 0; l < lanes; ++l)
+        if (cudaStreamWaitEvent(p->piece_stream[l], p->piece_ev[0], 0) != cudaSuccess)
+            return drain(SSMUL_CUDA_ERROR);
     for (size_t k = 0; k < pieces; ++k) {
         const size_t i0 = count * k / pieces, i1 = count * (k + 1) / pieces;
         uint64_t ea = 0, eb = 0;
@@ -1161,14 +1300,23 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
         if ((s = ua.upload(ea, p->hb_a, a_lo, h_a, p->up)) != SSMUL_OK) return drain(s);
         if ((s = ub.upload(eb, p->hb_b, b_lo, h_b, p->up)) != SSMUL_OK) return drain(s);
         cudaEvent_t in = p->hb_ev[2 * k], done = p->hb_ev[2 * k + 1];
+        const int lane = int(k % lanes);
+        OnLane on(p, p->piece_stream[lane], p->piece_gate[lane]);
         if (cudaEventRecord(in, p->up) != cudaSuccess ||
-            cudaStreamWaitEvent(p->stream, in, 0) != cudaSuccess)
+            cudaStreamWaitEvent(p->cur, in, 0) != cudaSuccess)
             return drain(SSMUL_CUDA_ERROR);
         s = prepare_batch(p, i0, i1 - i0, rd.data() + i0, p->hb_a, p->hb_b, p->hb_z,
-                          p->hb_res + i0);
+                          p->hb_res + i0, lane * window, window);
         if (s == SSMUL_OK) s = issue_batch(p, i0, i1 - i0);
         if (s != SSMUL_OK) return drain(s);
-        if (cudaEventRecord(done, p->stream) != cudaSuccess) return drain(SSMUL_CUDA_ERROR);
+        if (cudaEventRecord(done, p->cur) != cudaSuccess) return drain(SSMUL_CUDA_ERROR);
+    }
+    // the plan's stream joins the pieces' streams, so later work on it
+    // follows the call
+    for (int l = 0; l < lanes; ++l) {
+        if (cudaEventRecord(p->piece_ev[1 + l], p->piece_stream[l]) != cudaSuccess ||
+            cudaStreamWaitEvent(p->stream, p->piece_ev[1 + l], 0) != cudaSuccess)
+            return drain(SSMUL_CUDA_ERROR);
     }
     if (cudaEventRecord(p->desc_free, p->stream) != cudaSuccess) return drain(SSMUL_CUDA_ERROR);
     std::vector<std::pair<uint64_t, uint64_t>> zr;
@@ -1248,6 +1396,20 @@ void ssmul_plan_destroy(ssmul_plan_t p) {
     cudaFree(p->hb_b);
     cudaFree(p->hb_z);
     cudaFree(p->hb_res);
+    for (int l = 1; l < LANES; ++l) {
+        if (p->lane_stream[l]) cudaStreamSynchronize(p->lane_stream[l]);
+        if (p->lane_stream[l]) cudaStreamDestroy(p->lane_stream[l]);
+        cudaFree(p->lane_gate[l]);
+    }
+    for (cudaEvent_t e : p->lane_ev)
+        if (e) cudaEventDestroy(e);
+    for (int l = 0; l < p->piece_lanes; ++l) {
+        cudaStreamSynchronize(p->piece_stream[l]);
+        cudaStreamDestroy(p->piece_stream[l]);
+        cudaFree(p->piece_gate[l]);
+    }
+    for (cudaEvent_t e : p->piece_ev)
+        if (e) cudaEventDestroy(e);
     if (p->up) cudaStreamDestroy(p->up);
     if (p->down) cudaStreamDestroy(p->down);
     for (cudaEvent_t e : p->hb_ev) cudaEventDestroy(e);
@@ -1290,6 +1452,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
         return fail(SSMUL_CUDA_ERROR);
     p->stream = static_cast<cudaStream_t>(cuda_stream);
+    p->cur = p->stream;
     p->prec = prec;
     p->max_na = max_na;
     p->max_nb = max_nb;
@@ -1329,6 +1492,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     if (e == cudaSuccess) e = cudaMalloc(&p->st, slots * sizeof(ProdState));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, slots * sizeof(ProdDesc));
     if (e == cudaSuccess) e = cudaMalloc(&p->gate_list, (slots + 1) * sizeof(int));
+    p->cur_gate = p->gate_list;
     if (e == cudaSuccess) e = cudaMalloc(&p->d_res, slots * sizeof(ssmul_result));
     if (e == cudaSuccess) e = cudaMalloc(&p->stage, 2 * (max_na + max_nb));
     if (e == cudaSuccess) e = cudaMalloc(&p->pre, pre_bytes(max_na, max_nb));
@@ -1425,6 +1589,12 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
             SS_TRY(cudaStreamSynchronize(p->stream));
             graph_drop(p->cached);
             p->balanced = value != 0;
+            return SSMUL_OK;
+        case SSMUL_OPT_LANES:
+            if (value < 1 || value > LANES) return SSMUL_INVALID_ARG;
+            SS_TRY(cudaStreamSynchronize(p->stream));
+            graph_drop(p->cached);
+            p->group_lanes = int(value);
             return SSMUL_OK;
         case SSMUL_OPT_HOST_PIECES:
             if (value < 1 || value > 64) return SSMUL_INVALID_ARG;

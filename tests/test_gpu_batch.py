@@ -169,3 +169,31 @@ def test_bench_configuration_75k(prec):
             assert np.array_equal(z[z_off[i]:z_off[i] + 2 * n], expect[i]), i
             assert 0.0 <= res[i].max_width < 1.0
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("prec", [abi.SSMUL_PREC_LADDER, abi.SSMUL_PREC_LADDER_FAST])
+def test_group_lanes_same_outcomes_eager_and_graph(prec):
+    """SSMUL_OPT_LANES spreads the length groups over several streams: the
+    outcomes (status, deciding rung, width) and digits equal the one-lane
+    run's, eager and graph-replayed, and the digits are the oracle's."""
+    pairs = _pairs(3, 90, 3, 40000)
+    mx = max(max(len(a), len(b)) for a, b in pairs)
+    expect = [E.product(a, b) for a, b in pairs]
+    runs = []
+    for lanes, graph in [(1, 0), (4, 0), (3, 1), (2, 1)]:
+        with StreamPlan(mx, mx, 100, prec) as p:
+            with torch.cuda.stream(p.stream):
+                assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_LANES, lanes) == OK
+                assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_GRAPH, graph) == OK
+                pools = None
+                for _ in range(2 if graph else 1):       # capture, then a replay
+                    s, res, z, pools = _run_batch_on(p, pairs, pools)
+                    assert s == OK
+                    runs.append(([r.as_dict() for r in res], z))
+    for res, z in runs:
+        assert res == runs[0][0]
+        for r, zi, ei in zip(res, z, expect):
+            assert r["status"] == OK and np.array_equal(zi, ei)
+    with Plan(10, 10, 1) as p:
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_LANES, 0) == abi.SSMUL_INVALID_ARG
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_LANES, 5) == abi.SSMUL_INVALID_ARG
