@@ -78,10 +78,14 @@ def parse():
     ap.add_argument("--lengths", type=int, default=3, choices=[0, 1, 2, 3],
                     help="transform length families besides 2^k (SSMUL_OPT_LENGTHS bit mask: "
                          "1 = 3 2^k, 2 = 5 2^k)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "sweep", "ladder", "uneven", "split"],
-                    help="paper: the headline line; sweep / ladder / uneven / split: report "
-                         "lines of the size sweep, the precision ladder, the uneven batch and "
-                         "the products past the isolation limit")
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "c1", "sweep", "ladder", "uneven", "split"],
+                    help="paper: the headline line (with the c1, c3, c4 and c5 reports unless "
+                         "--no-reports); c1 / sweep / ladder / uneven / split: one report line "
+                         "(one 4096-digit product, the size sweep, the precision ladder, the "
+                         "uneven batch, the products past the isolation limit)")
+    ap.add_argument("--no-reports", action="store_true",
+                    help="headline line only (no c1 / c3 / c4 / c5 reports)")
     return ap.parse_args()
 
 
@@ -633,6 +637,20 @@ def run_ours(args):
                 alternatives[alt]["unverified_digits_matched"] = f"{a_match}/{args.steps * B}"
                 alternatives[alt]["unverified_multiplies_per_s"] = a_match / a_t
 
+    # the other configurations of the method, each verified bit-exact against
+    # the oracle (single GPU only: they are reports, not the weak-scaled step)
+    reports = None
+    if world == 1 and not args.no_reports:
+        import bench_reports
+        ctx = bench_reports.Ctx(lanes=args.lanes)
+        t_rep = time.perf_counter()
+        try:
+            reports = {"c1": bench_reports.c1(ctx), "c3": bench_reports.c3(ctx),
+                       "c4": bench_reports.c4(ctx), "c5": bench_reports.c5(ctx)}
+        finally:
+            ctx.close()
+        reports["wall_s"] = time.perf_counter() - t_rep
+
     t_steps = sum(step_ms) / 1e3
     value, e2e_value = aggregate_ranks(t_steps, verified, e2e_s, B, world, dev)
     if not e2e_ok:
@@ -715,6 +733,7 @@ def run_ours(args):
                                      "measured copy bandwidth; the path is arithmetic-pipe "
                                      "bound"},
             "cpu_baseline": cpu,
+            "reports": reports,
             "clocks": clk,
             "wall_s": wall,
         }

@@ -1,27 +1,31 @@
-"""Report workloads of bench.py (`--workload sweep | ladder | uneven`).
+"""Report workloads of the benchmark: the configurations besides the 75k headline.
 
-sweep   square products of 2^k uniform digits, k = 10 .. 22, and the
-        unbalanced pair 2^20 x 2^12, in binary64: status, largest interval
-        width, time per product; the largest length at which every
-        coefficient is still isolated.  Also the binary32 isolation limit
-        (square sizes 2 .. 64 digits).
-ladder  4,096 square products, n ~ U{512..32768}, 10% all-0xFF: the ladder
-        (binary32 first, binary64 on failure) in one batched call, plain
-        binary64 batched, and plain binary64 one product at a time; verified
-        digits/s of each and the fraction resolved in binary32.
-uneven  20,000 products with na, nb independent and log-uniform in
-        [64, 131072]: the ladder in one graph-captured batched call against
-        the same set one product at a time in binary64.
-split   square products of 2^19 .. 2^22 uniform digits, past the binary64
-        rectangles' isolation limit: rectangles on the whole product, the
-        same cut into parts of 2^18 digits (SSMUL_OPT_SPLIT_DIGITS, Section
-        1's "different algorithm"), and binary64 discs on the whole product;
-        status, time per product and residue verification of each.
+c1      one product of two 4,096-digit uniform operands (FFT length 8,192),
+        binary64 rectangles through ssmul_mul, checked against the oracle's
+        long multiplication (schoolbook), whose time on one host core is
+        reported beside it.
+c3      the size sweep: square products of 2^k uniform digits, k = 10 .. 22,
+        and the unbalanced 2^20 x 2^12, under binary64 rectangles, binary64
+        discs and double-binary32 discs: status, largest width and time per
+        product; the largest square size every rung still isolates.  Also
+        the binary32 rectangle limit (squares of 1 .. 64 digits).
+c4      the precision ladder: 4,096 square products, n ~ U{512..32768}, 10%
+        all-0xFF: the ladder (binary32 first, binary64 on failure) batched,
+        binary64 batched, the fast ladder batched, and binary64 one product
+        at a time; verified digits/s of each and the fraction resolved in
+        binary32, per size.
+c5      the uneven batch: 20,000 products with na, nb independent and
+        log-uniform in [64, 131072], the ladders in one graph-captured
+        batched call against binary64 one product at a time.
+split   square products of 2^19 .. 2^22 digits, past the rectangles'
+        isolation limit: rectangles on the whole product, the same cut into
+        parts of 2^18 digits (Section 1's "different algorithm"), and
+        binary64 discs on the whole product.
 
-Verification is against the CPU oracle: every product's digits against the
-exact product for sweep and ladder; for the uneven batch every product's
-residues modulo two primes plus the full digits of a seeded 5% sample.
-Each workload prints one JSON line.
+Every product counted as verified has status SSMUL_OK and digits equal to
+the CPU oracle's exact product (bench_verify).  `python bench.py --workload
+sweep|ladder|uneven|split` prints one report as a JSON line; the default
+`python bench.py` run embeds c1, c3, c4 and c5 in its line.
 """
 from __future__ import annotations
 
@@ -32,32 +36,47 @@ import time
 import numpy as np
 
 import synth
+from bench_verify import OraclePool, batch_jobs, digest
 
-PRIMES = (2**61 - 1, 1_000_000_007)
 
+class Ctx:
+    """torch, the C ABI and a lazily started oracle pool."""
 
-def _torch():
-    import torch
-    if not torch.cuda.is_available():
-        raise SystemExit("the report workloads need a CUDA device")
-    return torch
+    def __init__(self, lanes: int = 4):
+        import torch
+        if not torch.cuda.is_available():
+            raise SystemExit("the report workloads need a CUDA device")
+        from paper_1006_0405_gb300 import abi
+        abi.load()
+        self.torch, self.abi, self.lanes = torch, abi, lanes
+        self._pool = None
+
+    def pool(self) -> OraclePool:
+        if self._pool is None:
+            self._pool = OraclePool()
+        return self._pool
+
+    def close(self):
+        if self._pool is not None:
+            self._pool.close()
+            self._pool = None
 
 
 class Batch:
-    """Device pools and descriptors of a batch."""
+    """Device pools and descriptors of a batch drawn by synth.batch_operands."""
 
-    def __init__(self, torch, seed, na, nb, dists):
+    def __init__(self, torch, abi, seed, na, nb, dists):
+        self.seed, self.dists = seed, list(dists)
         self.na = np.asarray(na, np.int64)
         self.nb = np.asarray(nb, np.int64)
         (self.a_pool, self.b_pool, self.a_off, self.b_off, self.z_off) = \
             synth.batch_operands(seed, self.na, self.nb, dists)
         self.nz = self.na + self.nb
         self.count = len(self.na)
+        self.torch, self.abi = torch, abi
         self.da = torch.from_numpy(self.a_pool).cuda()
         self.db = torch.from_numpy(self.b_pool).cuda()
         self.dz = torch.zeros(int(self.nz.sum()), dtype=torch.uint8, device="cuda")
-        from paper_1006_0405_gb300 import abi
-        self.abi = abi
         self.res_bytes = ctypes.sizeof(abi.ssmul_result) * self.count
         self.dres = torch.zeros(self.res_bytes, dtype=torch.uint8, device="cuda")
         self.descs = (abi.ssmul_desc * self.count)()
@@ -65,11 +84,8 @@ class Batch:
             self.descs[i] = abi.ssmul_desc(int(self.a_off[i]), int(self.b_off[i]),
                                            int(self.z_off[i]), int(self.na[i]), int(self.nb[i]))
 
-    def a(self, i):
-        return self.a_pool[self.a_off[i]:self.a_off[i] + self.na[i]]
-
-    def b(self, i):
-        return self.b_pool[self.b_off[i]:self.b_off[i] + self.nb[i]]
+    def jobs(self):
+        return batch_jobs(self.seed, self.na, self.nb, self.dists)
 
     def run(self, plan):
         s = self.abi.ssmul_mul_batched(plan, self.descs, self.da.data_ptr(), self.db.data_ptr(),
@@ -87,11 +103,19 @@ class Batch:
         z = self.dz.cpu().numpy()
         return [z[self.z_off[i]:self.z_off[i] + self.nz[i]] for i in range(self.count)]
 
+    def clear(self):
+        self.dz.fill_(0xA5)
+        self.dres.zero_()
+        self.torch.cuda.synchronize()
+
 
 def _time_batch(torch, plan, batch, reps, stream):
+    """Seconds per batched call: one untimed call (it captures the CUDA graph
+    when the plan replays graphs), then `reps` calls timed with events on the
+    plan's stream."""
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
-        batch.run(plan)                     # warm-up (and graph capture)
+        batch.run(plan)
         stream.synchronize()
         ev0.record(stream)
         for _ in range(reps):
@@ -102,6 +126,8 @@ def _time_batch(torch, plan, batch, reps, stream):
 
 
 def _one_at_a_time(torch, abi, batch, max_n, prec):
+    """Every product by its own ssmul_mul call (which waits for it), binary64;
+    returns (seconds, results)."""
     plan = abi.ssmul_plan(max_n, max_n, 0, prec, 0)
     torch.cuda.synchronize()
     outs = []
@@ -111,240 +137,294 @@ def _one_at_a_time(torch, abi, batch, max_n, prec):
         s, r = abi.ssmul_mul(plan, batch.da.data_ptr() + int(batch.a_off[i]), int(batch.na[i]),
                              batch.db.data_ptr() + int(batch.b_off[i]), int(batch.nb[i]),
                              dz.data_ptr())
-        outs.append((s, r.precision_used))
+        outs.append(r)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     abi.ssmul_plan_destroy(plan)
     return el, outs
 
 
-def _expected(batch, idx=None):
-    """Exact products from the CPU oracle (NTT convolution and carry)."""
+def _size_buckets(nz):
+    """log2 buckets of the output digits (na + nb) of each product."""
+    return np.floor(np.log2(np.maximum(nz, 1))).astype(int)
+
+
+def _fp32_fraction_by_size(abi, results, nz):
+    b = _size_buckets(nz)
+    out = {}
+    for k in sorted(set(b.tolist())):
+        idx = np.nonzero(b == k)[0]
+        fp32 = sum(1 for i in idx if results[i].status == abi.SSMUL_OK and
+                   results[i].precision_used == abi.SSMUL_PREC_FP32)
+        out[f"2^{k}..2^{k + 1}"] = round(fp32 / len(idx), 4)
+    return out
+
+
+def _statuses(abi, results):
+    st = {}
+    for r in results:
+        k = abi.status_string(r.status)
+        st[k] = st.get(k, 0) + 1
+    return st
+
+
+def _used(abi, results):
+    names = {abi.SSMUL_PREC_FP32: "fp32", abi.SSMUL_PREC_FP64: "fp64",
+             abi.SSMUL_PREC_DISC64: "disc64", abi.SSMUL_PREC_DISC32X2: "disc32x2",
+             abi.SSMUL_PREC_NAIVE64: "naive64"}
+    out = {}
+    for r in results:
+        if r.status == abi.SSMUL_OK:
+            k = names.get(r.precision_used, str(r.precision_used))
+            out[k] = out.get(k, 0) + 1
+    return out
+
+
+# ---- C1: one 4,096 x 4,096-digit product ---------------------------------------
+
+def c1(ctx, reps: int = 20) -> dict:
+    torch, abi = ctx.torch, ctx.abi
     from oracle import exact as E
-    idx = range(batch.count) if idx is None else idx
-    return {i: E.carry(E.conv_ntt(batch.a(i), batch.b(i)), int(batch.nz[i])) for i in idx}
+    n = 4096
+    a, b = synth.operand_pair(synth.SEED_BASE + 1, n, n)
+    plan = abi.ssmul_plan(n, n, 0, abi.SSMUL_PREC_FP64, 0)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    dz = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
+    abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
+        times.append(time.perf_counter() - t0)
+    abi.ssmul_plan_destroy(plan)
+    z = dz.cpu().numpy()
+    t0 = time.perf_counter()
+    school = E.long_mul(a, b)                   # Section 2.1, single thread
+    t_school = time.perf_counter() - t0
+    ok = bool(s == abi.SSMUL_OK and np.array_equal(z, school))
+    return {"workload": f"{n}x{n} base-256 digits, uniform, binary64 rectangles, one product "
+                        f"per ssmul_mul call (which waits for it), FFT length "
+                        f"{r.fft_odd << r.fft_log2}",
+            "ms_per_product": 1e3 * float(np.median(times)), "multiplies_per_s":
+                1.0 / float(np.median(times)) if ok else 0.0,
+            "status": abi.status_string(s), "max_width": r.max_width,
+            "verified": f"{int(ok)}/1 against schoolbook long multiplication",
+            "schoolbook_cpu_ms_one_core": 1e3 * t_school}
 
 
-def _verify_full(rs, zs, expect):
-    return sum(1 for i, e in expect.items() if rs[i].status == 0 and np.array_equal(zs[i], e))
+# ---- C3: the size sweep ---------------------------------------------------------
+
+C3_SIZES = [(1 << k, 1 << k) for k in range(10, 23)] + [(1 << 20, 1 << 12)]
 
 
-def _verify_residues(batch, rs, zs):
-    from oracle import exact as E
-    ok = np.zeros(batch.count, bool)
-    for i in range(batch.count):
-        if rs[i].status != 0:
-            continue
-        good = True
-        for q in PRIMES:
-            if E.residue(zs[i], q) != E.residue(batch.a(i), q) * E.residue(batch.b(i), q) % q:
-                good = False
-                break
-        ok[i] = good
-    return ok
+def _rungs(abi):
+    return (("fp64", abi.SSMUL_PREC_FP64), ("disc64", abi.SSMUL_PREC_DISC64),
+            ("disc32x2", abi.SSMUL_PREC_DISC32X2))
 
 
-def sweep(args):
-    torch = _torch()
-    from oracle import exact as E
-    from paper_1006_0405_gb300 import abi
-    abi.load()
-    sizes = [(1 << k, 1 << k) for k in range(10, 23)] + [(1 << 20, 1 << 12)]
-    prec = {"fp64": abi.SSMUL_PREC_FP64, "disc64": abi.SSMUL_PREC_DISC64,
-            "naive64": abi.SSMUL_PREC_NAIVE64, "disc32x2": abi.SSMUL_PREC_DISC32X2,
-            "ladder_fast": abi.SSMUL_PREC_LADDER_FAST}[args.precision]
-    rows = []
-    largest = None
-    for na, nb in sizes:
-        for dist in ("uniform", "ff"):
-            a, b = synth.operand_pair(synth.SEED_BASE + 3, na, nb, dist)
+def c3(ctx, sizes=C3_SIZES, dists=("uniform",), balanced=False, fp32_limit=True) -> dict:
+    torch, abi = ctx.torch, ctx.abi
+    seed = synth.SEED_BASE + 3
+    cases = [(na, nb, dist) for na, nb in sizes for dist in dists]
+    rows, got = [], []
+    for na, nb, dist in cases:
+        a, b = synth.operand_pair(seed, na, nb, dist)
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        dz = torch.zeros(na + nb, dtype=torch.uint8, device="cuda")
+        row = {"na": na, "nb": nb, "dist": dist}
+        for name, prec in _rungs(abi):
             plan = abi.ssmul_plan(na, nb, 0, prec, 0)
-            if args.balanced:
+            if balanced:
                 abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
-            da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
-            dz = torch.zeros(na + nb, dtype=torch.uint8, device="cuda")
             abi.ssmul_mul(plan, da.data_ptr(), na, db.data_ptr(), nb, dz.data_ptr())
             reps = 3
-            torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
+                dz.fill_(0xA5)
                 s, r = abi.ssmul_mul(plan, da.data_ptr(), na, db.data_ptr(), nb, dz.data_ptr())
             el = (time.perf_counter() - t0) / reps
             abi.ssmul_plan_destroy(plan)
-            z = dz.cpu().numpy()
-            exact = bool(s in (abi.SSMUL_OK, abi.SSMUL_UNVERIFIED) and
-                         np.array_equal(z, E.carry(E.conv_ntt(a, b), na + nb)))
-            rows.append({"na": na, "nb": nb, "dist": dist, "log2_N": r.fft_log2, "N": r.fft_odd << r.fft_log2,
-                         "status": abi.status_string(s), "max_width": r.max_width,
-                         "n_unisolated": r.n_unisolated, "verified": exact, "ms": 1e3 * el})
-            if na == nb and dist == "uniform" and exact and (largest == na // 2 or largest is None):
-                largest = na
-    # binary32 isolation limit
-    f32_ok = []
-    plan = abi.ssmul_plan(64, 64, 0, abi.SSMUL_PREC_FP32, 0)
-    for n in range(1, 65):
-        good = True
-        for t in range(8):
+            row[name] = {"status": abi.status_string(s), "max_width": r.max_width,
+                         "N": r.fft_odd << r.fft_log2, "ms": 1e3 * el}
+            got.append((row, name, s, digest(dz.cpu().numpy())))
+        rows.append(row)
+    expected = ctx.pool().digests([("pair", seed, na, nb, dist, "ntt") for na, nb, dist in cases])
+    exp_of = {id(row): e for row, e in zip(rows, expected)}
+    for row, name, s, dg in got:
+        row[name]["verified"] = bool(s == abi.SSMUL_OK and dg == exp_of[id(row)])
+    largest = {}
+    for name, _ in _rungs(abi):
+        best = None
+        for row in rows:
+            if row["na"] != row["nb"] or row["dist"] != "uniform":
+                continue
+            if not row[name]["verified"]:
+                break
+            best = row["na"]
+        largest[name] = best
+    n_ok = sum(1 for row, name, s, _ in got if s == abi.SSMUL_OK)
+    n_ver = sum(1 for row, name, s, _ in got if row[name]["verified"])
+    out = {"workload": "square products of 2^k uniform digits, k = 10..22, and 2^20 x 2^12; "
+                       "one product per ssmul_mul call", "balanced_digits": balanced,
+           "rows": rows, "largest_isolated_square_digits": largest,
+           "verified": f"{n_ver}/{n_ok} products with status SSMUL_OK are bit-exact"}
+    if fp32_limit:
+        out["fp32_rectangles"] = fp32_isolation_limit(ctx, balanced=balanced)
+    return out
+
+
+def fp32_isolation_limit(ctx, max_n: int = 64, per_size: int = 8, balanced=False) -> dict:
+    """The largest n such that binary32 rectangles isolate every one of
+    `per_size` uniform n x n products for all sizes up to n."""
+    torch, abi = ctx.torch, ctx.abi
+    from oracle import exact as E
+    plan = abi.ssmul_plan(max_n, max_n, 0, abi.SSMUL_PREC_FP32, 0)
+    if balanced:
+        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
+    limit, done = 0, False
+    for n in range(1, max_n + 1):
+        for t in range(per_size):
             a, b = synth.operand_pair(synth.SEED_BASE + 1000 * n + t, n, n)
             da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
             dz = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
             s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
-            if s != abi.SSMUL_OK or not np.array_equal(dz.cpu().numpy(), E.product(a, b)):
-                good = False
-        f32_ok.append(good)
-    abi.ssmul_plan_destroy(plan)
-    f32_limit = 0
-    for n, g in enumerate(f32_ok, start=1):
-        if not g:
+            if s != abi.SSMUL_OK or not np.array_equal(dz.cpu().numpy(), E.long_mul(a, b)):
+                done = True
+                break
+        if done:
             break
-        f32_limit = n
-    print(json.dumps({"report": "sweep", "precision": args.precision,
-                      "balanced_digits": bool(args.balanced), "rows": rows,
-                      "largest_isolated_square_digits": largest,
-                      "largest_isolated_square_digits_fp32": f32_limit,
-                      "fp32_note": "8 uniform products per size, all isolated up to this size"}),
-          flush=True)
+        limit = n
+    abi.ssmul_plan_destroy(plan)
+    return {"largest_square_digits": limit, "note": f"{per_size} uniform products per size, "
+                                                    f"all isolated and exact up to this size"}
 
 
-def ladder(args):
-    torch = _torch()
-    from paper_1006_0405_gb300 import abi
-    abi.load()
-    seed = synth.SEED_BASE + 4
-    na, nb, dists = synth.ladder_batch(seed, count=4096)
-    batch = Batch(torch, seed, na, nb, dists)
-    max_n = int(max(na.max(), nb.max()))
+# ---- C4 and C5: batches of many products -------------------------------------------
+
+def _batch_report(ctx, seed, na, nb, dists, lanes, one_lane=False) -> dict:
+    torch, abi = ctx.torch, ctx.abi
+    batch = Batch(torch, abi, seed, na, nb, dists)
+    max_n = int(max(batch.na.max(), batch.nb.max()))
     stream = torch.cuda.Stream()
-    expect = _expected(batch)
-    out = {"report": "ladder", "count": batch.count, "digits_total": int(batch.nz.sum())}
-    for name, prec in (("ladder_batched", abi.SSMUL_PREC_LADDER), ("fp64_batched", abi.SSMUL_PREC_FP64),
-                       ("ladder_fast_batched", abi.SSMUL_PREC_LADDER_FAST)):
-        plan = abi.ssmul_plan(max_n, max_n, batch.count, prec, stream.cuda_stream)
-        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 1)
-        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_LANES, args.lanes)
-        t = _time_batch(torch, plan, batch, 3, stream)
-        rs, zs = batch.results(), batch.digits()
-        ok = _verify_full(rs, zs, expect)
-        fp32 = sum(1 for r in rs if r.status == 0 and r.precision_used == abi.SSMUL_PREC_FP32)
-        used = {}
-        for r in rs:
-            used[r.precision_used] = used.get(r.precision_used, 0) + 1
-        out[name] = {"s_per_batch": t, "verified": ok, "precision_used": used,
-                     "verified_digits_per_s": float(sum(batch.nz[i] for i in range(batch.count)
-                                                        if rs[i].status == 0)) / t,
-                     "resolved_fp32": fp32, "fraction_fp32": fp32 / batch.count}
-        abi.ssmul_plan_destroy(plan)
-    el, outs = _one_at_a_time(torch, abi, batch, max_n, abi.SSMUL_PREC_FP64)
-    zs = batch.digits()
-    rs1 = [type("R", (), {"status": s})() for s, _ in outs]
-    ok = _verify_full(rs1, zs, expect)
-    out["fp64_one_at_a_time"] = {"s_total": el, "verified": ok,
-                                 "verified_digits_per_s": float(batch.nz.sum()) / el}
-    print(json.dumps(out), flush=True)
+    out = {"count": batch.count, "output_digits_total": int(batch.nz.sum()), "lanes": lanes}
+    runs = [("ladder_batched", abi.SSMUL_PREC_LADDER), ("fp64_batched", abi.SSMUL_PREC_FP64),
+            ("ladder_fast_batched", abi.SSMUL_PREC_LADDER_FAST)]
+    # the GPU runs first, then the oracle (no host load during the timings)
+    digits = {}
+    for key, prec in runs:
+        digits[key] = _batched_gpu(ctx, batch, max_n, prec, stream, lanes)
+    if one_lane:
+        digits["ladder_batched_one_lane"] = _batched_gpu(ctx, batch, max_n, abi.SSMUL_PREC_LADDER,
+                                                         stream, 1)
+    batch.clear()
+    el, rs1 = _one_at_a_time(torch, abi, batch, max_n, abi.SSMUL_PREC_FP64)
+    digits["fp64_one_at_a_time"] = (el, rs1, [digest(z) for z in batch.digits()])
+    expected = ctx.pool().digests(batch.jobs())
+    for key, (t, rs, dg) in digits.items():
+        n_ver = d_ver = 0
+        for r, d, e, nz in zip(rs, dg, expected, batch.nz):
+            if r.status == abi.SSMUL_OK and d == e:
+                n_ver += 1
+                d_ver += int(nz)
+        fp32 = sum(1 for r in rs if r.status == abi.SSMUL_OK and
+                   r.precision_used == abi.SSMUL_PREC_FP32)
+        entry = {("s_total" if key == "fp64_one_at_a_time" else "s_per_batch"): t,
+                 "verified_digits_per_s": d_ver / t, "verified": f"{n_ver}/{batch.count}",
+                 "statuses": _statuses(abi, rs), "deciding_rung": _used(abi, rs)}
+        if key.startswith("ladder"):
+            entry["fraction_fp32"] = fp32 / batch.count
+            entry["fraction_fp32_by_output_digits"] = _fp32_fraction_by_size(abi, rs, batch.nz)
+        out[key] = entry
+    base = out["fp64_one_at_a_time"]["verified_digits_per_s"]
+    for key in ("ladder_batched", "fp64_batched", "ladder_fast_batched"):
+        out["speedup_" + key + "_vs_fp64_one_at_a_time"] = \
+            out[key]["verified_digits_per_s"] / base if base else None
+    if one_lane:
+        t1 = out["ladder_batched_one_lane"]["s_per_batch"]
+        out["lanes_saving"] = 1.0 - out["ladder_batched"]["s_per_batch"] / t1
+    return out
 
 
-def uneven(args):
-    torch = _torch()
-    from paper_1006_0405_gb300 import abi
-    abi.load()
-    seed = synth.SEED_BASE + 5
-    na, nb, dists = synth.uneven_batch(seed, count=20000)
-    batch = Batch(torch, seed, na, nb, dists)
-    max_n = int(max(na.max(), nb.max()))
-    stream = torch.cuda.Stream()
-    out = {"report": "uneven", "count": batch.count, "digits_total": int(batch.nz.sum()),
-           "lanes": args.lanes}
-    for name, prec in (("ladder_graph_batched", abi.SSMUL_PREC_LADDER),
-                       ("ladder_fast_graph_batched", abi.SSMUL_PREC_LADDER_FAST)):
-        out[name] = _uneven_batched(torch, abi, batch, max_n, prec, stream, seed, args.lanes)
-    el, outs = _one_at_a_time(torch, abi, batch, max_n, abi.SSMUL_PREC_FP64)
-    zs = batch.digits()
-    rs1 = [type("R", (), {"status": s})() for s, _ in outs]
-    ok1 = _verify_residues(batch, rs1, zs)
-    out["fp64_one_at_a_time"] = {"s_total": el,
-                                 "verified_digits_per_s": float(sum(batch.nz[i] for i in range(batch.count) if ok1[i])) / el,
-                                 "residue_verified": int(ok1.sum())}
-    for name in ("ladder_graph_batched", "ladder_fast_graph_batched"):
-        out["speedup_" + name] = out[name]["verified_digits_per_s"] / \
-            out["fp64_one_at_a_time"]["verified_digits_per_s"]
-    print(json.dumps(out), flush=True)
-
-
-def _uneven_batched(torch, abi, batch, max_n, prec, stream, seed, lanes=1):
+def _batched_gpu(ctx, batch, max_n, prec, stream, lanes):
+    """(seconds per graph-replayed batched call, results, digit digests)."""
+    torch, abi = ctx.torch, ctx.abi
     plan = abi.ssmul_plan(max_n, max_n, batch.count, prec, stream.cuda_stream)
     abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 1)
     abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_LANES, lanes)
-    abi.ssmul_debug_kernel_stats(plan, False)
+    batch.clear()
     t = _time_batch(torch, plan, batch, 3, stream)
-    _, kst = abi.ssmul_debug_kernel_stats(plan, False)
-    # the same batch once more without the graph and with every launch timed:
-    # the summed kernel time against the graph-replayed wall time shows how
-    # much of a batched call the GPU spends outside the kernels
-    abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_GRAPH, 0)
-    abi.ssmul_debug_kernel_stats(plan, True)
-    with torch.cuda.stream(stream):
-        batch.run(plan)
-        stream.synchronize()
-    _, kt = abi.ssmul_debug_kernel_stats(plan, False)
-    kernel_s = sum(ms for _, ms in kt.values()) / 1e3
     abi.ssmul_plan_destroy(plan)
-    rs, zs = batch.results(), batch.digits()
-    res_ok = _verify_residues(batch, rs, zs)
-    rng = np.random.default_rng(seed)
-    sample = sorted(rng.choice(batch.count, size=batch.count // 20, replace=False).tolist())
-    full_ok = _verify_full(rs, zs, _expected(batch, sample))
-    statuses = {}
-    for r in rs:
-        k = abi.status_string(r.status)
-        statuses[k] = statuses.get(k, 0) + 1
-    ver_digits = float(sum(batch.nz[i] for i in range(batch.count) if res_ok[i]))
-    used = {}
-    for r in rs:
-        used[r.precision_used] = used.get(r.precision_used, 0) + 1
-    return {
-        "s_per_batch": t, "verified_digits_per_s": ver_digits / t, "statuses": statuses,
-        "residue_verified": int(res_ok.sum()), "full_sample": len(sample),
-        "full_sample_verified": full_ok, "precision_used": used,
-        "launches_per_batch": {k: v[0] // 4 for k, v in kst.items() if v[0]},
-        "kernel_s_per_batch": kernel_s, "kernel_time_fraction": kernel_s / t}
+    return t, batch.results(), [digest(z) for z in batch.digits()]
 
 
-def split(args):
-    torch = _torch()
-    from oracle import exact as E
-    from paper_1006_0405_gb300 import abi
-    abi.load()
+def c4(ctx) -> dict:
+    seed = synth.SEED_BASE + 4
+    na, nb, dists = synth.ladder_batch(seed, count=4096)
+    out = _batch_report(ctx, seed, na, nb, dists, ctx.lanes)
+    out["workload"] = ("4,096 square products, n ~ U{512..32768}, 10% all-0xFF; batched calls "
+                       "replay a CUDA graph")
+    return out
+
+
+def c5(ctx, one_lane=True) -> dict:
+    seed = synth.SEED_BASE + 5
+    na, nb, dists = synth.uneven_batch(seed, count=20000)
+    out = _batch_report(ctx, seed, na, nb, dists, ctx.lanes, one_lane=one_lane)
+    out["workload"] = ("20,000 products, na and nb independent, log-uniform in [64, 131072], "
+                       "uniform bytes; batched calls replay a CUDA graph")
+    return out
+
+
+# ---- products past the rectangles' isolation limit ------------------------------
+
+def split(ctx) -> dict:
+    torch, abi = ctx.torch, ctx.abi
     part = 1 << 18
-    rows = []
-    for k in (19, 20, 21, 22):
-        n = 1 << k
-        a, b = synth.operand_pair(synth.SEED_BASE + 6, n, n)
+    seed = synth.SEED_BASE + 6
+    rows, got = [], []
+    sizes = [1 << k for k in (19, 20, 21, 22)]
+    for n in sizes:
+        a, b = synth.operand_pair(seed, n, n)
         da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
         dz = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
-        want = [E.residue(a, q) * E.residue(b, q) % q for q in PRIMES]
         for name, prec, split_m in (("fp64", abi.SSMUL_PREC_FP64, 0),
                                     ("fp64_split_2^18", abi.SSMUL_PREC_FP64, part),
                                     ("disc64", abi.SSMUL_PREC_DISC64, 0)):
             plan = abi.ssmul_plan(n, n, 0, prec, 0)
             if split_m:
                 assert abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_SPLIT_DIGITS, split_m) == 0
-            s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
+            abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
             reps = 3
-            torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
                 s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
             el = (time.perf_counter() - t0) / reps
             abi.ssmul_plan_destroy(plan)
-            z = dz.cpu().numpy()
-            ok = bool(s == abi.SSMUL_OK and
-                      all(E.residue(z, q) == w for q, w in zip(PRIMES, want)))
-            rows.append({"digits": n, "method": name, "status": abi.status_string(s),
-                         "max_width": r.max_width, "N": r.fft_odd << r.fft_log2,
-                         "residue_verified": ok, "ms": 1e3 * el,
-                         "verified_digits_per_s": (2 * n / el) if ok else 0.0})
-    print(json.dumps({"report": "split", "part_digits": part, "rows": rows}), flush=True)
+            row = {"digits": n, "method": name, "status": abi.status_string(s),
+                   "max_width": r.max_width, "N": r.fft_odd << r.fft_log2, "ms": 1e3 * el}
+            rows.append(row)
+            got.append((row, n, s, digest(dz.cpu().numpy())))
+    expected = dict(zip(sizes, ctx.pool().digests([("pair", seed, n, n, "uniform", "ntt")
+                                                   for n in sizes])))
+    for row, n, s, dg in got:
+        row["verified"] = bool(s == abi.SSMUL_OK and dg == expected[n])
+        row["verified_digits_per_s"] = (2 * n / (row["ms"] / 1e3)) if row["verified"] else 0.0
+    return {"part_digits": part, "rows": rows}
 
 
 def run(args):
-    {"sweep": sweep, "ladder": ladder, "uneven": uneven, "split": split}[args.workload](args)
+    ctx = Ctx(lanes=args.lanes)
+    try:
+        if args.workload == "sweep":
+            out = {"report": "sweep", **c3(ctx, dists=("uniform", "ff"), balanced=args.balanced)}
+        elif args.workload == "ladder":
+            out = {"report": "ladder", **c4(ctx)}
+        elif args.workload == "uneven":
+            out = {"report": "uneven", **c5(ctx)}
+        elif args.workload == "c1":
+            out = {"report": "c1", **c1(ctx)}
+        else:
+            out = {"report": "split", **split(ctx)}
+    finally:
+        ctx.close()
+    print(json.dumps(out), flush=True)
