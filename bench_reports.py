@@ -269,34 +269,47 @@ def c3(ctx, sizes=C3_SIZES, dists=("uniform",), balanced=False, fp32_limit=True)
            "rows": rows, "largest_isolated_square_digits": largest,
            "verified": f"{n_ver}/{n_ok} products with status SSMUL_OK are bit-exact"}
     if fp32_limit:
-        out["fp32_rectangles"] = fp32_isolation_limit(ctx, balanced=balanced)
+        out["fp32_rectangles"] = fp32_isolation_limit(ctx)
     return out
 
 
-def fp32_isolation_limit(ctx, max_n: int = 64, per_size: int = 8, balanced=False) -> dict:
-    """The largest n such that binary32 rectangles isolate every one of
-    `per_size` uniform n x n products for all sizes up to n."""
+FP32_LIMIT_SIZES = list(range(1, 65)) + list(range(72, 513, 8)) + list(range(544, 2049, 32))
+
+
+def fp32_isolation_limit(ctx, dists=("uniform", "ff")) -> dict:
+    """Binary32 rectangles on squares n x n for n on FP32_LIMIT_SIZES, in three
+    representations (bytes, balanced bytes, 4-bit digits): the largest n
+    such that every product of every size up to n isolates and is exact (8
+    uniform products per size, seeds SEED_BASE + 1000 n + t; one all-0xFF)."""
     torch, abi = ctx.torch, ctx.abi
     from oracle import exact as E
-    plan = abi.ssmul_plan(max_n, max_n, 0, abi.SSMUL_PREC_FP32, 0)
-    if balanced:
-        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
-    limit, done = 0, False
-    for n in range(1, max_n + 1):
-        for t in range(per_size):
-            a, b = synth.operand_pair(synth.SEED_BASE + 1000 * n + t, n, n)
-            da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
-            dz = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
-            s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
-            if s != abi.SSMUL_OK or not np.array_equal(dz.cpu().numpy(), E.long_mul(a, b)):
-                done = True
-                break
-        if done:
-            break
-        limit = n
-    abi.ssmul_plan_destroy(plan)
-    return {"largest_square_digits": limit, "note": f"{per_size} uniform products per size, "
-                                                    f"all isolated and exact up to this size"}
+    out = {}
+    for mode, balanced, nibbles in (("bytes", 0, 0), ("balanced_bytes", 1, 0),
+                                    ("nibbles", 0, 1)):
+        plan = abi.ssmul_plan(2048, 2048, 0, abi.SSMUL_PREC_FP32, 0)
+        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, balanced)
+        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_FP32_NIBBLES, nibbles)
+        for dist in dists:
+            limit, width = 0, 0.0
+            for n in FP32_LIMIT_SIZES:
+                good, w = True, 0.0
+                for t in range(8 if dist == "uniform" else 1):
+                    a, b = synth.operand_pair(synth.SEED_BASE + 1000 * n + t, n, n, dist)
+                    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+                    dz = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
+                    s, r = abi.ssmul_mul(plan, da.data_ptr(), n, db.data_ptr(), n, dz.data_ptr())
+                    w = max(w, r.max_width)
+                    if s != abi.SSMUL_OK or not np.array_equal(dz.cpu().numpy(), E.long_mul(a, b)):
+                        good = False
+                        break
+                if not good:
+                    break
+                limit, width = n, w
+            out[f"{mode}_{dist}"] = {"largest_square_digits": limit, "max_width_there": width}
+        abi.ssmul_plan_destroy(plan)
+    out["note"] = ("sizes 1..64, then every 8 to 512, then every 32 to 2048; 8 uniform "
+                   "products (1 all-0xFF) per size, all isolated and exact up to the size given")
+    return out
 
 
 # ---- C4 and C5: batches of many products -------------------------------------------

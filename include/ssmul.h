@@ -84,8 +84,9 @@ typedef struct {
     int32_t  precision_used;    /* ssmul_precision of the deciding rung:
                                  * SSMUL_PREC_FP32, _FP64, _DISC64,
                                  * _DISC32X2 or _NAIVE64 */
-    uint32_t fft_log2;          /* the transform length is
-                                 * N = fft_odd << fft_log2 */
+    uint32_t fft_log2;          /* the deciding rung's transform length
+                                 * is N = fft_odd << fft_log2 (binary32 on
+                                 * 4-bit digits: >= 2 (na + nb) - 1) */
     uint32_t n_unisolated;      /* coefficients whose set holds >= 2 integers */
     uint32_t n_empty;           /* coefficients whose set holds no integer */
     uint32_t fft_odd;           /* 1, 3 or 5 (SSMUL_OPT_LENGTHS) */
@@ -140,8 +141,10 @@ typedef enum {
      * The factorisation of the DFT of Section 2.2 changes, not its value. */
     SSMUL_OPT_AUTOTUNE = 1,
     /* under the ladders, try binary32 only for products with
-     * na + nb <= value digits (and N <= 4096); default 32.  The first rung
-     * of Section 1's "more precision on failure". */
+     * na + nb <= value digits (and N <= 4096); 0: never.  Default 464 with
+     * SSMUL_OPT_FP32_NIBBLES (binary32 rectangles isolated every uniform
+     * square product up to 232 x 232 digits), 32 without it (16 x 16).  The
+     * first rung of Section 1's "more precision on failure". */
     SSMUL_OPT_FP32_MAX_DIGITS = 2,
     /* value != 0: balanced digits.  The transforms carry a_j - 128 and
      * b_j - 128 instead of the digits, so their values (and the widths of
@@ -183,7 +186,17 @@ typedef enum {
      * partly filled last wave of thread blocks overlaps another group's
      * work; they join the plan's stream before the outcomes are written.
      * Default 4; 1 puts every launch on the plan's stream. */
-    SSMUL_OPT_LANES = 7
+    SSMUL_OPT_LANES = 7,
+    /* value != 0: the binary32 rung transforms the operands' 4-bit digits
+     * (a = sum_j a'_j 16^j, a'_j in 0..15) for products with na + nb <= 2048:
+     * coefficients at most 225 min(2 na, 2 nb) instead of 65025 min(na, nb),
+     * so narrower containment sets for twice the transform length.  The
+     * isolated base-16 coefficients c'_i become the base-256 coefficients
+     * c'_{2k} + 16 c'_{2k+1} exactly before the carry (the product identity
+     * of Section 2.1 in base 16).  The 4-bit digits are not balanced.
+     * Default 1; 0: the binary32 rung transforms the bytes like the other
+     * rungs. */
+    SSMUL_OPT_FP32_NIBBLES = 8
 } ssmul_option;
 
 /*

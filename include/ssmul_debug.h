@@ -34,8 +34,14 @@ ssmul_status ssmul_debug_twiddles(ssmul_plan_t plan, int f32, double* h_out, siz
  * every convolution coefficient c_i = sum_j a_j b_{i-j} (Section 2.1) to
  * d_iv (device memory, 2 * (na + nb - 1) doubles: lo_i, hi_i) after the
  * inverse transform and the division by N (Sections 2.3, 2.5).  For
- * _NAIVE64 both values are the unverified point result.
+ * _NAIVE64 both values are the unverified point result.  _FP32 transforms
+ * the bytes here whatever SSMUL_OPT_FP32_NIBBLES says.
+ * prec = SSMUL_DEBUG_PREC_FP32_NIBBLES (na + nb <= 2048): binary32
+ * rectangles on the 4-bit digits a'_j, b'_j (a = sum_j a'_j 16^j); d_iv
+ * receives the enclosures of c'_i = sum_j a'_j b'_{i-j}, i < 2 (na + nb) - 1
+ * (2 * (2 (na + nb) - 1) doubles).
  */
+#define SSMUL_DEBUG_PREC_FP32_NIBBLES 100
 ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t plan, const uint8_t* d_a, size_t na,
                                        const uint8_t* d_b, size_t nb, uint8_t* d_z,
                                        ssmul_result* h_res, ssmul_precision prec,

@@ -31,6 +31,8 @@ SSMUL_PREC_NAIVE64 = 4
 SSMUL_PREC_LADDER_DISC = 5
 SSMUL_PREC_DISC32X2 = 6
 SSMUL_PREC_LADDER_FAST = 7
+#: ssmul_debug_mul_intervals only: binary32 rectangles on 4-bit digits
+SSMUL_DEBUG_PREC_FP32_NIBBLES = 100
 
 #: every symbol the headers declare
 EXPORTS = (
@@ -51,6 +53,7 @@ SSMUL_OPT_SPLIT_DIGITS = 4
 SSMUL_OPT_LENGTHS = 5
 SSMUL_OPT_HOST_PIECES = 6
 SSMUL_OPT_LANES = 7
+SSMUL_OPT_FP32_NIBBLES = 8
 
 #: kernel kinds of ssmul_debug_kernel_stats, in index order
 KERNEL_KINDS = tuple(f"{k}<{r}>" for k in ("k_small", "k_fwd_cols", "k_rows", "k_inv_cols")

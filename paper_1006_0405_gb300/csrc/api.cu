@@ -23,11 +23,14 @@ using namespace ssm;
 namespace {
 
 // the binary32 rung is tried when the product has at most this many digits
-// in total (na + nb, a plan option): binary32 rectangles were measured to
-// isolate every uniform square product up to 16 x 16 digits, and the width
-// grows with the transform length
+// in total (na + nb, a plan option; the default follows the digits the rung
+// transforms): binary32 rectangles were measured to isolate every uniform
+// square product up to 16 x 16 bytes (all-0xFF: 8 x 8), and up to 232 x 232
+// digits on 4-bit digits (all-0xFF: 256 x 256); the width grows with the
+// transform length
 constexpr int FP32_MAX_LOG_N = LOG_SMALL;
-constexpr size_t FP32_MAX_DIGITS = 32;
+constexpr size_t FP32_MAX_DIGITS = 32;          // bytes
+constexpr size_t FP32_MAX_DIGITS_NIB = 464;     // 4-bit digits
 
 // largest batch arena a plan allocates (the batch runs in chunks beyond it)
 constexpr size_t ARENA_CAP = size_t(4) << 30;
@@ -251,7 +254,9 @@ struct ssmul_plan_s {
     float* rho = nullptr;               // device, 2 per family: largest td radius, tdd radius
     Geom geom[GEOM_CODES] = {};           // by length code
     int lengths = 3;                    // SSMUL_OPT_LENGTHS
-    size_t fp32_max_digits = FP32_MAX_DIGITS;
+    size_t fp32_max_digits = 0;         // SSMUL_OPT_FP32_MAX_DIGITS; 0: the default
+    bool fp32_max_zero = false;         // the option was set to 0: never binary32 (ladders)
+    bool fp32_nibbles = true;           // SSMUL_OPT_FP32_NIBBLES
     bool balanced = false;
     uint32_t* pre = nullptr;            // balanced: digit prefix sums of one product
     int fault_widen = 0, fault_stall = 0;   // ssmul_debug_set_fault
@@ -516,7 +521,10 @@ ssmul_status enqueue_rung_as(ssmul_plan_t p, const ProdDesc* d_desc, int count, 
     constexpr int B = plan_bpt<V>();
     const int ko = kind_off<T>();
     if (g.small) {
-        const int n = 1 << g.log_n;
+        // binary32 rectangles on 4-bit digits need up to 4 times the length
+        // of the bytes' transform (2 (na + nb) - 1 <= 4096 coefficients)
+        const int n = (std::is_same<T, float>::value && p->fp32_nibbles)
+                          ? std::min(1 << LOG_SMALL, 4 << g.log_n) : 1 << g.log_n;
         LaunchScope ls(p, SSMUL_K_SMALL + ko);
         k_small<T, B, LIST><<<count, fft_threads<V>(n), n * sizeof(V),
                               p->cur>>>(d_desc, p->tw(), list);
@@ -550,7 +558,10 @@ ssmul_status enqueue_rung(ssmul_plan_t p, const ProdDesc* d_desc, int count, con
 }
 
 bool fp32_eligible(ssmul_plan_t p, size_t na, size_t nb, int log_n) {
-    return log_n <= FP32_MAX_LOG_N && na + nb <= p->fp32_max_digits;
+    if (p->fp32_max_zero) return false;
+    const size_t limit = p->fp32_max_digits ? p->fp32_max_digits
+                         : (p->fp32_nibbles ? FP32_MAX_DIGITS_NIB : FP32_MAX_DIGITS);
+    return log_n <= FP32_MAX_LOG_N && na + nb <= limit;
 }
 
 bool uses_fp32(ssmul_precision prec) {
@@ -668,6 +679,8 @@ ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t*
     d.balanced = p->balanced ? 1 : 0;
     d.fault_widen = p->fault_widen;
     d.fault_stall = p->fault_stall;
+    d.fp32_nib = (p->fp32_nibbles && na + nb <= size_t(NIB_MAX_DIGITS)) ? 1 : 0;
+    d.coef_nz = 0;
     d.pre_a = p->pre;
     d.pre_b = p->pre + pre_words(p->max_na);
     return d;
@@ -683,6 +696,7 @@ ssmul_status run_split(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint
     SS_TRY(cudaEventSynchronize(p->desc_free));
     ProdDesc parent = single_desc(p, d_a, na, d_b, nb, d_z, 0);
     parent.coeff = p->coeff_total;
+    parent.coef_nz = 1;                  // na + nb accumulated coefficients, zeroed below
     p->h_desc[0] = parent;
     size_t np = 0;
     for (size_t k = 0; k < ka; ++k) {
@@ -742,7 +756,7 @@ ssmul_status run_split(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint
 // one product on device buffers; fills h_res; waits for the result
 ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
                         size_t nb, uint8_t* d_z, ssmul_result* h_res, ssmul_precision prec,
-                        double* d_iv) {
+                        double* d_iv, bool iv_nibbles = false) {
     if (!d_a || !d_b || !d_z || na == 0 || nb == 0) return SSMUL_INVALID_ARG;
     if (na > p->max_na || nb > p->max_nb) return SSMUL_TOO_LARGE;
     ssmul_status s = check_device(p);
@@ -752,6 +766,9 @@ ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uin
     SS_TRY(cudaEventSynchronize(p->desc_free));
     p->h_desc[0] = single_desc(p, d_a, na, d_b, nb, d_z, 0);
     p->h_desc[0].iv = d_iv;
+    // the exported sets are those of the digits' coefficients, or with
+    // iv_nibbles those of the 4-bit digits' (binary32 only)
+    if (d_iv) p->h_desc[0].fp32_nib = iv_nibbles ? 1 : 0;
     SS_TRY(cudaMemsetAsync(p->st, 0, sizeof(ProdState), p->stream));
     SS_TRY(cudaMemsetAsync(p->flags, 0, carry_tiles(na + nb) * sizeof(uint32_t), p->stream));
     SS_TRY(cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ProdDesc), cudaMemcpyHostToDevice,
@@ -769,10 +786,11 @@ ssmul_status run_single(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uin
 // Bytes of arena one product needs (256-byte aligned pieces): the forward
 // spectrum Z (N intervals; the integer coefficients reuse it once it is
 // consumed) and the half-length inverse W (N/2 intervals) for four-step
-// products, the coefficients alone for single-CTA products.
+// products, the coefficients alone for single-CTA products (N + 1: the 4-bit
+// digits of the binary32 rung give na + nb <= N + 1 coefficients).
 size_t arena_need(int log_n) {
     const size_t n = len_of(log_n);
-    if (log_n <= LOG_SMALL) return (n * sizeof(int64_t) + 255) & ~size_t(255);
+    if (log_n <= LOG_SMALL) return ((n + 1) * sizeof(int64_t) + 255) & ~size_t(255);
     return ((n * sizeof(CI<double>) + 255) & ~size_t(255)) +
            (((n / 2) * sizeof(CI<double>) + 255) & ~size_t(255));
 }
@@ -1461,7 +1479,9 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     // families: Ntab = 2^log_n; 3 2^(log_n - 2) and 5 2^(log_n - 3) hold every
     // odd length R 2^j the plan's products can take (R 2^j < 2^log_n)
     for (int f = 0; f < FAMILIES; ++f) p->fam[f].R = FAMILY_R[f];
-    p->fam[0].log_tab = log_n < 4 ? 4 : log_n;
+    // the power-of-two table also serves the binary32 rung's 4-bit digits,
+    // whose transforms are up to 4 times longer (at most 2^LOG_SMALL)
+    p->fam[0].log_tab = std::max(log_n < 4 ? 4 : log_n, std::min(LOG_SMALL, log_n + 2));
     p->fam[1].log_tab = log_n - 2 >= LOG3_MIN ? (log_n - 2 > LOG3_MAX ? LOG3_MAX : log_n - 2) : 0;
     p->fam[2].log_tab = log_n - 3 >= LOG5_MIN ? (log_n - 3 > LOG5_MAX ? LOG5_MAX : log_n - 3) : 0;
     for (int c = 0; c < GEOM_CODES; ++c) p->geom[c] = default_geom_code(c);
@@ -1487,7 +1507,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->Z, n * sizeof(CI<double>));
     if (e == cudaSuccess) e = cudaMalloc(&p->W, (n / 2) * sizeof(CI<double>));
-    if (e == cudaSuccess) e = cudaMalloc(&p->coeff, n * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->coeff, (n + 1) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->flags, slots * p->flags_per_product * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->st, slots * sizeof(ProdState));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, slots * sizeof(ProdDesc));
@@ -1583,7 +1603,13 @@ ssmul_status ssmul_plan_set_option(ssmul_plan_t p, ssmul_option option, long lon
         case SSMUL_OPT_FP32_MAX_DIGITS:
             if (value < 0) return SSMUL_INVALID_ARG;
             graph_drop(p->cached);
-            p->fp32_max_digits = size_t(value);
+            p->fp32_max_digits = value ? size_t(value) : 0;
+            p->fp32_max_zero = value == 0;
+            return SSMUL_OK;
+        case SSMUL_OPT_FP32_NIBBLES:
+            SS_TRY(cudaStreamSynchronize(p->stream));
+            graph_drop(p->cached);
+            p->fp32_nibbles = value != 0;
             return SSMUL_OK;
         case SSMUL_OPT_BALANCED:
             SS_TRY(cudaStreamSynchronize(p->stream));
@@ -1790,6 +1816,10 @@ ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t p, const uint8_t* d_a, size_
                                        ssmul_result* h_res, ssmul_precision prec,
                                        double* d_iv) {
     if (!p || !d_iv) return SSMUL_INVALID_ARG;
+    if (int(prec) == SSMUL_DEBUG_PREC_FP32_NIBBLES) {
+        if (na + nb > size_t(NIB_MAX_DIGITS)) return SSMUL_INVALID_ARG;
+        return run_single(p, d_a, na, d_b, nb, d_z, h_res, SSMUL_PREC_FP32, d_iv, true);
+    }
     if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32 && prec != SSMUL_PREC_DISC64 &&
         prec != SSMUL_PREC_NAIVE64 && prec != SSMUL_PREC_DISC32X2)
         return SSMUL_INVALID_ARG;

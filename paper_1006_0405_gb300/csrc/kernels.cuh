@@ -91,6 +91,12 @@ struct ProdDesc {
     // widened by 4 so it cannot isolate; carry tile + 1 that never publishes
     int32_t fault_widen;
     int32_t fault_stall;
+    // the binary32 rung transforms the operands' 4-bit digits (see
+    // isolate_nib_value); set only when na + nb <= NIB_MAX_DIGITS
+    int32_t fp32_nib;
+    // coeff holds na + nb coefficients whatever rung decides (products
+    // assembled from split parts); the carry then reads index na + nb - 1 too
+    int32_t coef_nz;
 };
 
 // ---- balanced digits --------------------------------------------------------
@@ -535,6 +541,74 @@ __device__ __forceinline__ void isolate_value(const DDisc& v, int64_t j, const P
     isolate_pair<R>(v.yh, v.yl, v.r, 2 * j + 1, d, acc, 4);
 }
 
+// ---- binary32 rectangles on 4-bit digits ------------------------------------------
+//
+// With d.fp32_nib the binary32 rung transforms the operands' base-16 digits
+// a'_j = (a_{j/2} >> 4 (j mod 2)) & 15 (j < 2 na; likewise b'), whose
+// coefficients c'_i = sum_j a'_j b'_{i-j} (i < 2 (na + nb) - 1, the product
+// identity of Section 2.1 in base 16) are at most 225 min(2 na, 2 nb) instead
+// of 65025 min(na, nb): narrower sets for twice the transform length.  Since
+//   sum_i c'_i 16^i = sum_k (c'_{2k} + 16 c'_{2k+1}) 256^k,
+// the base-256 carry of Section 2.4 takes C_k = c'_{2k} + 16 c'_{2k+1} for
+// k < na + nb (one coefficient more than the na + nb - 1 of the bytes).  The
+// packed inverse hands one thread c'_{2k} (real part) and c'_{2k+1}
+// (imaginary part), so each thread isolates both (Section 1) and writes C_k,
+// an exact integer sum.  The 4-bit digits are not balanced (SSMUL_OPT_BALANCED
+// applies to the bytes of the other rungs).
+
+constexpr int NIB_MAX_DIGITS = 2048;      // na + nb: 2 (na + nb) - 1 <= 4096 = k_small's N
+
+__device__ __forceinline__ int nib_log_n(const ProdDesc& d) {
+    const int64_t lp = 2 * (int64_t(d.na) + d.nb) - 1;
+    int k = 2;
+    while ((int64_t(1) << k) < lp) ++k;
+    return k;
+}
+
+// base-16 digit j of the n-digit operand x (0 past its 2 n digits)
+__device__ __forceinline__ int nibble(const uint8_t* x, uint32_t n, int j) {
+    return uint32_t(j) < 2u * n ? (x[j >> 1] >> ((j & 1) * 4)) & 15 : 0;
+}
+
+// The decision of isolate_one for nibble coefficient idx (lp of them) from
+// the set [lo, hi] 2^-k; returns the isolated integer (0 otherwise).
+__device__ __forceinline__ int64_t isolate_nib_one(float lo, float hi, int k, int64_t idx,
+                                                   int64_t lp, const ProdDesc& d, IsoAcc& acc) {
+    double dl = double(lo), dh = double(hi);          // exact widening
+    if (d.fault_widen == 1) {                         // test fault of the binary32 rung
+        const double f = 4.0 * pow2_pos(k);
+        dl = __dsub_rd(dl, f);
+        dh = __dadd_ru(dh, f);
+    }
+    const unsigned long long wb = (unsigned long long)__double_as_longlong(__dsub_ru(dh, dl));
+    acc.maxw_bits = wb > acc.maxw_bits ? wb : acc.maxw_bits;
+    acc.wscale = k;
+    long long kl, kh, unused;
+    floor_ceil_scaled(dl, k, unused, kl);
+    floor_ceil_scaled(dh, k, kh, unused);
+    constexpr long long KMAX = 1ll << 53;
+    if (idx < lp) {
+        if (d.iv != nullptr) {                        // the set of c'_idx (tests)
+            d.iv[2 * idx] = __dmul_rd(dl, pow2_neg(k));
+            d.iv[2 * idx + 1] = __dmul_ru(dh, pow2_neg(k));
+        }
+        if (kl == kh && kl >= 0 && kl < KMAX) return kl;
+        if (kl < kh) acc.unisolated++;
+        else acc.empty++;              // no integer, a negative one, NaN or overflow
+        return 0;
+    }
+    if (!(kl <= 0 && kh >= 0)) acc.empty++;          // the exact value is 0
+    return 0;
+}
+
+__device__ __forceinline__ void isolate_nib_value(const CI<float>& v, int k, int64_t j,
+                                                  const ProdDesc& d, IsoAcc& acc) {
+    const int64_t nz = int64_t(d.na) + d.nb, lp = 2 * nz - 1;
+    const int64_t c0 = isolate_nib_one(v.rl, v.rh, k, 2 * j, lp, d, acc);
+    const int64_t c1 = isolate_nib_one(v.il, v.ih, k, 2 * j + 1, lp, d, acc);
+    if (j < nz) d.coeff[j] = c0 + 16 * c1;
+}
+
 // the naive transform rounds to the nearest integer without any proof; its
 // "width" statistic is the largest distance to that integer (R = 3, 5: v
 // approximates R c; the distance is kept for R c like the enclosures' widths)
@@ -607,14 +681,19 @@ __device__ __forceinline__ void small_one(const ProdDesc d, const TwTable& tw) {
     constexpr int RUNG = VTraits<V>::rung;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SBuf<V> sm{reinterpret_cast<V*>(smem_raw)};
-    const int logN = d.log_n, N = 1 << logN;
-    const int bias = d.balanced ? 128 : 0;
+    // binary32 rectangles may take the 4-bit digits (isolate_nib_value): the
+    // transform length then covers 2 (na + nb) - 1 coefficients
+    constexpr bool F32 = std::is_same<V, CI<float>>::value;
+    const bool nib = F32 && d.fp32_nib != 0;
+    const int logN = nib ? nib_log_n(d) : d.log_n, N = 1 << logN;
+    const int bias = (d.balanced && !nib) ? 128 : 0;
     // the digit pairs as integers (8 bytes each, inside the buffer), then the
     // forward transform's exact first step (logN >= 2 for every plan length)
     int2* const si = reinterpret_cast<int2*>(smem_raw);
     stage<4 * BPT, int2>(
         N,
         [&](int j) {
+            if (nib) return make_int2(nibble(d.a, d.na, j), nibble(d.b, d.nb, j));
             return make_int2(j < int(d.na) ? int(d.a[j]) - bias : 0,
                              j < int(d.nb) ? int(d.b[j]) - bias : 0);
         },
@@ -630,8 +709,15 @@ __device__ __forceinline__ void small_one(const ProdDesc d, const TwTable& tw) {
     __syncthreads();
     block_fft<V, -1, BPT, 1, false>(sm, logN - 1, 1, N, tw);
     IsoAcc acc;
-    for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x)
+    for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) {
+        if constexpr (F32) {
+            if (nib) {
+                isolate_nib_value(sm[j], logN + 2, j, d, acc);
+                continue;
+            }
+        }
         isolate_scaled<1>(sm[j], logN + 2, j, d, acc);
+    }
     flush_acc(acc, d.st, RUNG);
     if (threadIdx.x == 0) atomicOr(&d.st->ran[RUNG], 1u);
 }
@@ -877,15 +963,19 @@ __global__ void __launch_bounds__(CARRY_THREADS, 4) k_carry(const ProdDesc* desc
     __shared__ uint32_t s_uprev;
     __shared__ uint32_t s_tile, s_status, s_wA[CARRY_THREADS / 32], s_wB[CARRY_THREADS / 32];
     __shared__ uint32_t s_warp_cin[CARRY_THREADS / 32];
+    __shared__ uint32_t s_ncoef;
     const ProdDesc d = descs[blockIdx.y];
     const int64_t nz = int64_t(d.na) + d.nb;
-    const int64_t L = nz - 1;
     if (threadIdx.x == 0) {
         s_tile = atomicAdd(&d.st->carry_ticket, 1u);   // tiles in start order
         int rung;
         s_status = decide(d.st, &rung);
+        // na + nb - 1 coefficients of the digits, or na + nb when they came
+        // from 4-bit digits (isolate_nib_value) or from split parts
+        s_ncoef = (d.coef_nz || (rung == 0 && d.fp32_nib)) ? 1u : 0u;
     }
     __syncthreads();
+    const int64_t L = nz - 1 + int64_t(s_ncoef);
     const uint32_t tile = s_tile;
     const int64_t k0 = int64_t(tile) * CARRY_TILE + int64_t(threadIdx.x) * CARRY_PER_THREAD;
     if (s_status != SSMUL_OK && s_status != SSMUL_UNVERIFIED) {
@@ -1038,13 +1128,15 @@ __global__ void __launch_bounds__(CARRY_THREADS, 4) k_carry(const ProdDesc* desc
 __global__ void k_split_accumulate(const ProdDesc* part, int64_t* total, uint64_t shift,
                                    ProdState* parent) {
     const ProdDesc d = *part;
-    const int64_t L = int64_t(d.na) + d.nb - 1;
+    // the part's coefficients: na + nb of them when its binary32 rung took
+    // 4-bit digits and decided (isolate_nib_value), else na + nb - 1
+    int rung;
+    const int status = decide(d.st, &rung);
+    const int64_t L = int64_t(d.na) + d.nb - ((rung == 0 && d.fp32_nib) ? 0 : 1);
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < L;
          i += int64_t(gridDim.x) * blockDim.x)
         total[shift + i] += d.coeff[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int rung;
-        const int status = decide(d.st, &rung);
         parent->ran[rung] = 1u;
         parent->unisolated[rung] += d.st->unisolated[rung];
         parent->empty[rung] += d.st->empty[rung];
@@ -1065,10 +1157,12 @@ __global__ void k_finalize(const ProdDesc* descs) {
         ssmul_result r;
         r.status = status;
         r.precision_used = rung_precision(rung);
-        r.fft_log2 = uint32_t(d.log_n % LEN3);
+        // the deciding rung's transform: 4-bit digits double the bytes' length
+        const bool nib = rung == 0 && d.fp32_nib;
+        r.fft_log2 = nib ? uint32_t(nib_log_n(d)) : uint32_t(d.log_n % LEN3);
         r.n_unisolated = d.st->unisolated[rung];
         r.n_empty = d.st->empty[rung];
-        r.fft_odd = d.log_n >= LEN5 ? 5u : (d.log_n >= LEN3 ? 3u : 1u);
+        r.fft_odd = nib ? 1u : (d.log_n >= LEN5 ? 5u : (d.log_n >= LEN3 ? 3u : 1u));
         r.max_width = __longlong_as_double((long long)d.st->maxw[rung]);
         *d.res = r;
         s_status = status;

@@ -32,14 +32,36 @@ def _balanced_plan(na, nb, max_products=0, prec=abi.SSMUL_PREC_FP64):
                                         (2048, 2047, "uniform"), (2049, 5000, "uniform"),
                                         (4095, 1, "raw"), (40000, 40000, "ff"), (100000, 3001, "raw")])
 def test_balanced_products_bit_exact(prec, na, nb, dist):
-    if prec == abi.SSMUL_PREC_FP32 and max(na, nb) > 12:
-        pytest.skip("beyond the binary32 isolation limit")
     a, b = synth.operand_pair(synth.SEED_BASE + 3 * na + nb, na, nb, dist)
     with _balanced_plan(na, nb, 0, prec) as p:
         s, r, z = p.mul(a, b)
+    if prec == abi.SSMUL_PREC_FP32 and max(na, nb) > 12:
+        # past binary32's isolation limit the failure is reported, never rounded
+        assert s in (OK, abi.SSMUL_ISOLATION_FAILED), abi.status_string(s)
+        if s != OK:
+            assert not z.any()
+            return
     expect = abi.SSMUL_UNVERIFIED if prec == abi.SSMUL_PREC_NAIVE64 else OK
     assert s == expect, abi.status_string(s)
     assert np.array_equal(z, E.product(a, b))
+
+
+# binary32 rectangles at their measured isolation limits (squares, 8 uniform
+# products per size drawn as the bench's limit search draws them): bytes
+# 16 (all-0xFF 8), balanced bytes 30 (all-0xFF 16), 4-bit digits 232
+# (all-0xFF 256)
+@pytest.mark.parametrize("balanced,nibbles,n,dist", [
+    (0, 0, 16, "uniform"), (0, 0, 8, "ff"), (1, 0, 30, "uniform"), (1, 0, 16, "ff"),
+    (0, 1, 232, "uniform"), (0, 1, 256, "ff"), (1, 1, 232, "uniform")])
+def test_fp32_isolation_limits(balanced, nibbles, n, dist):
+    with Plan(n, n, 0, abi.SSMUL_PREC_FP32) as p:
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_BALANCED, balanced) == OK
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_NIBBLES, nibbles) == OK
+        for t in range(8 if dist == "uniform" else 1):
+            a, b = synth.operand_pair(synth.SEED_BASE + 1000 * n + t, n, n, dist)
+            s, r, z = p.mul(a, b)
+            assert s == OK and r.precision_used == abi.SSMUL_PREC_FP32, abi.status_string(s)
+            assert np.array_equal(z, E.long_mul(a, b))
 
 
 @pytest.mark.parametrize("prec", [abi.SSMUL_PREC_FP64, abi.SSMUL_PREC_DISC64])

@@ -111,13 +111,25 @@ def test_autotuned_geometry_is_exact(tmp_path):
 
 
 def test_fp32_router_option():
-    a, b = synth.operand_pair(5, 40, 40)
-    with Plan(64, 64, 0, abi.SSMUL_PREC_LADDER) as p:
-        s, r, z = p.mul(a, b)                       # 80 digits: above the default threshold
+    a, b = synth.operand_pair(5, 300, 300)
+    small = synth.operand_pair(6, 40, 40)
+    with Plan(300, 300, 0, abi.SSMUL_PREC_LADDER) as p:
+        s, r, z = p.mul(a, b)                       # 600 digits: above the default 464
         assert s == OK and r.precision_used == abi.SSMUL_PREC_FP64
-        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_MAX_DIGITS, 100) == OK
-        s, r, z = p.mul(a, b)                       # tried in binary32, escalated
+        s, r, z = p.mul(*small)                     # 80 digits: binary32 on 4-bit digits
+        assert s == OK and r.precision_used == abi.SSMUL_PREC_FP32
+        assert np.array_equal(z, E.product(*small))
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_MAX_DIGITS, 700) == OK
+        s, r, z = p.mul(a, b)                       # tried in binary32 (beyond its limit), escalated
         assert s == OK and np.array_equal(z, E.product(a, b))
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_MAX_DIGITS, 0) == OK
+        s, r, z = p.mul(*small)                     # 0: never binary32
+        assert s == OK and r.precision_used == abi.SSMUL_PREC_FP64
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_NIBBLES, 0) == OK
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_MAX_DIGITS, 100) == OK
+        s, r, z = p.mul(*small)                     # bytes: 80 digits do not isolate in binary32
+        assert s == OK and r.precision_used == abi.SSMUL_PREC_FP64
+        assert np.array_equal(z, E.product(*small))
         assert abi.ssmul_plan_set_option(p.h, 99, 1) == abi.SSMUL_INVALID_ARG
 
 

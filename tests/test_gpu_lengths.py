@@ -142,7 +142,11 @@ def test_batched_mix_of_families():
     seen = set()
     for (a, b), r, z in zip(pairs, res, digits):
         assert r.status == OK and np.array_equal(z, E.product(a, b))
-        assert (r.fft_odd, r.fft_log2) == expect_len(len(a), len(b))
+        if r.precision_used == abi.SSMUL_PREC_FP32:
+            # binary32 on 4-bit digits: 2 (na + nb) - 1 coefficients, powers of two
+            assert (r.fft_odd, r.fft_log2) == (1, (2 * (len(a) + len(b)) - 2).bit_length())
+        else:
+            assert (r.fft_odd, r.fft_log2) == expect_len(len(a), len(b))
         seen.add(r.fft_odd)
     assert seen == {1, 3, 5}
 
