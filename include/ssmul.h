@@ -152,13 +152,17 @@ typedef enum {
      * corrected exactly with integer window sums of the digits.  The
      * product is the same.  Default 0 (the paper's digits 0..255). */
     SSMUL_OPT_BALANCED = 3,
-    /* value m >= 1024: ssmul_mul / ssmul_mul_host cut a product whose longer
+    /* value m >= 1024: the product calls cut a product whose longer
      * operand has more than m digits into parts of at most m digits per
      * operand, run each part's interval convolution (which isolates at
      * sizes the whole product would not), and add the parts' exact integer
      * coefficients before one carry: the way past the isolation limit that
      * Section 1 names ("use a different algorithm").  The status is the
-     * worst of the parts'.  0 (default): off.  Batched calls do not split. */
+     * worst of the parts'.  0 (default): off.  Batched calls split too:
+     * their products past m digits run after the batch's other products,
+     * one after another, each in its parts (such a batch is not captured in
+     * a CUDA graph, and ssmul_mul_batched_host runs its pieces on one
+     * stream). */
     SSMUL_OPT_SPLIT_DIGITS = 4,
     /* bit mask of the transform length families besides 2^k: bit 0 the
      * lengths 3 * 2^k, bit 1 the lengths 5 * 2^k (default 3: both).  A

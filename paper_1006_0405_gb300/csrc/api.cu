@@ -307,6 +307,8 @@ struct ssmul_plan_s {
     size_t arena_bytes = 0;
     std::vector<int> order;             // host scratch of a batched call
     std::vector<BatchChunk> chunks;
+    size_t batch_nreg = 0;              // products of the prepared batch that are not split
+    size_t split_cursor = 0;            // next free part entry of the current batched call
     // host-buffer batches (ssmul_mul_batched_host): device copies of the
     // pools and outcomes (grown on demand), two copy streams and the events
     // that order the pieces of a call
@@ -686,66 +688,114 @@ ProdDesc single_desc(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t*
     return d;
 }
 
-// One product cut into parts of at most m digits per operand (see
-// k_split_accumulate); waits for the result.
-ssmul_status run_split(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
-                       size_t nb, uint8_t* d_z, ssmul_result* h_res, ssmul_precision prec) {
+// The parts of a product of na x nb digits cut into at most m digits per
+// operand: ceil(na / m) ceil(nb / m).
+size_t split_parts(size_t na, size_t nb, size_t m) { return ((na + m - 1) / m) * ((nb + m - 1) / m); }
+
+// Room for `parts` part descriptors and states (grown after waiting for the
+// plan's queued work).
+ssmul_status ensure_split_capacity(ssmul_plan_t p, size_t parts) {
+    if (parts <= p->split_slots) return SSMUL_OK;
+    SS_TRY(cudaStreamSynchronize(p->stream));
+    cudaFree(p->split_st);
+    cudaFree(p->d_split);
+    cudaFreeHost(p->h_split);
+    p->split_st = nullptr;
+    p->d_split = nullptr;
+    p->h_split = nullptr;
+    p->split_slots = 0;
+    SS_TRY(cudaMalloc(&p->split_st, parts * sizeof(ProdState)));
+    SS_TRY(cudaMalloc(&p->d_split, parts * sizeof(ProdDesc)));
+    SS_TRY(cudaMallocHost(&p->h_split, parts * sizeof(ProdDesc)));
+    p->split_slots = parts;
+    return SSMUL_OK;
+}
+
+// Enqueue one product cut into parts of at most m = split_digits digits per
+// operand (see k_split_accumulate) on the current lane: parent (host copy)
+// and d_parent (its descriptor on the device, uploaded by the caller, whose
+// state and look-back words the caller cleared); the parts take entries
+// [off, off + parts) of the part arrays.  The parts run one after another
+// in the plan's single-product workspace, add their exact coefficients into
+// coeff_total, and the parent's carry and outcome follow.
+ssmul_status enqueue_split(ssmul_plan_t p, const ProdDesc& parent, const ProdDesc* d_parent,
+                           size_t off, ssmul_precision prec) {
     const size_t m = p->split_digits;
+    const size_t na = parent.na, nb = parent.nb;
     const size_t ka = (na + m - 1) / m, kb = (nb + m - 1) / m;
-    if (ka * kb > p->split_slots) return SSMUL_TOO_LARGE;
-    SS_TRY(cudaEventSynchronize(p->desc_free));
-    ProdDesc parent = single_desc(p, d_a, na, d_b, nb, d_z, 0);
-    parent.coeff = p->coeff_total;
-    parent.coef_nz = 1;                  // na + nb accumulated coefficients, zeroed below
-    p->h_desc[0] = parent;
+    ProdDesc* const hs = p->h_split + off;
     size_t np = 0;
     for (size_t k = 0; k < ka; ++k) {
         for (size_t l = 0; l < kb; ++l, ++np) {
             const size_t la = (k + 1) * m <= na ? m : na - k * m;
             const size_t lb = (l + 1) * m <= nb ? m : nb - l * m;
-            ProdDesc d = single_desc(p, d_a + k * m, la, d_b + l * m, lb, nullptr, 0);
-            d.st = p->split_st + np;
+            ProdDesc d = single_desc(p, parent.a + k * m, la, parent.b + l * m, lb, nullptr, 0);
+            d.st = p->split_st + off + np;
             d.res = nullptr;
             d.flags = nullptr;
-            p->h_split[np] = d;
+            hs[np] = d;
         }
     }
-    SS_TRY(cudaMemsetAsync(p->st, 0, sizeof(ProdState), p->stream));
-    SS_TRY(cudaMemsetAsync(p->split_st, 0, np * sizeof(ProdState), p->stream));
-    SS_TRY(cudaMemsetAsync(p->coeff_total, 0, (na + nb) * sizeof(int64_t), p->stream));
-    SS_TRY(cudaMemsetAsync(p->flags, 0, carry_tiles(na + nb) * sizeof(uint32_t), p->stream));
-    SS_TRY(cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ProdDesc), cudaMemcpyHostToDevice,
-                           p->stream));
-    SS_TRY(cudaMemcpyAsync(p->d_split, p->h_split, np * sizeof(ProdDesc), cudaMemcpyHostToDevice,
-                           p->stream));
-    SS_TRY(cudaEventRecord(p->desc_free, p->stream));
+    SS_TRY(cudaMemsetAsync(p->split_st + off, 0, np * sizeof(ProdState), p->cur));
+    SS_TRY(cudaMemsetAsync(p->coeff_total, 0, (na + nb) * sizeof(int64_t), p->cur));
+    SS_TRY(cudaMemcpyAsync(p->d_split + off, hs, np * sizeof(ProdDesc), cudaMemcpyHostToDevice,
+                           p->cur));
     ssmul_status s = SSMUL_OK;
     np = 0;
     for (size_t k = 0; k < ka; ++k) {
         for (size_t l = 0; l < kb; ++l, ++np) {
-            const ProdDesc& hd = p->h_split[np];
+            const ProdDesc& hd = hs[np];
+            const ProdDesc* dd = p->d_split + off + np;
             const Geom& g = p->geom[hd.log_n];
-            s = enqueue_prefix(p, p->d_split + np, 1, hd.na > hd.nb ? hd.na : hd.nb);
+            s = enqueue_prefix(p, dd, 1, hd.na > hd.nb ? hd.na : hd.nb);
             if (s != SSMUL_OK) return s;
             const bool try32 = prec == SSMUL_PREC_FP32 ||
                                (uses_fp32(prec) && fp32_eligible(p, hd.na, hd.nb, g.log_n));
-            s = enqueue_rungs(p, prec, p->d_split + np, 1, try32 ? 1 : 0, g);
+            s = enqueue_rungs(p, prec, dd, 1, try32 ? 1 : 0, g);
             if (s != SSMUL_OK) return s;
-            const size_t L = size_t(hd.na) + hd.nb - 1;
+            const size_t L = size_t(hd.na) + hd.nb;
             k_split_accumulate<<<unsigned((L + 255) / 256 < 1024 ? (L + 255) / 256 : 1024), 256, 0,
-                                 p->stream>>>(p->d_split + np, p->coeff_total, (k + l) * m, p->st);
+                                 p->cur>>>(dd, p->coeff_total, (k + l) * m, parent.st);
             SS_TRY(cudaGetLastError());
         }
     }
     {
         LaunchScope ls(p, SSMUL_K_CARRY);
-        k_carry<<<dim3(unsigned(carry_tiles(na + nb)), 1), CARRY_THREADS, 0, p->stream>>>(p->d_desc);
+        k_carry<<<dim3(unsigned(carry_tiles(na + nb)), 1), CARRY_THREADS, 0, p->cur>>>(d_parent);
     }
     {
         LaunchScope ls(p, SSMUL_K_FINALIZE);
-        k_finalize<<<1, 256, 0, p->stream>>>(p->d_desc);
+        k_finalize<<<1, 256, 0, p->cur>>>(d_parent);
     }
-    SS_TRY(cudaGetLastError());
+    return cuda_status(cudaGetLastError());
+}
+
+// The parent descriptor of a split product in slot `slot`: its
+// coefficients are the parts' sums in coeff_total (na + nb of them).
+ProdDesc split_parent(ssmul_plan_t p, const uint8_t* a, size_t na, const uint8_t* b, size_t nb,
+                      uint8_t* z, size_t slot) {
+    ProdDesc d = single_desc(p, a, na, b, nb, z, slot);
+    d.coeff = p->coeff_total;
+    d.coef_nz = 1;
+    d.Z = nullptr;
+    d.W = nullptr;
+    return d;
+}
+
+// One product cut into parts; waits for the result.
+ssmul_status run_split(ssmul_plan_t p, const uint8_t* d_a, size_t na, const uint8_t* d_b,
+                       size_t nb, uint8_t* d_z, ssmul_result* h_res, ssmul_precision prec) {
+    SS_TRY(cudaEventSynchronize(p->desc_free));
+    ssmul_status s = ensure_split_capacity(p, split_parts(na, nb, p->split_digits));
+    if (s != SSMUL_OK) return s;
+    p->h_desc[0] = split_parent(p, d_a, na, d_b, nb, d_z, 0);
+    SS_TRY(cudaMemsetAsync(p->st, 0, sizeof(ProdState), p->stream));
+    SS_TRY(cudaMemsetAsync(p->flags, 0, carry_tiles(na + nb) * sizeof(uint32_t), p->stream));
+    SS_TRY(cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ProdDesc), cudaMemcpyHostToDevice,
+                           p->stream));
+    s = enqueue_split(p, p->h_desc[0], p->d_desc, 0, prec);
+    if (s != SSMUL_OK) return s;
+    SS_TRY(cudaEventRecord(p->desc_free, p->stream));
     SS_TRY(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(ssmul_result), cudaMemcpyDeviceToHost,
                            p->stream));
     SS_TRY(cudaStreamSynchronize(p->stream));
@@ -811,33 +861,44 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t base, size_t count, const ssmu
     std::vector<int>& order = p->order;
     order.resize(count);
     std::vector<int> logn(count);
-    std::vector<char> elig(count);
+    std::vector<char> elig(count), cut(count);
+    const size_t m = p->split_digits;
+    size_t nsplit = 0;
     for (size_t i = 0; i < count; ++i) {
         order[i] = int(i);
         logn[i] = length_code(h_desc[i].na, h_desc[i].nb, p->lengths);
         elig[i] = p->prec == SSMUL_PREC_FP32 ||
                   (uses_fp32(p->prec) && fp32_eligible(p, h_desc[i].na, h_desc[i].nb, logn[i]));
+        cut[i] = m && (h_desc[i].na > m || h_desc[i].nb > m);
+        nsplit += cut[i];
     }
+    // products past SSMUL_OPT_SPLIT_DIGITS go last: they run in parts after
+    // the others (issue_batch), outside the length groups and the arena
     std::sort(order.begin(), order.end(), [&](int x, int y) {
+        if (cut[x] != cut[y]) return cut[x] < cut[y];
         if (logn[x] != logn[y]) return logn[x] > logn[y];
         if (elig[x] != elig[y]) return elig[x] > elig[y];
         return x < y;
     });
+    const size_t nreg = count - nsplit;
     for (size_t k = 0; k < count; ++k) {
         const int i = order[k];
         const ssmul_desc& h = h_desc[i];
-        ProdDesc d = single_desc(p, d_a_pool + h.a_off, h.na, d_b_pool + h.b_off, h.nb,
-                                 d_z_pool + h.z_off, base + k);
+        ProdDesc d = k < nreg ? single_desc(p, d_a_pool + h.a_off, h.na, d_b_pool + h.b_off, h.nb,
+                                            d_z_pool + h.z_off, base + k)
+                              : split_parent(p, d_a_pool + h.a_off, h.na, d_b_pool + h.b_off, h.nb,
+                                             d_z_pool + h.z_off, base + k);
         d.res = d_res + i;
         p->h_desc[base + k] = d;
     }
+    p->batch_nreg = nreg;
     p->chunks.clear();
     size_t k0 = 0;
-    while (k0 < count) {
+    while (k0 < nreg) {
         BatchChunk c;
         c.k0 = k0;
         size_t used = 0, k1 = k0;
-        while (k1 < count) {
+        while (k1 < nreg) {
             const int ln = logn[order[k1]];
             const ssmul_desc& hd = h_desc[order[k1]];
             const size_t pb = p->balanced ? pre_bytes(hd.na, hd.nb) : 0;
@@ -945,6 +1006,19 @@ ssmul_status issue_batch(ssmul_plan_t p, size_t base, size_t count, bool fork_gr
         }
         SS_TRY(cudaGetLastError());
     }
+    // products past the split size, one after another in parts (Section 1's
+    // "different algorithm"); their part entries follow the call's cursor
+    const size_t nreg = p->batch_nreg;
+    if (nreg < count) {
+        SS_TRY(cudaMemcpyAsync(dd + nreg, p->h_desc + base + nreg, (count - nreg) * sizeof(ProdDesc),
+                               cudaMemcpyHostToDevice, p->cur));
+        for (size_t k = nreg; k < count; ++k) {
+            const ProdDesc& hd = p->h_desc[base + k];
+            s = enqueue_split(p, hd, dd + k, p->split_cursor, p->prec);
+            if (s != SSMUL_OK) return s;
+            p->split_cursor += split_parts(hd.na, hd.nb, p->split_digits);
+        }
+    }
     return SSMUL_OK;
 }
 
@@ -959,12 +1033,30 @@ void graph_drop(GraphEntry& e) {
     e = GraphEntry();
 }
 
+// Part entries the products of a batched call past SSMUL_OPT_SPLIT_DIGITS
+// need (they take consecutive entries from the call's cursor).
+size_t batch_split_parts(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc) {
+    const size_t m = p->split_digits;
+    size_t parts = 0;
+    for (size_t i = 0; m && i < count; ++i)
+        if (h_desc[i].na > m || h_desc[i].nb > m) parts += split_parts(h_desc[i].na, h_desc[i].nb, m);
+    return parts;
+}
+
 ssmul_status enqueue_batch(ssmul_plan_t p, size_t count, const ssmul_desc* h_desc,
                            const uint8_t* d_a_pool, const uint8_t* d_b_pool, uint8_t* d_z_pool,
                            ssmul_result* d_res) {
     SS_TRY(cudaEventSynchronize(p->desc_free));
-    // a stream capture needs a stream other than the legacy default stream
-    const bool use_graph = p->graph && p->stream != nullptr;
+    const size_t parts = batch_split_parts(p, count, h_desc);
+    if (parts) {
+        const ssmul_status sc = ensure_split_capacity(p, parts);
+        if (sc != SSMUL_OK) return sc;
+    }
+    p->split_cursor = 0;
+    // a stream capture needs a stream other than the legacy default stream;
+    // batches with split products run their parts' descriptors from the
+    // host arrays of this call, so they are not captured
+    const bool use_graph = p->graph && p->stream != nullptr && parts == 0;
     if (use_graph &&
         graph_key_matches(p->cached, count, h_desc, d_a_pool, d_b_pool, d_z_pool, d_res)) {
         std::memcpy(p->h_desc, p->cached.prepared.data(), count * sizeof(ProdDesc));
@@ -1273,6 +1365,14 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
     int lanes = ensure_piece_lanes(p, int(pieces), &s);
     if (s != SSMUL_OK) return s;
     while (lanes > 1 && ((p->arena_bytes / lanes) & ~size_t(255)) < one) --lanes;
+    // split products share the plan's single-product workspace: their pieces
+    // run on one stream
+    const size_t parts = batch_split_parts(p, count, h_desc);
+    if (parts) {
+        lanes = 1;
+        if ((s = ensure_split_capacity(p, parts)) != SSMUL_OK) return s;
+    }
+    p->split_cursor = 0;
     const size_t window = lanes > 1 ? (p->arena_bytes / lanes) & ~size_t(255) : p->arena_bytes;
     while (p->hb_ev.size() < 2 * pieces) {
         cudaEvent_t e = nullptr;
