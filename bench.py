@@ -79,7 +79,7 @@ def parse():
                     help="transform length families besides 2^k (SSMUL_OPT_LENGTHS bit mask: "
                          "1 = 3 2^k, 2 = 5 2^k)")
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "c1", "sweep", "ladder", "uneven", "split"],
+                    choices=["paper", "c1", "sweep", "ladder", "uneven", "split", "probe"],
                     help="paper: the headline line (with the c1, c3, c4 and c5 reports unless "
                          "--no-reports); c1 / sweep / ladder / uneven / split: one report line "
                          "(one 4096-digit product, the size sweep, the precision ladder, the "
@@ -289,6 +289,40 @@ def algorithmic_bytes(n: int) -> float:
 def fft_len_str(n: int) -> str:
     R, k = length_code(n, n)
     return f"2^{k}" if R == 1 else f"{R}*2^{k}"
+
+
+def pipe_rates() -> dict:
+    """Measured throughput (G operations/s) of each operation of the
+    library's pipe probe (ssmul_debug_pipe_rate): the ceilings the kernels'
+    operation mixes run against, beside the nominal peaks."""
+    from paper_1006_0405_gb300 import abi
+    out = {}
+    for i, name in enumerate(abi.PIPE_OPS):
+        st, g = abi.ssmul_debug_pipe_rate(i)
+        out[name] = g if st == abi.SSMUL_OK else None
+    return out
+
+
+def run_probe(args):
+    import torch
+    from paper_1006_0405_gb300 import abi
+    if not torch.cuda.is_available():
+        raise SystemExit("the probe needs a CUDA device")
+    abi.load()
+    prop = torch.cuda.get_device_properties(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    rates = pipe_rates()
+    t1 = time.perf_counter()
+    clk = clocks.stop(t0, t1)
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    print(json.dumps({"report": "pipe_probe", "device": prop.name, "sms": prop.multi_processor_count,
+                      "gops": rates, "clocks": clk,
+                      "nominal_gops": {"f64": fp64_peak_gops(sm_mhz, prop.multi_processor_count),
+                                       "f32": fp32_peak_gops(sm_mhz, prop.multi_processor_count)}}),
+          flush=True)
 
 
 def fp64_peak_gops(sm_mhz: float, sms: int) -> float:
@@ -670,6 +704,7 @@ def run_ours(args):
         R_, k_ = length_code(n, n)
         geo = abi.ssmul_debug_geometry(plan, (64 if R_ == 5 else 32 if R_ == 3 else 0) + k_)[1]
         traffic_pp, traffic_why = captured_traffic(dom, n, geo)
+        rates = pipe_rates() if world == 1 else None
         total_ms = sum(v[1] for v in kstats.values())
         shares = {k: round(v[1] / total_ms, 4) for k, v in kstats.items() if v[0]}
         cpu = None
@@ -725,7 +760,8 @@ def run_ours(args):
                                        if model == "disc32x2" else
                                        f"binary64 pipe: {sms} SMs x 2 ops/clk")
                                       + " at the median sampled SM clock (recipe unit counts "
-                                        "and clocks)"},
+                                        "and clocks)",
+                         "measured_op_gops": rates},
             "hbm_roofline": {"achieved_gbs": value * algorithmic_bytes(n) / 1e9,
                              "peak_gbs": HBM_PEAK_GBS,
                              "frac": value * algorithmic_bytes(n) / 1e9 / HBM_PEAK_GBS,
@@ -750,6 +786,8 @@ def main():
     LENGTHS = args.lengths
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "probe":
+        run_probe(args)
     elif args.workload == "paper":
         run_ours(args)
     else:

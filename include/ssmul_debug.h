@@ -162,6 +162,19 @@ ssmul_status ssmul_debug_set_fault(ssmul_plan_t plan, int kind, long long value)
 ssmul_status ssmul_debug_geometry(ssmul_plan_t plan, int log_n, int* log_n1, int* log_n2,
                                   int* log_cta);
 
+/*
+ * Throughput of one arithmetic operation on this device, in operations per
+ * second / 1e9 (*gops): every thread of 8 CTAs per SM runs 16 independent
+ * chains of the operation on run-time operands near 1 (the legacy default
+ * stream, timed with CUDA events, best of 3 after a warm-up).  op: 0 binary64
+ * add rounded down, 1 binary64 product rounded up, 2 binary64 fma rounded
+ * down, 3 binary64 add written as an fma by a run-time 1, 4 binary64 add
+ * rounded to nearest, 5 binary32 add rounded down, 6 binary32 fma rounded
+ * down.  The ceilings the transforms' operation mixes run against; the paper
+ * has no counterpart.
+ */
+ssmul_status ssmul_debug_pipe_rate(int op, double* gops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,7 @@ EXPORTS = (
     "ssmul_debug_twiddles", "ssmul_debug_mul_intervals", "ssmul_debug_ci_op", "ssmul_debug_disc_op",
     "ssmul_debug_ddisc_op", "ssmul_debug_isolate", "ssmul_debug_floor_ceil",
     "ssmul_debug_kernel_stats", "ssmul_debug_geometry", "ssmul_debug_set_fault",
+    "ssmul_debug_pipe_rate",
 )
 
 # ssmul_option
@@ -149,6 +150,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
     L.ssmul_debug_floor_ceil.restype = st
     L.ssmul_debug_kernel_stats.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.ssmul_debug_kernel_stats.restype = st
+    L.ssmul_debug_pipe_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.ssmul_debug_pipe_rate.restype = st
     _lib = L
     return L
 
@@ -299,3 +302,15 @@ def ssmul_debug_kernel_stats(plan: int, enable: bool):
     la = (ctypes.c_ulonglong * n)()
     s = load().ssmul_debug_kernel_stats(ctypes.c_void_p(plan), int(enable), ms, la, n)
     return s, {KERNEL_KINDS[i]: (int(la[i]), float(ms[i])) for i in range(n)}
+
+
+#: operations of ssmul_debug_pipe_rate, in index order
+PIPE_OPS = ("f64_add_rd", "f64_mul_ru", "f64_fma_rd", "f64_add_as_fma_rd", "f64_add_rn",
+            "f32_add_rd", "f32_fma_rd")
+
+
+def ssmul_debug_pipe_rate(op: int):
+    """Returns (status, G operations per second) of one arithmetic operation."""
+    g = ctypes.c_double()
+    s = load().ssmul_debug_pipe_rate(op, ctypes.byref(g))
+    return s, g.value

@@ -2120,6 +2120,87 @@ extern "C" ssmul_status ssmul_debug_ci_op(int op, int f32, const double* d_x, co
     return SSMUL_OK;
 }
 
+// ---- arithmetic pipe rates (ssmul_debug_pipe_rate) ---------------------------------
+//
+// Each thread runs PROBE_CHAINS independent dependency chains of one
+// operation for `iters` rounds; the operands are run-time values near 1, so
+// the chains stay normal and the compiler cannot fold them.
+
+namespace {
+
+constexpr int PROBE_CHAINS = 16;
+constexpr int PROBE_THREADS = 256;
+
+template <int OP>
+__global__ void __launch_bounds__(PROBE_THREADS) k_pipe_probe(double* sink, double seed, int iters) {
+    const double a = 1.0 + seed * 0x1p-40, b = seed * 0x1p-30, one = 1.0 + seed * 0.0;
+    const float af = float(a), bf = float(b);
+    double x[PROBE_CHAINS];
+    float y[PROBE_CHAINS];
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; ++i) {
+        x[i] = 1.0 + (threadIdx.x * PROBE_CHAINS + i) * 0x1p-20;
+        y[i] = float(x[i]);
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < PROBE_CHAINS; ++i) {
+            if (OP == 0) x[i] = __dadd_rd(x[i], b);            // directed add
+            if (OP == 1) x[i] = __dmul_ru(x[i], a);            // directed product
+            if (OP == 2) x[i] = __fma_rd(x[i], a, -b);         // directed fma
+            if (OP == 3) x[i] = __fma_rd(x[i], one, b);        // an add written as an fma
+            if (OP == 4) x[i] = __dadd_rn(x[i], b);            // round-to-nearest add
+            if (OP == 5) y[i] = __fadd_rd(y[i], bf);           // binary32 directed add
+            if (OP == 6) y[i] = __fmaf_rd(y[i], af, -bf);      // binary32 directed fma
+        }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; ++i) acc += x[i] + double(y[i]);
+    if (acc == seed) sink[0] = acc;                            // never true; keeps the chains
+}
+
+}  // namespace
+
+extern "C" ssmul_status ssmul_debug_pipe_rate(int op, double* gops) {
+    if (op < 0 || op > 6 || !gops) return SSMUL_INVALID_ARG;
+    int dev = 0, sms = 0;
+    SS_TRY(cudaGetDevice(&dev));
+    SS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    double* sink = nullptr;
+    SS_TRY(cudaMalloc(&sink, sizeof(double)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = sms * 8, iters = 2048;
+    float best = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, 0);
+        switch (op) {
+            case 0: k_pipe_probe<0><<<blocks, PROBE_THREADS>>>(sink, 0.5, iters); break;
+            case 1: k_pipe_probe<1><<<blocks, PROBE_THREADS>>>(sink, 0.5, iters); break;
+            case 2: k_pipe_probe<2><<<blocks, PROBE_THREADS>>>(sink, 0.5, iters); break;
+            case 3: k_pipe_probe<3><<<blocks, PROBE_THREADS>>>(sink, 0.5, iters); break;
+            case 4: k_pipe_probe<4><<<blocks, PROBE_THREADS>>>(sink, 0.5, iters); break;
+            case 5: k_pipe_probe<5><<<blocks, PROBE_THREADS>>>(sink, 0.5, iters); break;
+            default: k_pipe_probe<6><<<blocks, PROBE_THREADS>>>(sink, 0.5, iters); break;
+        }
+        cudaEventRecord(e1, 0);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best)
+            best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_status(e);
+    *gops = double(blocks) * PROBE_THREADS * PROBE_CHAINS * iters / (best * 1e-3) / 1e9;
+    return SSMUL_OK;
+}
+
 // ---- allocation-free entry point (ssmul_mul_noalloc) -----------------------------
 //
 // Everything the one-CTA binary64 path needs beyond the caller's inputs and

@@ -781,7 +781,7 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
 }
 
 template <typename Tag, int BPT = 2, int R = 1, bool LIST = false>
-__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols)
+__global__ void __maxnreg__((cols_regs<typename ValOf<Tag>::type, R>()))
 k_fwd_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC, const int* list) {
     if constexpr (LIST) {
         // rows past the list's length have nothing to do: they end after one load
@@ -868,7 +868,7 @@ __device__ __forceinline__ void inv_cols_one(const ProdDesc d, const TwTable& tw
 }
 
 template <typename Tag, int BPT = 2, int R = 1, bool LIST = false>
-__global__ void __maxnreg__(VTraits<typename ValOf<Tag>::type>::reg_cols)
+__global__ void __maxnreg__((cols_regs<typename ValOf<Tag>::type, R>()))
 k_inv_cols(const ProdDesc* descs, TwTable tw, int logN1, int logN2, int logC, const int* list) {
     if constexpr (LIST) {
         // rows past the list's length have nothing to do: they end after one load

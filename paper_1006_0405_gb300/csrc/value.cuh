@@ -33,10 +33,18 @@ template <> struct VTraits<CI<float>> {
     static constexpr int rung = 0, sw_src = 3, sw_mask = 3;
     static constexpr int reg_rows = 64, reg_cols = 72;
 };
+#ifndef SSMUL_REG_COLS5_F64
+#define SSMUL_REG_COLS5_F64 96
+#endif
 template <> struct VTraits<CI<double>> {
     using Tw = CI<double>;
     static constexpr int rung = 1, sw_src = 2, sw_mask = 3;
     static constexpr int reg_rows = 96, reg_cols = 80;
+    // the columns of the lengths 5 2^k run 5-warp CTAs (160 threads for the
+    // 320-point columns, four columns per CTA): at 96 registers four CTAs
+    // still fit an SM (5 warps x 3072 registers per 16,384-register quarter),
+    // as at 80, with fewer spills
+    static constexpr int reg_cols5 = SSMUL_REG_COLS5_F64;
 };
 template <> struct VTraits<Disc> {
     using Tw = DiscTw;
@@ -53,6 +61,13 @@ template <> struct VTraits<DDisc> {
     static constexpr int rung = 4, sw_src = 3, sw_mask = 7;
     static constexpr int reg_rows = 64, reg_cols = 64;
 };
+
+// register cap of the column kernels of family R
+template <typename V, int R>
+__host__ __device__ constexpr int cols_regs() {
+    if constexpr (std::is_same<V, CI<double>>::value) return R == 5 ? VTraits<V>::reg_cols5 : VTraits<V>::reg_cols;
+    else return VTraits<V>::reg_cols;
+}
 
 // A transform buffer in shared memory.  Element i lives in slot
 // i ^ ((i >> sw_src) & sw_mask): the swizzle permutes each aligned group of
