@@ -1325,6 +1325,21 @@ struct PoolUpload {
     }
 };
 
+// First descriptor of piece k of a host-buffer batch cut into `pieces`
+// pieces (k = pieces: count).  With three or more pieces the first and the
+// last take about a sixteenth of the batch each (at least one product): the
+// first piece's upload and the last one's download are the copies no
+// computation hides.
+size_t piece_start(size_t count, size_t pieces, size_t k) {
+    if (k == 0) return 0;
+    if (k >= pieces) return count;
+    if (pieces < 3) return count * k / pieces;
+    const size_t edge = std::max<size_t>(1, count / 16);
+    if (count < 2 * edge + (pieces - 2)) return count * k / pieces;
+    const size_t mid = count - 2 * edge;
+    return edge + mid * (k - 1) / (pieces - 2);
+}
+
 // The pieces of a host-buffer batch, in the caller's descriptor order:
 // piece k waits for the uploads that reach its operands' last byte, runs
 // as a batch in slots [i0, i1) of the plan's arrays, and its digits and
@@ -1409,7 +1424,7 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
         if (cudaStreamWaitEvent(p->piece_stream[l], p->piece_ev[0], 0) != cudaSuccess)
             return drain(SSMUL_CUDA_ERROR);
     for (size_t k = 0; k < pieces; ++k) {
-        const size_t i0 = count * k / pieces, i1 = count * (k + 1) / pieces;
+        const size_t i0 = piece_start(count, pieces, k), i1 = piece_start(count, pieces, k + 1);
         uint64_t ea = 0, eb = 0;
         for (size_t i = i0; i < i1; ++i) {
             ea = std::max(ea, h_desc[i].a_off + h_desc[i].na);
@@ -1439,7 +1454,7 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
     if (cudaEventRecord(p->desc_free, p->stream) != cudaSuccess) return drain(SSMUL_CUDA_ERROR);
     std::vector<std::pair<uint64_t, uint64_t>> zr;
     for (size_t k = 0; k < pieces; ++k) {
-        const size_t i0 = count * k / pieces, i1 = count * (k + 1) / pieces;
+        const size_t i0 = piece_start(count, pieces, k), i1 = piece_start(count, pieces, k + 1);
         if (cudaStreamWaitEvent(p->down, p->hb_ev[2 * k + 1], 0) != cudaSuccess)
             return drain(SSMUL_CUDA_ERROR);
         zr.clear();
