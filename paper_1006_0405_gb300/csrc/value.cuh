@@ -36,13 +36,10 @@ template <> struct VTraits<CI<float>> {
 #ifndef SSMUL_REG_COLS5_F64
 #define SSMUL_REG_COLS5_F64 96
 #endif
-#ifndef SSMUL_REG_ROWS_F64
-#define SSMUL_REG_ROWS_F64 96
-#endif
 template <> struct VTraits<CI<double>> {
     using Tw = CI<double>;
     static constexpr int rung = 1, sw_src = 2, sw_mask = 3;
-    static constexpr int reg_rows = SSMUL_REG_ROWS_F64, reg_cols = 80;
+    static constexpr int reg_rows = 96, reg_cols = 80;
     // the columns of the lengths 5 2^k run 5-warp CTAs (160 threads for the
     // 320-point columns, four columns per CTA): at 96 registers four CTAs
     // still fit an SM (5 warps x 3072 registers per 16,384-register quarter),
