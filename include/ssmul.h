@@ -162,7 +162,9 @@ typedef enum {
      * their products past m digits run after the batch's other products,
      * one after another, each in its parts (such a batch is not captured in
      * a CUDA graph, and ssmul_mul_batched_host runs its pieces on one
-     * stream). */
+     * stream).  A call whose products have more parts than any call before
+     * grows the plan's part arrays first, after waiting for the plan's
+     * queued work. */
     SSMUL_OPT_SPLIT_DIGITS = 4,
     /* bit mask of the transform length families besides 2^k: bit 0 the
      * lengths 3 * 2^k, bit 1 the lengths 5 * 2^k (default 3: both).  A
