@@ -243,12 +243,12 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # (log2(N1 / 5), log2 N2, log2 column CTA elements); the bench checks both
 # at run time and reports null traffic when either differs.
 NCU_TRAFFIC = {
-    "cuh_sha256_16": "54566cde433c864a",
+    "cuh_sha256_16": "53bf7fe274d5e295",
     "geometry_75k": (6, 9, 10),
     "per_product": {
-        "k_rows<double>": (84.808704e6 + 10.278400e6) / 16,
-        "k_rows<disc>": (63.533312e6 + 2.748928e6) / 16,
-        "k_rows<disc32x2>": (63.329536e6 + 3.716608e6) / 16,
+        "k_rows<double>": (84.648192e6 + 10.014464e6) / 16,
+        "k_rows<disc>": (63.492096e6 + 2.413056e6) / 16,
+        "k_rows<disc32x2>": (63.323648e6 + 3.144192e6) / 16,
     },
 }
 

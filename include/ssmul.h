@@ -141,9 +141,9 @@ typedef enum {
      * The factorisation of the DFT of Section 2.2 changes, not its value. */
     SSMUL_OPT_AUTOTUNE = 1,
     /* under the ladders, try binary32 only for products with
-     * na + nb <= value digits (and N <= 4096); 0: never.  Default 464 with
+     * na + nb <= value digits (and N <= 4096); 0: never.  Default 512 with
      * SSMUL_OPT_FP32_NIBBLES (binary32 rectangles isolated every uniform
-     * square product up to 232 x 232 digits), 32 without it (16 x 16).  The
+     * square product up to 256 x 256 digits), 32 without it (16 x 16).  The
      * first rung of Section 1's "more precision on failure". */
     SSMUL_OPT_FP32_MAX_DIGITS = 2,
     /* value != 0: balanced digits.  The transforms carry a_j - 128 and
@@ -199,7 +199,11 @@ typedef enum {
      * so narrower containment sets for twice the transform length.  The
      * isolated base-16 coefficients c'_i become the base-256 coefficients
      * c'_{2k} + 16 c'_{2k+1} exactly before the carry (the product identity
-     * of Section 2.1 in base 16).  The 4-bit digits are not balanced.
+     * of Section 2.1 in base 16).  The transform carries the centred 4-bit
+     * digits a'_j - ma and b'_j - mb, ma and mb the rounded means of each
+     * operand's 4-bit digits (whatever SSMUL_OPT_BALANCED says, which is
+     * about the bytes of the other rungs); the isolated coefficients are
+     * corrected exactly with integer window sums of the 4-bit digits.
      * Default 1; 0: the binary32 rung transforms the bytes like the other
      * rungs. */
     SSMUL_OPT_FP32_NIBBLES = 8

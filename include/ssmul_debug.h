@@ -39,7 +39,9 @@ ssmul_status ssmul_debug_twiddles(ssmul_plan_t plan, int f32, double* h_out, siz
  * prec = SSMUL_DEBUG_PREC_FP32_NIBBLES (na + nb <= 2048): binary32
  * rectangles on the 4-bit digits a'_j, b'_j (a = sum_j a'_j 16^j); d_iv
  * receives the enclosures of c'_i = sum_j a'_j b'_{i-j}, i < 2 (na + nb) - 1
- * (2 * (2 (na + nb) - 1) doubles).
+ * (2 * (2 (na + nb) - 1) doubles): the enclosures of the centred digits'
+ * coefficients plus their exact correction, rounded outwards.
+ * SSMUL_INVALID_ARG when the plan's SSMUL_OPT_FP32_NIBBLES is 0.
  */
 #define SSMUL_DEBUG_PREC_FP32_NIBBLES 100
 ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t plan, const uint8_t* d_a, size_t na,

@@ -25,12 +25,12 @@ namespace {
 // the binary32 rung is tried when the product has at most this many digits
 // in total (na + nb, a plan option; the default follows the digits the rung
 // transforms): binary32 rectangles were measured to isolate every uniform
-// square product up to 16 x 16 bytes (all-0xFF: 8 x 8), and up to 232 x 232
-// digits on 4-bit digits (all-0xFF: 256 x 256); the width grows with the
-// transform length
+// square product up to 16 x 16 bytes (all-0xFF: 8 x 8), and up to 256 x 256
+// digits on 4-bit digits centred on their means (all-0xFF: 1024 x 1024, all
+// the 4-bit digits take); the width grows with the transform length
 constexpr int FP32_MAX_LOG_N = LOG_SMALL;
 constexpr size_t FP32_MAX_DIGITS = 32;          // bytes
-constexpr size_t FP32_MAX_DIGITS_NIB = 464;     // 4-bit digits
+constexpr size_t FP32_MAX_DIGITS_NIB = 512;     // 4-bit digits
 
 // largest batch arena a plan allocates (the batch runs in chunks beyond it)
 constexpr size_t ARENA_CAP = size_t(4) << 30;
@@ -524,12 +524,13 @@ ssmul_status enqueue_rung_as(ssmul_plan_t p, const ProdDesc* d_desc, int count, 
     const int ko = kind_off<T>();
     if (g.small) {
         // binary32 rectangles on 4-bit digits need up to 4 times the length
-        // of the bytes' transform (2 (na + nb) - 1 <= 4096 coefficients)
-        const int n = (std::is_same<T, float>::value && p->fp32_nibbles)
-                          ? std::min(1 << LOG_SMALL, 4 << g.log_n) : 1 << g.log_n;
+        // of the bytes' transform (2 (na + nb) - 1 <= 4096 coefficients) and
+        // room for the prefix sums of their balancing (nib_prefix_scan)
+        const bool nib = std::is_same<T, float>::value && p->fp32_nibbles;
+        const int n = nib ? std::min(1 << LOG_SMALL, 4 << g.log_n) : 1 << g.log_n;
+        const size_t smem = n * sizeof(V) + (nib ? size_t(nib_prefix_bytes(n)) : 0);
         LaunchScope ls(p, SSMUL_K_SMALL + ko);
-        k_small<T, B, LIST><<<count, fft_threads<V>(n), n * sizeof(V),
-                              p->cur>>>(d_desc, p->tw(), list);
+        k_small<T, B, LIST><<<count, fft_threads<V>(n), smem, p->cur>>>(d_desc, p->tw(), list);
     } else if (g.r == 3) {
         enqueue_four_step<T, 3, LIST>(p, d_desc, count, g, list, p->tw(1));
     } else if (g.r == 5) {
@@ -1932,7 +1933,9 @@ ssmul_status ssmul_debug_mul_intervals(ssmul_plan_t p, const uint8_t* d_a, size_
                                        double* d_iv) {
     if (!p || !d_iv) return SSMUL_INVALID_ARG;
     if (int(prec) == SSMUL_DEBUG_PREC_FP32_NIBBLES) {
-        if (na + nb > size_t(NIB_MAX_DIGITS)) return SSMUL_INVALID_ARG;
+        // the binary32 launches are sized for 4-bit digits only while the
+        // plan's SSMUL_OPT_FP32_NIBBLES is on
+        if (na + nb > size_t(NIB_MAX_DIGITS) || !p->fp32_nibbles) return SSMUL_INVALID_ARG;
         return run_single(p, d_a, na, d_b, nb, d_z, h_res, SSMUL_PREC_FP32, d_iv, true);
     }
     if (prec != SSMUL_PREC_FP64 && prec != SSMUL_PREC_FP32 && prec != SSMUL_PREC_DISC64 &&

@@ -553,8 +553,20 @@ __device__ __forceinline__ void isolate_value(const DDisc& v, int64_t j, const P
 // k < na + nb (one coefficient more than the na + nb - 1 of the bytes).  The
 // packed inverse hands one thread c'_{2k} (real part) and c'_{2k+1}
 // (imaginary part), so each thread isolates both (Section 1) and writes C_k,
-// an exact integer sum.  The 4-bit digits are not balanced (SSMUL_OPT_BALANCED
-// applies to the bytes of the other rungs).
+// an exact integer sum.
+//
+// The transform carries the centred 4-bit digits e_j = a'_j - ma and
+// f_j = b'_j - mb (zero past the operands), ma and mb the rounded means of
+// a's and b's 4-bit digits: with J_i the pairs (j, i - j) that meet in
+// coefficient i,
+//   c'_i = sum_J (e_j + ma) (f_{i-j} + mb) = c''_i + mb Wa_i + ma Wb_i - ma mb |J_i|,
+// Wa_i and Wb_i the sums of the 4-bit digits of a and b over J_i, which
+// come from prefix sums Q of the 4-bit digits (a's, then b's) that the CTA
+// builds in shared memory (nib_prefix_scan); c''_i is what the transform
+// encloses.  Like the balanced bytes of the other rungs (balance_corr), this
+// makes the transformed values and so the sets smaller without changing the
+// product; the mean (8 for uniform digits, 0 for sparse operands, 15 for
+// all-0xFF ones) is the constant that makes the digits' sum of squares least.
 
 constexpr int NIB_MAX_DIGITS = 2048;      // na + nb: 2 (na + nb) - 1 <= 4096 = k_small's N
 
@@ -565,15 +577,92 @@ __device__ __forceinline__ int nib_log_n(const ProdDesc& d) {
     return k;
 }
 
-// base-16 digit j of the n-digit operand x (0 past its 2 n digits)
-__device__ __forceinline__ int nibble(const uint8_t* x, uint32_t n, int j) {
-    return uint32_t(j) < 2u * n ? (x[j >> 1] >> ((j & 1) * 4)) & 15 : 0;
+// the centred base-16 digit j of the n-digit operand x: its 4-bit digit
+// (x_{j/2} >> 4 (j mod 2)) & 15 minus m, and 0 past its 2 n digits
+__device__ __forceinline__ int nibble_c(const uint8_t* x, uint32_t n, int j, int m) {
+    return uint32_t(j) < 2u * n ? ((x[j >> 1] >> ((j & 1) * 4)) & 15) - m : 0;
+}
+
+// the prefix sums of the 4-bit digits and the two means they are centred on
+struct NibCentre {
+    const uint16_t* Q;
+    int ma, mb;
+};
+
+// Shared-memory room of the prefix sums Q (uint16: sums of at most 4096
+// digits of 15) and the scan's warp totals, after a transform buffer of n
+// elements (2 (na + nb) - 1 <= n)
+__host__ __device__ constexpr int nib_prefix_bytes(int n) { return 2 * n + 256; }
+
+// Q[m] = the sum of the first m of the M = 2 (na + nb) 4-bit digits a'_0 ..
+// a'_{2na-1}, b'_0 .. b'_{2nb-1} (m <= M), by one block scan: thread t sums
+// a contiguous run of digits, the runs' totals are scanned across the warps
+__device__ void nib_prefix_scan(const ProdDesc& d, uint16_t* Q, int* warp_tot) {
+    const int na2 = 2 * int(d.na), M = na2 + 2 * int(d.nb);
+    const auto digit = [&](int i) -> int {
+        const uint8_t* x = i < na2 ? d.a : d.b;
+        const int j = i < na2 ? i : i - na2;
+        return (x[j >> 1] >> ((j & 1) * 4)) & 15;
+    };
+    const int T = blockDim.x, per = (M + T - 1) / T;
+    const int i0 = threadIdx.x * per, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int s = 0;
+    for (int q = 0; q < per; ++q)
+        if (i0 + q < M) s += digit(i0 + q);
+    int x = s;                                      // inclusive scan within the warp
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (T >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < (T >> 5)) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int run = x - s + (warp > 0 ? warp_tot[warp - 1] : 0);
+    if (threadIdx.x == 0) Q[0] = 0;
+    for (int q = 0; q < per; ++q) {
+        if (i0 + q < M) {
+            run += digit(i0 + q);
+            Q[i0 + q + 1] = uint16_t(run);
+        }
+    }
+    __syncthreads();
+}
+
+// the rounded means of a's 2 na and b's 2 nb 4-bit digits, from Q
+__device__ __forceinline__ NibCentre nib_centre(const ProdDesc& d, const uint16_t* Q) {
+    const int na2 = 2 * int(d.na), nb2 = 2 * int(d.nb);
+    const int sa = Q[na2], sb = int(Q[na2 + nb2]) - sa;
+    return NibCentre{Q, (2 * sa + na2) / (2 * na2), (2 * sb + nb2) / (2 * nb2)};
+}
+
+// the exact term that turns c''_i into c'_i (i < 2 (na + nb) - 1), from Q
+__device__ __forceinline__ int64_t nib_centre_corr(const ProdDesc& d, const NibCentre& c,
+                                                   int64_t i) {
+    const int64_t na2 = 2 * int64_t(d.na), nb2 = 2 * int64_t(d.nb);
+    const int64_t ja_lo = i - nb2 + 1 > 0 ? i - nb2 + 1 : 0, ja_hi = i < na2 - 1 ? i : na2 - 1;
+    const int64_t jb_lo = i - na2 + 1 > 0 ? i - na2 + 1 : 0, jb_hi = i < nb2 - 1 ? i : nb2 - 1;
+    const int64_t wa = int64_t(c.Q[ja_hi + 1]) - int64_t(c.Q[ja_lo]);
+    const int64_t wb = int64_t(c.Q[na2 + jb_hi + 1]) - int64_t(c.Q[na2 + jb_lo]);
+    return int64_t(c.mb) * wa + int64_t(c.ma) * wb -
+           int64_t(c.ma) * c.mb * (ja_hi - ja_lo + 1);
 }
 
 // The decision of isolate_one for nibble coefficient idx (lp of them) from
-// the set [lo, hi] 2^-k; returns the isolated integer (0 otherwise).
+// the set [lo, hi] 2^-k of c''_idx; returns the isolated integer c'_idx
+// (0 otherwise).
 __device__ __forceinline__ int64_t isolate_nib_one(float lo, float hi, int k, int64_t idx,
-                                                   int64_t lp, const ProdDesc& d, IsoAcc& acc) {
+                                                   int64_t lp, const ProdDesc& d,
+                                                   const NibCentre& c, IsoAcc& acc) {
     double dl = double(lo), dh = double(hi);          // exact widening
     if (d.fault_widen == 1) {                         // test fault of the binary32 rung
         const double f = 4.0 * pow2_pos(k);
@@ -588,11 +677,12 @@ __device__ __forceinline__ int64_t isolate_nib_one(float lo, float hi, int k, in
     floor_ceil_scaled(dh, k, kh, unused);
     constexpr long long KMAX = 1ll << 53;
     if (idx < lp) {
+        const int64_t corr = nib_centre_corr(d, c, idx);
         if (d.iv != nullptr) {                        // the set of c'_idx (tests)
-            d.iv[2 * idx] = __dmul_rd(dl, pow2_neg(k));
-            d.iv[2 * idx + 1] = __dmul_ru(dh, pow2_neg(k));
+            d.iv[2 * idx] = __dadd_rd(__dmul_rd(dl, pow2_neg(k)), double(corr));
+            d.iv[2 * idx + 1] = __dadd_ru(__dmul_ru(dh, pow2_neg(k)), double(corr));
         }
-        if (kl == kh && kl >= 0 && kl < KMAX) return kl;
+        if (kl == kh && kl > -KMAX && kl < KMAX && kl + corr >= 0) return kl + corr;
         if (kl < kh) acc.unisolated++;
         else acc.empty++;              // no integer, a negative one, NaN or overflow
         return 0;
@@ -602,10 +692,11 @@ __device__ __forceinline__ int64_t isolate_nib_one(float lo, float hi, int k, in
 }
 
 __device__ __forceinline__ void isolate_nib_value(const CI<float>& v, int k, int64_t j,
-                                                  const ProdDesc& d, IsoAcc& acc) {
+                                                  const ProdDesc& d, const NibCentre& c,
+                                                  IsoAcc& acc) {
     const int64_t nz = int64_t(d.na) + d.nb, lp = 2 * nz - 1;
-    const int64_t c0 = isolate_nib_one(v.rl, v.rh, k, 2 * j, lp, d, acc);
-    const int64_t c1 = isolate_nib_one(v.il, v.ih, k, 2 * j + 1, lp, d, acc);
+    const int64_t c0 = isolate_nib_one(v.rl, v.rh, k, 2 * j, lp, d, c, acc);
+    const int64_t c1 = isolate_nib_one(v.il, v.ih, k, 2 * j + 1, lp, d, c, acc);
     if (j < nz) d.coeff[j] = c0 + 16 * c1;
 }
 
@@ -687,13 +778,19 @@ __device__ __forceinline__ void small_one(const ProdDesc d, const TwTable& tw) {
     const bool nib = F32 && d.fp32_nib != 0;
     const int logN = nib ? nib_log_n(d) : d.log_n, N = 1 << logN;
     const int bias = (d.balanced && !nib) ? 128 : 0;
+    // 4-bit digits: their prefix sums after the transform buffer (the launch
+    // adds nib_prefix_bytes to its N sizeof(V) bytes), then their means
+    uint16_t* const Q = reinterpret_cast<uint16_t*>(smem_raw + size_t(N) * sizeof(V));
+    if (nib) nib_prefix_scan(d, Q, reinterpret_cast<int*>(smem_raw + size_t(N) * sizeof(V) +
+                                                          ((2 * N + 4 + 15) & ~15)));
+    const NibCentre cen = nib ? nib_centre(d, Q) : NibCentre{Q, 0, 0};
     // the digit pairs as integers (8 bytes each, inside the buffer), then the
     // forward transform's exact first step (logN >= 2 for every plan length)
     int2* const si = reinterpret_cast<int2*>(smem_raw);
     stage<4 * BPT, int2>(
         N,
         [&](int j) {
-            if (nib) return make_int2(nibble(d.a, d.na, j), nibble(d.b, d.nb, j));
+            if (nib) return make_int2(nibble_c(d.a, d.na, j, cen.ma), nibble_c(d.b, d.nb, j, cen.mb));
             return make_int2(j < int(d.na) ? int(d.a[j]) - bias : 0,
                              j < int(d.nb) ? int(d.b[j]) - bias : 0);
         },
@@ -712,7 +809,7 @@ __device__ __forceinline__ void small_one(const ProdDesc d, const TwTable& tw) {
     for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) {
         if constexpr (F32) {
             if (nib) {
-                isolate_nib_value(sm[j], logN + 2, j, d, acc);
+                isolate_nib_value(sm[j], logN + 2, j, d, cen, acc);
                 continue;
             }
         }

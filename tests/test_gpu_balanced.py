@@ -48,11 +48,11 @@ def test_balanced_products_bit_exact(prec, na, nb, dist):
 
 # binary32 rectangles at their measured isolation limits (squares, 8 uniform
 # products per size drawn as the bench's limit search draws them): bytes
-# 16 (all-0xFF 8), balanced bytes 30 (all-0xFF 16), 4-bit digits 232
-# (all-0xFF 256)
+# 16 (all-0xFF 8), balanced bytes 30 (all-0xFF 16), 4-bit digits centred on
+# their means 256 (all-0xFF: every size the 4-bit digits take, 1024)
 @pytest.mark.parametrize("balanced,nibbles,n,dist", [
     (0, 0, 16, "uniform"), (0, 0, 8, "ff"), (1, 0, 30, "uniform"), (1, 0, 16, "ff"),
-    (0, 1, 232, "uniform"), (0, 1, 256, "ff"), (1, 1, 232, "uniform")])
+    (0, 1, 256, "uniform"), (0, 1, 1024, "ff"), (1, 1, 256, "uniform")])
 def test_fp32_isolation_limits(balanced, nibbles, n, dist):
     with Plan(n, n, 0, abi.SSMUL_PREC_FP32) as p:
         assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_BALANCED, balanced) == OK

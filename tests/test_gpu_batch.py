@@ -114,7 +114,7 @@ def test_fp32_router_option():
     a, b = synth.operand_pair(5, 300, 300)
     small = synth.operand_pair(6, 40, 40)
     with Plan(300, 300, 0, abi.SSMUL_PREC_LADDER) as p:
-        s, r, z = p.mul(a, b)                       # 600 digits: above the default 464
+        s, r, z = p.mul(a, b)                       # 600 digits: above the default 512
         assert s == OK and r.precision_used == abi.SSMUL_PREC_FP64
         s, r, z = p.mul(*small)                     # 80 digits: binary32 on 4-bit digits
         assert s == OK and r.precision_used == abi.SSMUL_PREC_FP32

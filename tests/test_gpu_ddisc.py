@@ -135,7 +135,7 @@ def test_pair_disc_intervals_contain_exact(na, nb):
 
 def test_fast_ladder_escalates_and_stays_exact():
     pairs = [synth.operand_pair(synth.SEED_BASE + 800 + i, na, nb) for i, (na, nb) in
-             enumerate([(5, 4), (300, 200), (5000, 6000), (75000, 75000), (200000, 150000)])]
+             enumerate([(5, 4), (300, 260), (5000, 6000), (75000, 75000), (200000, 150000)])]
     with Plan(200000, 200000, 8, abi.SSMUL_PREC_LADDER_FAST) as p:
         used = []
         for a, b in pairs:

@@ -136,7 +136,7 @@ def test_naive_comparator():
 
 def test_ladder_disc_rungs():
     with Plan(40000, 40000, 0, abi.SSMUL_PREC_LADDER_DISC) as p:
-        for na, nb, prec in [(4, 5, abi.SSMUL_PREC_FP32), (300, 200, abi.SSMUL_PREC_DISC64),
+        for na, nb, prec in [(4, 5, abi.SSMUL_PREC_FP32), (300, 260, abi.SSMUL_PREC_DISC64),
                              (40000, 33333, abi.SSMUL_PREC_DISC64)]:
             a, b = synth.operand_pair(synth.SEED_BASE + na, na, nb)
             s, r, z = p.mul(a, b)

@@ -3,7 +3,9 @@
 The binary32 rung transforms the operands' base-16 digits and turns the
 isolated base-16 coefficients into base-256 ones (c'_{2k} + 16 c'_{2k+1})
 before the carry; a product with na + nb digits then has na + nb
-coefficients, one more than its bytes give.  Every product is compared bit
+coefficients, one more than its bytes give.  The transform carries each
+operand's 4-bit digits minus their rounded mean, and the isolated
+coefficients get the exact correction back.  Every product is compared bit
 for bit with oracle.exact.product.
 """
 import numpy as np
@@ -104,7 +106,8 @@ def _nibbles(x):
 
 
 @pytest.mark.parametrize("na,nb,dist", [(1, 1, "uniform"), (5, 7, "uniform"), (100, 90, "ff"),
-                                        (231, 231, "uniform"), (1024, 1, "uniform")])
+                                        (231, 231, "uniform"), (256, 256, "uniform"),
+                                        (1024, 1024, "ff"), (1024, 1, "uniform"), (40, 41, "raw")])
 def test_nibble_intervals_contain_exact(na, nb, dist):
     """Every binary32 set of a 4-bit-digit coefficient contains the exact
     c'_i of the oracle's convolution of the 4-bit digit vectors, and those
@@ -127,3 +130,61 @@ def test_nibble_intervals_contain_exact(na, nb, dist):
     assert np.all((iv[:, 0] <= c) & (c <= iv[:, 1]))
     if s == OK:
         assert np.array_equal(dz.cpu().numpy(), E.product(a, b))
+
+
+def _interval_check(a, b):
+    """The 4-bit-digit sets of one product contain the oracle's c'_i; returns
+    the product's status and digits."""
+    na, nb = len(a), len(b)
+    c4 = E.conv(_nibbles(a), _nibbles(b)).astype(np.float64)
+    with Plan(na, nb, 0, abi.SSMUL_PREC_FP32) as p:
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        dz = torch.zeros(na + nb, dtype=torch.uint8, device="cuda")
+        lp = 2 * (na + nb) - 1
+        div = torch.zeros(2 * lp, dtype=torch.float64, device="cuda")
+        s, r = abi.ssmul_debug_mul_intervals(p.h, da.data_ptr(), na, db.data_ptr(), nb,
+                                             dz.data_ptr(), abi.SSMUL_DEBUG_PREC_FP32_NIBBLES,
+                                             div.data_ptr())
+        iv = div.cpu().numpy().reshape(lp, 2)
+    assert r.n_empty == 0
+    assert np.all((iv[:, 0] <= c4) & (c4 <= iv[:, 1]))
+    return s, dz.cpu().numpy()
+
+
+@pytest.mark.parametrize("case", ["uniform_sparse", "ff_zero", "ff_uniform", "zero_zero",
+                                  "sparse_ff", "one_digit_ff"])
+def test_nibbles_operands_of_different_means(case):
+    """Each operand is centred on its own mean (0 for sparse and zero
+    operands, 15 for all-0xFF, about 8 for uniform digits): pairs of
+    different means isolate, stay exact and keep the sets around c'_i."""
+    seed = synth.SEED_BASE + 700
+    n = 200
+    ops = {
+        "uniform": synth.operand_pair(seed, n, 1)[0],
+        "sparse": _sparse(seed + 1, n, 5),
+        "ff": np.full(n, 0xFF, np.uint8),
+        "zero": np.zeros(n, np.uint8),
+    }
+    if case == "one_digit_ff":
+        a, b = np.array([0xFF], np.uint8), np.full(1023, 0xFF, np.uint8)
+    else:
+        ka, kb = case.split("_")
+        a, b = ops[ka], ops[kb]
+    s, z = _interval_check(a, b)
+    assert s == OK
+    assert np.array_equal(z, E.product(a, b))
+
+
+def test_nibble_export_needs_the_option():
+    """The 4-bit export is refused on a plan whose binary32 rung transforms
+    bytes (its launches have no room for the 4-bit transform)."""
+    a, b = synth.operand_pair(synth.SEED_BASE + 710, 50, 50)
+    with Plan(50, 50, 0, abi.SSMUL_PREC_FP32) as p:
+        assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_FP32_NIBBLES, 0) == OK
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        dz = torch.zeros(100, dtype=torch.uint8, device="cuda")
+        div = torch.zeros(2 * 199, dtype=torch.float64, device="cuda")
+        s, _ = abi.ssmul_debug_mul_intervals(p.h, da.data_ptr(), 50, db.data_ptr(), 50,
+                                             dz.data_ptr(), abi.SSMUL_DEBUG_PREC_FP32_NIBBLES,
+                                             div.data_ptr())
+    assert s == abi.SSMUL_INVALID_ARG
