@@ -228,7 +228,7 @@ struct GraphEntry {
 struct TwFamily {
     int R = 1;
     int log_tab = 0;
-    TwEntry<double>* t64 = nullptr;
+    TwMid* t64 = nullptr;                 // values before the widening (tw_expand_w)
     TwEntry<float>* t32 = nullptr;
     DiscTw* td = nullptr;
     DDiscC* tdd = nullptr;
@@ -1611,7 +1611,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
     for (TwFamily& F : p->fam) {
         const size_t t = F.entries();
         if (!t) continue;
-        if (e == cudaSuccess) e = cudaMalloc(&F.t64, t * sizeof(TwEntry<double>));
+        if (e == cudaSuccess) e = cudaMalloc(&F.t64, t * sizeof(TwMid));
         if (e == cudaSuccess) e = cudaMalloc(&F.t32, t * sizeof(TwEntry<float>));
         if (e == cudaSuccess) e = cudaMalloc(&F.td, t * sizeof(DiscTw));
         if (e == cudaSuccess) e = cudaMalloc(&F.tdd, t * sizeof(DDiscC));
@@ -1667,7 +1667,7 @@ ssmul_status ssmul_plan(ssmul_plan_t* out, size_t max_na, size_t max_nb, size_t 
         if (!t) continue;
         const int blocks = int((t + threads - 1) / threads);
         k_twiddle_gen<<<blocks, threads, 0, p->stream>>>(F.t64, F.t32, F.log_tab, F.R);
-        k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(F.t64, F.td, p->rho + 2 * f, int64_t(t));
+        k_disc_tw_gen<<<blocks, threads, 0, p->stream>>>(F.t64, F.R, F.td, p->rho + 2 * f, int64_t(t));
         k_ddisc_tw_gen<<<blocks, threads, 0, p->stream>>>(F.td, p->rho + 2 * f, F.tdd, int64_t(t));
     }
     {
@@ -1913,7 +1913,16 @@ ssmul_status ssmul_debug_twiddles(ssmul_plan_t p, int f32, double* h_out, size_t
     if (s != SSMUL_OK) return s;
     *log_ntab = F.log_tab;
     if (!(f32 & 1)) {
-        SS_TRY(cudaMemcpy(h_out, F.t64, tab * sizeof(TwEntry<double>), cudaMemcpyDeviceToHost));
+        // the bounds the kernels rebuild from the stored values
+        std::vector<TwMid> t(tab);
+        SS_TRY(cudaMemcpy(t.data(), F.t64, tab * sizeof(TwMid), cudaMemcpyDeviceToHost));
+        for (size_t j = 0; j < tab; ++j) {
+            const TwEntry<double> e = tw_expand_w(t[j], tw_widen_r(uint32_t(j), F.R));
+            h_out[4 * j] = e.cl;
+            h_out[4 * j + 1] = e.ch;
+            h_out[4 * j + 2] = e.sl;
+            h_out[4 * j + 3] = e.sh;
+        }
     } else {
         std::vector<TwEntry<float>> t(tab);
         SS_TRY(cudaMemcpy(t.data(), F.t32, tab * sizeof(TwEntry<float>), cudaMemcpyDeviceToHost));
@@ -2238,7 +2247,7 @@ constexpr size_t NOALLOC_TILES = (NOALLOC_N + 1 + CARRY_TILE - 1) / CARRY_TILE;
 
 constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t NA_OFF_T64 = 0;
-constexpr size_t NA_OFF_T32 = na_align(NA_OFF_T64 + NOALLOC_TAB * sizeof(TwEntry<double>));
+constexpr size_t NA_OFF_T32 = na_align(NA_OFF_T64 + NOALLOC_TAB * sizeof(TwMid));
 constexpr size_t NA_OFF_DESC = na_align(NA_OFF_T32 + NOALLOC_TAB * sizeof(TwEntry<float>));
 constexpr size_t NA_OFF_ST = na_align(NA_OFF_DESC + sizeof(ProdDesc));
 constexpr size_t NA_OFF_RES = na_align(NA_OFF_ST + sizeof(ProdState));
@@ -2300,7 +2309,7 @@ unsigned char* noalloc_setup(int dev, cudaStream_t stream, bool rebuild, ssmul_s
                              int(NOALLOC_N * sizeof(CI<double>)));
     if (e == cudaSuccess) {
         k_twiddle_gen<<<int((NOALLOC_TAB + 255) / 256), 256, 0, stream>>>(
-            reinterpret_cast<TwEntry<double>*>(base + NA_OFF_T64),
+            reinterpret_cast<TwMid*>(base + NA_OFF_T64),
             reinterpret_cast<TwEntry<float>*>(base + NA_OFF_T32), NOALLOC_LOG_N, 1);
         k_noalloc_mark<<<1, 1, 0, stream>>>(base);
         e = cudaGetLastError();
@@ -2329,7 +2338,7 @@ ssmul_status noalloc_run(unsigned char* base, const uint8_t* d_a, size_t na, con
     d.st = reinterpret_cast<ProdState*>(base + NA_OFF_ST);
     d.res = reinterpret_cast<ssmul_result*>(base + NA_OFF_RES);
     const ProdDesc* slot = reinterpret_cast<const ProdDesc*>(base + NA_OFF_DESC);
-    const TwTable tw{reinterpret_cast<const TwEntry<double>*>(base + NA_OFF_T64),
+    const TwTable tw{reinterpret_cast<const TwMid*>(base + NA_OFF_T64),
                      reinterpret_cast<const TwEntry<float>*>(base + NA_OFF_T32), NOALLOC_LOG_N};
     const int n = 1 << d.log_n;
 

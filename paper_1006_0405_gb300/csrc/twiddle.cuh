@@ -30,7 +30,19 @@
 // The values are then clamped to what is known exactly on the first octant
 // (cos in [0, 1], sin in [0, 1]); j = 0 is the exact point (1, 0).  The
 // binary32 table is the binary64 one rounded outward.
+//
+// The binary64 table stores, per entry, only the two values before the
+// widening (TwMid, 16 bytes); the bounds are rebuilt where they are read
+// (tw_expand).  For the positive finite values of the first octant one
+// nextafter step is one unit of the binary64 bit pattern, and the bit
+// patterns of nonnegative doubles order like the integers, so the widening
+// and the clamp are integer additions and min / max on the bit patterns:
+// the rebuilt bounds are those the widening computes, bit for bit, from
+// half the bytes (the per-element twiddles of the four-step and packing
+// passes are read from L2 once per element).
 #pragma once
+#include <cstring>
+
 #include "interval.cuh"
 #include "disc.cuh"
 
@@ -43,6 +55,45 @@ template <typename T>
 struct TwEntry {
     T cl, ch, sl, sh;
 };
+
+// an entry of the binary64 table before its widening
+struct alignas(16) TwMid {
+    double c, s;
+};
+
+__host__ __device__ __forceinline__ long long tw_bits(double x) {
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    long long b;
+    memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ double tw_from_bits(long long b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double x;
+    memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+
+// The widening steps of entry j of a table of family R: none at j = 0,
+// TW_WIDEN_ULPS where the argument is exact, TW3_WIDEN_ULPS otherwise.
+template <int R>
+__host__ __device__ __forceinline__ int tw_widen(uint32_t j);
+
+// Entry j's bounds from its values: each value moved w binary64 steps down
+// and up (integer steps of the bit pattern), then clamped to [0, 1].
+__host__ __device__ __forceinline__ TwEntry<double> tw_expand_w(TwMid m, int w) {
+    constexpr long long ONE = 0x3FF0000000000000ll;          // the bit pattern of 1.0
+    const long long bc = tw_bits(m.c), bs = tw_bits(m.s);
+    const long long cl = bc - w, ch = bc + w, sl = bs - w, sh = bs + w;
+    return {tw_from_bits(cl > 0 ? cl : 0), tw_from_bits(ch < ONE ? ch : ONE),
+            tw_from_bits(sl > 0 ? sl : 0), tw_from_bits(sh < ONE ? sh : ONE)};
+}
 
 struct DDiscC;
 struct ScalarSet;
@@ -59,7 +110,7 @@ constexpr int LOG_STEP_MAX = 12;
 constexpr int STEP_TAB = 1 << (LOG_STEP_MAX - 1);
 
 struct TwTable {
-    const TwEntry<double>* t64;   // Ntab/8 + 1 entries
+    const TwMid* t64;             // Ntab/8 + 1 entries (values before the widening)
     const TwEntry<float>* t32;    // same, binary32
     int log_n;                    // Ntab = R 2^log_n (R: the kernel's family)
     const DiscTw* td;             // same, as discs (centre, radius)
@@ -80,14 +131,24 @@ struct TwTable {
     const ScalarSet* scal;
 };
 
-__global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log_n, int R) {
+template <int R>
+__host__ __device__ __forceinline__ int tw_widen(uint32_t j) {
+    return j == 0 ? 0 : ((R == 1 || j % uint32_t(R) == 0) ? TW_WIDEN_ULPS : TW3_WIDEN_ULPS);
+}
+
+// tw_widen for a family R known at run time
+__host__ __device__ __forceinline__ int tw_widen_r(uint32_t j, int R) {
+    return R == 1 ? tw_widen<1>(j) : (R == 3 ? tw_widen<3>(j) : tw_widen<5>(j));
+}
+
+__global__ void k_twiddle_gen(TwMid* t64, TwEntry<float>* t32, int log_n, int R) {
     const int64_t ntab = int64_t(R) << log_n;
     const int64_t count = ntab / 8 + 1;
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
-        TwEntry<double> e;
+        TwMid m;
         if (j == 0) {
-            e = {1.0, 1.0, 0.0, 0.0};
+            m = {1.0, 0.0};
         } else {
             // 2 j / ntab: exact for R = 1 and for j divisible by R
             const bool exact = R == 1 || j % R == 0;
@@ -102,18 +163,11 @@ __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log
                 s = __fma_rn(pd, c, s);
                 c = __fma_rn(-pd, s0, c);
             }
-            const int widen = exact ? TW_WIDEN_ULPS : TW3_WIDEN_ULPS;
-            double cl = c, ch = c, sl = s, sh = s;
-            for (int k = 0; k < widen; ++k) {
-                cl = nextafter(cl, -1.0e300);
-                ch = nextafter(ch, 1.0e300);
-                sl = nextafter(sl, -1.0e300);
-                sh = nextafter(sh, 1.0e300);
-            }
-            // first octant: 0 < sin <= cos <= 1
-            e = {fmax(cl, 0.0), fmin(ch, 1.0), fmax(sl, 0.0), fmin(sh, 1.0)};
+            m = {c, s};
         }
-        t64[j] = e;
+        // the widening and the clamp to the first octant (0 < sin <= cos <= 1)
+        const TwEntry<double> e = tw_expand_w(m, tw_widen_r(uint32_t(j), R));
+        t64[j] = m;
         t32[j] = {__double2float_rd(e.cl), __double2float_ru(e.ch),
                   __double2float_rd(e.sl), __double2float_ru(e.sh)};
     }
@@ -125,10 +179,10 @@ __global__ void k_twiddle_gen(TwEntry<double>* t64, TwEntry<float>* t32, int log
 // distance to any point of the rectangle.  *rho (zero on entry) becomes the
 // largest of these radii (nonnegative binary32 values order like their bit
 // patterns), the radius the double-binary32 table shares.
-__global__ void k_disc_tw_gen(const TwEntry<double>* t64, DiscTw* td, float* rho, int64_t count) {
+__global__ void k_disc_tw_gen(const TwMid* t64, int R, DiscTw* td, float* rho, int64_t count) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < count;
          j += int64_t(gridDim.x) * blockDim.x) {
-        const TwEntry<double> e = t64[j];
+        const TwEntry<double> e = tw_expand_w(t64[j], tw_widen_r(uint32_t(j), R));
         const double c = __dadd_rn(0.5 * e.cl, 0.5 * e.ch);
         const double s = __dadd_rn(0.5 * e.sl, 0.5 * e.sh);
         const double ec = fmax(__dsub_ru(c, e.cl), __dsub_ru(e.ch, c));
@@ -177,18 +231,33 @@ __device__ __forceinline__ DiscTw twiddle_disc(const TwTable& tw, uint32_t j) {
     return {negr ? flip(wc) : wc, negi ? flip(ws) : ws, e.rho, e.mod};
 }
 
-template <typename T>
-__device__ __forceinline__ const TwEntry<T>* tw_ptr(const TwTable& tw);
+// entry jj of a family-R table, as bounds
+template <typename T, int R>
+__device__ __forceinline__ TwEntry<T> tw_entry(const TwTable& tw, uint32_t jj);
 template <>
-__device__ __forceinline__ const TwEntry<double>* tw_ptr<double>(const TwTable& tw) { return tw.t64; }
+__device__ __forceinline__ TwEntry<float> tw_entry<float, 1>(const TwTable& tw, uint32_t jj) { return tw.t32[jj]; }
 template <>
-__device__ __forceinline__ const TwEntry<float>* tw_ptr<float>(const TwTable& tw) { return tw.t32; }
+__device__ __forceinline__ TwEntry<float> tw_entry<float, 3>(const TwTable& tw, uint32_t jj) { return tw.t32[jj]; }
+template <>
+__device__ __forceinline__ TwEntry<float> tw_entry<float, 5>(const TwTable& tw, uint32_t jj) { return tw.t32[jj]; }
+template <>
+__device__ __forceinline__ TwEntry<double> tw_entry<double, 1>(const TwTable& tw, uint32_t jj) {
+    return tw_expand_w(tw.t64[jj], tw_widen<1>(jj));
+}
+template <>
+__device__ __forceinline__ TwEntry<double> tw_entry<double, 3>(const TwTable& tw, uint32_t jj) {
+    return tw_expand_w(tw.t64[jj], tw_widen<3>(jj));
+}
+template <>
+__device__ __forceinline__ TwEntry<double> tw_entry<double, 5>(const TwTable& tw, uint32_t jj) {
+    return tw_expand_w(tw.t64[jj], tw_widen<5>(jj));
+}
 
 // Enclosure of omega_Ntab^(sign * j) for any integer j (taken mod Ntab).
 template <typename T, int SIGN, int R = 1>
 __device__ __forceinline__ CI<T> twiddle(const TwTable& tw, uint32_t j) {
     const TwPos ps = tw_pos<R>(tw.log_n, j);
-    const TwEntry<T> e = tw_ptr<T>(tw)[ps.jj];
+    const TwEntry<T> e = tw_entry<T, R>(tw, ps.jj);
     const T cl = ps.refl ? e.sl : e.cl, ch = ps.refl ? e.sh : e.ch;
     const T sl = ps.refl ? e.cl : e.sl, sh = ps.refl ? e.ch : e.sh;
     // a quarter turn maps (c, s) to (-s, c); the negations are sign-bit

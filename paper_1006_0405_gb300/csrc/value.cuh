@@ -24,9 +24,9 @@ constexpr int RUNGS = 5;
 
 // sw_src, sw_mask: the shared-memory swizzle of SBuf for the type's size;
 // reg_rows, reg_cols: register caps of k_rows and of the column kernels,
-// chosen so that one more CTA shares an SM than the natural register count
-// allows (an explicit cap for every type: a cap of 255 is not the same as
-// none)
+// mostly chosen so that one more CTA shares an SM than the natural register
+// count allows (an explicit cap for every type: a cap of 255 is not the
+// same as none)
 template <typename V> struct VTraits;
 template <> struct VTraits<CI<float>> {
     using Tw = CI<float>;
@@ -39,7 +39,10 @@ template <> struct VTraits<CI<float>> {
 template <> struct VTraits<CI<double>> {
     using Tw = CI<double>;
     static constexpr int rung = 1, sw_src = 2, sw_mask = 3;
-    static constexpr int reg_rows = 96, reg_cols = 80;
+    // k_rows: 128 registers hold its whole state (no spills, 4 CTAs of 4
+    // warps per SM); at 96 (5 CTAs) it spilled 72 bytes per thread and
+    // moved 1.6 times the L1 <-> L2 bytes in the same time
+    static constexpr int reg_rows = 128, reg_cols = 80;
     // the columns of the lengths 5 2^k run 5-warp CTAs (160 threads for the
     // 320-point columns, four columns per CTA): at 96 registers four CTAs
     // still fit an SM (5 warps x 3072 registers per 16,384-register quarter),

@@ -57,6 +57,28 @@ def test_odd_family_twiddles_contain_exact(odd, K):
         assert np.all(fcl <= cl) and np.all(ch <= fch) and np.all(fsl <= sl) and np.all(sh <= fsh)
 
 
+@pytest.mark.parametrize("odd,K", [(1, 16), (3, 14), (5, 13)])
+def test_twiddle_bounds_are_the_widened_values(odd, K):
+    """The binary64 table keeps the values before the widening and rebuilds
+    the bounds where they are read: every entry j >= 1 spans exactly 2 w
+    binary64 steps (w = 4 where the argument 2 j / Ntab is exact, R = 1 or R
+    divides j; 6 otherwise), or fewer only where it was clamped at 1, and
+    entry 0 is the exact point (1, 0)."""
+    n = 1 << 15
+    with Plan(n, n) as p:
+        ln, cl, ch, sl, sh = p.twiddles(False, odd=odd)
+    assert ln == K
+    j = np.arange(len(cl))
+    w = np.where((odd == 1) | (j % odd == 0), 4, 6)
+    for lo, hi in ((cl, ch), (sl, sh)):
+        steps = hi.view(np.int64) - lo.view(np.int64)
+        clamped = hi == 1.0
+        assert np.all(steps[1:][~clamped[1:]] == 2 * w[1:][~clamped[1:]])
+        assert np.all(steps[1:][clamped[1:]] <= 2 * w[1:][clamped[1:]])
+        assert np.all(lo[1:] > 0.0)
+    assert (cl[0], ch[0], sl[0], sh[0]) == (1.0, 1.0, 0.0, 0.0)
+
+
 def test_short_plans_have_no_odd_tables():
     with Plan(2000, 2000) as p:
         buf = np.zeros(64)
