@@ -332,7 +332,15 @@ def _batch_report(ctx, seed, na, nb, dists, lanes, one_lane=False) -> dict:
     batch.clear()
     el, rs1 = _one_at_a_time(torch, abi, batch, max_n, abi.SSMUL_PREC_FP64)
     digits["fp64_one_at_a_time"] = (el, rs1, [digest(z) for z in batch.digits()])
-    expected = ctx.pool().digests(batch.jobs())
+    pool = ctx.pool()
+    t0 = time.perf_counter()
+    expected = pool.digests(batch.jobs())
+    t_oracle = time.perf_counter() - t0
+    # the oracle's own throughput on the host cores (exact convolution + carry per product)
+    out["oracle_cpu"] = {"s_total": t_oracle, "digits_per_s": float(batch.nz.sum()) / t_oracle,
+                         "cores": pool.processes, "kind": "oracle",
+                         "sample": "every product of the batch (its operands drawn again in the worker), "
+                                   "one worker process per core"}
     for key, (t, rs, dg) in digits.items():
         n_ver = d_ver = 0
         for r, d, e, nz in zip(rs, dg, expected, batch.nz):
