@@ -243,12 +243,12 @@ def kernel_ops(na: int, nb: int, precision: str = "fp64") -> dict:
 # (log2(N1 / 5), log2 N2, log2 column CTA elements); the bench checks both
 # at run time and reports null traffic when either differs.
 NCU_TRAFFIC = {
-    "cuh_sha256_16": "53bf7fe274d5e295",
+    "cuh_sha256_16": "ecbcf5c5efa479f0",
     "geometry_75k": (6, 9, 10),
     "per_product": {
-        "k_rows<double>": (84.648192e6 + 10.014464e6) / 16,
-        "k_rows<disc>": (63.492096e6 + 2.413056e6) / 16,
-        "k_rows<disc32x2>": (63.323648e6 + 3.144192e6) / 16,
+        "k_rows<double>": (84.438272e6 + 9.890560e6) / 16,
+        "k_rows<disc>": (63.491840e6 + 3.433984e6) / 16,
+        "k_rows<disc32x2>": (63.323392e6 + 4.709120e6) / 16,
     },
 }
 

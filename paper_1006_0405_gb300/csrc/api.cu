@@ -846,6 +846,16 @@ size_t arena_need(int log_n) {
            (((n / 2) * sizeof(CI<double>) + 255) & ~size_t(255));
 }
 
+// Arena bytes of one product of a batch (its workspace at its transform
+// length, and its digit prefix sums when the digits are balanced); 0 for a
+// product that runs split, outside the arena.
+size_t product_arena_bytes(ssmul_plan_t p, const ssmul_desc& hd) {
+    const size_t m = p->split_digits;
+    if (m && (hd.na > m || hd.nb > m)) return 0;
+    return arena_need(length_code(hd.na, hd.nb, p->lengths)) +
+           (p->balanced ? pre_bytes(hd.na, hd.nb) : 0);
+}
+
 // Host half of a batch: products sorted by transform length (longest
 // first) and, inside one length, binary32-eligible products first, so that
 // every launch covers a contiguous run of descriptors; descriptors written
@@ -903,7 +913,7 @@ ssmul_status prepare_batch(ssmul_plan_t p, size_t base, size_t count, const ssmu
             const int ln = logn[order[k1]];
             const ssmul_desc& hd = h_desc[order[k1]];
             const size_t pb = p->balanced ? pre_bytes(hd.na, hd.nb) : 0;
-            const size_t need = arena_need(ln) + pb;
+            const size_t need = product_arena_bytes(p, hd);
             if (used + need > arena_len) break;
             ProdDesc& d = p->h_desc[base + k1];
             unsigned char* const ws = p->arena + arena_off + used;   // this product's workspace
@@ -1389,7 +1399,28 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
         if ((s = ensure_split_capacity(p, parts)) != SSMUL_OK) return s;
     }
     p->split_cursor = 0;
-    const size_t window = lanes > 1 ? (p->arena_bytes / lanes) & ~size_t(255) : p->arena_bytes;
+    // each lane's window of the arena: what its largest piece needs (at
+    // least one product of the plan's largest size), when those fit the
+    // arena together, so that no piece is cut into chunks; else equal shares
+    std::vector<size_t> win_off(lanes, 0), win_len(lanes, p->arena_bytes);
+    if (lanes > 1) {
+        const size_t eq = (p->arena_bytes / lanes) & ~size_t(255);
+        std::vector<size_t> need(lanes, (one + 255) & ~size_t(255));
+        for (size_t k = 0; k < pieces; ++k) {
+            size_t b = 0;
+            for (size_t i = piece_start(count, pieces, k); i < piece_start(count, pieces, k + 1); ++i)
+                b += product_arena_bytes(p, h_desc[i]);
+            b = (b + 255) & ~size_t(255);
+            need[k % lanes] = std::max(need[k % lanes], b);
+        }
+        size_t total = 0;
+        for (int l = 0; l < lanes; ++l) total += need[l];
+        const bool fit = total <= p->arena_bytes;
+        for (int l = 0; l < lanes; ++l) {
+            win_len[l] = fit ? need[l] : eq;
+            win_off[l] = fit ? (l ? win_off[l - 1] + win_len[l - 1] : 0) : size_t(l) * eq;
+        }
+    }
     while (p->hb_ev.size() < 2 * pieces) {
         cudaEvent_t e = nullptr;
         SS_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1440,7 +1471,7 @@ ssmul_status run_batched_host(ssmul_plan_t p, size_t count, const ssmul_desc* h_
             cudaStreamWaitEvent(p->cur, in, 0) != cudaSuccess)
             return drain(SSMUL_CUDA_ERROR);
         s = prepare_batch(p, i0, i1 - i0, rd.data() + i0, p->hb_a, p->hb_b, p->hb_z,
-                          p->hb_res + i0, lane * window, window);
+                          p->hb_res + i0, win_off[lane], win_len[lane]);
         if (s == SSMUL_OK) s = issue_batch(p, i0, i1 - i0);
         if (s != SSMUL_OK) return drain(s);
         if (cudaEventRecord(done, p->cur) != cudaSuccess) return drain(SSMUL_CUDA_ERROR);
