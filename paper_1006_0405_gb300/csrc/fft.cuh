@@ -249,9 +249,18 @@ __device__ __forceinline__ typename VTraits<V>::Tw scalar_tw(const TwTable& tw, 
     return SIGN > 0 ? w : tw_conj(w);
 }
 
-template <typename V, int SIGN, int BPT = 2, int R = 3>
+// The radix-R step's outputs go to buf (ToBuf, then a barrier), or, with an
+// epilogue functor out(line, k, y), straight from the registers of the
+// thread that computed them (element k of line `line`), with no barrier
+// after: the kernels whose next use of an element is per element (the
+// forward columns' four-step twiddle and store, the inverse columns'
+// isolation) skip a round trip through shared memory.
+struct ToBuf {};
+
+template <typename V, int SIGN, int BPT = 2, int R = 3, typename Out = ToBuf>
 __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw,
-                              bool skip_first = false) {
+                              bool skip_first = false, Out out = Out{}) {
+    constexpr bool TO_BUF = std::is_same<Out, ToBuf>::value;
     static_assert(R == 3 || R == 5, "odd factor 3 or 5");
     const int L = R << loga;
     const int Lq = L >> 2;                      // butterflies per line in a radix-4 step
@@ -299,24 +308,31 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
     }
     // radix-R step: n = R, s = 2^loga; each thread owns its R elements
     const int part = 1 << loga;
+    // output u of the butterfly at (line, q): element q + u part of the line
+    const auto put = [&](int line, int q, int u, const V& y) {
+        if constexpr (TO_BUF) buf[line * pitch + q + u * part] = y;
+        else out(line, q + u * part, y);
+    };
     if (R == 3) {
         const auto w3 = scalar_tw<V, SIGN>(tw, 0);        // i Im omega_3^SIGN
         for (int b = threadIdx.x; b < nl * part; b += blockDim.x) {
-            const int x = (b >> loga) * pitch + (b & (part - 1));
+            const int line = b >> loga, q = b & (part - 1);
+            const int x = line * pitch + q;
             const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];
             const V S = x1 + x2, D = x1 - x2;
             const V T = x0 - scale_pow2(S, 1);
             const V U = mul_imag(D, w3);
-            buf[x] = x0 + S;
-            buf[x + part] = T + U;
-            buf[x + 2 * part] = T - U;
+            put(line, q, 0, x0 + S);
+            put(line, q, 1, T + U);
+            put(line, q, 2, T - U);
         }
     } else {
         // omega_5^(SIGN k) = c_k + i s_k, k = 1, 2
         const auto c1 = scalar_tw<V, SIGN>(tw, 0), c2 = scalar_tw<V, SIGN>(tw, 1);
         const auto s1 = scalar_tw<V, SIGN>(tw, 2), s2 = scalar_tw<V, SIGN>(tw, 3);
         for (int b = threadIdx.x; b < nl * part; b += blockDim.x) {
-            const int x = (b >> loga) * pitch + (b & (part - 1));
+            const int line = b >> loga, q = b & (part - 1);
+            const int x = line * pitch + q;
             const V x0 = buf[x], x1 = buf[x + part], x2 = buf[x + 2 * part];
             const V x3 = buf[x + 3 * part], x4 = buf[x + 4 * part];
             const V S1 = x1 + x4, D1 = x1 - x4, S2 = x2 + x3, D2 = x2 - x3;
@@ -324,14 +340,14 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
             const V B = (x0 + mul_real(S1, c2)) + mul_real(S2, c1);
             const V U = mul_imag(D1, s1) + mul_imag(D2, s2);
             const V W = mul_imag(D1, s2) - mul_imag(D2, s1);
-            buf[x] = (x0 + S1) + S2;
-            buf[x + part] = A + U;
-            buf[x + 4 * part] = A - U;
-            buf[x + 2 * part] = B + W;
-            buf[x + 3 * part] = B - W;
+            put(line, q, 0, (x0 + S1) + S2);
+            put(line, q, 1, A + U);
+            put(line, q, 4, A - U);
+            put(line, q, 2, B + W);
+            put(line, q, 3, B - W);
         }
     }
-    __syncthreads();
+    if constexpr (TO_BUF) __syncthreads();
 }
 
 // ---- the first step of a forward transform of digits ---------------------------------

@@ -847,6 +847,14 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
         const uint32_t j = (uint32_t(idx >> logC) << logN2) + j2_0 + (idx & (C - 1));
         return make_int2(j < d.na ? int(d.a[j]) - bias : 0, j < d.nb ? int(d.b[j]) - bias : 0);
     };
+    const int logN = logN1 + logN2;
+    // element k1 of column c: times the four-step twiddle omega_N^{j2 k1}, to Z
+    const auto to_z = [&](int c, int k1, V v) {
+        const uint32_t j2 = j2_0 + c;
+        const uint32_t e = j2 * uint32_t(k1);             // < N
+        if (e) v = mul_tw(v, get_twiddle<V, +1, R>(tw, e << (tw.log_n - logN)));
+        Z[(size_t(k1) << logN2) + j2] = v;
+    };
     if (R > 1 || logN1 >= 2) {
         // the digit pairs as integers, column c at c (N1 + 1) (the odd pitch
         // spreads the staging stores over the banks; C (N1 + 1) 8 bytes fit
@@ -857,8 +865,15 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
                              [&](int idx, int2 v) { si[(idx & (C - 1)) * ip + (idx >> logC)] = v; });
         __syncthreads();
         first_step_exact<V, BPT, R, (R > 1)>(si, ip, sm, logN1, C, N1, tw);
-        if constexpr (R == 1) block_fft<V, +1, BPT>(sm, logN1, C, N1, tw, true);
-        else block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true);
+        if constexpr (R == 1) {
+            block_fft<V, +1, BPT>(sm, logN1, C, N1, tw, true);
+        } else if constexpr (z_from_registers<V>()) {
+            // the last (radix-R) step hands its outputs to to_z from registers
+            block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true, to_z);
+            return;
+        } else {
+            block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true);
+        }
     } else {
         stage<4 * BPT, int2>(C * N1, digits, [&](int idx, int2 v) {
             sm[(idx & (C - 1)) * N1 + (idx >> logC)] = make_point<V>(v.x, v.y);
@@ -866,14 +881,9 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
         __syncthreads();
         block_fft<V, +1, BPT>(sm, logN1, C, N1, tw);
     }
-    const int logN = logN1 + logN2;
     for (int idx = threadIdx.x; idx < C * N1; idx += blockDim.x) {
         const int c = idx & (C - 1), k1 = idx >> logC;
-        const uint32_t j2 = j2_0 + c;
-        V v = sm[c * N1 + k1];
-        const uint32_t e = j2 * uint32_t(k1);             // < N
-        if (e) v = mul_tw(v, get_twiddle<V, +1, R>(tw, e << (tw.log_n - logN)));
-        Z[(size_t(k1) << logN2) + j2] = v;
+        to_z(c, k1, sm[c * N1 + k1]);
     }
 }
 

@@ -65,6 +65,18 @@ template <> struct VTraits<DDisc> {
     static constexpr int reg_rows = 64, reg_cols = 64;
 };
 
+// the forward columns of lengths R 2^k apply the four-step twiddle and
+// store Z straight from the radix-R step's registers (block_fft_odd's
+// epilogue) for the binary64 rectangles, whose 32-byte elements fill a
+// sector per lane; the other types keep the pass through shared memory and
+// its coalesced stores (pair discs 10% and discs 0.5% slower without it).
+// The inverse columns isolate after that pass for every type: isolating
+// from the registers made the binary64 kernel 9% slower.
+template <typename V>
+__host__ __device__ constexpr bool z_from_registers() {
+    return std::is_same<V, CI<double>>::value;
+}
+
 // register cap of the column kernels of family R
 template <typename V, int R>
 __host__ __device__ constexpr int cols_regs() {
