@@ -833,6 +833,18 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, const int* list) {
 
 // R: 1, 3 or 5 for N = R 2^k; N1 = R 2^logN1 (logN1 even when R > 1),
 // N2 = 2^logN2, and tw is the twiddle table of family R.
+// One element of Z to global memory.  A binary64 rectangle (32 bytes,
+// 32-byte aligned: Z starts on a 256-byte boundary) goes out as one 256-bit
+// store, so that a lane's element is one full sector even where the lanes
+// of a warp write far apart.
+template <typename V>
+__device__ __forceinline__ void store_z(V* p, const V& v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_z<CI<double>>(CI<double>* p, const CI<double>& v) {
+    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};"
+                 :: "l"(p), "d"(v.rl), "d"(v.rh), "d"(v.il), "d"(v.ih) : "memory");
+}
+
 template <typename Tag, int BPT, int R>
 __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw, int logN1,
                                              int logN2, int logC) {
@@ -853,7 +865,7 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
         const uint32_t j2 = j2_0 + c;
         const uint32_t e = j2 * uint32_t(k1);             // < N
         if (e) v = mul_tw(v, get_twiddle<V, +1, R>(tw, e << (tw.log_n - logN)));
-        Z[(size_t(k1) << logN2) + j2] = v;
+        store_z(Z + ((size_t(k1) << logN2) + j2), v);
     };
     if (R > 1 || logN1 >= 2) {
         // the digit pairs as integers, column c at c (N1 + 1) (the odd pitch
