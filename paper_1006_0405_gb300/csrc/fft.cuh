@@ -89,23 +89,40 @@ __device__ void radix8_last(SBuf<V> buf, int logL, int nl, int pitch, const TwTa
 template <typename V>
 __host__ __device__ constexpr bool last_radix8() { return std::is_same<V, DDisc>::value; }
 
+// The first step's inputs come from buf (FromBuf), or, with a loader
+// in(line, k) (element k of line `line`, from global memory), straight into
+// the registers of the thread that combines them, with no staging pass; the
+// last step's outputs go to buf (ToBuf, then a barrier), or to an epilogue
+// out(line, k, y) from registers, with no barrier after.
+struct FromBuf {};
+struct ToBuf {};
+
 // R: the family of the twiddle table tw (the line length is 2^logL either way).
 // skip_first: the first radix-4 step (n = L) is done already
 // (first_step_exact), so the steps start at n = L / 4, s = 4.  LAST8: an
-// odd-length line of a last_radix8 type ends with radix8_last.
-template <typename V, int SIGN, int BPT = 2, int R = 1, bool LAST8 = true>
+// odd-length line of a last_radix8 type ends with radix8_last.  A loader
+// (In) needs a first radix-4 step (logL >= 2, not skip_first); an epilogue
+// (Out) a type without the radix-8 last step.
+template <typename V, int SIGN, int BPT = 2, int R = 1, bool LAST8 = true,
+          typename In = FromBuf, typename Out = ToBuf>
 __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTable& tw,
-                          bool skip_first = false) {
+                          bool skip_first = false, In in = In{}, Out out = Out{}) {
+    constexpr bool FROM_BUF = std::is_same<In, FromBuf>::value;
+    constexpr bool TO_BUF = std::is_same<Out, ToBuf>::value;
+    static_assert(TO_BUF || !(LAST8 && last_radix8<V>()), "no epilogue after radix8_last");
     const int L = 1 << logL;
     const int quarter_log = logL - 2;
     int logn = skip_first ? logL - 2 : logL, logs = skip_first ? 2 : 0;
     const int stop = (LAST8 && last_radix8<V>() && (logL & 1) && logL >= 3) ? 3 : 1;
+    bool first = !skip_first;
     while (logn > stop) {
         const int m = 1 << (logn - 2);          // n / 4
         const int s = 1 << logs;
         const int nbf = nl << (logL - 2);       // butterflies in this step
+        const bool load = !FROM_BUF && first;   // inputs from the loader
+        const bool emit = !TO_BUF && logn == 2; // the transform's last step: to the epilogue
         V v[BPT][4];
-        int base[BPT], pp[BPT];
+        int base[BPT], pp[BPT], ln[BPT], kq[BPT];
         bool act[BPT];
 #pragma unroll
         for (int h = 0; h < BPT; ++h) {
@@ -116,8 +133,18 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
                 const int bb = b & ((L >> 2) - 1);
                 const int p = bb >> logs, q = bb & (s - 1);
                 const int x = line * pitch + q;
+                if constexpr (!FROM_BUF) {
+                    if (load) {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
+                        for (int t = 0; t < 4; ++t) v[h][t] = in(line, q + s * (p + t * m));
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
+                }
                 bfly4<V, SIGN>(v[h][0], v[h][1], v[h][2], v[h][3]);
                 if (p != 0) {
                     // omega_n^{p u}
@@ -127,9 +154,25 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
                 }
                 base[h] = line * pitch + q + s * 4 * p;
                 pp[h] = s;
+                ln[h] = line;
+                kq[h] = q + s * 4 * p;
             }
         }
-        __syncthreads();
+        if constexpr (!TO_BUF) {
+            if (emit) {
+                // the last step (n = 4, p = 0): element q + u s of each line
+#pragma unroll
+                for (int h = 0; h < BPT; ++h) {
+                    if (act[h]) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) out(ln[h], kq[h] + u * pp[h], v[h][u]);
+                    }
+                }
+                return;
+            }
+        }
+        // the writes wait for every read of this step (none when loaded)
+        if (!load) __syncthreads();
 #pragma unroll
         for (int h = 0; h < BPT; ++h) {
             if (act[h]) {
@@ -140,6 +183,7 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
         __syncthreads();
         logn -= 2;
         logs += 2;
+        first = false;
     }
     if (logn == 3 && stop == 3) {
         radix8_last<V, SIGN, R>(buf, logL, nl, pitch, tw);
@@ -151,10 +195,15 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
             const int line = b / half, q = b - line * half;
             const int x = line * pitch + q;
             const V a = buf[x], c = buf[x + half];
-            buf[x] = a + c;
-            buf[x + half] = a - c;
+            if constexpr (TO_BUF) {
+                buf[x] = a + c;
+                buf[x + half] = a - c;
+            } else {
+                out(line, q, a + c);
+                out(line, q + half, a - c);
+            }
         }
-        __syncthreads();
+        if constexpr (TO_BUF) __syncthreads();
     }
 }
 
@@ -255,7 +304,6 @@ __device__ __forceinline__ typename VTraits<V>::Tw scalar_tw(const TwTable& tw, 
 // after: the kernels whose next use of an element is per element (the
 // forward columns' four-step twiddle and store, the inverse columns'
 // isolation) skip a round trip through shared memory.
-struct ToBuf {};
 
 template <typename V, int SIGN, int BPT = 2, int R = 3, typename Out = ToBuf>
 __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw,

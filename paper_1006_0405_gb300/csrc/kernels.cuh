@@ -833,16 +833,25 @@ __global__ void k_small(const ProdDesc* descs, TwTable tw, const int* list) {
 
 // R: 1, 3 or 5 for N = R 2^k; N1 = R 2^logN1 (logN1 even when R > 1),
 // N2 = 2^logN2, and tw is the twiddle table of family R.
-// One element of Z to global memory.  A binary64 rectangle (32 bytes,
-// 32-byte aligned: Z starts on a 256-byte boundary) goes out as one 256-bit
-// store, so that a lane's element is one full sector even where the lanes
-// of a warp write far apart.
+// One element of Z or W to or from global memory.  A binary64 rectangle
+// (32 bytes, 32-byte aligned: Z and W start on 256-byte boundaries) moves
+// as one 256-bit access, so that a lane's element is one full sector even
+// where the lanes of a warp touch addresses far apart.
 template <typename V>
 __device__ __forceinline__ void store_z(V* p, const V& v) { *p = v; }
 template <>
 __device__ __forceinline__ void store_z<CI<double>>(CI<double>* p, const CI<double>& v) {
     asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};"
                  :: "l"(p), "d"(v.rl), "d"(v.rh), "d"(v.il), "d"(v.ih) : "memory");
+}
+template <typename V>
+__device__ __forceinline__ V load_z(const V* p) { return *p; }
+template <>
+__device__ __forceinline__ CI<double> load_z<CI<double>>(const CI<double>* p) {
+    CI<double> v;
+    asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
+                 : "=d"(v.rl), "=d"(v.rh), "=d"(v.il), "=d"(v.ih) : "l"(p));
+    return v;
 }
 
 template <typename Tag, int BPT, int R>
@@ -879,7 +888,7 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
         first_step_exact<V, BPT, R, (R > 1)>(si, ip, sm, logN1, C, N1, tw);
         if constexpr (R == 1) {
             block_fft<V, +1, BPT>(sm, logN1, C, N1, tw, true);
-        } else if constexpr (z_from_registers<V>()) {
+        } else if constexpr (io_from_registers<V>()) {
             // the last (radix-R) step hands its outputs to to_z from registers
             block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true, to_z);
             return;
@@ -923,25 +932,41 @@ __device__ __forceinline__ void rows_one(const ProdDesc d, const TwTable& tw, in
     const int nl = (k1 == k1b) ? 1 : 2;
     const V* Z = reinterpret_cast<const V*>(d.Z);
     V* W = reinterpret_cast<V*>(d.W);
-    stage<4 * BPT, V>(
-        nl * N2,
-        [&](int t) { return Z[(size_t((t >> logN2) ? k1b : k1) << logN2) + (t & (N2 - 1))]; },
-        [&](int t, const V& v) { sm[t] = v; });
-    __syncthreads();
-    block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw);
+    const int logM = logN1 + logN2 - 1;
+    // element j2 of line l: times the four-step twiddle omega_M^{-row j2}, to W
+    const auto to_w = [&](int l, int j2, V v) {
+        const int row = l ? k1b : k1;
+        const uint32_t e = uint32_t(row) * uint32_t(j2);        // < N/2
+        if (e) v = mul_tw(v, get_twiddle<V, -1, R>(tw, e << (tw.log_n - logM)));
+        store_z(W + ((size_t(row) << (logN2 - 1)) + j2), v);
+    };
+    if constexpr (io_from_registers<V>()) {
+        // the forward transform's first step reads Z itself
+        const auto from_z = [&](int l, int k) {
+            return load_z(Z + ((size_t(l ? k1b : k1) << logN2) + k));
+        };
+        block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw, false, from_z);
+    } else {
+        stage<4 * BPT, V>(
+            nl * N2,
+            [&](int t) { return Z[(size_t((t >> logN2) ? k1b : k1) << logN2) + (t & (N2 - 1))]; },
+            [&](int t, const V& v) { sm[t] = v; });
+        __syncthreads();
+        block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw);
+    }
     pair_products(sm, nl, k1, logN2);
     __syncthreads();
     pack_half<V, R>(sm, nl, k1, k1b, logN1, logN2, tw);
     __syncthreads();
-    block_fft<V, -1, BPT, R>(sm, logN2 - 1, nl, N2, tw);
-    const int logM = logN1 + logN2 - 1;
-    for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
-        const int l = t >> (logN2 - 1), j2 = t & (M2 - 1);
-        V v = sm[l * N2 + j2];
-        const int row = l ? k1b : k1;
-        const uint32_t e = uint32_t(row) * uint32_t(j2);        // < N/2
-        if (e) v = mul_tw(v, get_twiddle<V, -1, R>(tw, e << (tw.log_n - logM)));
-        W[(size_t(row) << (logN2 - 1)) + j2] = v;
+    if constexpr (io_from_registers<V>()) {
+        // the inverse transform's last step hands its outputs to to_w
+        block_fft<V, -1, BPT, R>(sm, logN2 - 1, nl, N2, tw, false, FromBuf{}, to_w);
+    } else {
+        block_fft<V, -1, BPT, R>(sm, logN2 - 1, nl, N2, tw);
+        for (int t = threadIdx.x; t < nl * M2; t += blockDim.x) {
+            const int l = t >> (logN2 - 1), j2 = t & (M2 - 1);
+            to_w(l, j2, sm[l * N2 + j2]);
+        }
     }
 }
 

@@ -65,15 +65,18 @@ template <> struct VTraits<DDisc> {
     static constexpr int reg_rows = 64, reg_cols = 64;
 };
 
-// the forward columns of lengths R 2^k apply the four-step twiddle and
-// store Z straight from the radix-R step's registers (block_fft_odd's
-// epilogue) for the binary64 rectangles, whose 32-byte elements fill a
-// sector per lane; the other types keep the pass through shared memory and
-// its coalesced stores (pair discs 10% and discs 0.5% slower without it).
-// The inverse columns isolate after that pass for every type: isolating
-// from the registers made the binary64 kernel 9% slower.
+// The binary64 rectangles move Z and W between global memory and the
+// registers of the transform steps that use them, with no pass through
+// shared memory: the forward columns of lengths R 2^k twiddle and store Z
+// from the radix-R step (block_fft_odd's epilogue), k_rows loads its first
+// radix-4 step from Z and twiddles and stores W from its last step
+// (block_fft's loader and epilogue).  Their 32-byte elements fill a sector
+// per lane; the other types keep the passes (pair discs were 10% and discs
+// 0.5% slower with the forward columns' epilogue).  The inverse columns
+// isolate after the pass for every type: isolating from the registers made
+// the binary64 kernel 9% slower.
 template <typename V>
-__host__ __device__ constexpr bool z_from_registers() {
+__host__ __device__ constexpr bool io_from_registers() {
     return std::is_same<V, CI<double>>::value;
 }
 
