@@ -298,26 +298,29 @@ __device__ __forceinline__ typename VTraits<V>::Tw scalar_tw(const TwTable& tw, 
     return SIGN > 0 ? w : tw_conj(w);
 }
 
-// The radix-R step's outputs go to buf (ToBuf, then a barrier), or, with an
-// epilogue functor out(line, k, y), straight from the registers of the
-// thread that computed them (element k of line `line`), with no barrier
+// As in block_fft, the first radix-4 step may take its inputs from a
+// loader in(line, k) instead of buf (not with skip_first; loga >= 2), and
+// the radix-R step may hand its outputs to an epilogue out(line, k, y)
+// from the registers of the thread that computed them, with no barrier
 // after: the kernels whose next use of an element is per element (the
-// forward columns' four-step twiddle and store, the inverse columns'
-// isolation) skip a round trip through shared memory.
-
-template <typename V, int SIGN, int BPT = 2, int R = 3, typename Out = ToBuf>
+// forward columns' four-step twiddle and store) skip a round trip through
+// shared memory.
+template <typename V, int SIGN, int BPT = 2, int R = 3, typename In = FromBuf, typename Out = ToBuf>
 __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const TwTable& tw,
-                              bool skip_first = false, Out out = Out{}) {
+                              bool skip_first = false, In in = In{}, Out out = Out{}) {
+    constexpr bool FROM_BUF = std::is_same<In, FromBuf>::value;
     constexpr bool TO_BUF = std::is_same<Out, ToBuf>::value;
     static_assert(R == 3 || R == 5, "odd factor 3 or 5");
     const int L = R << loga;
     const int Lq = L >> 2;                      // butterflies per line in a radix-4 step
     int logn2 = skip_first ? loga - 2 : loga;   // n = R 2^logn2, s = 2^logs
     int logs = skip_first ? 2 : 0;
+    bool first = !skip_first;
     while (logn2 >= 2) {
         const int m = R << (logn2 - 2);         // n / 4
         const int s = 1 << logs;
         const int nbf = nl * Lq;
+        const bool load = !FROM_BUF && first;   // inputs from the loader
         V v[BPT][4];
         int base[BPT], pp[BPT];
         bool act[BPT];
@@ -330,8 +333,18 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
                 const int bb = b - line * Lq;
                 const int p = bb >> logs, q = bb & (s - 1);
                 const int x = line * pitch + q;
+                if constexpr (!FROM_BUF) {
+                    if (load) {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
+                        for (int t = 0; t < 4; ++t) v[h][t] = in(line, q + s * (p + t * m));
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) v[h][t] = buf[x + s * (p + t * m)];
+                }
                 bfly4<V, SIGN>(v[h][0], v[h][1], v[h][2], v[h][3]);
                 if (p != 0) {
                     v[h][1] = mul_tw(v[h][1], step_twiddle_r<V, SIGN, R>(tw, logn2, p, 1));
@@ -342,7 +355,8 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
                 pp[h] = s;
             }
         }
-        __syncthreads();
+        // the writes wait for every read of this step (none when loaded)
+        if (!load) __syncthreads();
 #pragma unroll
         for (int h = 0; h < BPT; ++h) {
             if (act[h]) {
@@ -353,6 +367,7 @@ __device__ void block_fft_odd(SBuf<V> buf, int loga, int nl, int pitch, const Tw
         __syncthreads();
         logn2 -= 2;
         logs += 2;
+        first = false;
     }
     // radix-R step: n = R, s = 2^loga; each thread owns its R elements
     const int part = 1 << loga;

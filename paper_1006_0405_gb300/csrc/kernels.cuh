@@ -890,7 +890,7 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
             block_fft<V, +1, BPT>(sm, logN1, C, N1, tw, true);
         } else if constexpr (io_from_registers<V>()) {
             // the last (radix-R) step hands its outputs to to_z from registers
-            block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true, to_z);
+            block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true, FromBuf{}, to_z);
             return;
         } else {
             block_fft_odd<V, +1, BPT, R>(sm, logN1, C, N1, tw, true);
@@ -992,13 +992,21 @@ __device__ __forceinline__ void inv_cols_one(const ProdDesc d, const TwTable& tw
     const int logM2 = logN2 - 1;
     const uint32_t j2_0 = blockIdx.x << logC;
     const V* W = reinterpret_cast<const V*>(d.W);
-    stage<4 * BPT, V>(
-        C * N1,
-        [&](int idx) { return W[(size_t(idx >> logC) << logM2) + j2_0 + (idx & (C - 1))]; },
-        [&](int idx, const V& v) { sm[(idx & (C - 1)) * N1 + (idx >> logC)] = v; });
-    __syncthreads();
-    if constexpr (R == 1) block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
-    else block_fft_odd<V, -1, BPT, R>(sm, logN1, C, N1, tw);
+    if constexpr (R > 1 && io_from_registers<V>()) {
+        // the first radix-4 step reads element j1 of column c from W itself
+        const auto from_w = [&](int c, int j1) {
+            return load_z(W + ((size_t(j1) << logM2) + j2_0 + c));
+        };
+        block_fft_odd<V, -1, BPT, R>(sm, logN1, C, N1, tw, false, from_w);
+    } else {
+        stage<4 * BPT, V>(
+            C * N1,
+            [&](int idx) { return W[(size_t(idx >> logC) << logM2) + j2_0 + (idx & (C - 1))]; },
+            [&](int idx, const V& v) { sm[(idx & (C - 1)) * N1 + (idx >> logC)] = v; });
+        __syncthreads();
+        if constexpr (R == 1) block_fft<V, -1, BPT>(sm, logN1, C, N1, tw);
+        else block_fft_odd<V, -1, BPT, R>(sm, logN1, C, N1, tw);
+    }
     const int logN = logN1 + logN2;
     IsoAcc acc;
     for (int idx = threadIdx.x; idx < C * N1; idx += blockDim.x) {
