@@ -276,6 +276,40 @@ __device__ void pack_half(SBuf<V> sm, int nl, int row0, int row1, int logN1, int
     }
 }
 
+// pair_products and pack_half of a row pair (two lines, rows row0 != 0 and
+// row1 = N1 - row0) in one pass.  For k < N2/2 the elements line 0 at k and
+// k + M2 and line 1 at M2 - 1 - k and N2 - 1 - k hold both partners of two
+// pair products (k with N2 - 1 - k, k + M2 with M2 - 1 - k) and both inputs
+// of the packed outputs line 0 at k and line 1 at M2 - 1 - k, so one thread
+// computes them with the same operations as the two passes and writes only
+// elements it read: no barrier between the steps.
+template <typename V, int R = 1>
+__device__ void pair_pack2(SBuf<V> sm, int row0, int row1, int logN1, int logN2,
+                           const TwTable& tw) {
+    const int N2 = 1 << logN2, M2 = N2 >> 1;
+    const uint32_t N1 = uint32_t(R) << logN1;
+    const int logN = logN1 + logN2;
+    const auto prod = [](const V& zk, const V& zp) {       // 4 C_k from Z_k and its partner
+        const V czp = conj(zp);
+        const V a2 = zk + czp;                     // 2 A_k
+        const V b2 = mul_negi_flip(zk - czp);      // 2 B_k
+        return mul_ci(a2, b2);                     // 4 C_k
+    };
+    const auto pack = [&](const V& c0, const V& c1, int row, int k2) {
+        const uint32_t k = uint32_t(row) + uint32_t(k2) * N1;
+        const auto w = get_twiddle<V, -1, R>(tw, k << (tw.log_n - logN));
+        return (c0 + c1) + mul_i(mul_tw(c0 - c1, w));
+    };
+    for (int k2 = threadIdx.x; k2 < M2; k2 += blockDim.x) {
+        const int kb = M2 - 1 - k2;
+        const V c_lo = prod(sm[k2], sm[N2 + (N2 - 1 - k2)]);        // line 0 at k2
+        const V c_hi = prod(sm[k2 + M2], sm[N2 + kb]);              // line 0 at k2 + M2
+        // line 1 at kb and kb + M2 = N2 - 1 - k2: the conjugate-flipped partners
+        sm[k2] = pack(c_lo, c_hi, row0, k2);
+        sm[N2 + kb] = pack(conj_flip(c_hi), conj_flip(c_lo), row1, kb);
+    }
+}
+
 // ---- isolation (Section 1) --------------------------------------------------
 
 struct IsoAcc {
@@ -954,9 +988,13 @@ __device__ __forceinline__ void rows_one(const ProdDesc d, const TwTable& tw, in
         __syncthreads();
         block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw);
     }
-    pair_products(sm, nl, k1, logN2);
-    __syncthreads();
-    pack_half<V, R>(sm, nl, k1, k1b, logN1, logN2, tw);
+    if (nl == 2) {
+        pair_pack2<V, R>(sm, k1, k1b, logN1, logN2, tw);
+    } else {
+        pair_products(sm, nl, k1, logN2);
+        __syncthreads();
+        pack_half<V, R>(sm, nl, k1, k1b, logN1, logN2, tw);
+    }
     __syncthreads();
     if constexpr (io_from_registers<V>()) {
         // the inverse transform's last step hands its outputs to to_w
