@@ -102,11 +102,14 @@ struct ToBuf {};
 // (first_step_exact), so the steps start at n = L / 4, s = 4.  LAST8: an
 // odd-length line of a last_radix8 type ends with radix8_last.  A loader
 // (In) needs a first radix-4 step (logL >= 2, not skip_first); an epilogue
-// (Out) a type without the radix-8 last step.
+// (Out) a type without the radix-8 last step.  leave_radix2: an odd-length
+// transform stops before its final radix-2 step (n = 2, s = L/2, no
+// twiddle), which the caller then does itself, fused with what follows.
 template <typename V, int SIGN, int BPT = 2, int R = 1, bool LAST8 = true,
           typename In = FromBuf, typename Out = ToBuf>
 __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTable& tw,
-                          bool skip_first = false, In in = In{}, Out out = Out{}) {
+                          bool skip_first = false, In in = In{}, Out out = Out{},
+                          bool leave_radix2 = false) {
     constexpr bool FROM_BUF = std::is_same<In, FromBuf>::value;
     constexpr bool TO_BUF = std::is_same<Out, ToBuf>::value;
     static_assert(TO_BUF || !(LAST8 && last_radix8<V>()), "no epilogue after radix8_last");
@@ -187,7 +190,7 @@ __device__ void block_fft(SBuf<V> buf, int logL, int nl, int pitch, const TwTabl
     }
     if (logn == 3 && stop == 3) {
         radix8_last<V, SIGN, R>(buf, logL, nl, pitch, tw);
-    } else if (logn == 1) {
+    } else if (logn == 1 && !leave_radix2) {
         // final radix-2 step: n = 2, s = L/2, no twiddle
         const int half = L >> 1;
         const int nbf = nl * half;

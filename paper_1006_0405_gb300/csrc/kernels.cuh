@@ -282,8 +282,11 @@ __device__ void pack_half(SBuf<V> sm, int nl, int row0, int row1, int logN1, int
 // pair products (k with N2 - 1 - k, k + M2 with M2 - 1 - k) and both inputs
 // of the packed outputs line 0 at k and line 1 at M2 - 1 - k, so one thread
 // computes them with the same operations as the two passes and writes only
-// elements it read: no barrier between the steps.
-template <typename V, int R = 1>
+// elements it read: no barrier between the steps.  R2: the forward
+// transform left its final radix-2 step (odd log2 N2), whose butterflies for
+// line 0 at k and line 1 at M2 - 1 - k produce exactly those four elements;
+// the thread does them first, from the step's inputs at the same places.
+template <typename V, int R = 1, bool R2 = false>
 __device__ void pair_pack2(SBuf<V> sm, int row0, int row1, int logN1, int logN2,
                            const TwTable& tw) {
     const int N2 = 1 << logN2, M2 = N2 >> 1;
@@ -302,8 +305,21 @@ __device__ void pair_pack2(SBuf<V> sm, int row0, int row1, int logN1, int logN2,
     };
     for (int k2 = threadIdx.x; k2 < M2; k2 += blockDim.x) {
         const int kb = M2 - 1 - k2;
-        const V c_lo = prod(sm[k2], sm[N2 + (N2 - 1 - k2)]);        // line 0 at k2
-        const V c_hi = prod(sm[k2 + M2], sm[N2 + kb]);              // line 0 at k2 + M2
+        V z0lo, z0hi, z1lo, z1hi;       // line 0 at k2, k2 + M2; line 1 at kb, kb + M2
+        if constexpr (R2) {
+            const V a0 = sm[k2], b0 = sm[k2 + M2], a1 = sm[N2 + kb], b1 = sm[N2 + kb + M2];
+            z0lo = a0 + b0;
+            z0hi = a0 - b0;
+            z1lo = a1 + b1;
+            z1hi = a1 - b1;
+        } else {
+            z0lo = sm[k2];
+            z0hi = sm[k2 + M2];
+            z1lo = sm[N2 + kb];
+            z1hi = sm[N2 + kb + M2];
+        }
+        const V c_lo = prod(z0lo, z1hi);        // line 0 at k2 (partner N2 - 1 - k2)
+        const V c_hi = prod(z0hi, z1lo);        // line 0 at k2 + M2 (partner kb)
         // line 1 at kb and kb + M2 = N2 - 1 - k2: the conjugate-flipped partners
         sm[k2] = pack(c_lo, c_hi, row0, k2);
         sm[N2 + kb] = pack(conj_flip(c_hi), conj_flip(c_lo), row1, kb);
@@ -974,21 +990,26 @@ __device__ __forceinline__ void rows_one(const ProdDesc d, const TwTable& tw, in
         if (e) v = mul_tw(v, get_twiddle<V, -1, R>(tw, e << (tw.log_n - logM)));
         store_z(W + ((size_t(row) << (logN2 - 1)) + j2), v);
     };
+    // a row pair with an odd log2 N2 leaves the forward transform's final
+    // radix-2 step to pair_pack2
+    const bool r2 = nl == 2 && (logN2 & 1) && !(last_radix8<V>() && logN2 >= 3);
     if constexpr (io_from_registers<V>()) {
         // the forward transform's first step reads Z itself
         const auto from_z = [&](int l, int k) {
             return load_z(Z + ((size_t(l ? k1b : k1) << logN2) + k));
         };
-        block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw, false, from_z);
+        block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw, false, from_z, ToBuf{}, r2);
     } else {
         stage<4 * BPT, V>(
             nl * N2,
             [&](int t) { return Z[(size_t((t >> logN2) ? k1b : k1) << logN2) + (t & (N2 - 1))]; },
             [&](int t, const V& v) { sm[t] = v; });
         __syncthreads();
-        block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw);
+        block_fft<V, +1, BPT, R>(sm, logN2, nl, N2, tw, false, FromBuf{}, ToBuf{}, r2);
     }
-    if (nl == 2) {
+    if (r2) {
+        pair_pack2<V, R, true>(sm, k1, k1b, logN1, logN2, tw);
+    } else if (nl == 2) {
         pair_pack2<V, R>(sm, k1, k1b, logN1, logN2, tw);
     } else {
         pair_products(sm, nl, k1, logN2);
