@@ -84,6 +84,9 @@ def parse():
                          "--no-reports); c1 / sweep / ladder / uneven / split: one report line "
                          "(one 4096-digit product, the size sweep, the precision ladder, the "
                          "uneven batch, the products past the isolation limit)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the candidate four-step geometries of the plan's lengths first "
+                         "(SSMUL_OPT_AUTOTUNE), outside every timed region")
     ap.add_argument("--no-reports", action="store_true",
                     help="headline line only (no c1 / c3 / c4 / c5 reports)")
     return ap.parse_args()
@@ -504,6 +507,8 @@ def run_ours(args):
         abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_BALANCED, 1)
     if args.lengths != 3:
         abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_LENGTHS, args.lengths)
+    if args.autotune:
+        abi.ssmul_plan_set_option(plan, abi.SSMUL_OPT_AUTOTUNE, 1)
     descs = (abi.ssmul_desc * B)()
     for i in range(B):
         descs[i] = abi.ssmul_desc(int(a_off[i]), int(b_off[i]), int(z_off[i]), n, n)
@@ -744,7 +749,9 @@ def run_ours(args):
                                    f"all-0xFF) per GPU",
                        "batch_per_gpu": B, "digits": n, "precision": args.precision,
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "geometry": {"log_n1": geo[0], "log_n2": geo[1], "log_cta": geo[2],
+                                    "autotuned": bool(args.autotune)}},
             "verified": f"{verified}/{args.steps * B} per rank 0",
             "digits_matched": f"{matched}/{args.steps * B} per rank 0",
             "statuses": statuses,
