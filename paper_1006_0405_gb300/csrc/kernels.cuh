@@ -937,6 +937,14 @@ __device__ __forceinline__ void fwd_cols_one(const ProdDesc d, const TwTable& tw
         __syncthreads();
         first_step_exact<V, BPT, R, (R > 1)>(si, ip, sm, logN1, C, N1, tw);
         if constexpr (R == 1) {
+            if constexpr (io_from_registers<V>()) {
+                if (logN1 >= 3) {
+                    // the last radix-4 or radix-2 step hands its outputs to
+                    // to_z (N1 >= 8: a step remains after the exact first one)
+                    block_fft<V, +1, BPT>(sm, logN1, C, N1, tw, true, FromBuf{}, to_z);
+                    return;
+                }
+            }
             block_fft<V, +1, BPT>(sm, logN1, C, N1, tw, true);
         } else if constexpr (io_from_registers<V>()) {
             // the last (radix-R) step hands its outputs to to_z from registers
@@ -1051,13 +1059,20 @@ __device__ __forceinline__ void inv_cols_one(const ProdDesc d, const TwTable& tw
     const int logM2 = logN2 - 1;
     const uint32_t j2_0 = blockIdx.x << logC;
     const V* W = reinterpret_cast<const V*>(d.W);
-    if constexpr (R > 1 && io_from_registers<V>()) {
+    bool staged = true;
+    if constexpr (io_from_registers<V>()) {
         // the first radix-4 step reads element j1 of column c from W itself
+        // (columns of length N1 >= 4 for the lengths 2^k)
         const auto from_w = [&](int c, int j1) {
             return load_z(W + ((size_t(j1) << logM2) + j2_0 + c));
         };
-        block_fft_odd<V, -1, BPT, R>(sm, logN1, C, N1, tw, false, from_w);
-    } else {
+        if (R > 1 || logN1 >= 2) {
+            if constexpr (R == 1) block_fft<V, -1, BPT>(sm, logN1, C, N1, tw, false, from_w);
+            else block_fft_odd<V, -1, BPT, R>(sm, logN1, C, N1, tw, false, from_w);
+            staged = false;
+        }
+    }
+    if (staged) {
         stage<4 * BPT, V>(
             C * N1,
             [&](int idx) { return W[(size_t(idx >> logC) << logM2) + j2_0 + (idx & (C - 1))]; },
