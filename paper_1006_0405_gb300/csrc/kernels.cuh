@@ -1001,7 +1001,7 @@ __device__ __forceinline__ void rows_one(const ProdDesc d, const TwTable& tw, in
     // a row pair with an odd log2 N2 leaves the forward transform's final
     // radix-2 step to pair_pack2
     const bool r2 = nl == 2 && (logN2 & 1) && !(last_radix8<V>() && logN2 >= 3);
-    if constexpr (io_from_registers<V>()) {
+    if constexpr (rows_load_from_registers<V>()) {
         // the forward transform's first step reads Z itself
         const auto from_z = [&](int l, int k) {
             return load_z(Z + ((size_t(l ? k1b : k1) << logN2) + k));
@@ -1025,7 +1025,7 @@ __device__ __forceinline__ void rows_one(const ProdDesc d, const TwTable& tw, in
         pack_half<V, R>(sm, nl, k1, k1b, logN1, logN2, tw);
     }
     __syncthreads();
-    if constexpr (io_from_registers<V>()) {
+    if constexpr (rows_store_from_registers<V>()) {
         // the inverse transform's last step hands its outputs to to_w
         block_fft<V, -1, BPT, R>(sm, logN2 - 1, nl, N2, tw, false, FromBuf{}, to_w);
     } else {

@@ -80,6 +80,19 @@ __host__ __device__ constexpr bool io_from_registers() {
     return std::is_same<V, CI<double>>::value;
 }
 
+// k_rows' register-fed first step (every type) and last step (every type
+// whose inverse rows cannot end with the radix-8 step): there the lanes of a
+// warp read and write consecutive elements, so elements of any size stay
+// coalesced
+template <typename V>
+__host__ __device__ constexpr bool rows_load_from_registers() {
+    return true;
+}
+template <typename V>
+__host__ __device__ constexpr bool rows_store_from_registers() {
+    return !std::is_same<V, DDisc>::value;
+}
+
 // register cap of the column kernels of family R
 template <typename V, int R>
 __host__ __device__ constexpr int cols_regs() {
