@@ -525,7 +525,7 @@ ssmul_status enqueue_rung_as(ssmul_plan_t p, const ProdDesc* d_desc, int count, 
     if (g.small) {
         // binary32 rectangles on 4-bit digits need up to 4 times the length
         // of the bytes' transform (2 (na + nb) - 1 <= 4096 coefficients) and
-        // room for the prefix sums of their balancing (nib_prefix_scan)
+        // room for the prefix sums of their centring (nib_prefix_scan)
         const bool nib = std::is_same<T, float>::value && p->fp32_nibbles;
         const int n = nib ? std::min(1 << LOG_SMALL, 4 << g.log_n) : 1 << g.log_n;
         const size_t smem = n * sizeof(V) + (nib ? size_t(nib_prefix_bytes(n)) : 0);
