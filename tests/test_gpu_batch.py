@@ -110,6 +110,41 @@ def test_autotuned_geometry_is_exact(tmp_path):
         del os.environ["SSMUL_TUNE_CACHE"]
 
 
+def test_forced_short_column_geometries_are_exact(tmp_path):
+    """Power-of-two lengths split into the shortest columns the four-step
+    kernels take (forced through the tuning cache): N1 = 4 (the forward
+    columns' exact first step is their only step; the inverse columns' first
+    step, which reads W itself, is their only step), N1 = 8 (the forward
+    columns end with a radix-2 step that stores Z), N1 = 16 and 32; batched
+    and single products bit-exact against the oracle."""
+    name = torch.cuda.get_device_properties(0).name
+    cache = tmp_path / "tune.txt"
+    forced = {13: (11, 9), 14: (11, 10), 15: (11, 11), 16: (11, 12)}
+    cache.write_text("".join(f"{name}\t{ln} {l2} {cta}\n" for ln, (l2, cta) in forced.items()))
+    os.environ["SSMUL_TUNE_CACHE"] = str(cache)
+    try:
+        n = 1 << 15
+        pairs = [synth.operand_pair(7000 + i, na, nb) for i, (na, nb) in
+                 enumerate([(4000, 4000), (3000, 5190), (8000, 8000), (16000, 16000),
+                            (32000, 32000), (30000, 1000)])]
+        pairs.append(synth.operand_pair(7100, 16000, 16000, "ff"))
+        with Plan(n, n, len(pairs)) as p:
+            assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_LENGTHS, 0) == OK
+            assert abi.ssmul_plan_set_option(p.h, abi.SSMUL_OPT_AUTOTUNE, 1) == OK
+            for ln, (l2, cta) in forced.items():
+                s, (g1, g2, gc) = abi.ssmul_debug_geometry(p.h, ln)
+                assert s == OK and (g1, g2, gc) == (ln - l2, l2, cta)
+            s, res, digits = batched(p, pairs)
+            assert s == OK
+            for (a, b), r, z in zip(pairs, res, digits):
+                assert r.status == OK and np.array_equal(z, E.product(a, b))
+            for a, b in pairs[:4]:
+                s1, r1, z1 = p.mul(a, b)
+                assert s1 == OK and np.array_equal(z1, E.product(a, b))
+    finally:
+        del os.environ["SSMUL_TUNE_CACHE"]
+
+
 def test_fp32_router_option():
     a, b = synth.operand_pair(5, 300, 300)
     small = synth.operand_pair(6, 40, 40)
